@@ -650,6 +650,37 @@ static void baldwin_lomax(const Solver& S, Level& g) {
 }
 
 // ---------------------------------------------------------------- preconditioner
+// Thin-layer viscous Jacobian of j-face (i, j) in scalar form (reading G37): the face flux
+// behaves like nu |S|^2 / Omega_f (u_R - u_L) with nu = max(mu + mu_t, gamma (mu/Pr + mu_t/Pr_t)) / rho,
+// so it adds +V I to A+ and -V I to A- of that face (A+ + A- keeps the convective Jacobian).
+static double visc_radius(const Solver& S, const Level& g, int i, int j, double rho) {
+  const int nj = g.nj;
+  double volL, volR, mutf;
+  if (j == 0) {
+    volR = g.vol[g.C(i, 0)];
+    if (g.cut(i)) {
+      volL = g.vol[g.C(g.mirror(i), 0)];
+      mutf = 0.5 * (g.mut[g.C(i, 0)] + g.mut[g.C(g.mirror(i), 0)]);
+    } else {
+      volL = volR;
+      mutf = 0.0;
+    }
+  } else if (j == nj) {
+    volL = g.vol[g.C(i, nj - 1)];
+    volR = volL;
+    mutf = g.mut[g.C(i, nj - 1)];
+  } else {
+    volL = g.vol[g.C(i, j - 1)];
+    volR = g.vol[g.C(i, j)];
+    mutf = 0.5 * (g.mut[g.C(i, j - 1)] + g.mut[g.C(i, j)]);
+  }
+  const double volf = 0.5 * (volL + volR);
+  const double mu = 1.0 / S.P.re;
+  const double nu = std::max(mu + mutf, GAM * (mu / S.P.pr + mutf / S.P.prt)) / rho;
+  const double sx = g.seta_x[g.FE(i, j)], sy = g.seta_y[g.FE(i, j)];
+  return nu * (sx * sx + sy * sy) / volf;
+}
+
 // Pseudo time step (G17): dt*_i = c* Omega_i / (r_xi + r_eta).
 static void pseudo_dt(const Solver& S, Level& g, double cfl) {
   for (int j = 0; j < g.nj; ++j)
@@ -681,6 +712,13 @@ static void build_blocks(const Solver& S, Level& g) {
       for (int k = 0; k < 4; ++k) ub[k] = 0.5 * (a[k] + b[k]);
       split_jacobians(ub, g.seta_x[g.FE(i, j)], g.seta_y[g.FE(i, j)], S.P.d_cut, g.Aep[g.FE(i, j)],
                       g.Aem[g.FE(i, j)]);
+      if (S.P.viscous) {
+        const double V = visc_radius(S, g, i, j, ub[0]);
+        for (int k = 0; k < 4; ++k) {
+          g.Aep[g.FE(i, j)][k][k] += V;
+          g.Aem[g.FE(i, j)][k][k] -= V;
+        }
+      }
     }
   for (int j = 0; j < nj; ++j)
     for (int i = 0; i < ni; ++i) {
