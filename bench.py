@@ -1,0 +1,346 @@
+"""Benchmark: FAS cycles of the preconditioned AW3 smoother on the 256x64 thin-layer RANS
+C-grid workload (M = 0.5, Re = 1e7, wall spacing 1e-5, 4-level V-cycle, Baldwin-Lomax).
+
+One step = one FAS cycle over the whole grid (all steps of the method's hot path).  Prints
+one JSON line.  Metric: Mcell-iterations/s (fine cells x cycles / s), plus the wall time to a
+6-order residual drop for the FP64 and the mixed-precision preconditioner.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision fp64|mixed]
+
+Multi-GPU: the exact method does not shard (the SGS sweep is one global wavefront), so N GPUs
+run N independent replicas of the same case; value = all ranks' cell-iterations / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth.cgrid import make_cgrid  # noqa: E402
+
+WORKLOAD = dict(name="rans_256x64_thin_layer_bl", ni=256, nj=64, n_wake=32, wall_spacing=1e-5,
+                mach=0.5, alpha_deg=0.0, re=1e7, nlevels=4, gamma_cycle=2, scheme="AW3", eta=0.8,
+                d_cut=0.5, cfl=100.0, cfl_ramp=20.0, ramp_cycles=2, viscous=1, turb=1)
+METRIC = "Mcell-iter/s"
+L2_FLUSH_BYTES = 256 << 20
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 peak from unit counts and clock: 152 SMs x 4 FP64 flop/clk (2 DFMA) x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+# algorithmic FP64 flops per cell and launch, counted from the kernels (FMA = 2)
+FLOPS_PER_CELL = {"sgs": 230.0, "residual": 310.0, "face_blocks": 380.0, "diag_blocks": 100.0}
+
+
+def level_visits(nlevels, gamma):
+    """Smoothing visits per cycle of each level (index 0 = coarsest) for a V (1) / W (2) cycle."""
+    v = [0] * nlevels
+    def rec(l):
+        v[l] += 1
+        if l > 0:
+            for _ in range(gamma):
+                rec(l - 1)
+    rec(nlevels - 1)
+    return v
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.lines: list[str] = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[3 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_grid():
+    w = WORKLOAD
+    return make_cgrid(w["ni"], w["nj"], n_wake=w["n_wake"], wall_spacing=w["wall_spacing"])
+
+
+def gpu_params(P, precision):
+    w = WORKLOAD
+    return P.default_params(scheme=w["scheme"], nlevels=w["nlevels"], gamma_cycle=w["gamma_cycle"],
+                            viscous=w["viscous"], turb=w["turb"],
+                            sensor=1, mach=w["mach"], alpha_deg=w["alpha_deg"], re=w["re"], eta=w["eta"],
+                            d_cut=w["d_cut"], cfl=w["cfl"], cfl_ramp=w["cfl_ramp"], ramp_cycles=w["ramp_cycles"],
+                            precision=precision)
+
+
+def oracle_solver():
+    import oracle as O
+    w = WORKLOAD
+    p = O.make_params(w["scheme"], nlevels=w["nlevels"], gamma_cycle=w["gamma_cycle"], viscous=w["viscous"],
+                      turb=w["turb"], sensor=1,
+                      mach=w["mach"], alpha_deg=w["alpha_deg"], re=w["re"], eta=w["eta"], d_cut=w["d_cut"],
+                      cfl=w["cfl"], cfl_ramp=w["cfl_ramp"], ramp_cycles=w["ramp_cycles"])
+    return O.Oracle(workload_grid(), p)
+
+
+def cpu_oracle_sample(budget_s=12.0, max_cycles=400, min_cycles=3):
+    """Time the oracle (as it stands, one host thread) on consecutive cycles of the workload."""
+    o = oracle_solver()
+    ncell = WORKLOAD["ni"] * WORKLOAD["nj"]
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_cycles and (k < min_cycles or time.perf_counter() - t0 < budget_s):
+        o.fas_cycle(k)
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": ncell * k / dt / 1e6, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{k} FAS cycles of the 256x64 RANS workload from the free stream, single thread, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    ncell = WORKLOAD["ni"] * WORKLOAD["nj"]
+    o = oracle_solver()
+    for k in range(args.warmup):
+        o.fas_cycle(k)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        o.fas_cycle(args.warmup + k)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = ncell * args.steps / tot / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD["name"], "cells": ncell, "levels": WORKLOAD["nlevels"],
+                                             "l2": "host run"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed FAS cycles after {args.warmup} warm-up cycles, "
+                                       "single host thread"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_cycles(s, stream, flush, steps, k0):
+    """Device time of `steps` FAS cycles (CUDA events on the solver's stream), L2 flushed
+    between cycles outside the timed intervals.  Returns per-cycle ms."""
+    import torch
+    ms = []
+    for k in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.fas_cycle(k0 + k)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_1710_04875_gb300 as P
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    g = workload_grid()
+    ncell = g.ni * g.nj
+    s = P.Solver(g, gpu_params(P, args.precision), stream=stream.cuda_stream)
+
+    # warm-up cycles (untimed) from the free stream
+    for k in range(args.warmup):
+        s.fas_cycle(k)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = s.launch_count()
+    with ClockSampler(local) as clk:
+        ms = time_cycles(s, stream, flush, args.steps, args.warmup)
+    launches = (s.launch_count() - l0) // max(args.steps, 1) * args.steps
+    torch.cuda.synchronize()
+    tot_ms = float(sum(ms))
+    if dist:
+        t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        dist.barrier()
+    value = world * ncell * args.steps / (tot_ms / 1e3) / 1e6
+
+    # same measurement with the mixed-precision preconditioner (FP32 blocks / sweeps)
+    sm = P.Solver(g, gpu_params(P, "mixed" if args.precision == "fp64" else "fp64"), stream=stream.cuda_stream)
+    for k in range(args.warmup):
+        sm.fas_cycle(k)
+    ms_other = time_cycles(sm, stream, flush, args.steps, args.warmup)
+    other_value = world * ncell * args.steps / (sum(ms_other) / 1e3) / 1e6
+    sm.close()
+
+    # per-kernel device time over a second pass of the same number of cycles
+    s.profile(True)
+    for k in range(args.steps):
+        flush.zero_()
+        s.fas_cycle(args.warmup + args.steps + k)
+    kt = {name: s.kernel_time(i) for i, name in enumerate(P.fasw.KERNEL_CLASSES)}
+    s.profile(False)
+
+    # e2e through the public API with host buffers: per cycle, H2D of the state from pinned
+    # memory, one cycle, D2H of the new state and the residual norm
+    u_host = torch.from_numpy(s.get_state()).pin_memory()
+    u_out = torch.empty_like(u_host).pin_memory()
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        s.set_state(u_host.numpy())
+        s.fas_cycle(10**6)
+        s.get_state(out=u_out.numpy())
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * ncell * e2e_steps / e2e_s / 1e6
+    state_bytes = 4 * ncell * 8
+
+    # time to a 6-order drop from the free stream, FP64 and mixed preconditioner
+    drops = {}
+    for prec in ("fp64", "mixed"):
+        sd = P.Solver(g, gpu_params(P, prec), stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        code, nc, hist = sd.solve(1e-6, 600)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        drops[prec] = {"seconds": dt if code == 0 else None, "cycles": nc, "status": int(code),
+                       "final_drop": float(hist[-1] / hist[0]) if len(hist) else None}
+        sd.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel class: algorithmic FP64 flops per cell of each class
+    # (counted from the kernels) x cells processed per launch / average launch time
+    dom = max(kt, key=lambda k: kt[k][1])
+    n_l, ms_l = kt[dom]
+    avg_ms = ms_l / max(n_l, 1)
+    visits = level_visits(WORKLOAD["nlevels"], WORKLOAD["gamma_cycle"])
+    cells = [ncell // (4 ** (WORKLOAD["nlevels"] - 1 - l)) for l in range(WORKLOAD["nlevels"])]
+    per_cycle_cells = {
+        "sgs": sum(3 * visits[l] * cells[l] for l in range(len(cells))),
+        "residual": sum(3 * visits[l] * cells[l] for l in range(len(cells)))
+        + sum(visits[l] * cells[l] for l in range(1, len(cells)))
+        + sum(visits[l] * cells[l] for l in range(0, len(cells) - 1)),
+        "face_blocks": sum(visits[l] * cells[l] for l in range(len(cells))),
+        "diag_blocks": sum(visits[l] * cells[l] for l in range(len(cells))),
+    }
+    if dom in FLOPS_PER_CELL:
+        cells_per_launch = per_cycle_cells[dom] / (n_l / (2 * args.steps) * 2)
+        achieved = FLOPS_PER_CELL[dom] * cells_per_launch / (avg_ms / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "avg_launch_ms": avg_ms,
+                "launches_per_cycle": n_l / args.steps, "cells_per_launch": cells_per_launch,
+                "flops_per_cell": FLOPS_PER_CELL[dom],
+                "peak_source": "FP64 from unit counts and clock (152 SMs x 4 flop/clk x 2.07 GHz)"}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "avg_launch_ms": avg_ms}
+    share = {k: round(v[1] / max(sum(x[1] for x in kt.values()), 1e-12), 4) for k, v in kt.items()}
+    cpu = None if args.no_cpu_baseline else cpu_oracle_sample()
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "cells": ncell, "levels": WORKLOAD["nlevels"],
+                       "cycle": "W", "scheme": "AW3", "precision": args.precision, "cfl": WORKLOAD["cfl"],
+                       "l2": "flushed (256 MiB write) between timed cycles", "parallelism": "replicas"},
+            "other_precision": {"precision": "mixed" if args.precision == "fp64" else "fp64",
+                                "value": other_value, "ms_per_step": sum(ms_other) / args.steps},
+            "time_to_6_orders": drops, "kernel_share": share,
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes + 8},
+            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * fasw.h -- C ABI of the GB300 (sm_103a) library for preconditioned FAS smoothers
+ * on 2D finite-volume Euler / thin-layer RANS on structured C-grids.
+ *
+ * Method: Birken, Bull & Jameson, "Preconditioned smoothers for the full
+ * approximation scheme for the RANS equations" (arXiv 1710.04875):
+ *   - JST residual, section 2 (eqs. e2, e4, spectralcorrection), steady system
+ *     eq. (nonlin-eq-steady), BDF2 system eq. (nonlin-eq);
+ *   - FAS cycle with agglomeration restriction and bilinear prolongation, section 3,
+ *     coarse equation eq. (coarse-nonlin-eq);
+ *   - additive W (AW) and preconditioned additive Runge-Kutta (ARK) low-storage
+ *     stage loops, sections 4.1-4.2, coefficients of Table "RK smoothers";
+ *   - block SGS preconditioner (D+L) D^-1 (D+U), eq. (sgs-precon), built from
+ *     flux-vector-split Jacobians at face-averaged states with the parabolic
+ *     eigenvalue cutoff, eqs. (cutoff), (d-l-u-matrices-J), (d-l-u-matrices-W).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns int: FASW_OK (0) or a negative FASW_ERR_* code.
+ *   - Grid: vertex (i, j) of an ni x nj-cell C-grid at index j*(ni+1)+i; i runs
+ *     along the C (lower wake outflow .. trailing edge .. lower surface .. leading
+ *     edge .. upper surface .. trailing edge .. upper wake outflow), j from the
+ *     wall / wake cut (j = 0) to the far field.  Cells (i,0) with i < n_wake or
+ *     i >= ni - n_wake lie on the wake cut, whose vertices coincide pairwise
+ *     (vertex i with vertex ni - i).
+ *   - State / residual arrays: 4 x nj x ni doubles, component-major (rho, rho u,
+ *     rho v, rho E), cell (i, j) at c*ni*nj + j*ni + i; nondimensional with
+ *     rho_inf = 1, |v_inf| = 1, p_inf = 1/(gamma M^2), chord 1.
+ *   - Caller buffers are borrowed for the duration of the call and never retained.
+ *     Pointers flagged on_device are device pointers; otherwise host pointers.
+ *   - All device work is enqueued on the stream given to fasw_create.  Calls that
+ *     return host values (norms, histories, host copies) synchronize that stream.
+ *   - A context is not thread-safe.  The library owns every device buffer it
+ *     allocates (cudaMalloc at create, cudaFree at destroy).
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     touches the device returns FASW_ERR_CUDA.
+ */
+#ifndef FASW_H
+#define FASW_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FASW_OK 0
+#define FASW_ERR_ARG (-1)            /* invalid argument or grid not coarsenable */
+#define FASW_ERR_OOM (-2)            /* device allocation failed */
+#define FASW_ERR_CUDA (-3)           /* CUDA runtime error (message via fasw_last_cuda_error) */
+#define FASW_ERR_DIVERGED (-4)       /* residual norm became NaN/Inf or grew by > 1e8 */
+#define FASW_ERR_DEVICE_TIMEOUT (-5) /* a bounded device-side wait ran out */
+#define FASW_ERR_NOT_CONVERGED (-6)  /* soft: max_cycles reached; history is filled */
+
+/* Smoother schemes (Table "RK smoothers"; AW uses the same alpha/beta as ARK). */
+enum fasw_scheme {
+  FASW_AW3 = 0, FASW_AW5J = 1, FASW_AW51 = 2, FASW_AW52 = 3,
+  FASW_ARK3J = 4, FASW_ARK5J = 5, FASW_ARK51 = 6, FASW_ARK52 = 7
+};
+
+/* Arithmetic of the preconditioner (blocks, LU and sweeps). */
+enum fasw_precision { FASW_FP64 = 0, FASW_MIXED = 1 };
+
+typedef struct fasw_params {
+  int scheme;          /* enum fasw_scheme */
+  int nlevels;         /* multigrid levels, >= 1; ni, nj, n_wake divisible by 2^(nlevels-1) */
+  int gamma_cycle;     /* 1 = V-cycle, 2 = W-cycle (section 3) */
+  int nu1;             /* presmoothing steps per level visit (>= 1) */
+  int viscous;         /* 0 = Euler (slip wall), 1 = thin-layer Navier-Stokes (no-slip wall) */
+  int turb;            /* 0 = laminar, 1 = Baldwin-Lomax eddy viscosity (finest level, once per cycle) */
+  int sensor;          /* 0 = pressure sensor, 1 = entropy sensor p/rho^gamma */
+  double mach, alpha_deg, re, pr, prt;
+  double eta;          /* W-method parameter */
+  double d_cut;        /* eigenvalue cutoff fraction d in [0,1], eq. (cutoff) */
+  double cfl;          /* pseudo CFL number c* */
+  double cfl_ramp;     /* cap on c* during the first ramp_cycles cycles (section 6: 20 for 2) */
+  int ramp_cycles;
+  double s_coarse;     /* constant sensor value of the first-order coarse-level JST */
+  int precision;       /* enum fasw_precision */
+  int norm_all;        /* 0: RMS of the density residual; 1: RMS over all 4 components */
+  long long spin_limit;/* bound on device-side waits (iterations); <= 0 picks the default */
+} fasw_params;
+
+typedef struct fasw_ctx fasw_ctx;
+
+/* Fill *p with the defaults (robust mode: AW3, d = 0.5, eta = 0.8, c* = 1e4, ramp 20 for 2
+ * cycles, 3-level V-cycle, M = 0.8, Euler, FP64). */
+void fasw_default_params(fasw_params* p);
+
+/* Create a solver for one grid.  x, y: (ni+1)*(nj+1) vertex coordinates (host, or device if
+ * coords_on_device).  stream: a cudaStream_t (NULL = legacy default stream).  The state of
+ * every level starts at the free stream.  Errors: FASW_ERR_ARG (sizes, NULL pointers,
+ * levels), FASW_ERR_OOM, FASW_ERR_CUDA. */
+int fasw_create(int ni, int nj, int n_wake, const double* x, const double* y, int coords_on_device,
+                const fasw_params* p, void* stream, fasw_ctx** out);
+
+/* Release every device buffer of the context.  NULL is ignored. */
+void fasw_destroy(fasw_ctx* ctx);
+
+/* Level l in the paper's numbering: 0 = coarsest, nlevels-1 = finest.  Dimensions of a level. */
+int fasw_level_dims(fasw_ctx* ctx, int level, int* ni, int* nj, int* n_wake);
+
+/* Copy the interior state of a level in / out (4 x nj x ni).  set_state refills the ghosts. */
+int fasw_set_state(fasw_ctx* ctx, int level, const double* u, int on_device);
+int fasw_get_state(fasw_ctx* ctx, int level, double* u, int on_device);
+
+/* FAS forcing s_l of a level (4 x nj x ni); zero on the finest level of a steady solve. */
+int fasw_set_forcing(fasw_ctx* ctx, int level, const double* s, int on_device);
+int fasw_get_forcing(fasw_ctx* ctx, int level, double* s, int on_device);
+
+/* Residual of level l at its current state, per unit volume, split as eq. (split-rhs):
+ * F = F^c + F^v with F^c = Omega^-1 (central fluxes) + a_t u + src - s_l and
+ * F^v = Omega^-1 (-(JST dissipation) - (viscous fluxes)).  Any output may be NULL.
+ * norm (nullable): RMS of the density component of F (all components if norm_all). */
+int fasw_residual(fasw_ctx* ctx, int level, double* F, double* Fc, double* Fv, int on_device, double* norm);
+
+/* Local pseudo time step dt*_i = cfl Omega_i / (r_xi + r_eta) at the current state (n doubles). */
+int fasw_pseudo_dt(fasw_ctx* ctx, int level, double cfl, double* dts, int on_device);
+
+/* Build dt* (with cfl) and the preconditioner at the current state, then z = P^-1 r with
+ * P = (D+L) D^-1 (D+U) (eq. sgs-precon); r, z: 4 x nj x ni.  AW blocks of eq.
+ * (d-l-u-matrices-W) or ARK blocks of eq. (d-l-u-matrices-J) by the context's scheme. */
+int fasw_precond_apply(fasw_ctx* ctx, int level, double cfl, const double* r, double* z, int on_device);
+
+/* Split face Jacobians A+ and A- (times the face length) at the current state:
+ * i-faces (nj x (ni+1) x 16 each) and j-faces ((nj+1) x ni x 16), row-major 4x4.
+ * Always FP64 (independent of the precision setting).  Any output may be NULL. */
+int fasw_face_blocks(fasw_ctx* ctx, int level, double* axp, double* axm, double* aep, double* aem, int on_device);
+
+/* nsteps smoothing steps of the context's scheme on level l with pseudo CFL cfl
+ * (dt* and the preconditioner frozen at the start of each step). */
+int fasw_smooth(fasw_ctx* ctx, int level, int nsteps, double cfl);
+
+/* One FAS cycle (V or W, section 3) from the finest level.  cycle_index selects the
+ * c* ramp.  res_norm (nullable): residual norm at the start of the cycle. */
+int fasw_fas_cycle(fasw_ctx* ctx, int cycle_index, double* res_norm);
+
+/* Cycles until norm_k <= drop * norm_0 (k >= 1) or max_cycles.  history (nullable, max_cycles
+ * doubles): norm at the start of each cycle.  *ncycles: cycles run.  Returns FASW_OK,
+ * FASW_ERR_NOT_CONVERGED, or FASW_ERR_DIVERGED. */
+int fasw_solve_steady(fasw_ctx* ctx, double drop, int max_cycles, double* history, int* ncycles);
+
+/* enable != 0 (the default): each FAS cycle is captured once per pseudo CFL value into a CUDA
+ * graph and replayed; 0 launches every kernel individually.  Capture needs a non-default
+ * stream; with the legacy default stream (NULL) cycles are always launched individually. */
+int fasw_use_graphs(fasw_ctx* ctx, int enable);
+
+/* Eddy viscosity of the finest level (Baldwin-Lomax from the current state); n doubles. */
+int fasw_get_mut(fasw_ctx* ctx, double* mut, int on_device);
+
+/* Dual time stepping, eq. (nonlin-eq): set a_t (3/(2 dt) for BDF2, 1/dt for implicit Euler;
+ * 0 = steady) on every level and the history source src (finest level, 4 x nj x ni;
+ * NULL = zero), so that F gains a_t u + src and D gains eta dt* a_t I (AW) or a_t I (ARK). */
+int fasw_set_time_source(fasw_ctx* ctx, double a_t, const double* src, int on_device);
+
+/* Number of kernel launches the context has enqueued since creation (instrumentation). */
+long long fasw_launch_count(fasw_ctx* ctx);
+
+/* Kernel classes for per-kernel timing. */
+enum fasw_kernel_class {
+  FASW_K_BC = 0, FASW_K_CELL_AUX = 1, FASW_K_RESIDUAL = 2, FASW_K_FACE_BLOCKS = 3, FASW_K_DIAG_BLOCKS = 4,
+  FASW_K_SGS = 5, FASW_K_COPY = 6, FASW_K_RESTRICT = 7, FASW_K_PROLONG = 8, FASW_K_NORM = 9, FASW_K_BL = 10,
+  FASW_NKERNELS = 11
+};
+
+/* enable != 0: bracket every subsequent launch with CUDA events on the context's stream and
+ * accumulate per-class device time (adds an event pair per launch); resets the counters.
+ * Synchronizes the stream. */
+int fasw_profile(fasw_ctx* ctx, int enable);
+
+/* Launch count and summed device milliseconds of one kernel class since fasw_profile. */
+int fasw_kernel_time(fasw_ctx* ctx, int kernel, long long* count, double* total_ms);
+
+/* Message for an error code; and the last CUDA error string seen by the library. */
+const char* fasw_strerror(int code);
+const char* fasw_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASW_H */

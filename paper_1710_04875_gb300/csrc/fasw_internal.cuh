@@ -1,0 +1,105 @@
+// Internal declarations shared by the CUDA translation units of the fasw library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace fasw {
+
+constexpr double GAM = 1.4;
+
+// Device view of one multigrid level (paper's numbering: level 0 coarsest).
+// Ghosted arrays have two ghost layers on every side: cell (i, j), -2 <= i < ni+2,
+// -2 <= j < nj+2, at (j+2)*P + (i+2) with pitch P = ni + 4.  Interior arrays hold
+// cell (i, j) at j*ni + i.  Vector fields are component-major (4 planes).
+struct LevelDev {
+  int ni, nj, nw;
+  int P;        // ghost pitch ni + 4
+  int Gn;       // ghosted plane size P * (nj + 4)
+  int n;        // ni * nj
+  int nfx;      // i-faces (ni+1)*nj
+  int nfe;      // j-faces ni*(nj+1)
+  int finest;   // full JST (sensor + fourth differences) on the finest level only
+  double a_t;   // time-derivative coefficient (0 = steady)
+  double* u;    // 4*Gn ghosted conservative state
+  double* u0;   // 4*n  state at the start of the smoothing step
+  double* fvc;  // 4*n  beta-blended F^v carry
+  double* rhs;  // 4*n  stage right-hand side / FAS residual
+  double* s;    // 4*n  FAS forcing
+  double* ut;   // 4*n  restricted state (coarse levels)
+  double* src;  // 4*n  dual-time history source (finest level)
+  double* p;    // Gn   pressure (ghosted)
+  double* q;    // Gn   sensor quantity (ghosted)
+  double* rt;   // 2*n  Martinelli-corrected radii (xi plane, eta plane)
+  double* dts;  // n    local pseudo time step
+  double* sxi;  // 2*nfx  i-face area vectors (x plane, y plane), index j*(ni+1)+i
+  double* seta; // 2*nfe  j-face area vectors, index j*ni+i
+  double* vol;  // n
+  double* mut;  // n    eddy viscosity
+  double* wdist;// n    distance to the wall-face midpoint of the column (finest level)
+  double* omega;// n    vorticity magnitude scratch (finest level)
+  double* coef; // n    block scale c_i
+  double* blk64;   // face blocks FP64: Axp[16*nfx] Axm[16*nfx] Aep[16*nfe] Aem[16*nfe], entry-major
+  double* dlu64;   // 16*n LU of D (FP64), entry-major
+  double* yz64;    // 4*n sweep vector (FP64)
+  float* blk32;    // FP32 copies for the mixed-precision preconditioner
+  float* dlu32;
+  float* yz32;
+  double* norm_part;  // per-block partial sums of the residual norm
+};
+
+struct PhysParams {
+  double mach, alpha_deg, re, pr, prt;
+  double uinf[4];
+  double s_coarse;
+  int viscous, turb, sensor;
+};
+
+struct SchemeParams {
+  int aw;        // 1 = additive W, 0 = preconditioned ARK
+  int nstages;
+  double alpha[5], beta[5];
+  double eta, d_cut;
+};
+
+// Residual kernel modes
+enum ResMode {
+  RES_FULL = 0,     // F (and optionally Fc, Fv) to caller arrays
+  RES_STAGE = 1,    // stage rhs with carry update
+  RES_FORCING = 2,  // s = F(u) (with s excluded) + rhs (restricted residual)
+  RES_FASRES = 3    // rhs = -(F)  (r_l = s_l - F_l(u_l))
+};
+
+struct ResArgs {
+  int mode;
+  int stage;          // 1-based stage (RES_STAGE)
+  double beta;        // beta_stage
+  int aw;             // scale rhs by dt* (AW)
+  int want_norm;      // accumulate norm partials (stage 1 / FULL)
+  int norm_all;
+  double* F;          // RES_FULL outputs (may be null), interior layout
+  double* Fc;
+  double* Fv;
+};
+
+// ---- launchers (kernels_residual.cu)
+void launch_bc(const LevelDev& L, const PhysParams& ph, cudaStream_t st);
+void launch_cell_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st);
+void launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, cudaStream_t st);
+int residual_blocks(const LevelDev& L);
+void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* out, cudaStream_t st);
+void launch_bl(const LevelDev& L, const PhysParams& ph, cudaStream_t st);
+
+// ---- launchers (kernels_sgs.cu)
+void launch_face_blocks(const LevelDev& L, const PhysParams& ph, const SchemeParams& sc, int mixed, cudaStream_t st);
+void launch_diag_blocks(const LevelDev& L, const SchemeParams& sc, int mixed, cudaStream_t st);
+// forward/backward sweeps; backward fuses the stage update u = u0 - alpha * z (scaled by dt* for ARK)
+void launch_sgs(const LevelDev& L, const SchemeParams& sc, int mixed, int do_update, double alpha,
+                const double* r_in, double* z_out, cudaStream_t st);
+
+// ---- launchers (kernels_transfer.cu)
+void launch_copy_u0(const LevelDev& L, cudaStream_t st);
+void launch_restrict(const LevelDev& F, const LevelDev& C, int restrict_mut, cudaStream_t st);
+void launch_prolong(const LevelDev& F, const LevelDev& C, cudaStream_t st);
+void launch_pack(const LevelDev& L, const double* interior_in, int to_ghosted, double* out, cudaStream_t st);
+
+}  // namespace fasw

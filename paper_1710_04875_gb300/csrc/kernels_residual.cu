@@ -1,0 +1,492 @@
+// Boundary ghosts, per-cell auxiliaries, the JST / thin-layer residual (section 2 of
+// arXiv 1710.04875) and the Baldwin-Lomax closure, FP64.
+#include "fasw_internal.cuh"
+
+namespace fasw {
+
+namespace {
+
+constexpr int TX = 32;   // residual tile: TX x TY cells, (TX+1) x (TY+1) threads
+constexpr int TY = 4;
+constexpr int RES_THREADS = (TX + 1) * (TY + 1);
+
+__device__ __forceinline__ int gidx(const LevelDev& L, int i, int j) { return (j + 2) * L.P + (i + 2); }
+__device__ __forceinline__ bool on_cut(const LevelDev& L, int i) { return L.nw > 0 && (i < L.nw || i >= L.ni - L.nw); }
+
+__device__ __forceinline__ void load4(const LevelDev& L, int g, double w[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) w[k] = L.u[k * L.Gn + g];
+}
+__device__ __forceinline__ void store4(const LevelDev& L, int g, const double w[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) L.u[k * L.Gn + g] = w[k];
+}
+
+__device__ __forceinline__ double pressure(const double w[4]) {
+  return (GAM - 1.0) * (w[3] - 0.5 * (w[1] * w[1] + w[2] * w[2]) / w[0]);
+}
+
+// Far-field boundary state by 1-D Riemann invariants along the outward unit normal (nx, ny).
+__device__ void farfield(const double wi[4], const double wf[4], double nx, double ny, double out[4]) {
+  const double ri = wi[0], ui = wi[1] / ri, vi = wi[2] / ri, pi = pressure(wi);
+  const double rf = wf[0], uf = wf[1] / rf, vf = wf[2] / rf, pf = pressure(wf);
+  const double ai = sqrt(GAM * pi / ri), af = sqrt(GAM * pf / rf);
+  const double vni = ui * nx + vi * ny, vnf = uf * nx + vf * ny;
+  if (fabs(vni) >= ai) {
+    const double* src = vni > 0.0 ? wi : wf;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = src[k];
+    return;
+  }
+  const double Rp = vni + 2.0 * ai / (GAM - 1.0);
+  const double Rm = vnf - 2.0 * af / (GAM - 1.0);
+  const double vnb = 0.5 * (Rp + Rm);
+  const double ab = 0.25 * (GAM - 1.0) * (Rp - Rm);
+  double s, ut, vt;
+  if (vnb > 0.0) {
+    s = pi / pow(ri, GAM);
+    ut = ui - vni * nx;
+    vt = vi - vni * ny;
+  } else {
+    s = pf / pow(rf, GAM);
+    ut = uf - vnf * nx;
+    vt = vf - vnf * ny;
+  }
+  const double rho = pow(ab * ab / (GAM * s), 1.0 / (GAM - 1.0));
+  const double p = rho * ab * ab / GAM;
+  const double u = ut + vnb * nx, v = vt + vnb * ny;
+  out[0] = rho;
+  out[1] = rho * u;
+  out[2] = rho * v;
+  out[3] = p / (GAM - 1.0) + 0.5 * rho * (u * u + v * v);
+}
+
+__global__ void k_bc(LevelDev L, PhysParams ph) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ni = L.ni, nj = L.nj;
+  if (t < ni) {                      // j = 0: wall or wake cut
+    const int i = t;
+    if (on_cut(L, i)) {
+      const int m = ni - 1 - i;
+      double w[4];
+      load4(L, gidx(L, m, 0), w);
+      store4(L, gidx(L, i, -1), w);
+      load4(L, gidx(L, m, 1), w);
+      store4(L, gidx(L, i, -2), w);
+    } else {
+      const double sx = L.seta[i], sy = L.seta[L.nfe + i];
+      const double len = sqrt(sx * sx + sy * sy);
+      const double nx = sx / len, ny = sy / len;
+      for (int k = 0; k < 2; ++k) {
+        double w[4], g[4];
+        load4(L, gidx(L, i, k), w);
+        g[0] = w[0];
+        g[3] = w[3];
+        if (ph.viscous) {
+          g[1] = -w[1];
+          g[2] = -w[2];
+        } else {
+          const double mn = w[1] * nx + w[2] * ny;
+          g[1] = w[1] - 2.0 * mn * nx;
+          g[2] = w[2] - 2.0 * mn * ny;
+        }
+        store4(L, gidx(L, i, -1 - k), g);
+      }
+    }
+  } else if (t < 2 * ni) {           // j = nj: far field, outward +S_eta
+    const int i = t - ni;
+    const int f = nj * ni + i;
+    const double sx = L.seta[f], sy = L.seta[L.nfe + f];
+    const double len = sqrt(sx * sx + sy * sy);
+    double w[4], b[4];
+    load4(L, gidx(L, i, nj - 1), w);
+    farfield(w, ph.uinf, sx / len, sy / len, b);
+    store4(L, gidx(L, i, nj), b);
+    store4(L, gidx(L, i, nj + 1), b);
+  } else if (t < 2 * ni + nj) {      // i = 0: far field, outward -S_xi
+    const int j = t - 2 * ni;
+    const int f = j * (ni + 1);
+    const double sx = L.sxi[f], sy = L.sxi[L.nfx + f];
+    const double len = sqrt(sx * sx + sy * sy);
+    double w[4], b[4];
+    load4(L, gidx(L, 0, j), w);
+    farfield(w, ph.uinf, -sx / len, -sy / len, b);
+    store4(L, gidx(L, -1, j), b);
+    store4(L, gidx(L, -2, j), b);
+  } else if (t < 2 * ni + 2 * nj) {  // i = ni: far field, outward +S_xi
+    const int j = t - 2 * ni - nj;
+    const int f = j * (ni + 1) + ni;
+    const double sx = L.sxi[f], sy = L.sxi[L.nfx + f];
+    const double len = sqrt(sx * sx + sy * sy);
+    double w[4], b[4];
+    load4(L, gidx(L, ni - 1, j), w);
+    farfield(w, ph.uinf, sx / len, sy / len, b);
+    store4(L, gidx(L, ni, j), b);
+    store4(L, gidx(L, ni + 1, j), b);
+  }
+}
+
+// Pressure and sensor quantity on the ghosted domain; Martinelli radii and dt* on the interior.
+__global__ void k_cell_aux(LevelDev L, PhysParams ph, double cfl, int want_dts) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L.Gn) return;
+  const int gi = t % L.P - 2, gj = t / L.P - 2;
+  double w[4];
+  load4(L, t, w);
+  const double p = pressure(w);
+  L.p[t] = p;
+  L.q[t] = ph.sensor ? p / pow(w[0], GAM) : p;
+  if (gi < 0 || gi >= L.ni || gj < 0 || gj >= L.nj) return;
+  const int i = gi, j = gj, ni = L.ni;
+  const double a = sqrt(GAM * p / w[0]);
+  const double u = w[1] / w[0], v = w[2] / w[0];
+  const int fw = j * (ni + 1) + i, fs = j * ni + i;
+  const double sx = 0.5 * (L.sxi[fw] + L.sxi[fw + 1]);
+  const double sy = 0.5 * (L.sxi[L.nfx + fw] + L.sxi[L.nfx + fw + 1]);
+  const double ex = 0.5 * (L.seta[fs] + L.seta[fs + ni]);
+  const double ey = 0.5 * (L.seta[L.nfe + fs] + L.seta[L.nfe + fs + ni]);
+  const double rxi = fabs(u * sx + v * sy) + a * sqrt(sx * sx + sy * sy);
+  const double reta = fabs(u * ex + v * ey) + a * sqrt(ex * ex + ey * ey);
+  const int c = j * ni + i;
+  L.rt[c] = rxi * (1.0 + pow(reta / rxi, 2.0 / 3.0));
+  L.rt[L.n + c] = reta * (1.0 + pow(rxi / reta, 2.0 / 3.0));
+  if (want_dts) L.dts[c] = cfl * L.vol[c] / (rxi + reta);
+}
+
+// Martinelli radius of a possibly-ghost cell: ghosts take the adjacent interior cell's value,
+// across the wake cut the mirror cell's.
+__device__ __forceinline__ double rt_cell(const LevelDev& L, int i, int j, int dir) {
+  if (j < 0) {
+    int ic = min(max(i, 0), L.ni - 1);
+    i = on_cut(L, ic) ? L.ni - 1 - ic : ic;
+    j = 0;
+  }
+  i = min(max(i, 0), L.ni - 1);
+  j = min(j, L.nj - 1);
+  return L.rt[dir * L.n + j * L.ni + i];
+}
+
+__device__ __forceinline__ double sensor_val(double qm, double q0, double qp) {
+  return fabs(qp - 2.0 * q0 + qm) / (qp + 2.0 * q0 + qm + 0.001);
+}
+
+// JST flux through a face with area vector (sx, sy) from L to R; stencil LL, L, R, RR
+// given as ghosted indices.  hc: central part; hd: dissipation d (section 2).
+__device__ void jst_face(const LevelDev& L, int gLL, int gL, int gR, int gRR, double sx, double sy,
+                         double rtL, double rtR, double s_coarse, double hc[4], double hd[4]) {
+  double uL[4], uR[4];
+  load4(L, gL, uL);
+  load4(L, gR, uR);
+  const double pL = L.p[gL], pR = L.p[gR];
+  {
+    const double qnL = (uL[1] * sx + uL[2] * sy) / uL[0];
+    const double qnR = (uR[1] * sx + uR[2] * sy) / uR[0];
+    hc[0] = 0.5 * (uL[0] * qnL + uR[0] * qnR);
+    hc[1] = 0.5 * ((uL[1] * qnL + pL * sx) + (uR[1] * qnR + pR * sx));
+    hc[2] = 0.5 * ((uL[2] * qnL + pL * sy) + (uR[2] * qnR + pR * sy));
+    hc[3] = 0.5 * ((uL[3] + pL) * qnL + (uR[3] + pR) * qnR);
+  }
+  const double r = fmax(rtL, rtR);
+  double eps2, eps4;
+  if (L.finest) {
+    const double qLL = L.q[gLL], qL = L.q[gL], qR = L.q[gR], qRR = L.q[gRR];
+    const double sL = sensor_val(qLL, qL, qR), sR = sensor_val(qL, qR, qRR);
+    const double s = fmin(0.25, fmax(sL, sR));
+    eps2 = s * r;
+    eps4 = fmax(0.0, r / 32.0 - 2.0 * eps2);
+  } else {
+    eps2 = s_coarse * r;
+    eps4 = 0.0;
+  }
+  double uLL[4], uRR[4];
+  if (eps4 != 0.0) {
+    load4(L, gLL, uLL);
+    load4(L, gRR, uRR);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double wL = k == 3 ? uL[3] + pL : uL[k];
+    const double wR = k == 3 ? uR[3] + pR : uR[k];
+    const double dw0 = wR - wL;
+    double d = eps2 * dw0;
+    if (eps4 != 0.0) {
+      const double wLL = k == 3 ? uLL[3] + L.p[gLL] : uLL[k];
+      const double wRR = k == 3 ? uRR[3] + L.p[gRR] : uRR[k];
+      const double dwm = wL - wLL, dwp = wRR - wR;
+      d -= eps4 * ((dwp + dwm) - 2.0 * dw0);
+    }
+    hd[k] = d;
+  }
+}
+
+// Thin-layer viscous flux through j-face (i, j): gradients = jump across the face times S over
+// the mean volume of the two cells (ghost volumes: interior neighbour; across the cut: mirror).
+__device__ void visc_face(const LevelDev& L, const PhysParams& ph, int i, int j, double sx, double sy, double hv[4]) {
+  const int ni = L.ni, nj = L.nj;
+  double volL, volR, mutf;
+  if (j == 0) {
+    volR = L.vol[i];
+    if (on_cut(L, i)) {
+      const int m = ni - 1 - i;
+      volL = L.vol[m];
+      mutf = 0.5 * (L.mut[i] + L.mut[m]);
+    } else {
+      volL = volR;
+      mutf = 0.0;
+    }
+  } else if (j == nj) {
+    volL = L.vol[(nj - 1) * ni + i];
+    volR = volL;
+    mutf = L.mut[(nj - 1) * ni + i];
+  } else {
+    volL = L.vol[(j - 1) * ni + i];
+    volR = L.vol[j * ni + i];
+    mutf = 0.5 * (L.mut[(j - 1) * ni + i] + L.mut[j * ni + i]);
+  }
+  const double volf = 0.5 * (volL + volR);
+  double wL[4], wR[4];
+  const int gL = gidx(L, i, j - 1), gR = gidx(L, i, j);
+  load4(L, gL, wL);
+  load4(L, gR, wR);
+  const double uL = wL[1] / wL[0], vL = wL[2] / wL[0], uR = wR[1] / wR[0], vR = wR[2] / wR[0];
+  const double hL = GAM / (GAM - 1.0) * L.p[gL] / wL[0], hR = GAM / (GAM - 1.0) * L.p[gR] / wR[0];
+  const double mu = 1.0 / ph.re;
+  const double mueff = mu + mutf;
+  const double keff = mu / ph.pr + mutf / ph.prt;
+  const double gux = (uR - uL) * sx / volf, guy = (uR - uL) * sy / volf;
+  const double gvx = (vR - vL) * sx / volf, gvy = (vR - vL) * sy / volf;
+  const double ghx = (hR - hL) * sx / volf, ghy = (hR - hL) * sy / volf;
+  const double div = gux + gvy;
+  const double txx = mueff * (2.0 * gux - 2.0 / 3.0 * div);
+  const double tyy = mueff * (2.0 * gvy - 2.0 / 3.0 * div);
+  const double txy = mueff * (guy + gvx);
+  const double uf = 0.5 * (uL + uR), vf = 0.5 * (vL + vR);
+  const double fx = txx * sx + txy * sy, fy = txy * sx + tyy * sy;
+  hv[0] = 0.0;
+  hv[1] = fx;
+  hv[2] = fy;
+  hv[3] = uf * fx + vf * fy + keff * (ghx * sx + ghy * sy);
+}
+
+// One tile of TX x TY cells: every face of the tile is computed once into shared memory,
+// then each cell assembles F^c and F^v and writes what the mode asks for.
+__global__ void __launch_bounds__(RES_THREADS) k_residual(LevelDev L, PhysParams ph, ResArgs a) {
+  __shared__ double xc[4][TY][TX + 1], xd[4][TY][TX + 1];
+  __shared__ double ec[4][TY + 1][TX], ed[4][TY + 1][TX];
+  __shared__ double red[RES_THREADS];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int ni = L.ni, nj = L.nj;
+  const int tid = ty * (TX + 1) + tx;
+  // i-face (i0+tx, j0+ty)
+  if (ty < TY) {
+    const int i = i0 + tx, j = j0 + ty;
+    if (i <= ni && j < nj) {
+      const int f = j * (ni + 1) + i;
+      double hc[4], hd[4];
+      jst_face(L, gidx(L, i - 2, j), gidx(L, i - 1, j), gidx(L, i, j), gidx(L, i + 1, j), L.sxi[f],
+               L.sxi[L.nfx + f], rt_cell(L, i - 1, j, 0), rt_cell(L, i, j, 0), ph.s_coarse, hc, hd);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        xc[k][ty][tx] = hc[k];
+        xd[k][ty][tx] = hd[k];
+      }
+    }
+  }
+  // j-face (i0+tx, j0+ty)
+  if (tx < TX) {
+    const int i = i0 + tx, j = j0 + ty;
+    if (i < ni && j <= nj) {
+      const int f = j * ni + i;
+      const double sx = L.seta[f], sy = L.seta[L.nfe + f];
+      double hc[4], hd[4];
+      jst_face(L, gidx(L, i, j - 2), gidx(L, i, j - 1), gidx(L, i, j), gidx(L, i, j + 1), sx, sy,
+               rt_cell(L, i, j - 1, 1), rt_cell(L, i, j, 1), ph.s_coarse, hc, hd);
+      if (ph.viscous) {
+        double hv[4];
+        visc_face(L, ph, i, j, sx, sy, hv);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) hd[k] += hv[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        ec[k][ty][tx] = hc[k];
+        ed[k][ty][tx] = hd[k];
+      }
+    }
+  }
+  __syncthreads();
+  double nacc = 0.0;
+  if (tx < TX && ty < TY) {
+    const int i = i0 + tx, j = j0 + ty;
+    if (i < ni && j < nj) {
+      const int c = j * ni + i;
+      const int n = L.n;
+      const double vol = L.vol[c];
+      const int g = gidx(L, i, j);
+      double Fc[4], Fv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double fc = (xc[k][ty][tx + 1] - xc[k][ty][tx]) + (ec[k][ty + 1][tx] - ec[k][ty][tx]);
+        const double fd = -((xd[k][ty][tx + 1] - xd[k][ty][tx]) + (ed[k][ty + 1][tx] - ed[k][ty][tx]));
+        double fcv = fc / vol + L.a_t * L.u[k * L.Gn + g] + L.src[k * n + c];
+        if (a.mode != RES_FORCING) fcv -= L.s[k * n + c];
+        Fc[k] = fcv;
+        Fv[k] = fd / vol;
+      }
+      if (a.want_norm) {
+        if (a.norm_all) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) nacc += (Fc[k] + Fv[k]) * (Fc[k] + Fv[k]);
+        } else {
+          nacc = (Fc[0] + Fv[0]) * (Fc[0] + Fv[0]);
+        }
+      }
+      if (a.mode == RES_STAGE) {
+        const double sc = a.aw ? L.dts[c] : 1.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          double carry;
+          if (a.stage == 1) {
+            carry = Fv[k];
+          } else {
+            carry = a.beta * Fv[k] + (1.0 - a.beta) * L.fvc[k * n + c];
+          }
+          L.fvc[k * n + c] = carry;
+          L.rhs[k * n + c] = sc * (Fc[k] + carry);
+        }
+      } else if (a.mode == RES_FULL) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (a.F) a.F[k * n + c] = Fc[k] + Fv[k];
+          if (a.Fc) a.Fc[k * n + c] = Fc[k];
+          if (a.Fv) a.Fv[k * n + c] = Fv[k];
+        }
+      } else if (a.mode == RES_FORCING) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) L.s[k * n + c] = (Fc[k] + Fv[k]) + L.rhs[k * n + c];
+      } else {  // RES_FASRES
+#pragma unroll
+        for (int k = 0; k < 4; ++k) L.rhs[k * n + c] = -(Fc[k] + Fv[k]);
+      }
+    }
+  }
+  if (a.want_norm) {
+    red[tid] = nacc;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int k = 0; k < RES_THREADS; ++k) s += red[k];
+      L.norm_part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+    }
+  }
+}
+
+__global__ void k_norm_final(const double* part, int nparts, double count, double* out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) s += part[k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) t += red[k];
+    out[0] = sqrt(t / count);
+  }
+}
+
+// ---- Baldwin-Lomax (finest level): vorticity by Green-Gauss, then one thread per i-line.
+__global__ void k_vorticity(LevelDev L) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  const int ni = L.ni, i = c % ni, j = c / ni;
+  double w[4];
+  load4(L, gidx(L, i, j), w);
+  const double u0 = w[1] / w[0], v0 = w[2] / w[0];
+  double fu[4], fv[4];
+  const int nb[4][2] = {{i + 1, j}, {i - 1, j}, {i, j + 1}, {i, j - 1}};
+  for (int k = 0; k < 4; ++k) {
+    double z[4];
+    load4(L, gidx(L, nb[k][0], nb[k][1]), z);
+    fu[k] = 0.5 * (u0 + z[1] / z[0]);
+    fv[k] = 0.5 * (v0 + z[2] / z[0]);
+  }
+  const int fe = j * (ni + 1) + i + 1, fw = j * (ni + 1) + i, fn = (j + 1) * ni + i, fs = j * ni + i;
+  const double circ = (fv[0] * L.sxi[fe] - fu[0] * L.sxi[L.nfx + fe]) - (fv[1] * L.sxi[fw] - fu[1] * L.sxi[L.nfx + fw]) +
+                      (fv[2] * L.seta[fn] - fu[2] * L.seta[L.nfe + fn]) - (fv[3] * L.seta[fs] - fu[3] * L.seta[L.nfe + fs]);
+  L.omega[c] = fabs(circ / L.vol[c]);
+}
+
+__global__ void k_bl_lines(LevelDev L, PhysParams ph) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.ni) return;
+  const double Aplus = 26.0, Ccp = 1.6, Ckleb = 0.3, Cwk = 0.25, kap = 0.4, Kc = 0.0168;
+  const int ni = L.ni, nj = L.nj;
+  const double mu = 1.0 / ph.re;
+  const bool wake = on_cut(L, i);
+  const double rhow = L.u[gidx(L, i, 0)];
+  const double tauw = mu * L.omega[i];
+  const double utr = sqrt(rhow * tauw);
+  const int jsearch = max(1, nj / 2);
+  double Fmax = 0.0, ymax = 0.0, smax = 0.0, smin = 1e300;
+  for (int j = 0; j < jsearch; ++j) {
+    const int c = j * ni + i;
+    const double y = L.wdist[c];
+    const double damp = wake ? 1.0 : 1.0 - exp(-(utr * y / mu) / Aplus);
+    const double F = y * L.omega[c] * damp;
+    if (F > Fmax) {
+      Fmax = F;
+      ymax = y;
+    }
+    const int g = gidx(L, i, j);
+    const double r = L.u[g], uu = L.u[L.Gn + g] / r, vv = L.u[2 * L.Gn + g] / r;
+    const double sp = sqrt(uu * uu + vv * vv);
+    smax = fmax(smax, sp);
+    smin = fmin(smin, sp);
+  }
+  const double udif = wake ? smax - smin : smax;
+  const double Fwake = Fmax > 0.0 ? fmin(ymax * Fmax, Cwk * ymax * udif * udif / Fmax) : 0.0;
+  bool outer = wake;
+  for (int j = 0; j < nj; ++j) {
+    const int c = j * ni + i;
+    const double y = L.wdist[c];
+    const double rho = L.u[gidx(L, i, j)];
+    const double fk = ymax > 0.0 ? 1.0 / (1.0 + 5.5 * pow(Ckleb * y / ymax, 6.0)) : 0.0;
+    const double mo = Kc * Ccp * rho * Fwake * fk;
+    const double damp = wake ? 1.0 : 1.0 - exp(-(utr * y / mu) / Aplus);
+    const double l = kap * y * damp;
+    const double mi = rho * l * l * L.omega[c];
+    if (!outer && mi >= mo) outer = true;
+    L.mut[c] = outer ? mo : mi;
+  }
+}
+
+}  // namespace
+
+void launch_bc(const LevelDev& L, const PhysParams& ph, cudaStream_t st) {
+  const int nt = 2 * L.ni + 2 * L.nj;
+  k_bc<<<(nt + 127) / 128, 128, 0, st>>>(L, ph);
+}
+
+void launch_cell_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st) {
+  k_cell_aux<<<(L.Gn + 255) / 256, 256, 0, st>>>(L, ph, cfl, want_dts);
+}
+
+int residual_blocks(const LevelDev& L) { return ((L.ni + TX - 1) / TX) * ((L.nj + TY - 1) / TY); }
+
+void launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, cudaStream_t st) {
+  dim3 grid((L.ni + TX - 1) / TX, (L.nj + TY - 1) / TY);
+  dim3 block(TX + 1, TY + 1);
+  k_residual<<<grid, block, 0, st>>>(L, ph, a);
+}
+
+void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* out, cudaStream_t st) {
+  k_norm_final<<<1, 256, 0, st>>>(L.norm_part, nparts, (double)ncomp_cells, out);
+}
+
+void launch_bl(const LevelDev& L, const PhysParams& ph, cudaStream_t st) {
+  k_vorticity<<<(L.n + 255) / 256, 256, 0, st>>>(L);
+  k_bl_lines<<<(L.ni + 63) / 64, 64, 0, st>>>(L, ph);
+}
+
+}  // namespace fasw

@@ -1,0 +1,255 @@
+"""ctypes binding of the C ABI declared in ``include/fasw.h`` (argument marshalling only).
+
+Arrays are numpy (host) or torch CUDA tensors (device, passed by data pointer).  Every
+step of the solver runs in the CUDA library; loading fails loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+FASW_OK = 0
+ERRORS = {-1: "FASW_ERR_ARG", -2: "FASW_ERR_OOM", -3: "FASW_ERR_CUDA", -4: "FASW_ERR_DIVERGED",
+          -5: "FASW_ERR_DEVICE_TIMEOUT", -6: "FASW_ERR_NOT_CONVERGED"}
+FASW_AW3, FASW_AW5J, FASW_AW51, FASW_AW52, FASW_ARK3J, FASW_ARK5J, FASW_ARK51, FASW_ARK52 = range(8)
+FASW_FP64, FASW_MIXED = 0, 1
+KERNEL_CLASSES = ["bc", "cell_aux", "residual", "face_blocks", "diag_blocks", "sgs", "copy", "restrict",
+                  "prolong", "norm", "bl"]
+SCHEME_IDS = {"AW3": 0, "AW5J": 1, "AW51": 2, "AW52": 3, "ARK3J": 4, "ARK5J": 5, "ARK51": 6, "ARK52": 7}
+
+
+class FaswError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = ERRORS.get(code, str(code))
+        extra = ""
+        if code == -3 and _lib is not None:
+            extra = ": " + _lib.fasw_last_cuda_error().decode()
+        super().__init__(f"{where} failed with {msg}{extra}")
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("scheme", C.c_int), ("nlevels", C.c_int), ("gamma_cycle", C.c_int), ("nu1", C.c_int),
+        ("viscous", C.c_int), ("turb", C.c_int), ("sensor", C.c_int),
+        ("mach", C.c_double), ("alpha_deg", C.c_double), ("re", C.c_double), ("pr", C.c_double),
+        ("prt", C.c_double), ("eta", C.c_double), ("d_cut", C.c_double), ("cfl", C.c_double),
+        ("cfl_ramp", C.c_double), ("ramp_cycles", C.c_int), ("s_coarse", C.c_double),
+        ("precision", C.c_int), ("norm_all", C.c_int), ("spin_limit", C.c_longlong),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def library():
+    """Load libfasw.so (building it first when sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+        lib = C.CDLL(path)
+        i, d, p, ll = C.c_int, C.c_double, C.c_void_p, C.c_longlong
+        dp = C.c_void_p
+        sig = {
+            "fasw_default_params": (None, [C.POINTER(Params)]),
+            "fasw_create": (i, [i, i, i, dp, dp, i, C.POINTER(Params), p, C.POINTER(p)]),
+            "fasw_destroy": (None, [p]),
+            "fasw_level_dims": (i, [p, i, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
+            "fasw_set_state": (i, [p, i, dp, i]),
+            "fasw_get_state": (i, [p, i, dp, i]),
+            "fasw_set_forcing": (i, [p, i, dp, i]),
+            "fasw_get_forcing": (i, [p, i, dp, i]),
+            "fasw_residual": (i, [p, i, dp, dp, dp, i, C.POINTER(d)]),
+            "fasw_pseudo_dt": (i, [p, i, d, dp, i]),
+            "fasw_precond_apply": (i, [p, i, d, dp, dp, i]),
+            "fasw_face_blocks": (i, [p, i, dp, dp, dp, dp, i]),
+            "fasw_smooth": (i, [p, i, i, d]),
+            "fasw_fas_cycle": (i, [p, i, C.POINTER(d)]),
+            "fasw_solve_steady": (i, [p, d, i, dp, C.POINTER(i)]),
+            "fasw_get_mut": (i, [p, dp, i]),
+            "fasw_set_time_source": (i, [p, d, dp, i]),
+            "fasw_launch_count": (ll, [p]),
+            "fasw_profile": (i, [p, i]),
+            "fasw_use_graphs": (i, [p, i]),
+            "fasw_kernel_time": (i, [p, i, C.POINTER(ll), C.POINTER(d)]),
+            "fasw_strerror": (C.c_char_p, [i]),
+            "fasw_last_cuda_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    library().fasw_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "scheme" and isinstance(v, str):
+            v = SCHEME_IDS[v]
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": FASW_FP64, "mixed": FASW_MIXED}[v]
+        setattr(p, k, v)
+    return p
+
+
+def _check(code: int, where: str):
+    if code != FASW_OK:
+        raise FaswError(code, where)
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a torch tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], "need contiguous float64"
+        return a.ctypes.data, 0
+    # torch tensor
+    assert a.is_contiguous() and str(a.dtype) == "torch.float64", "need contiguous float64 tensor"
+    return a.data_ptr(), 1 if a.is_cuda else 0
+
+
+class Solver:
+    """One solver context on one grid; methods mirror the C entry points."""
+
+    def __init__(self, grid, params: Params, stream=None, coords_on_device=False):
+        self.lib = library()
+        self.grid = grid
+        self.params = params
+        x, y = grid.coords() if not coords_on_device else grid
+        self._x, self._y = x, y
+        xp, xd = _ptr(x)
+        yp, _ = _ptr(y)
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if stream is not None else None
+        ni, nj, nw = (grid.ni, grid.nj, grid.n_wake)
+        _check(self.lib.fasw_create(ni, nj, nw, xp, yp, xd, C.byref(params), st, C.byref(h)), "fasw_create")
+        self.h = h
+        self.nlevels = params.nlevels
+        self.finest = self.nlevels - 1
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fasw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def dims(self, l):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _check(self.lib.fasw_level_dims(self.h, l, C.byref(a), C.byref(b), C.byref(c)), "fasw_level_dims")
+        return a.value, b.value, c.value
+
+    def _shape(self, l):
+        ni, nj, _ = self.dims(l)
+        return (4, nj, ni)
+
+    def set_state(self, u, l=None):
+        l = self.finest if l is None else l
+        p, dev = _ptr(u)
+        _check(self.lib.fasw_set_state(self.h, l, p, dev), "fasw_set_state")
+
+    def get_state(self, l=None, out=None):
+        l = self.finest if l is None else l
+        out = np.zeros(self._shape(l)) if out is None else out
+        p, dev = _ptr(out)
+        _check(self.lib.fasw_get_state(self.h, l, p, dev), "fasw_get_state")
+        return out
+
+    def set_forcing(self, s, l):
+        p, dev = _ptr(s)
+        _check(self.lib.fasw_set_forcing(self.h, l, p, dev), "fasw_set_forcing")
+
+    def get_forcing(self, l):
+        out = np.zeros(self._shape(l))
+        _check(self.lib.fasw_get_forcing(self.h, l, out.ctypes.data, 0), "fasw_get_forcing")
+        return out
+
+    def residual(self, l=None, want_norm=False):
+        l = self.finest if l is None else l
+        F = np.zeros(self._shape(l)); Fc = np.zeros_like(F); Fv = np.zeros_like(F)
+        nrm = C.c_double()
+        _check(self.lib.fasw_residual(self.h, l, F.ctypes.data, Fc.ctypes.data, Fv.ctypes.data, 0,
+                                      C.byref(nrm) if want_norm else None), "fasw_residual")
+        return (F, Fc, Fv, nrm.value) if want_norm else (F, Fc, Fv)
+
+    def pseudo_dt(self, cfl, l=None):
+        l = self.finest if l is None else l
+        ni, nj, _ = self.dims(l)
+        out = np.zeros((nj, ni))
+        _check(self.lib.fasw_pseudo_dt(self.h, l, cfl, out.ctypes.data, 0), "fasw_pseudo_dt")
+        return out
+
+    def precond_apply(self, r, cfl, l=None):
+        l = self.finest if l is None else l
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        z = np.zeros(self._shape(l))
+        _check(self.lib.fasw_precond_apply(self.h, l, cfl, r.ctypes.data, z.ctypes.data, 0), "fasw_precond_apply")
+        return z
+
+    def face_blocks(self, l=None):
+        l = self.finest if l is None else l
+        ni, nj, _ = self.dims(l)
+        axp = np.zeros((nj, ni + 1, 4, 4)); axm = np.zeros_like(axp)
+        aep = np.zeros((nj + 1, ni, 4, 4)); aem = np.zeros_like(aep)
+        _check(self.lib.fasw_face_blocks(self.h, l, axp.ctypes.data, axm.ctypes.data, aep.ctypes.data,
+                                         aem.ctypes.data, 0), "fasw_face_blocks")
+        return axp, axm, aep, aem
+
+    def smooth(self, nsteps=1, cfl=None, l=None):
+        l = self.finest if l is None else l
+        cfl = self.params.cfl if cfl is None else cfl
+        _check(self.lib.fasw_smooth(self.h, l, nsteps, cfl), "fasw_smooth")
+
+    def fas_cycle(self, k: int) -> float:
+        n = C.c_double()
+        _check(self.lib.fasw_fas_cycle(self.h, k, C.byref(n)), "fasw_fas_cycle")
+        return n.value
+
+    def solve(self, drop: float, max_cycles: int):
+        hist = np.zeros(max_cycles)
+        nc = C.c_int(0)
+        code = self.lib.fasw_solve_steady(self.h, drop, max_cycles, hist.ctypes.data, C.byref(nc))
+        if code not in (0, -4, -6):
+            _check(code, "fasw_solve_steady")
+        return code, nc.value, hist[:nc.value]
+
+    def get_mut(self):
+        ni, nj, _ = self.dims(self.finest)
+        out = np.zeros((nj, ni))
+        _check(self.lib.fasw_get_mut(self.h, out.ctypes.data, 0), "fasw_get_mut")
+        return out
+
+    def set_time_source(self, a_t, src=None):
+        p, dev = _ptr(src)
+        _check(self.lib.fasw_set_time_source(self.h, a_t, p, dev), "fasw_set_time_source")
+
+    def launch_count(self) -> int:
+        return int(self.lib.fasw_launch_count(self.h))
+
+    def use_graphs(self, enable: bool):
+        _check(self.lib.fasw_use_graphs(self.h, 1 if enable else 0), "fasw_use_graphs")
+
+    def profile(self, enable: bool):
+        _check(self.lib.fasw_profile(self.h, 1 if enable else 0), "fasw_profile")
+
+    def kernel_time(self, kernel: int):
+        """(launches, total device ms) of one kernel class since profile(True)."""
+        n = C.c_longlong()
+        ms = C.c_double()
+        _check(self.lib.fasw_kernel_time(self.h, kernel, C.byref(n), C.byref(ms)), "fasw_kernel_time")
+        return n.value, ms.value
