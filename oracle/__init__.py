@@ -103,6 +103,7 @@ def lib():
             "or_stage_scalar": (d, [i, dp, dp, d, d, d, d]),
             "or_restrict": (None, [p, i, dp, dp]),
             "or_prolong": (None, [p, i, dp, dp]),
+            "or_linear_step": (None, [dp, d, d, i, i, d, d, d, d, i, i, i, dp, dp, dp, dp, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -336,3 +337,17 @@ def stage_scalar(scheme, lc, lv, dts, w):
     a = np.zeros(5); b = np.zeros(5)
     a[:len(al)] = al; b[:len(be)] = be
     return lib().or_stage_scalar(len(al), _dp(a), _dp(b), lc, lv, dts, w)
+
+
+def linear_step(w, dx, dy, nx, ny, u, dts, eta=0.8, a_t=0.0, d=0.5, scheme="AW3", circulant=True):
+    """One smoothing step of the linear model (section 5) on u (4, ny, nx); returns (u_new, A, B, M)."""
+    al, be = SCHEMES[scheme]
+    a = np.zeros(5); b = np.zeros(5)
+    a[:len(al)] = al; b[:len(be)] = be
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.ascontiguousarray(u, dtype=np.float64).copy()
+    A = np.zeros((4, 4)); B = np.zeros((4, 4)); M = np.zeros((4, 4))
+    aw = 0 if (scheme.startswith("ARK") or scheme.startswith("ERK")) else 1
+    lib().or_linear_step(_dp(w), dx, dy, nx, ny, dts, eta, a_t, d, aw, 1 if circulant else 0, len(al),
+                         _dp(a), _dp(b), _dp(out), _dp(A), _dp(B), _dp(M))
+    return out, A, B, M

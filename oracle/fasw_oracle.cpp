@@ -1080,6 +1080,192 @@ static void fas_cycle(Solver& S, int l, double cfl) {
   bc_fill(S, g);
 }
 
+// ---------------------------------------------------------------- linear model (section 5)
+// Linearized Euler u_t + A u_x + B u_y = 0 on a periodic nx x ny Cartesian grid (eq.
+// linearized-euler), discretized as in section 5.1 with the sensor switched off (eps2 = 0,
+// eps4 = r/32 per direction): H = H_c + H_v,
+//   H_c u = (A (u_{i+1} - u_{i-1}) dy + B (u_{j+1} - u_{j-1}) dx) / (2 dx dy) [+ a_t u],
+//   H_v u = M (eps4x (u_{i+2} - 4u_{i+1} + 6u_i - 4u_{i-1} + u_{i-2}) dy + eps4y (...) dx) / (dx dy).
+// The preconditioner uses the blocks of section 5.2 (cell values, not face averages):
+//   L = -(s/Omega) (dy A+ E_x^-1 + dx B+ E_y^-1),  U = (s/Omega) (dy A- E_x + dx B- E_y),
+//   D = sigma I + (s/Omega) (dy (A+ - A-) + dx (B+ - B-)), Omega = dx dy,
+// with s = eta dt* (AW) and sigma = 1 + eta dt* a_t, applied either as the circulant operator
+// (wrap-around couplings in L and U, dense solve) or as a real lexicographic sweep in which
+// wrap-around neighbours are treated like every other neighbour of lower or higher index.
+struct LinModel {
+  int nx, ny;
+  double dx, dy, dts, eta, a_t, eps4x, eps4y;
+  M4 A, B, Ap, Am, Bp, Bm, M;
+  int aw;
+  int circulant;
+  int idx(int i, int j) const { return ((j + ny) % ny) * nx + ((i + nx) % nx); }
+};
+
+struct LinOps : StageOps {
+  const LinModel& m;
+  std::vector<V4> u;
+  LinOps(const LinModel& mm) : m(mm) {}
+  void get_state(std::vector<V4>& v) override { v = u; }
+  void residual(std::vector<V4>& fc, std::vector<V4>& fv) override {
+    const int n = m.nx * m.ny;
+    fc.assign(n, V4{});
+    fv.assign(n, V4{});
+    const double om = m.dx * m.dy;
+    for (int j = 0; j < m.ny; ++j)
+      for (int i = 0; i < m.nx; ++i) {
+        const int c = m.idx(i, j);
+        V4 dxu, dyu, d4x, d4y;
+        for (int k = 0; k < 4; ++k) {
+          dxu[k] = u[m.idx(i + 1, j)][k] - u[m.idx(i - 1, j)][k];
+          dyu[k] = u[m.idx(i, j + 1)][k] - u[m.idx(i, j - 1)][k];
+          d4x[k] = u[m.idx(i + 2, j)][k] - 4.0 * u[m.idx(i + 1, j)][k] + 6.0 * u[c][k] - 4.0 * u[m.idx(i - 1, j)][k] +
+                   u[m.idx(i - 2, j)][k];
+          d4y[k] = u[m.idx(i, j + 2)][k] - 4.0 * u[m.idx(i, j + 1)][k] + 6.0 * u[c][k] - 4.0 * u[m.idx(i, j - 1)][k] +
+                   u[m.idx(i, j - 2)][k];
+        }
+        const V4 ax = matvec(m.A, dxu), by = matvec(m.B, dyu);
+        V4 diss;
+        for (int k = 0; k < 4; ++k) diss[k] = (m.eps4x * d4x[k] * m.dy + m.eps4y * d4y[k] * m.dx) / om;
+        const V4 md = matvec(m.M, diss);
+        for (int k = 0; k < 4; ++k) {
+          fc[c][k] = (ax[k] * m.dy + by[k] * m.dx) / (2.0 * om) + m.a_t * u[c][k];
+          fv[c][k] = md[k];
+        }
+      }
+  }
+  // coupling blocks of cell c: D, and neighbour blocks with their cell index
+  void blocks(M4& D, std::vector<Nb>& lower, std::vector<Nb>& upper, int i, int j) const {
+    const double om = m.dx * m.dy;
+    const double sc = (m.aw ? m.eta * m.dts : 1.0) / om;
+    const double sigma = m.aw ? 1.0 + m.eta * m.dts * m.a_t : m.a_t;
+    for (int r = 0; r < 4; ++r)
+      for (int k = 0; k < 4; ++k)
+        D[r][k] = (r == k ? sigma : 0.0) + sc * (m.dy * (m.Ap[r][k] - m.Am[r][k]) + m.dx * (m.Bp[r][k] - m.Bm[r][k]));
+    lower.clear();
+    upper.clear();
+    const int c = m.idx(i, j);
+    auto blk = [&](const M4& X, double f) {
+      M4 Y;
+      for (int r = 0; r < 4; ++r)
+        for (int k = 0; k < 4; ++k) Y[r][k] = f * X[r][k];
+      return Y;
+    };
+    // L couples E_x^-1 (west) and E_y^-1 (south); U couples east and north
+    const Nb w{m.idx(i - 1, j), blk(m.Ap, -sc * m.dy)}, s{m.idx(i, j - 1), blk(m.Bp, -sc * m.dx)};
+    const Nb e{m.idx(i + 1, j), blk(m.Am, sc * m.dy)}, n{m.idx(i, j + 1), blk(m.Bm, sc * m.dx)};
+    if (m.circulant) {
+      lower.push_back(w);
+      lower.push_back(s);
+      upper.push_back(e);
+      upper.push_back(n);
+    } else {
+      for (const Nb* q : {&w, &s, &e, &n}) (q->c < c ? lower : upper).push_back(*q);
+    }
+  }
+  void apply_P(const std::vector<V4>& r, std::vector<V4>& z) const {
+    const int n = m.nx * m.ny;
+    std::vector<Nb> lo, up;
+    M4 D;
+    if (!m.circulant) {  // real lexicographic sweep
+      std::vector<V4> y(n);
+      for (int c = 0; c < n; ++c) {
+        blocks(D, lo, up, c % m.nx, c / m.nx);
+        V4 t = r[c];
+        for (const Nb& b : lo) {
+          const V4 v = matvec(b.B, y[b.c]);
+          for (int k = 0; k < 4; ++k) t[k] -= v[k];
+        }
+        y[c] = solve4(D, t);
+      }
+      z.assign(n, V4{});
+      for (int c = n - 1; c >= 0; --c) {
+        blocks(D, lo, up, c % m.nx, c / m.nx);
+        V4 t{};
+        for (const Nb& b : up) {
+          const V4 v = matvec(b.B, z[b.c]);
+          for (int k = 0; k < 4; ++k) t[k] += v[k];
+        }
+        const V4 q = solve4(D, t);
+        for (int k = 0; k < 4; ++k) z[c][k] = y[c][k] - q[k];
+      }
+      return;
+    }
+    // circulant: dense (D+L) D^-1 (D+U), solved with partial pivoting
+    const int N = 4 * n;
+    std::vector<double> DL(N * N, 0.0), DU(N * N, 0.0), Dinv(N * N, 0.0);
+    for (int c = 0; c < n; ++c) {
+      blocks(D, lo, up, c % m.nx, c / m.nx);
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          DL[(4 * c + a) * N + 4 * c + b] += D[a][b];
+          DU[(4 * c + a) * N + 4 * c + b] += D[a][b];
+        }
+      for (const Nb& q : lo)
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) DL[(4 * c + a) * N + 4 * q.c + b] += q.B[a][b];
+      for (const Nb& q : up)
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) DU[(4 * c + a) * N + 4 * q.c + b] += q.B[a][b];
+      for (int col = 0; col < 4; ++col) {
+        V4 e{};
+        e[col] = 1.0;
+        const V4 x = solve4(D, e);
+        for (int a = 0; a < 4; ++a) Dinv[(4 * c + a) * N + 4 * c + col] = x[a];
+      }
+    }
+    std::vector<double> T(N * N, 0.0), P(N * N, 0.0);
+    for (int a = 0; a < N; ++a)
+      for (int k = 0; k < N; ++k) {
+        const double v = DL[a * N + k];
+        if (v != 0.0)
+          for (int b = 0; b < N; ++b) T[a * N + b] += v * Dinv[k * N + b];
+      }
+    for (int a = 0; a < N; ++a)
+      for (int k = 0; k < N; ++k) {
+        const double v = T[a * N + k];
+        if (v != 0.0)
+          for (int b = 0; b < N; ++b) P[a * N + b] += v * DU[k * N + b];
+      }
+    std::vector<double> rhs(N);
+    for (int c = 0; c < n; ++c)
+      for (int a = 0; a < 4; ++a) rhs[4 * c + a] = r[c][a];
+    for (int k = 0; k < N; ++k) {
+      int piv = k;
+      for (int a = k + 1; a < N; ++a)
+        if (std::fabs(P[a * N + k]) > std::fabs(P[piv * N + k])) piv = a;
+      if (piv != k) {
+        for (int b = 0; b < N; ++b) std::swap(P[k * N + b], P[piv * N + b]);
+        std::swap(rhs[k], rhs[piv]);
+      }
+      for (int a = k + 1; a < N; ++a) {
+        const double f = P[a * N + k] / P[k * N + k];
+        if (f == 0.0) continue;
+        for (int b = k; b < N; ++b) P[a * N + b] -= f * P[k * N + b];
+        rhs[a] -= f * rhs[k];
+      }
+    }
+    std::vector<double> x(N);
+    for (int a = N - 1; a >= 0; --a) {
+      double acc = rhs[a];
+      for (int b = a + 1; b < N; ++b) acc -= P[a * N + b] * x[b];
+      x[a] = acc / P[a * N + a];
+    }
+    z.assign(n, V4{});
+    for (int c = 0; c < n; ++c)
+      for (int a = 0; a < 4; ++a) z[c][a] = x[4 * c + a];
+  }
+  // AW: z = W^-1 (dt* r); ARK: z = dt* P^-1 r (uniform dt*: the two orders coincide)
+  void apply_Winv(const std::vector<V4>& r, std::vector<V4>& z) override {
+    apply_P(r, z);
+    for (auto& v : z)
+      for (int k = 0; k < 4; ++k) v[k] *= m.dts;
+  }
+  void set_state(const std::vector<V4>& u0, double alpha, const std::vector<V4>& z) override {
+    for (size_t c = 0; c < u.size(); ++c)
+      for (int k = 0; k < 4; ++k) u[c][k] = u0[c][k] - alpha * z[c][k];
+  }
+};
+
 }  // namespace orc
 
 using namespace orc;
@@ -1405,6 +1591,56 @@ void or_prolong(void* h, int l, const double* dc, double* df) {
     for (int i = 0; i < f.ni; ++i)
       for (int k = 0; k < 4; ++k) df[k * nf + f.C(i, j)] = f.u[f.G(i, j)][k];
   f.u = save;
+}
+
+// Linear model: one smoothing step of the generic stage loop on u (4 x ny x nx SoA, in place).
+// w: linearization state; d: cutoff; aw: 1 = AW (W blocks), 0 = ARK; circulant: 1 = wrap-around
+// couplings in L and U (dense solve), 0 = real lexicographic sweep.  Mout (16, nullable): the
+// dissipation matrix M used, Aout/Bout (16 each, nullable): the flux Jacobians used.
+void or_linear_step(const double* w, double dx, double dy, int nx, int ny, double dts, double eta, double a_t,
+                    double d, int aw, int circulant, int s, const double* alpha, const double* beta, double* u,
+                    double* Aout, double* Bout, double* Mout) {
+  LinModel m;
+  m.nx = nx;
+  m.ny = ny;
+  m.dx = dx;
+  m.dy = dy;
+  m.dts = dts;
+  m.eta = eta;
+  m.a_t = a_t;
+  m.aw = aw;
+  m.circulant = circulant;
+  const V4 st{w[0], w[1], w[2], w[3]};
+  split_jacobians(st, 1.0, 0.0, d, m.Ap, m.Am);
+  split_jacobians(st, 0.0, 1.0, d, m.Bp, m.Bm);
+  for (int r = 0; r < 4; ++r)
+    for (int k = 0; k < 4; ++k) {
+      m.A[r][k] = m.Ap[r][k] + m.Am[r][k];
+      m.B[r][k] = m.Bp[r][k] + m.Bm[r][k];
+    }
+  const Prim q = prim(st);
+  const double a = std::sqrt(GAM * q.p / q.rho);
+  m.eps4x = (std::fabs(q.u) + a) / 32.0;
+  m.eps4y = (std::fabs(q.v) + a) / 32.0;
+  // M of section 5.1: identity with last row (-(gamma-1)|v|^2/2, 0, 0, gamma)
+  m.M = M4{};
+  for (int k = 0; k < 3; ++k) m.M[k][k] = 1.0;
+  m.M[3][0] = -(GAM - 1.0) * 0.5 * (q.u * q.u + q.v * q.v);
+  m.M[3][3] = GAM;
+  LinOps op(m);
+  const int n = nx * ny;
+  op.u.assign(n, V4{});
+  for (int c = 0; c < n; ++c)
+    for (int k = 0; k < 4; ++k) op.u[c][k] = u[k * n + c];
+  stage_loop(op, s, alpha, beta);
+  for (int c = 0; c < n; ++c)
+    for (int k = 0; k < 4; ++k) u[k * n + c] = op.u[c][k];
+  for (int r = 0; r < 4; ++r)
+    for (int k = 0; k < 4; ++k) {
+      if (Aout) Aout[4 * r + k] = m.A[r][k];
+      if (Bout) Bout[4 * r + k] = m.B[r][k];
+      if (Mout) Mout[4 * r + k] = m.M[r][k];
+    }
 }
 
 }  // extern "C"
