@@ -104,6 +104,9 @@ def lib():
             "or_restrict": (None, [p, i, dp, dp]),
             "or_prolong": (None, [p, i, dp, dp]),
             "or_linear_step": (None, [dp, d, d, i, i, d, d, d, d, i, i, i, dp, dp, dp, dp, dp, dp]),
+            "or_set_motion": (None, [p, d, d, d, d]),
+            "or_dual_time_step": (i, [p, d, d, i, dp]),
+            "or_grid_fluxes": (None, [p, i, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -273,6 +276,21 @@ class Oracle:
         else:
             src = np.ascontiguousarray(src, dtype=np.float64)
             self.L.or_set_time_source(self.h, a_t, _dp(src))
+
+    def set_motion(self, phi, phidot, xc=0.25, yc=0.0):
+        self.L.or_set_motion(self.h, phi, phidot, xc, yc)
+
+    def dual_time_step(self, dt, drop, max_cycles):
+        hist = np.zeros(max_cycles)
+        nc = self.L.or_dual_time_step(self.h, dt, drop, max_cycles, _dp(hist))
+        return nc, hist[:abs(nc)]
+
+    def grid_fluxes(self, l=None):
+        l = self.finest if l is None else l
+        ni, nj, _ = self.dims(l)
+        vfx = np.zeros((nj, ni + 1)); vfe = np.zeros((nj + 1, ni))
+        self.L.or_grid_fluxes(self.h, l, _dp(vfx), _dp(vfe))
+        return vfx, vfe
 
     def restrict(self, l, vf):
         vf = np.ascontiguousarray(vf, dtype=np.float64)

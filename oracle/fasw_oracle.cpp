@@ -187,13 +187,16 @@ static void eigvecs(const V4& w, double nx, double ny, M4& R, M4& Ri, double& vn
 
 // A^+ = R diag((lambda + |lambda|_cut)/2) R^{-1}, A^- = R diag((lambda - |lambda|_cut)/2) R^{-1}
 // (section 4.4), each multiplied by the face length |S|.
-static void split_jacobians(const V4& w, double sx, double sy, double d, M4& Ap, M4& Am) {
+// On a moving face with grid volume flux vf (= v_grid . S) the eigenvalues are shifted by
+// -vf/|S| (relative normal velocity); the eigenvectors are those of the fixed face.
+static void split_jacobians(const V4& w, double sx, double sy, double vf, double d, M4& Ap, M4& Am) {
   const double len = std::sqrt(sx * sx + sy * sy);
   const double nx = sx / len, ny = sy / len;
   M4 R, Ri;
   double vn, a;
   eigvecs(w, nx, ny, R, Ri, vn, a);
-  const double lam[4] = {vn, vn, vn + a, vn - a};
+  const double vr = vn - vf / len;
+  const double lam[4] = {vr, vr, vr + a, vr - a};
   M4 Lp{}, Lm{};
   for (int k = 0; k < 4; ++k) {
     const double ab = cutoff_abs(lam[k], a, d);
@@ -211,6 +214,8 @@ struct Level {
   std::vector<double> seta_x, seta_y;  // j-faces, ni*(nj+1), index j*ni+i; area vector towards +j
   std::vector<double> vol;             // ni*nj
   std::vector<double> wdist;           // distance of cell centroid to its j=0 face midpoint (finest)
+  std::vector<double> vfx, vfe;        // grid volume flux v_grid . S of each face (zero on a fixed grid)
+  std::vector<double> wvx, wvy;        // grid velocity at the j=0 face midpoints (moving wall)
   std::vector<V4> u;                   // ghosted state, (ni+4)*(nj+4)
   std::vector<V4> ut;                  // restricted state u~ (coarse levels), interior
   std::vector<V4> s;                   // FAS forcing s_l, interior (zero on the finest level)
@@ -237,10 +242,17 @@ struct Solver {
   V4 uinf{};
   double norm_first = 0.0;  // residual norm recorded at the first stage of the finest smoothing step
   bool record_norm = false;
+  // rigid motion of the whole grid (pitching): rotation by phi about (xc, yc) at rate phidot
+  std::vector<double> x0, y0;
+  double xc = 0.25, yc = 0.0, phi = 0.0, phidot = 0.0;
+  bool moving = false;
+  std::vector<V4> un, unm1;  // dual-time history of the finest level (interior)
+  int steps_done = 0;
   int L() const { return (int)lev.size() - 1; }
 };
 
-static void fine_metrics(Level& g, const double* x, const double* y) {
+static void fine_metrics(Level& g, const double* x, const double* y, double phidot = 0.0, double xc = 0.0,
+                         double yc = 0.0) {
   const int ni = g.ni, nj = g.nj;
   auto X = [&](int i, int j) { return x[j * (ni + 1) + i]; };
   auto Y = [&](int i, int j) { return y[j * (ni + 1) + i]; };
@@ -250,12 +262,22 @@ static void fine_metrics(Level& g, const double* x, const double* y) {
   g.seta_y.assign(ni * (nj + 1), 0.0);
   g.vol.assign(ni * nj, 0.0);
   g.wdist.assign(ni * nj, 0.0);
+  g.vfx.assign((ni + 1) * nj, 0.0);
+  g.vfe.assign(ni * (nj + 1), 0.0);
+  g.wvx.assign(ni, 0.0);
+  g.wvy.assign(ni, 0.0);
+  // rigid rotation: v_grid(x, y) = phidot (-(y - yc), x - xc); linear, so its flux through a
+  // straight face is its value at the face midpoint dotted with S
+  auto vgx = [&](double, double py) { return -phidot * (py - yc); };
+  auto vgy = [&](double px, double) { return phidot * (px - xc); };
   // i-face from vertex (i,j) to (i,j+1): S = (dy, -dx)
   for (int j = 0; j < nj; ++j)
     for (int i = 0; i <= ni; ++i) {
       const double dx = X(i, j + 1) - X(i, j), dy = Y(i, j + 1) - Y(i, j);
       g.sxi_x[g.FX(i, j)] = dy;
       g.sxi_y[g.FX(i, j)] = -dx;
+      const double mx = 0.5 * (X(i, j) + X(i, j + 1)), my = 0.5 * (Y(i, j) + Y(i, j + 1));
+      g.vfx[g.FX(i, j)] = vgx(mx, my) * dy + vgy(mx, my) * (-dx);
     }
   // j-face from vertex (i,j) to (i+1,j): S = (-dy, dx)
   for (int j = 0; j <= nj; ++j)
@@ -263,6 +285,12 @@ static void fine_metrics(Level& g, const double* x, const double* y) {
       const double dx = X(i + 1, j) - X(i, j), dy = Y(i + 1, j) - Y(i, j);
       g.seta_x[g.FE(i, j)] = -dy;
       g.seta_y[g.FE(i, j)] = dx;
+      const double mx = 0.5 * (X(i, j) + X(i + 1, j)), my = 0.5 * (Y(i, j) + Y(i + 1, j));
+      g.vfe[g.FE(i, j)] = vgx(mx, my) * (-dy) + vgy(mx, my) * dx;
+      if (j == 0) {
+        g.wvx[i] = vgx(mx, my);
+        g.wvy[i] = vgy(mx, my);
+      }
     }
   // volume: half the cross product of the diagonals
   for (int j = 0; j < nj; ++j)
@@ -289,13 +317,23 @@ static void agglomerate(const Level& f, Level& c) {
   c.seta_x.assign(ni * (nj + 1), 0.0);
   c.seta_y.assign(ni * (nj + 1), 0.0);
   c.vol.assign(ni * nj, 0.0);
+  c.vfx.assign((ni + 1) * nj, 0.0);
+  c.vfe.assign(ni * (nj + 1), 0.0);
+  c.wvx.assign(ni, 0.0);
+  c.wvy.assign(ni, 0.0);
   for (int j = 0; j < nj; ++j)
     for (int i = 0; i <= ni; ++i) {
+      c.vfx[c.FX(i, j)] = f.vfx[f.FX(2 * i, 2 * j)] + f.vfx[f.FX(2 * i, 2 * j + 1)];
       c.sxi_x[c.FX(i, j)] = f.sxi_x[f.FX(2 * i, 2 * j)] + f.sxi_x[f.FX(2 * i, 2 * j + 1)];
       c.sxi_y[c.FX(i, j)] = f.sxi_y[f.FX(2 * i, 2 * j)] + f.sxi_y[f.FX(2 * i, 2 * j + 1)];
     }
   for (int j = 0; j <= nj; ++j)
     for (int i = 0; i < ni; ++i) {
+      c.vfe[c.FE(i, j)] = f.vfe[f.FE(2 * i, 2 * j)] + f.vfe[f.FE(2 * i + 1, 2 * j)];
+      if (j == 0) {
+        c.wvx[i] = 0.5 * (f.wvx[2 * i] + f.wvx[2 * i + 1]);
+        c.wvy[i] = 0.5 * (f.wvy[2 * i] + f.wvy[2 * i + 1]);
+      }
       c.seta_x[c.FE(i, j)] = f.seta_x[f.FE(2 * i, 2 * j)] + f.seta_x[f.FE(2 * i + 1, 2 * j)];
       c.seta_y[c.FE(i, j)] = f.seta_y[f.FE(2 * i, 2 * j)] + f.seta_y[f.FE(2 * i + 1, 2 * j)];
     }
@@ -324,17 +362,17 @@ static void alloc_level_state(Level& g) {
 // ---------------------------------------------------------------- boundary conditions
 // Far field by 1-D Riemann invariants normal to the boundary (section 2, G9);
 // n = outward unit normal.  Returns the boundary state given to both ghost layers.
-static V4 farfield_state(const V4& wi, const V4& winf, double nx, double ny) {
+static V4 farfield_state(const V4& wi, const V4& winf, double nx, double ny, double vb = 0.0) {
   const Prim qi = prim(wi), qf = prim(winf);
   const double ai = std::sqrt(GAM * qi.p / qi.rho), af = std::sqrt(GAM * qf.p / qf.rho);
   const double vni = qi.u * nx + qi.v * ny, vnf = qf.u * nx + qf.v * ny;
-  if (std::fabs(vni) >= ai) return vni > 0.0 ? wi : winf;
+  if (std::fabs(vni - vb) >= ai) return vni - vb > 0.0 ? wi : winf;
   const double Rp = vni + 2.0 * ai / (GAM - 1.0);
   const double Rm = vnf - 2.0 * af / (GAM - 1.0);
   const double vnb = 0.5 * (Rp + Rm);
   const double ab = 0.25 * (GAM - 1.0) * (Rp - Rm);
   double s, ut, vt;
-  if (vnb > 0.0) {
+  if (vnb - vb > 0.0) {
     s = qi.p / std::pow(qi.rho, GAM);
     ut = qi.u - vni * nx;
     vt = qi.v - vni * ny;
@@ -369,15 +407,35 @@ static void bc_fill(const Solver& S, Level& g) {
       for (int k = 0; k < 2; ++k) {
         const V4 w = g.u[g.G(i, k)];
         V4 gw;
-        gw[0] = w[0];
-        gw[3] = w[3];
-        if (noslip) {
-          gw[1] = -w[1];
-          gw[2] = -w[2];
+        if (!S.moving) {
+          gw[0] = w[0];
+          gw[3] = w[3];
+          if (noslip) {
+            gw[1] = -w[1];
+            gw[2] = -w[2];
+          } else {
+            const double mn = w[1] * nx + w[2] * ny;
+            gw[1] = w[1] - 2.0 * mn * nx;
+            gw[2] = w[2] - 2.0 * mn * ny;
+          }
         } else {
-          const double mn = w[1] * nx + w[2] * ny;
-          gw[1] = w[1] - 2.0 * mn * nx;
-          gw[2] = w[2] - 2.0 * mn * ny;
+          // moving wall with velocity (wx, wy): same density and pressure, velocity mirrored
+          // about the wall velocity (no-slip) or its normal component reflected relative to it
+          const Prim q = prim(w);
+          const double wx = g.wvx[i], wy = g.wvy[i];
+          double ug, vg;
+          if (noslip) {
+            ug = 2.0 * wx - q.u;
+            vg = 2.0 * wy - q.v;
+          } else {
+            const double rn = (q.u - wx) * nx + (q.v - wy) * ny;
+            ug = q.u - 2.0 * rn * nx;
+            vg = q.v - 2.0 * rn * ny;
+          }
+          gw[0] = q.rho;
+          gw[1] = q.rho * ug;
+          gw[2] = q.rho * vg;
+          gw[3] = q.p / (GAM - 1.0) + 0.5 * q.rho * (ug * ug + vg * vg);
         }
         g.u[g.G(i, -1 - k)] = gw;
       }
@@ -387,7 +445,7 @@ static void bc_fill(const Solver& S, Level& g) {
   for (int i = 0; i < ni; ++i) {
     const double sx = g.seta_x[g.FE(i, nj)], sy = g.seta_y[g.FE(i, nj)];
     const double len = std::sqrt(sx * sx + sy * sy);
-    const V4 b = farfield_state(g.u[g.G(i, nj - 1)], S.uinf, sx / len, sy / len);
+    const V4 b = farfield_state(g.u[g.G(i, nj - 1)], S.uinf, sx / len, sy / len, g.vfe[g.FE(i, nj)] / len);
     g.u[g.G(i, nj)] = b;
     g.u[g.G(i, nj + 1)] = b;
   }
@@ -396,14 +454,14 @@ static void bc_fill(const Solver& S, Level& g) {
     {
       const double sx = g.sxi_x[g.FX(0, j)], sy = g.sxi_y[g.FX(0, j)];
       const double len = std::sqrt(sx * sx + sy * sy);
-      const V4 b = farfield_state(g.u[g.G(0, j)], S.uinf, -sx / len, -sy / len);
+      const V4 b = farfield_state(g.u[g.G(0, j)], S.uinf, -sx / len, -sy / len, -g.vfx[g.FX(0, j)] / len);
       g.u[g.G(-1, j)] = b;
       g.u[g.G(-2, j)] = b;
     }
     {
       const double sx = g.sxi_x[g.FX(ni, j)], sy = g.sxi_y[g.FX(ni, j)];
       const double len = std::sqrt(sx * sx + sy * sy);
-      const V4 b = farfield_state(g.u[g.G(ni - 1, j)], S.uinf, sx / len, sy / len);
+      const V4 b = farfield_state(g.u[g.G(ni - 1, j)], S.uinf, sx / len, sy / len, g.vfx[g.FX(ni, j)] / len);
       g.u[g.G(ni, j)] = b;
       g.u[g.G(ni + 1, j)] = b;
     }
@@ -413,6 +471,8 @@ static void bc_fill(const Solver& S, Level& g) {
 // ---------------------------------------------------------------- JST residual
 // Directional spectral radii of a cell: r = |v . S_bar| + a |S_bar|, with S_bar
 // the mean of the cell's two opposite face area vectors (G6).
+// On a moving grid the convective speed is relative: |v . S_bar - V_bar| with V_bar the mean
+// grid volume flux of the same two faces.
 static void cell_radii(const Level& g, const V4& w, int i, int j, double& rxi, double& reta) {
   const Prim q = prim(w);
   const double a = std::sqrt(GAM * q.p / q.rho);
@@ -420,8 +480,10 @@ static void cell_radii(const Level& g, const V4& w, int i, int j, double& rxi, d
   const double sy = 0.5 * (g.sxi_y[g.FX(i, j)] + g.sxi_y[g.FX(i + 1, j)]);
   const double ex = 0.5 * (g.seta_x[g.FE(i, j)] + g.seta_x[g.FE(i, j + 1)]);
   const double ey = 0.5 * (g.seta_y[g.FE(i, j)] + g.seta_y[g.FE(i, j + 1)]);
-  rxi = std::fabs(q.u * sx + q.v * sy) + a * std::sqrt(sx * sx + sy * sy);
-  reta = std::fabs(q.u * ex + q.v * ey) + a * std::sqrt(ex * ex + ey * ey);
+  const double vx = 0.5 * (g.vfx[g.FX(i, j)] + g.vfx[g.FX(i + 1, j)]);
+  const double ve = 0.5 * (g.vfe[g.FE(i, j)] + g.vfe[g.FE(i, j + 1)]);
+  rxi = std::fabs(q.u * sx + q.v * sy - vx) + a * std::sqrt(sx * sx + sy * sy);
+  reta = std::fabs(q.u * ex + q.v * ey - ve) + a * std::sqrt(ex * ex + ey * ey);
 }
 
 // Martinelli correction (eq. spectralcorrection): r~_i = r_i (1 + (r_j/r_i)^(2/3)).
@@ -449,11 +511,12 @@ struct FaceFlux { V4 hc, hd; };
 //   d = eps2 dw - eps4 (dw_+ - 2 dw + dw_-),  w = (rho, rho u, rho v, rho H),
 //   eps2 = s r, eps4 = max(0, r/32 - 2 eps2),  s = min(0.25, max(s_L, s_R)),
 //   r = max(r~_L, r~_R).   On coarse levels: s = s_coarse and no eps4 term.
+// On a moving face (grid volume flux vf) the convective flux is F . S - u vf.
 static FaceFlux jst_face(const Solver& S, const V4& uLL, const V4& uL, const V4& uR, const V4& uRR,
-                         double sx, double sy, double rtL, double rtR, bool finest) {
+                         double sx, double sy, double vf, double rtL, double rtR, bool finest) {
   FaceFlux out;
   const V4 fL = conv_flux(uL, sx, sy), fR = conv_flux(uR, sx, sy);
-  for (int k = 0; k < 4; ++k) out.hc[k] = 0.5 * (fL[k] + fR[k]);
+  for (int k = 0; k < 4; ++k) out.hc[k] = 0.5 * ((fL[k] - uL[k] * vf) + (fR[k] - uR[k] * vf));
   auto wvec = [](const V4& w) {
     const Prim q = prim(w);
     return V4{w[0], w[1], w[2], w[3] + q.p};
@@ -555,12 +618,12 @@ static void residual(const Solver& S, Level& g, bool finest, std::vector<V4>& Fc
   for (int j = 0; j < nj; ++j)
     for (int i = 0; i <= ni; ++i)
       fx[g.FX(i, j)] = jst_face(S, g.u[g.G(i - 2, j)], g.u[g.G(i - 1, j)], g.u[g.G(i, j)],
-                                g.u[g.G(i + 1, j)], g.sxi_x[g.FX(i, j)], g.sxi_y[g.FX(i, j)],
+                                g.u[g.G(i + 1, j)], g.sxi_x[g.FX(i, j)], g.sxi_y[g.FX(i, j)], g.vfx[g.FX(i, j)],
                                 rtilde(g, i - 1, j, 0), rtilde(g, i, j, 0), finest);
   for (int j = 0; j <= nj; ++j)
     for (int i = 0; i < ni; ++i) {
       fe[g.FE(i, j)] = jst_face(S, g.u[g.G(i, j - 2)], g.u[g.G(i, j - 1)], g.u[g.G(i, j)],
-                                g.u[g.G(i, j + 1)], g.seta_x[g.FE(i, j)], g.seta_y[g.FE(i, j)],
+                                g.u[g.G(i, j + 1)], g.seta_x[g.FE(i, j)], g.seta_y[g.FE(i, j)], g.vfe[g.FE(i, j)],
                                 rtilde(g, i, j - 1, 1), rtilde(g, i, j, 1), finest);
       if (S.P.viscous) fvis[g.FE(i, j)] = visc_face(S, g, i, j);
     }
@@ -702,7 +765,7 @@ static void build_blocks(const Solver& S, Level& g) {
       V4 ub;
       const V4 &a = g.u[g.G(i - 1, j)], &b = g.u[g.G(i, j)];
       for (int k = 0; k < 4; ++k) ub[k] = 0.5 * (a[k] + b[k]);
-      split_jacobians(ub, g.sxi_x[g.FX(i, j)], g.sxi_y[g.FX(i, j)], S.P.d_cut, g.Axp[g.FX(i, j)],
+      split_jacobians(ub, g.sxi_x[g.FX(i, j)], g.sxi_y[g.FX(i, j)], g.vfx[g.FX(i, j)], S.P.d_cut, g.Axp[g.FX(i, j)],
                       g.Axm[g.FX(i, j)]);
     }
   for (int j = 0; j <= nj; ++j)
@@ -710,7 +773,7 @@ static void build_blocks(const Solver& S, Level& g) {
       V4 ub;
       const V4 &a = g.u[g.G(i, j - 1)], &b = g.u[g.G(i, j)];
       for (int k = 0; k < 4; ++k) ub[k] = 0.5 * (a[k] + b[k]);
-      split_jacobians(ub, g.seta_x[g.FE(i, j)], g.seta_y[g.FE(i, j)], S.P.d_cut, g.Aep[g.FE(i, j)],
+      split_jacobians(ub, g.seta_x[g.FE(i, j)], g.seta_y[g.FE(i, j)], g.vfe[g.FE(i, j)], S.P.d_cut, g.Aep[g.FE(i, j)],
                       g.Aem[g.FE(i, j)]);
       if (S.P.viscous) {
         const double V = visc_radius(S, g, i, j, ub[0]);
@@ -1285,6 +1348,9 @@ void* or_create(int ni, int nj, int nw, const double* x, const double* y, const 
   fine.ni = ni;
   fine.nj = nj;
   fine.nw = nw;
+  const size_t nv = (size_t)(ni + 1) * (nj + 1);
+  S->x0.assign(x, x + nv);
+  S->y0.assign(y, y + nv);
   fine_metrics(fine, x, y);
   for (int l = p->nlevels - 2; l >= 0; --l) agglomerate(S->lev[l + 1], S->lev[l]);
   for (auto& g : S->lev) alloc_level_state(g);
@@ -1509,7 +1575,7 @@ void or_conv_flux(const double* w, double sx, double sy, double* f) {
 
 void or_split_jacobians(const double* w, double sx, double sy, double d, double* Ap, double* Am) {
   M4 P, M;
-  split_jacobians(V4{w[0], w[1], w[2], w[3]}, sx, sy, d, P, M);
+  split_jacobians(V4{w[0], w[1], w[2], w[3]}, sx, sy, 0.0, d, P, M);
   for (int a = 0; a < 4; ++a)
     for (int b = 0; b < 4; ++b) {
       Ap[4 * a + b] = P[a][b];
@@ -1611,8 +1677,8 @@ void or_linear_step(const double* w, double dx, double dy, int nx, int ny, doubl
   m.aw = aw;
   m.circulant = circulant;
   const V4 st{w[0], w[1], w[2], w[3]};
-  split_jacobians(st, 1.0, 0.0, d, m.Ap, m.Am);
-  split_jacobians(st, 0.0, 1.0, d, m.Bp, m.Bm);
+  split_jacobians(st, 1.0, 0.0, 0.0, d, m.Ap, m.Am);
+  split_jacobians(st, 0.0, 1.0, 0.0, d, m.Bp, m.Bm);
   for (int r = 0; r < 4; ++r)
     for (int k = 0; k < 4; ++k) {
       m.A[r][k] = m.Ap[r][k] + m.Am[r][k];
@@ -1641,6 +1707,64 @@ void or_linear_step(const double* w, double dx, double dy, int nx, int ny, doubl
       if (Bout) Bout[4 * r + k] = m.B[r][k];
       if (Mout) Mout[4 * r + k] = m.M[r][k];
     }
+}
+
+// Rigid motion of the whole grid: rotation by phi about (xc, yc) at angular rate phidot
+// (the pitching motion of section 6).  Metrics and face grid fluxes of every level follow.
+void or_set_motion(void* h, double phi, double phidot, double xc, double yc) {
+  Solver* S = static_cast<Solver*>(h);
+  Level& f = S->lev[S->L()];
+  const size_t nv = S->x0.size();
+  std::vector<double> x(nv), y(nv);
+  const double c = std::cos(phi), s = std::sin(phi);
+  for (size_t k = 0; k < nv; ++k) {
+    const double dx = S->x0[k] - xc, dy = S->y0[k] - yc;
+    x[k] = xc + c * dx - s * dy;
+    y[k] = yc + s * dx + c * dy;
+  }
+  fine_metrics(f, x.data(), y.data(), phidot, xc, yc);
+  for (int l = S->L() - 1; l >= 0; --l) agglomerate(S->lev[l + 1], S->lev[l]);
+  S->phi = phi;
+  S->phidot = phidot;
+  S->xc = xc;
+  S->yc = yc;
+  S->moving = true;
+}
+
+// One physical time step of dual time stepping (eq. nonlin-eq; section 6: implicit Euler for
+// the first step, BDF2 afterwards) from the stored history to t + dt, with the grid already
+// placed at t + dt by or_set_motion.  Pseudo-time FAS cycles until the residual has dropped
+// by `drop` or max_cycles.  Returns the cycles run (negative on NaN); history[k] = norm of
+// cycle k.  The first call takes the current state as u^n.
+int or_dual_time_step(void* h, double dt, double drop, int max_cycles, double* history) {
+  Solver* S = static_cast<Solver*>(h);
+  Level& g = S->lev[S->L()];
+  const int n = g.ni * g.nj;
+  if (S->un.empty()) {
+    S->un.resize(n);
+    for (int j = 0; j < g.nj; ++j)
+      for (int i = 0; i < g.ni; ++i) S->un[g.C(i, j)] = g.u[g.G(i, j)];
+  }
+  const bool bdf2 = S->steps_done > 0 && S->P.bdf_order == 2;
+  const double a_t = bdf2 ? 1.5 / dt : 1.0 / dt;
+  std::vector<double> src(4 * (size_t)n);
+  for (int q = 0; q < n; ++q)
+    for (int k = 0; k < 4; ++k)
+      src[k * n + q] = bdf2 ? (-4.0 * S->un[q][k] + S->unm1[q][k]) / (2.0 * dt) : -S->un[q][k] / dt;
+  or_set_time_source(h, a_t, src.data());
+  const int nc = or_solve(h, drop, max_cycles, history);
+  S->unm1 = S->un;
+  for (int j = 0; j < g.nj; ++j)
+    for (int i = 0; i < g.ni; ++i) S->un[g.C(i, j)] = g.u[g.G(i, j)];
+  S->steps_done += 1;
+  return nc;
+}
+
+// Face grid volume fluxes of level l (i-faces then j-faces), for pins.
+void or_grid_fluxes(void* h, int l, double* vfx, double* vfe) {
+  const Level& g = static_cast<Solver*>(h)->lev[l];
+  std::memcpy(vfx, g.vfx.data(), g.vfx.size() * 8);
+  std::memcpy(vfe, g.vfe.data(), g.vfe.size() * 8);
 }
 
 }  // extern "C"

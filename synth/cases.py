@@ -25,10 +25,11 @@ class FlowCase:
     reynolds: float = 0.0          # 0 => Euler
     levels: int = 3
     extra: dict = field(default_factory=dict)
+    n_wake: int | None = None      # None => ni // 8
 
     def grid(self) -> CGrid:
         return make_cgrid(self.ni, self.nj, thickness=self.thickness,
-                          wall_spacing=self.wall_spacing)
+                          wall_spacing=self.wall_spacing, n_wake=self.n_wake)
 
 
 def config_c1(alpha_deg: float = 1.25) -> FlowCase:
@@ -54,7 +55,11 @@ def config_c3() -> FlowCase:
 
 
 def config_c4_cases(n: int = 64, seed: int = 1710) -> list[FlowCase]:
-    """Batched steady Euler cases of uneven size drawn from a seeded generator."""
+    """Batched steady Euler cases of uneven size drawn from a seeded generator.
+
+    Up to 4 multigrid levels, fewer where the coarsest grid would have fewer than 8 cells
+    across the j direction; the wake-cut length is a multiple of 8 cells so that every level
+    agglomerates it exactly."""
     rng = np.random.default_rng(seed)
     out = []
     for c in range(n):
@@ -63,7 +68,12 @@ def config_c4_cases(n: int = 64, seed: int = 1710) -> list[FlowCase]:
         mach = float(rng.uniform(0.5, 0.85))
         alpha = float(rng.uniform(-2.0, 4.0))
         t = float(rng.uniform(0.08, 0.12))
-        out.append(FlowCase(f"batch{c:02d}_{ni}x{nj}", ni, nj, t, 2e-3, mach, alpha, 0.0, 4))
+        levels = 1
+        while levels < 4 and nj // (2 ** levels) >= 8:
+            levels += 1
+        n_wake = 8 * max(1, round(ni / 64))
+        out.append(FlowCase(f"batch{c:02d}_{ni}x{nj}", ni, nj, t, 2e-3, mach, alpha, 0.0, levels,
+                            n_wake=n_wake))
     return out
 
 

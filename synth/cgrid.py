@@ -69,6 +69,8 @@ def _line_distribution(nj: int, dw: float, delta_bl: float, length: float) -> np
     """
     nh = nj // 2
     sp = np.empty(nj)
+    if dw * nh >= delta_bl:   # many wall-normal cells with a coarse wall spacing: widen the layer
+        delta_bl = 2.0 * dw * nh
     r_bl = _geometric_ratio(dw, nh, delta_bl) if nh > 0 else 1.0
     sp[:nh] = dw * r_bl ** np.arange(nh)
     rest = length - sp[:nh].sum()
