@@ -1,5 +1,5 @@
 """Benchmark: FAS cycles of the preconditioned AW3 smoother on the 256x64 thin-layer RANS
-C-grid workload (M = 0.5, Re = 1e7, wall spacing 1e-5, 4-level V-cycle, Baldwin-Lomax).
+C-grid workload (M = 0.5, Re = 1e7, wall spacing 1e-5, 4-level W-cycle, Baldwin-Lomax).
 
 One step = one FAS cycle over the whole grid (all steps of the method's hot path).  Prints
 one JSON line.  Metric: Mcell-iterations/s (fine cells x cycles / s), plus the wall time to a
@@ -197,6 +197,50 @@ def time_cycles(s, stream, flush, steps, k0):
     return ms
 
 
+def measure_batched(P, stream, flush, steps, warmup, precision="mixed"):
+    """64 uneven Euler cases (128x32 .. 512x128 cells, seeded M, alpha, thickness) advanced
+    together, one captured CUDA graph per cycle; sweep variants chosen by the autotuner."""
+    import torch
+    from synth.cases import config_c4_cases
+    cases = config_c4_cases()
+    grids, params = [], []
+    for c in cases:
+        grids.append(c.grid())
+        params.append(P.default_params(scheme="AW3", nlevels=c.levels, mach=c.mach, alpha_deg=c.alpha_deg,
+                                       cfl=100.0, precision=precision))
+    cells = sum(g.ni * g.nj for g in grids)
+    b = P.fasw.Batch(grids, params, stream=stream.cuda_stream)
+    choice = b.autotune()
+    for k in range(warmup):
+        b.cycle(k)
+    ms = []
+    for k in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.cycle(warmup + k)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    value = cells * steps / (sum(ms) / 1e3) / 1e6
+    b.close()
+    b = P.fasw.Batch(grids, params, stream=stream.cuda_stream)
+    b.autotune()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    code, cyc, drops, ncy = b.solve(1e-6, 300)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    b.close()
+    return {"cases": len(grids), "cells": cells, "precision": precision, "value": value, "unit": METRIC,
+            "ms_per_cycle": sum(ms) / steps,
+            "sweep_choice": {"cta": choice.count(2), "strips8": choice.count(3), "strips16": choice.count(4)},
+            "time_to_6_orders": {"seconds": dt, "cycles_run": ncy, "status": int(code),
+                                 "cases_converged": int((cyc > 0).sum()), "cases_diverged": int((cyc == -2).sum()),
+                                 "median_cycles": float(np.median(cyc[cyc > 0])) if (cyc > 0).any() else None}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -205,6 +249,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.warmup < 3:
@@ -221,7 +266,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()          # non-default stream: cycles are replayed as CUDA graphs
+    torch.cuda.set_stream(stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     g = workload_grid()
     ncell = g.ni * g.nj
@@ -278,8 +324,13 @@ def main():
     e2e_value = world * ncell * e2e_steps / e2e_s / 1e6
     state_bytes = 4 * ncell * 8
 
-    # time to a 6-order drop from the free stream, FP64 and mixed preconditioner
-    drops = {}
+    # time to a 6-order drop from the free stream, FP64 and mixed preconditioner; then the
+    # pitching motion (alpha = 2 deg sin(2kt), k = 0.2, 64 steps per period): an implicit-Euler
+    # start step and one BDF2 step, each to an 11-order drop in pseudo time
+    drops, unsteady = {}, {}
+    omega = 0.4
+    dt_phys = 2.0 * np.pi / omega / 64
+    amp = np.radians(2.0)
     for prec in ("fp64", "mixed"):
         sd = P.Solver(g, gpu_params(P, prec), stream=stream.cuda_stream)
         torch.cuda.synchronize()
@@ -289,7 +340,21 @@ def main():
         dt = time.perf_counter() - t0
         drops[prec] = {"seconds": dt if code == 0 else None, "cycles": nc, "status": int(code),
                        "final_drop": float(hist[-1] / hist[0]) if len(hist) else None}
+        steps = []
+        for step in (1, 2):
+            tt = step * dt_phys
+            sd.set_motion(-amp * np.sin(omega * tt), -amp * omega * np.cos(omega * tt))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c2, n2, h2 = sd.dual_time_step(dt_phys, 1e-11, 400)
+            torch.cuda.synchronize()
+            steps.append({"kind": "implicit Euler" if step == 1 else "BDF2", "seconds": time.perf_counter() - t0,
+                          "cycles": n2, "status": int(c2),
+                          "final_drop": float(h2[-1] / h2[0]) if len(h2) else None})
+        unsteady[prec] = steps
         sd.close()
+
+    batched = None if args.no_batched else measure_batched(P, stream, flush, args.steps, args.warmup)
 
     if rank != 0:
         if dist:
@@ -333,7 +398,8 @@ def main():
                        "l2": "flushed (256 MiB write) between timed cycles", "parallelism": "replicas"},
             "other_precision": {"precision": "mixed" if args.precision == "fp64" else "fp64",
                                 "value": other_value, "ms_per_step": sum(ms_other) / args.steps},
-            "time_to_6_orders": drops, "kernel_share": share,
+            "time_to_6_orders": drops, "time_to_11_orders_per_time_step": unsteady,
+            "batched_64_cases": batched, "kernel_share": share,
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes + 8},
             "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "cpu_baseline": cpu}

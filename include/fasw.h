@@ -142,6 +142,13 @@ int fasw_solve_steady(fasw_ctx* ctx, double drop, int max_cycles, double* histor
  * stream; with the legacy default stream (NULL) cycles are always launched individually. */
 int fasw_use_graphs(fasw_ctx* ctx, int enable);
 
+/* How the SGS sweeps run: 0 = automatic (FP64: strip-pipelined multi-CTA sweep; mixed: one-CTA
+ * sweep), 1 = one thread per cell applying the LU blocks (reference kernel), 2 = one CTA with
+ * precomputed transfer blocks (strips where a hyperplane exceeds 128 cells), 3 = strip-pipelined
+ * with 8 rows per strip, 4 = with 16 rows per strip.  All give the same
+ * Gauss-Seidel result up to rounding.  Synchronizes the stream; drops captured cycles. */
+int fasw_set_sweep(fasw_ctx* ctx, int kind);
+
 /* Eddy viscosity of the finest level (Baldwin-Lomax from the current state); n doubles. */
 int fasw_get_mut(fasw_ctx* ctx, double* mut, int on_device);
 
@@ -149,6 +156,24 @@ int fasw_get_mut(fasw_ctx* ctx, double* mut, int on_device);
  * 0 = steady) on every level and the history source src (finest level, 4 x nj x ni;
  * NULL = zero), so that F gains a_t u + src and D gains eta dt* a_t I (AW) or a_t I (ARK). */
 int fasw_set_time_source(fasw_ctx* ctx, double a_t, const double* src, int on_device);
+
+/* Rigid motion of the whole grid (the pitching motion of section 6): the reference grid rotated
+ * by phi (radians, counter-clockwise) about (xc, yc), moving at angular rate phidot.  Recomputes
+ * the metrics of every level and the face grid volume fluxes v_grid . S, which enter the
+ * convective fluxes (F . S - u v_grid . S), the spectral radii and the FVS eigenvalues
+ * (relative normal velocity), the wall ghosts (moving wall) and the far-field in/outflow
+ * test.  Volumes are unchanged by a rigid motion, so the discrete geometric conservation law
+ * holds.  Synchronizes the stream. */
+int fasw_set_motion(fasw_ctx* ctx, double phi, double phidot, double xc, double yc);
+
+/* One physical time step of dual time stepping, eq. (nonlin-eq): the first call takes the
+ * current finest-level state as u^n and uses implicit Euler (section 6); later calls use BDF2
+ * when bdf_order == 2.  Sets a_t and the history source, runs pseudo-time FAS cycles until the
+ * residual drops by `drop` (or max_cycles; history/ncycles as in fasw_solve_steady), then
+ * shifts the history.  Place the grid at the new time level first (fasw_set_motion).
+ * Returns FASW_OK, FASW_ERR_NOT_CONVERGED, FASW_ERR_DIVERGED or another error. */
+int fasw_dual_time_step(fasw_ctx* ctx, double dt, int bdf_order, double drop, int max_cycles, double* history,
+                        int* ncycles);
 
 /* Number of kernel launches the context has enqueued since creation (instrumentation). */
 long long fasw_launch_count(fasw_ctx* ctx);
@@ -167,6 +192,29 @@ int fasw_profile(fasw_ctx* ctx, int enable);
 
 /* Launch count and summed device milliseconds of one kernel class since fasw_profile. */
 int fasw_kernel_time(fasw_ctx* ctx, int kernel, long long* count, double* total_ms);
+
+/* ---- Batched cases (many independent airfoil cases of uneven size).  Each case is a context
+ * on its own stream (created and owned by the batch); fasw_batch_cycle runs one FAS cycle of
+ * every case as parallel branches of one captured CUDA graph launched on `stream` (NULL: the
+ * batch creates a stream).  Arrays are per case (ncases entries); params[k] is case k's. */
+typedef struct fasw_batch fasw_batch;
+int fasw_batch_create(int ncases, const int* ni, const int* nj, const int* n_wake, const double* const* x,
+                      const double* const* y, int coords_on_device, const fasw_params* params, void* stream,
+                      fasw_batch** out);
+void fasw_batch_destroy(fasw_batch* batch);
+/* The context of case k (owned by the batch; use it for fasw_get_state / fasw_set_state). */
+fasw_ctx* fasw_batch_case(fasw_batch* batch, int k);
+/* One cycle of every case; norms (nullable, ncases): each case's residual norm at its start. */
+int fasw_batch_cycle(fasw_batch* batch, int cycle_index, double* norms);
+/* Cycles until every case has dropped its residual by `drop` or diverged; cycles[k] = cycles case
+ * k needed (-1 not reached, -2 diverged: NaN or growth by 1e8; the other cases go on),
+ * final_drop[k] = its last finite norm ratio, *ncycles = cycles run.  Returns FASW_OK,
+ * FASW_ERR_NOT_CONVERGED or FASW_ERR_DIVERGED (some case diverged). */
+int fasw_batch_solve(fasw_batch* batch, double drop, int max_cycles, int* cycles, double* final_drop, int* ncycles);
+/* Picks the sweep variant (see fasw_set_sweep) by timing whole batch cycles with each candidate
+ * (states are saved and restored); choice[k] (nullable) receives the kind used for case k. */
+int fasw_batch_autotune(fasw_batch* batch, int* choice);
+long long fasw_batch_launch_count(fasw_batch* batch);
 
 /* Message for an error code; and the last CUDA error string seen by the library. */
 const char* fasw_strerror(int code);

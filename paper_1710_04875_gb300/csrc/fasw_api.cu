@@ -10,6 +10,7 @@
 
 #include "../../include/fasw.h"
 #include "fasw_internal.cuh"
+#include "fasw_sweep.cuh"
 #include "fasw_transfer.cuh"
 
 using namespace fasw;
@@ -67,6 +68,16 @@ struct fasw_ctx {
   struct CycleGraph { double cfl; cudaGraphExec_t exec; long long kernels; };
   std::vector<CycleGraph> graphs;
   int use_graphs = 1;
+  int sweep_kind = SWEEP_AUTO;
+  long long spin_limit = 1LL << 22;
+  long long* d_prog = nullptr;  // strip progress flags
+  int* d_err = nullptr;         // device error word (bounded waits)
+  int* h_err = nullptr;         // pinned copy
+  double* d_x0 = nullptr;       // reference vertices (the grid at rest)
+  double* d_y0 = nullptr;
+  double* d_un = nullptr;       // dual-time history of the finest level (4 x n)
+  double* d_unm1 = nullptr;
+  int steps_done = 0;
   int L() const { return (int)lev.size() - 1; }
 };
 
@@ -159,7 +170,16 @@ int alloc_level(fasw_ctx* c, LevelDev& L) {
   A(L.dlu32, 16 * n);
   A(L.yz32, 4 * n);
   A(L.norm_part, (size_t)residual_blocks(L));
+  A(L.tb, 80 * n);
+  A(L.vfx, nfx);
+  A(L.vfe, nfe);
+  A(L.wvx, (size_t)L.ni);
+  A(L.wvy, (size_t)L.ni);
 #undef A
+  CKR(cudaMemsetAsync(L.vfx, 0, nfx * sizeof(double), c->st));
+  CKR(cudaMemsetAsync(L.vfe, 0, nfe * sizeof(double), c->st));
+  CKR(cudaMemsetAsync(L.wvx, 0, (size_t)L.ni * sizeof(double), c->st));
+  CKR(cudaMemsetAsync(L.wvy, 0, (size_t)L.ni * sizeof(double), c->st));
   CKR(cudaMemsetAsync(L.s, 0, 4 * n * sizeof(double), c->st));
   CKR(cudaMemsetAsync(L.src, 0, 4 * n * sizeof(double), c->st));
   CKR(cudaMemsetAsync(L.mut, 0, n * sizeof(double), c->st));
@@ -181,10 +201,19 @@ void free_stream(double mach, double alpha_deg, double w[4]) {
 }
 
 // ---- driver steps
+void run_sweep(fasw_ctx* c, const LevelDev& L, int do_update, double alpha, const double* rhs) {
+  if (c->sweep_kind == SWEEP_LEGACY) {
+    launch_sgs(L, c->sc, c->mixed, do_update, alpha, rhs, nullptr, c->st);
+    return;
+  }
+  const int kind = c->sweep_kind == SWEEP_AUTO ? (c->mixed ? SWEEP_CTA : SWEEP_STRIPS) : c->sweep_kind;
+  launch_sweep(L, c->mixed, kind, do_update, c->sc.aw, alpha, rhs, c->d_prog, c->d_err, c->spin_limit, c->st);
+}
+
 void bc_aux(fasw_ctx* c, int l, double cfl, int want_dts) {
-  { Prof p(c, FASW_K_BC); launch_bc(c->lev[l], c->ph, c->st); }
-  { Prof p(c, FASW_K_CELL_AUX); launch_cell_aux(c->lev[l], c->ph, cfl, want_dts, c->st); }
-  c->launches += 2;
+  Prof p(c, FASW_K_CELL_AUX);
+  launch_bc_aux(c->lev[l], c->ph, cfl, want_dts, c->st);
+  ++c->launches;
 }
 
 // One smoothing step on level l: dt* and the preconditioner frozen at u^(0) (reading G19),
@@ -193,10 +222,14 @@ void smooth_step(fasw_ctx* c, int l, double cfl, bool record_norm) {
   LevelDev& L = c->lev[l];
   const SchemeParams& sc = c->sc;
   bc_aux(c, l, cfl, 1);
-  { Prof p(c, FASW_K_COPY); launch_copy_u0(L, c->st); }
   { Prof p(c, FASW_K_FACE_BLOCKS); launch_face_blocks(L, c->ph, sc, c->mixed, c->st); }
-  { Prof p(c, FASW_K_DIAG_BLOCKS); launch_diag_blocks(L, sc, c->mixed, c->st); }
-  c->launches += 3;
+  { Prof p(c, FASW_K_DIAG_BLOCKS); launch_diag_blocks(L, sc, c->mixed, c->st); }  // also saves u^(0)
+  c->launches += 2;
+  if (c->sweep_kind != SWEEP_LEGACY) {
+    Prof p(c, FASW_K_DIAG_BLOCKS);
+    launch_sgs_prep(L, c->mixed, c->st);
+    ++c->launches;
+  }
   for (int i = 1; i <= sc.nstages; ++i) {
     if (i > 1) bc_aux(c, l, cfl, 0);
     ResArgs a{};
@@ -212,11 +245,10 @@ void smooth_step(fasw_ctx* c, int l, double cfl, bool record_norm) {
       launch_norm_final(L, residual_blocks(L), L.n * (c->prm.norm_all ? 4 : 1), c->d_norm, c->st);
       ++c->launches;
     }
-    { Prof p(c, FASW_K_SGS); launch_sgs(L, sc, c->mixed, 1, sc.alpha[i - 1], L.rhs, nullptr, c->st); }
+    { Prof p(c, FASW_K_SGS); run_sweep(c, L, 1, sc.alpha[i - 1], L.rhs); }
     c->launches += 2;
   }
-  { Prof p(c, FASW_K_BC); launch_bc(L, c->ph, c->st); }
-  ++c->launches;
+  // no ghost refill here: every consumer of the ghosts starts with its own fill (bc_aux)
 }
 
 void fas_cycle_rec(fasw_ctx* c, int l, double cfl, bool record_norm) {
@@ -237,8 +269,7 @@ void fas_cycle_rec(fasw_ctx* c, int l, double cfl, bool record_norm) {
   ++c->launches;
   for (int g = 0; g < c->prm.gamma_cycle; ++g) fas_cycle_rec(c, l - 1, cfl, false);
   { Prof p(c, FASW_K_PROLONG); launch_prolong(F, C, c->st); }
-  { Prof p(c, FASW_K_BC); launch_bc(F, c->ph, c->st); }
-  c->launches += 2;
+  ++c->launches;
 }
 
 void drop_graphs(fasw_ctx* c) {
@@ -363,24 +394,36 @@ int fasw_create(int ni, int nj, int n_wake, const double* x, const double* y, in
     return r;
   }
   e = cudaMallocHost(&c->h_norm, sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(int));
   if (e != cudaSuccess) {
     fasw_destroy(c);
     return cuda_fail(e);
   }
-  // metrics on the finest level from the vertices, coarse levels by agglomeration
-  const size_t nv = (size_t)(ni + 1) * (nj + 1);
-  double *dx = nullptr, *dy = nullptr;
-  if (coords_on_device) {
-    dx = const_cast<double*>(x);
-    dy = const_cast<double*>(y);
-  } else {
-    if ((r = dalloc(c, &dx, nv)) != FASW_OK || (r = dalloc(c, &dy, nv)) != FASW_OK) {
+  *c->h_err = 0;
+  if (p->spin_limit > 0) c->spin_limit = p->spin_limit;
+  {
+    const int nstrips = (nj + 7) / 8 + 1;
+    if ((r = dalloc(c, &c->d_prog, 2 * (size_t)nstrips)) != FASW_OK || (r = dalloc(c, &c->d_err, 1)) != FASW_OK) {
       fasw_destroy(c);
       return r;
     }
-    cudaMemcpyAsync(dx, x, nv * sizeof(double), cudaMemcpyHostToDevice, c->st);
-    cudaMemcpyAsync(dy, y, nv * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+    cudaMemsetAsync(c->d_prog, 0, 2 * (size_t)nstrips * sizeof(long long), c->st);
   }
+  // metrics on the finest level from the vertices, coarse levels by agglomeration
+  const size_t nv = (size_t)(ni + 1) * (nj + 1);
+  double *dx = nullptr, *dy = nullptr;
+  if ((r = dalloc(c, &dx, nv)) != FASW_OK || (r = dalloc(c, &dy, nv)) != FASW_OK ||
+      (r = dalloc(c, &c->d_un, 4 * (size_t)ni * nj)) != FASW_OK ||
+      (r = dalloc(c, &c->d_unm1, 4 * (size_t)ni * nj)) != FASW_OK) {
+    fasw_destroy(c);
+    return r;
+  }
+  const cudaMemcpyKind kind = coords_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaMemcpyAsync(dx, x, nv * sizeof(double), kind, c->st);
+  cudaMemcpyAsync(dy, y, nv * sizeof(double), kind, c->st);
+  c->d_x0 = dx;
+  c->d_y0 = dy;
   launch_metrics_fine(c->lev[nl - 1], dx, dy, c->st);
   for (int l = nl - 2; l >= 0; --l) launch_agglomerate(c->lev[l + 1], c->lev[l], c->st);
   for (int l = 0; l < nl; ++l) launch_fill_state(c->lev[l], c->ph.uinf, c->st);
@@ -404,6 +447,7 @@ void fasw_destroy(fasw_ctx* c) {
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   for (void* q : c->allocs) cudaFree(q);
   if (c->h_norm) cudaFreeHost(c->h_norm);
+  if (c->h_err) cudaFreeHost(c->h_err);
   delete c;
 }
 
@@ -498,7 +542,11 @@ int fasw_precond_apply(fasw_ctx* c, int l, double cfl, const double* rin, double
   c->launches += 2;
   int r = copy_in(c, c->d_tmp2, rin, m, on_device);
   if (r) return r;
-  launch_sgs(L, c->sc, c->mixed, 0, 0.0, c->d_tmp2, nullptr, c->st);
+  if (c->sweep_kind != SWEEP_LEGACY) {
+    launch_sgs_prep(L, c->mixed, c->st);
+    ++c->launches;
+  }
+  run_sweep(c, L, 0, 0.0, c->d_tmp2);
   ++c->launches;
   const double* zsrc = L.yz64;
   if (c->mixed) {
@@ -546,6 +594,7 @@ static void enqueue_cycle(fasw_ctx* c, double cfl) {
   }
   fas_cycle_rec(c, Lf, cfl, true);
   cudaMemcpyAsync(c->h_norm, c->d_norm, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
 }
 
 // The launch sequence of a cycle depends only on c*, so each distinct c* is captured once
@@ -584,7 +633,17 @@ int fasw_fas_cycle(fasw_ctx* c, int cycle_index, double* res_norm) {
   if (r) return r;
   r = sync(c);
   if (r) return r;
+  if (*c->h_err) return FASW_ERR_DEVICE_TIMEOUT;
   if (res_norm) *res_norm = *c->h_norm;
+  return FASW_OK;
+}
+
+int fasw_set_sweep(fasw_ctx* c, int kind) {
+  if (!c || kind < SWEEP_AUTO || kind > SWEEP_STRIPS16) return FASW_ERR_ARG;
+  int r = sync(c);
+  if (r) return r;
+  c->sweep_kind = kind;
+  drop_graphs(c);
   return FASW_OK;
 }
 
@@ -643,6 +702,52 @@ int fasw_set_time_source(fasw_ctx* c, double a_t, const double* src, int on_devi
 
 long long fasw_launch_count(fasw_ctx* c) { return c ? c->launches : -1; }
 
+int fasw_set_motion(fasw_ctx* c, double phi, double phidot, double xc, double yc) {
+  if (!c) return FASW_ERR_ARG;
+  int r = sync(c);
+  if (r) return r;
+  if (!c->ph.moving) drop_graphs(c);  // the moving-wall flag is a by-value kernel argument
+  c->ph.moving = 1;
+  const int nl = (int)c->lev.size();
+  launch_metrics_fine(c->lev[nl - 1], c->d_x0, c->d_y0, c->st, 1, phi, phidot, xc, yc);
+  for (int l = nl - 2; l >= 0; --l) launch_agglomerate(c->lev[l + 1], c->lev[l], c->st);
+  c->launches += nl;
+  return sync(c);
+}
+
+int fasw_dual_time_step(fasw_ctx* c, double dt, int bdf_order, double drop, int max_cycles, double* history,
+                        int* ncycles) {
+  if (!c || !(dt > 0.0) || (bdf_order != 1 && bdf_order != 2) || max_cycles < 1) return FASW_ERR_ARG;
+  LevelDev& F = c->lev[c->L()];
+  const int m = 4 * F.n;
+  if (c->steps_done == 0) {  // the current state is u^n
+    launch_pack(F, nullptr, 0, c->d_un, c->st);
+    ++c->launches;
+  }
+  const bool bdf2 = c->steps_done > 0 && bdf_order == 2;
+  const double a_t = bdf2 ? 1.5 / dt : 1.0 / dt;
+  int r = sync(c);
+  if (r) return r;
+  if (a_t != F.a_t) {
+    drop_graphs(c);
+    for (auto& L : c->lev) L.a_t = a_t;
+  }
+  if (bdf2)
+    launch_time_source(F.src, c->d_un, c->d_unm1, -4.0 / (2.0 * dt), 1.0 / (2.0 * dt), m, c->st);
+  else
+    launch_time_source(F.src, c->d_un, nullptr, -1.0 / dt, 0.0, m, c->st);
+  ++c->launches;
+  r = fasw_solve_steady(c, drop, max_cycles, history, ncycles);
+  if (r != FASW_OK && r != FASW_ERR_NOT_CONVERGED) return r;
+  // shift the history: u^(n-1) <- u^n, u^n <- u
+  CKR(cudaMemcpyAsync(c->d_unm1, c->d_un, m * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  launch_pack(F, nullptr, 0, c->d_un, c->st);
+  ++c->launches;
+  c->steps_done += 1;
+  const int rs = sync(c);
+  return rs ? rs : r;
+}
+
 int fasw_profile(fasw_ctx* c, int enable) {
   if (!c) return FASW_ERR_ARG;
   int r = sync(c);
@@ -663,6 +768,224 @@ int fasw_kernel_time(fasw_ctx* c, int kernel, long long* count, double* total_ms
   if (total_ms) *total_ms = c->prof_ms[kernel];
   return FASW_OK;
 }
+
+// ---------------------------------------------------------------- batched cases
+// Many independent cases (own grids, sizes and flow conditions) advanced together: every
+// case is a context on its own stream, and one FAS cycle of all cases is captured into a
+// single CUDA graph as parallel branches (fork on the batch stream, join back), so the GPU
+// runs the cases' kernels concurrently.  The per-case sweep variant is chosen by timing.
+struct fasw_batch {
+  std::vector<fasw_ctx*> cases;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t st = nullptr;
+  int own_stream = 0;
+  struct G { int phase; cudaGraphExec_t exec; long long kernels; };
+  std::vector<G> graphs;
+  long long launches = 0;
+};
+
+static void batch_drop_graphs(fasw_batch* b) {
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  b->graphs.clear();
+}
+
+int fasw_batch_create(int ncases, const int* ni, const int* nj, const int* n_wake, const double* const* x,
+                      const double* const* y, int coords_on_device, const fasw_params* params, void* stream,
+                      fasw_batch** out) {
+  if (!out || ncases < 1 || !ni || !nj || !n_wake || !x || !y || !params) return FASW_ERR_ARG;
+  *out = nullptr;
+  fasw_batch* b = new (std::nothrow) fasw_batch();
+  if (!b) return FASW_ERR_OOM;
+  b->st = static_cast<cudaStream_t>(stream);
+  if (!b->st) {  // graph capture needs a non-default stream
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return FASW_ERR_CUDA;
+    }
+    b->own_stream = 1;
+  }
+  cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int k = 0; k < ncases; ++k) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      fasw_batch_destroy(b);
+      return FASW_ERR_CUDA;
+    }
+    b->streams.push_back(s);
+    b->joins.push_back(e);
+    fasw_ctx* c = nullptr;
+    const int r = fasw_create(ni[k], nj[k], n_wake[k], x[k], y[k], coords_on_device, &params[k], s, &c);
+    if (r != FASW_OK) {
+      fasw_batch_destroy(b);
+      return r;
+    }
+    b->cases.push_back(c);
+  }
+  *out = b;
+  return FASW_OK;
+}
+
+void fasw_batch_destroy(fasw_batch* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  batch_drop_graphs(b);
+  for (fasw_ctx* c : b->cases) fasw_destroy(c);
+  for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->own_stream) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+fasw_ctx* fasw_batch_case(fasw_batch* b, int k) {
+  return (b && k >= 0 && k < (int)b->cases.size()) ? b->cases[k] : nullptr;
+}
+
+static double case_cfl(const fasw_ctx* c, int cycle_index) {
+  return cycle_index < c->prm.ramp_cycles ? std::fmin(c->prm.cfl, c->prm.cfl_ramp) : c->prm.cfl;
+}
+
+int fasw_batch_cycle(fasw_batch* b, int cycle_index, double* norms) {
+  if (!b) return FASW_ERR_ARG;
+  // the cycle's launch sequence depends on each case's c*, i.e. on whether it is still ramped
+  int phase = 0;
+  for (size_t k = 0; k < b->cases.size(); ++k)
+    if (cycle_index < b->cases[k]->prm.ramp_cycles) phase |= 1;
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : b->graphs)
+    if (g.phase == phase) {
+      exec = g.exec;
+      b->launches += g.kernels;
+    }
+  if (!exec) {
+    long long before = 0;
+    for (fasw_ctx* c : b->cases) before += c->launches;
+    CKR(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+    cudaEventRecord(b->fork, b->st);
+    for (size_t k = 0; k < b->cases.size(); ++k) {
+      fasw_ctx* c = b->cases[k];
+      cudaStreamWaitEvent(c->st, b->fork, 0);
+      enqueue_cycle(c, case_cfl(c, cycle_index));
+      cudaEventRecord(b->joins[k], c->st);
+      cudaStreamWaitEvent(b->st, b->joins[k], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    CKR(cudaStreamEndCapture(b->st, &graph));
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e);
+    long long after = 0;
+    for (fasw_ctx* c : b->cases) after += c->launches;
+    b->graphs.push_back({phase, exec, after - before});
+    b->launches += after - before;
+  }
+  CKR(cudaGraphLaunch(exec, b->st));
+  CKR(cudaStreamSynchronize(b->st));
+  CKR(cudaGetLastError());
+  for (size_t k = 0; k < b->cases.size(); ++k) {
+    if (*b->cases[k]->h_err) return FASW_ERR_DEVICE_TIMEOUT;
+    if (norms) norms[k] = *b->cases[k]->h_norm;
+  }
+  return FASW_OK;
+}
+
+int fasw_batch_solve(fasw_batch* b, double drop, int max_cycles, int* cycles, double* final_drop, int* ncycles) {
+  if (!b || max_cycles < 1) return FASW_ERR_ARG;
+  const size_t nc = b->cases.size();
+  std::vector<double> n0(nc, 0.0), nk(nc, 0.0);
+  std::vector<int> done(nc, 0);  // 1 converged, 2 diverged (its cycles[] is -2)
+  int diverged = 0;
+  for (int k = 0; k < max_cycles; ++k) {
+    int r = fasw_batch_cycle(b, k, nk.data());
+    if (r) return r;
+    if (ncycles) *ncycles = k + 1;
+    size_t ndone = 0;
+    for (size_t q = 0; q < nc; ++q) {
+      if (k == 0) n0[q] = nk[q];
+      if (!done[q]) {
+        if (final_drop) final_drop[q] = nk[q] / n0[q];
+        if (!std::isfinite(nk[q]) || (k > 0 && nk[q] > 1e8 * n0[q])) {
+          done[q] = 2;
+          diverged = 1;
+          if (cycles) cycles[q] = -2;
+        } else if (k > 0 && nk[q] <= drop * n0[q]) {
+          done[q] = 1;
+          if (cycles) cycles[q] = k + 1;
+        }
+      }
+      ndone += done[q] != 0;
+    }
+    if (ndone == nc) return diverged ? FASW_ERR_DIVERGED : FASW_OK;
+  }
+  for (size_t q = 0; q < nc; ++q)
+    if (!done[q] && cycles) cycles[q] = -1;
+  return diverged ? FASW_ERR_DIVERGED : FASW_ERR_NOT_CONVERGED;
+}
+
+// Autotuner: the sweep variants (one CTA per sweep with transfer blocks; strips of 8 or 16
+// rows) trade SM count against per-step latency, and which wins depends on how full the GPU
+// is, so each candidate is timed on whole batch cycles (all cases concurrently, CUDA events)
+// and the fastest is kept.  The cases' states are saved before and restored after.
+// choice (nullable, ncases): the kind used for case k.
+int fasw_batch_autotune(fasw_batch* b, int* choice) {
+  if (!b) return FASW_ERR_ARG;
+  const int kinds[3] = {SWEEP_CTA, SWEEP_STRIPS, SWEEP_STRIPS16};
+  std::vector<double*> saved(b->cases.size(), nullptr);
+  for (size_t k = 0; k < b->cases.size(); ++k) {
+    fasw_ctx* c = b->cases[k];
+    saved[k] = c->d_tmp2;  // 4 x n of the finest level
+    launch_pack(c->lev[c->L()], nullptr, 0, saved[k], c->st);
+    CKR(cudaStreamSynchronize(c->st));
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = SWEEP_CTA;
+  float best_ms = 1e30f;
+  for (int kind : kinds) {
+    for (fasw_ctx* c : b->cases) {
+      c->sweep_kind = kind;
+      drop_graphs(c);
+    }
+    batch_drop_graphs(b);
+    int r = fasw_batch_cycle(b, 0, nullptr);  // capture + warm-up
+    if (r) return r;
+    cudaEventRecord(e0, b->st);
+    for (int rep = 0; rep < 2; ++rep) {
+      r = fasw_batch_cycle(b, 0, nullptr);
+      if (r) return r;
+    }
+    cudaEventRecord(e1, b->st);
+    CKR(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = kind;
+    }
+    for (size_t k = 0; k < b->cases.size(); ++k) {  // restore the states
+      fasw_ctx* c = b->cases[k];
+      launch_pack(c->lev[c->L()], saved[k], 1, nullptr, c->st);
+      launch_bc(c->lev[c->L()], c->ph, c->st);
+      CKR(cudaStreamSynchronize(c->st));
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (size_t k = 0; k < b->cases.size(); ++k) {
+    b->cases[k]->sweep_kind = best;
+    drop_graphs(b->cases[k]);
+    if (choice) choice[k] = best;
+  }
+  batch_drop_graphs(b);
+  return FASW_OK;
+}
+
+long long fasw_batch_launch_count(fasw_batch* b) { return b ? b->launches : -1; }
 
 const char* fasw_strerror(int code) {
   switch (code) {

@@ -45,6 +45,11 @@ struct LevelDev {
   float* dlu32;
   float* yz32;
   double* norm_part;  // per-block partial sums of the residual norm
+  double* tb;         // 80*n transfer blocks of the sweeps (FP64, or FP32 reinterpreted, mixed)
+  double* vfx;        // nfx grid volume flux v_grid . S of the i-faces (zero on a fixed grid)
+  double* vfe;        // nfe grid volume flux of the j-faces
+  double* wvx;        // ni  grid velocity at the j = 0 face midpoints (moving wall)
+  double* wvy;
 };
 
 struct PhysParams {
@@ -52,6 +57,7 @@ struct PhysParams {
   double uinf[4];
   double s_coarse;
   int viscous, turb, sensor;
+  int moving;  // grid in rigid motion: moving-wall ghosts
 };
 
 struct SchemeParams {
@@ -84,6 +90,8 @@ struct ResArgs {
 // ---- launchers (kernels_residual.cu)
 void launch_bc(const LevelDev& L, const PhysParams& ph, cudaStream_t st);
 void launch_cell_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st);
+// ghost fill and cell auxiliaries in one launch
+void launch_bc_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st);
 void launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, cudaStream_t st);
 int residual_blocks(const LevelDev& L);
 void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* out, cudaStream_t st);

@@ -27,13 +27,14 @@ __device__ __forceinline__ double pressure(const double w[4]) {
 }
 
 // Far-field boundary state by 1-D Riemann invariants along the outward unit normal (nx, ny).
-__device__ void farfield(const double wi[4], const double wf[4], double nx, double ny, double out[4]) {
+// vb: normal velocity of the (moving) boundary; in/outflow is decided on the relative velocity.
+__device__ void farfield(const double wi[4], const double wf[4], double nx, double ny, double vb, double out[4]) {
   const double ri = wi[0], ui = wi[1] / ri, vi = wi[2] / ri, pi = pressure(wi);
   const double rf = wf[0], uf = wf[1] / rf, vf = wf[2] / rf, pf = pressure(wf);
   const double ai = sqrt(GAM * pi / ri), af = sqrt(GAM * pf / rf);
   const double vni = ui * nx + vi * ny, vnf = uf * nx + vf * ny;
-  if (fabs(vni) >= ai) {
-    const double* src = vni > 0.0 ? wi : wf;
+  if (fabs(vni - vb) >= ai) {
+    const double* src = vni - vb > 0.0 ? wi : wf;
 #pragma unroll
     for (int k = 0; k < 4; ++k) out[k] = src[k];
     return;
@@ -43,7 +44,7 @@ __device__ void farfield(const double wi[4], const double wf[4], double nx, doub
   const double vnb = 0.5 * (Rp + Rm);
   const double ab = 0.25 * (GAM - 1.0) * (Rp - Rm);
   double s, ut, vt;
-  if (vnb > 0.0) {
+  if (vnb - vb > 0.0) {
     s = pi / pow(ri, GAM);
     ut = ui - vni * nx;
     vt = vi - vni * ny;
@@ -61,78 +62,114 @@ __device__ void farfield(const double wi[4], const double wf[4], double nx, doub
   out[3] = p / (GAM - 1.0) + 0.5 * rho * (u * u + v * v);
 }
 
-__global__ void k_bc(LevelDev L, PhysParams ph) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+// Boundary value of ghost cell (gi, gj) (two layers on every side; corners excluded):
+// j < 0: wake-cut copy of the mirror cell or wall reflection (slip / no-slip, moving wall);
+// j >= nj, i < 0, i >= ni: Riemann far-field state (section 2, G9).
+__device__ void ghost_state(const LevelDev& L, const PhysParams& ph, int gi, int gj, double g[4]) {
   const int ni = L.ni, nj = L.nj;
-  if (t < ni) {                      // j = 0: wall or wake cut
-    const int i = t;
+  if (gj < 0) {
+    const int i = gi, k = -1 - gj;  // source row 0 or 1
     if (on_cut(L, i)) {
-      const int m = ni - 1 - i;
-      double w[4];
-      load4(L, gidx(L, m, 0), w);
-      store4(L, gidx(L, i, -1), w);
-      load4(L, gidx(L, m, 1), w);
-      store4(L, gidx(L, i, -2), w);
-    } else {
-      const double sx = L.seta[i], sy = L.seta[L.nfe + i];
-      const double len = sqrt(sx * sx + sy * sy);
-      const double nx = sx / len, ny = sy / len;
-      for (int k = 0; k < 2; ++k) {
-        double w[4], g[4];
-        load4(L, gidx(L, i, k), w);
-        g[0] = w[0];
-        g[3] = w[3];
-        if (ph.viscous) {
-          g[1] = -w[1];
-          g[2] = -w[2];
-        } else {
-          const double mn = w[1] * nx + w[2] * ny;
-          g[1] = w[1] - 2.0 * mn * nx;
-          g[2] = w[2] - 2.0 * mn * ny;
-        }
-        store4(L, gidx(L, i, -1 - k), g);
-      }
+      load4(L, gidx(L, ni - 1 - i, k), g);
+      return;
     }
-  } else if (t < 2 * ni) {           // j = nj: far field, outward +S_eta
-    const int i = t - ni;
-    const int f = nj * ni + i;
+    const double sx = L.seta[i], sy = L.seta[L.nfe + i];
+    const double len = sqrt(sx * sx + sy * sy);
+    const double nx = sx / len, ny = sy / len;
+    double w[4];
+    load4(L, gidx(L, i, k), w);
+    if (!ph.moving) {
+      g[0] = w[0];
+      g[3] = w[3];
+      if (ph.viscous) {
+        g[1] = -w[1];
+        g[2] = -w[2];
+      } else {
+        const double mn = w[1] * nx + w[2] * ny;
+        g[1] = w[1] - 2.0 * mn * nx;
+        g[2] = w[2] - 2.0 * mn * ny;
+      }
+    } else {  // moving wall: velocity mirrored about the wall velocity, same rho and p
+      const double rho = w[0], u = w[1] / rho, v = w[2] / rho, p = pressure(w);
+      const double wx = L.wvx[i], wy = L.wvy[i];
+      double ug, vg;
+      if (ph.viscous) {
+        ug = 2.0 * wx - u;
+        vg = 2.0 * wy - v;
+      } else {
+        const double rn = (u - wx) * nx + (v - wy) * ny;
+        ug = u - 2.0 * rn * nx;
+        vg = v - 2.0 * rn * ny;
+      }
+      g[0] = rho;
+      g[1] = rho * ug;
+      g[2] = rho * vg;
+      g[3] = p / (GAM - 1.0) + 0.5 * rho * (ug * ug + vg * vg);
+    }
+    return;
+  }
+  double w[4];
+  if (gj >= nj) {  // outward +S_eta
+    const int i = gi, f = nj * ni + i;
     const double sx = L.seta[f], sy = L.seta[L.nfe + f];
     const double len = sqrt(sx * sx + sy * sy);
-    double w[4], b[4];
     load4(L, gidx(L, i, nj - 1), w);
-    farfield(w, ph.uinf, sx / len, sy / len, b);
-    store4(L, gidx(L, i, nj), b);
-    store4(L, gidx(L, i, nj + 1), b);
-  } else if (t < 2 * ni + nj) {      // i = 0: far field, outward -S_xi
-    const int j = t - 2 * ni;
-    const int f = j * (ni + 1);
+    farfield(w, ph.uinf, sx / len, sy / len, L.vfe[f] / len, g);
+  } else if (gi < 0) {  // outward -S_xi
+    const int j = gj, f = j * (ni + 1);
     const double sx = L.sxi[f], sy = L.sxi[L.nfx + f];
     const double len = sqrt(sx * sx + sy * sy);
-    double w[4], b[4];
     load4(L, gidx(L, 0, j), w);
-    farfield(w, ph.uinf, -sx / len, -sy / len, b);
-    store4(L, gidx(L, -1, j), b);
-    store4(L, gidx(L, -2, j), b);
-  } else if (t < 2 * ni + 2 * nj) {  // i = ni: far field, outward +S_xi
-    const int j = t - 2 * ni - nj;
-    const int f = j * (ni + 1) + ni;
+    farfield(w, ph.uinf, -sx / len, -sy / len, -L.vfx[f] / len, g);
+  } else {  // gi >= ni, outward +S_xi
+    const int j = gj, f = j * (ni + 1) + ni;
     const double sx = L.sxi[f], sy = L.sxi[L.nfx + f];
     const double len = sqrt(sx * sx + sy * sy);
-    double w[4], b[4];
     load4(L, gidx(L, ni - 1, j), w);
-    farfield(w, ph.uinf, sx / len, sy / len, b);
-    store4(L, gidx(L, ni, j), b);
-    store4(L, gidx(L, ni + 1, j), b);
+    farfield(w, ph.uinf, sx / len, sy / len, L.vfx[f] / len, g);
   }
 }
 
+// Ghost fill alone: one thread per ghost cell of the two layers (corners untouched).
+__global__ void k_bc(LevelDev L, PhysParams ph) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ni = L.ni, nj = L.nj;
+  int gi, gj;
+  if (t < 2 * ni) {  // rows j = -1, -2
+    gi = t % ni;
+    gj = -1 - t / ni;
+  } else if (t < 4 * ni) {  // rows j = nj, nj + 1
+    gi = (t - 2 * ni) % ni;
+    gj = nj + (t - 2 * ni) / ni;
+  } else if (t < 4 * ni + 2 * nj) {  // columns i = -1, -2
+    gj = (t - 4 * ni) % nj;
+    gi = -1 - (t - 4 * ni) / nj;
+  } else if (t < 4 * ni + 4 * nj) {  // columns i = ni, ni + 1
+    gj = (t - 4 * ni - 2 * nj) % nj;
+    gi = ni + (t - 4 * ni - 2 * nj) / nj;
+  } else {
+    return;
+  }
+  double g[4];
+  ghost_state(L, ph, gi, gj, g);
+  store4(L, gidx(L, gi, gj), g);
+}
+
 // Pressure and sensor quantity on the ghosted domain; Martinelli radii and dt* on the interior.
-__global__ void k_cell_aux(LevelDev L, PhysParams ph, double cfl, int want_dts) {
+// With fill_ghosts, ghost threads first compute and store their boundary value (it depends
+// on interior cells only), so ghost fill and auxiliaries take one launch.
+__global__ void k_cell_aux(LevelDev L, PhysParams ph, double cfl, int want_dts, int fill_ghosts) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= L.Gn) return;
   const int gi = t % L.P - 2, gj = t / L.P - 2;
   double w[4];
-  load4(L, t, w);
+  const bool gx = gi < 0 || gi >= L.ni, gy = gj < 0 || gj >= L.nj;
+  if (fill_ghosts && (gx != gy)) {  // ghost, not a corner
+    ghost_state(L, ph, gi, gj, w);
+    store4(L, t, w);
+  } else {
+    load4(L, t, w);
+  }
   const double p = pressure(w);
   L.p[t] = p;
   L.q[t] = ph.sensor ? p / pow(w[0], GAM) : p;
@@ -145,8 +182,10 @@ __global__ void k_cell_aux(LevelDev L, PhysParams ph, double cfl, int want_dts) 
   const double sy = 0.5 * (L.sxi[L.nfx + fw] + L.sxi[L.nfx + fw + 1]);
   const double ex = 0.5 * (L.seta[fs] + L.seta[fs + ni]);
   const double ey = 0.5 * (L.seta[L.nfe + fs] + L.seta[L.nfe + fs + ni]);
-  const double rxi = fabs(u * sx + v * sy) + a * sqrt(sx * sx + sy * sy);
-  const double reta = fabs(u * ex + v * ey) + a * sqrt(ex * ex + ey * ey);
+  const double vx = 0.5 * (L.vfx[fw] + L.vfx[fw + 1]);
+  const double ve = 0.5 * (L.vfe[fs] + L.vfe[fs + ni]);
+  const double rxi = fabs(u * sx + v * sy - vx) + a * sqrt(sx * sx + sy * sy);
+  const double reta = fabs(u * ex + v * ey - ve) + a * sqrt(ex * ex + ey * ey);
   const int c = j * ni + i;
   L.rt[c] = rxi * (1.0 + pow(reta / rxi, 2.0 / 3.0));
   L.rt[L.n + c] = reta * (1.0 + pow(rxi / reta, 2.0 / 3.0));
@@ -172,7 +211,8 @@ __device__ __forceinline__ double sensor_val(double qm, double q0, double qp) {
 
 // JST flux through a face with area vector (sx, sy) from L to R; stencil LL, L, R, RR
 // given as ghosted indices.  hc: central part; hd: dissipation d (section 2).
-__device__ void jst_face(const LevelDev& L, int gLL, int gL, int gR, int gRR, double sx, double sy,
+// On a moving face (grid volume flux vf) the convective flux is F . S - u vf.
+__device__ void jst_face(const LevelDev& L, int gLL, int gL, int gR, int gRR, double sx, double sy, double vf,
                          double rtL, double rtR, double s_coarse, double hc[4], double hd[4]) {
   double uL[4], uR[4];
   load4(L, gL, uL);
@@ -181,10 +221,10 @@ __device__ void jst_face(const LevelDev& L, int gLL, int gL, int gR, int gRR, do
   {
     const double qnL = (uL[1] * sx + uL[2] * sy) / uL[0];
     const double qnR = (uR[1] * sx + uR[2] * sy) / uR[0];
-    hc[0] = 0.5 * (uL[0] * qnL + uR[0] * qnR);
-    hc[1] = 0.5 * ((uL[1] * qnL + pL * sx) + (uR[1] * qnR + pR * sx));
-    hc[2] = 0.5 * ((uL[2] * qnL + pL * sy) + (uR[2] * qnR + pR * sy));
-    hc[3] = 0.5 * ((uL[3] + pL) * qnL + (uR[3] + pR) * qnR);
+    hc[0] = 0.5 * ((uL[0] * qnL - uL[0] * vf) + (uR[0] * qnR - uR[0] * vf));
+    hc[1] = 0.5 * (((uL[1] * qnL + pL * sx) - uL[1] * vf) + ((uR[1] * qnR + pR * sx) - uR[1] * vf));
+    hc[2] = 0.5 * (((uL[2] * qnL + pL * sy) - uL[2] * vf) + ((uR[2] * qnR + pR * sy) - uR[2] * vf));
+    hc[3] = 0.5 * (((uL[3] + pL) * qnL - uL[3] * vf) + ((uR[3] + pR) * qnR - uR[3] * vf));
   }
   const double r = fmax(rtL, rtR);
   double eps2, eps4;
@@ -285,7 +325,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(LevelDev L, PhysParams
       const int f = j * (ni + 1) + i;
       double hc[4], hd[4];
       jst_face(L, gidx(L, i - 2, j), gidx(L, i - 1, j), gidx(L, i, j), gidx(L, i + 1, j), L.sxi[f],
-               L.sxi[L.nfx + f], rt_cell(L, i - 1, j, 0), rt_cell(L, i, j, 0), ph.s_coarse, hc, hd);
+               L.sxi[L.nfx + f], L.vfx[f], rt_cell(L, i - 1, j, 0), rt_cell(L, i, j, 0), ph.s_coarse, hc, hd);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         xc[k][ty][tx] = hc[k];
@@ -300,7 +340,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(LevelDev L, PhysParams
       const int f = j * ni + i;
       const double sx = L.seta[f], sy = L.seta[L.nfe + f];
       double hc[4], hd[4];
-      jst_face(L, gidx(L, i, j - 2), gidx(L, i, j - 1), gidx(L, i, j), gidx(L, i, j + 1), sx, sy,
+      jst_face(L, gidx(L, i, j - 2), gidx(L, i, j - 1), gidx(L, i, j), gidx(L, i, j + 1), sx, sy, L.vfe[f],
                rt_cell(L, i, j - 1, 1), rt_cell(L, i, j, 1), ph.s_coarse, hc, hd);
       if (ph.viscous) {
         double hv[4];
@@ -464,12 +504,16 @@ __global__ void k_bl_lines(LevelDev L, PhysParams ph) {
 }  // namespace
 
 void launch_bc(const LevelDev& L, const PhysParams& ph, cudaStream_t st) {
-  const int nt = 2 * L.ni + 2 * L.nj;
+  const int nt = 4 * L.ni + 4 * L.nj;
   k_bc<<<(nt + 127) / 128, 128, 0, st>>>(L, ph);
 }
 
 void launch_cell_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st) {
-  k_cell_aux<<<(L.Gn + 255) / 256, 256, 0, st>>>(L, ph, cfl, want_dts);
+  k_cell_aux<<<(L.Gn + 255) / 256, 256, 0, st>>>(L, ph, cfl, want_dts, 0);
+}
+
+void launch_bc_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st) {
+  k_cell_aux<<<(L.Gn + 255) / 256, 256, 0, st>>>(L, ph, cfl, want_dts, 1);
 }
 
 int residual_blocks(const LevelDev& L) { return ((L.ni + TX - 1) / TX) * ((L.nj + TY - 1) / TY); }

@@ -30,8 +30,9 @@ __device__ __forceinline__ T cutabs(T lam, T a, T d) {
 }
 
 // Writes |S| A+ and |S| A- (row-major 4x4) for state w and area vector (sx, sy).
+// vf: grid volume flux of the face; the eigenvalues are those of the relative normal velocity.
 template <typename T>
-__device__ void split_blocks(const T w[4], T sx, T sy, T d, T Ap[16], T Am[16]) {
+__device__ void split_blocks(const T w[4], T sx, T sy, T vf, T d, T Ap[16], T Am[16]) {
   const T g1 = T(GAM - 1.0);
   const T len = sqrt(sx * sx + sy * sy);
   const T nx = sx / len, ny = sy / len;
@@ -45,7 +46,8 @@ __device__ void split_blocks(const T w[4], T sx, T sy, T d, T Ap[16], T Am[16]) 
   const T r1[4] = {T(0), nx, ny, vn};
   const T dp[4] = {g1 * T(0.5) * q2, -g1 * u, -g1 * v, g1};
   const T dv[4] = {-vn, nx, ny, T(0)};
-  const T lam1 = vn, lam3 = vn + a, lam4 = vn - a;
+  const T vr = vn - vf / len;
+  const T lam1 = vr, lam3 = vr + a, lam4 = vr - a;
   const T m1 = cutabs(lam1, a, d), m3 = cutabs(lam3, a, d), m4 = cutabs(lam4, a, d);
   const T inva = T(1) / a, inva2 = inva * inva;
 #pragma unroll
@@ -105,7 +107,7 @@ __global__ void k_face_blocks(LevelDev L, PhysParams ph, T* blk, T d) {
   const int ni = L.ni;
   if (f >= L.nfx + L.nfe) return;
   int gL, gR;
-  double sx, sy;
+  double sx, sy, vf;
   T *Ap, *Am;
   int stride;
   if (f < L.nfx) {
@@ -114,6 +116,7 @@ __global__ void k_face_blocks(LevelDev L, PhysParams ph, T* blk, T d) {
     gR = gidx(L, i, j);
     sx = L.sxi[f];
     sy = L.sxi[L.nfx + f];
+    vf = L.vfx[f];
     Ap = blk + f;
     Am = blk + 16 * L.nfx + f;
     stride = L.nfx;
@@ -124,6 +127,7 @@ __global__ void k_face_blocks(LevelDev L, PhysParams ph, T* blk, T d) {
     gR = gidx(L, i, j);
     sx = L.seta[e];
     sy = L.seta[L.nfe + e];
+    vf = L.vfe[e];
     Ap = blk + 32 * L.nfx + e;
     Am = blk + 32 * L.nfx + 16 * L.nfe + e;
     stride = L.nfe;
@@ -136,7 +140,7 @@ __global__ void k_face_blocks(LevelDev L, PhysParams ph, T* blk, T d) {
     w[k] = T(wd[k]);
   }
   T P[16], M[16];
-  split_blocks<T>(w, T(sx), T(sy), d, P, M);
+  split_blocks<T>(w, T(sx), T(sy), T(vf), d, P, M);
   if (ph.viscous && f >= L.nfx) {
     const int e = f - L.nfx;
     const T V = T(visc_radius(L, ph, e % ni, e / ni, wd[0]));
@@ -169,6 +173,11 @@ __global__ void k_diag_blocks(LevelDev L, const T* blk, T* dlu, int aw, double e
     sigma = L.a_t;
   }
   L.coef[c] = coef;
+  {  // u^(0) of the smoothing step (the state the blocks are frozen at)
+    const int g = (j + 2) * L.P + (i + 2);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) L.u0[k * L.n + c] = L.u[k * L.Gn + g];
+  }
   const int fw = j * (ni + 1) + i, fe = fw + 1, fs = j * ni + i, fn = fs + ni;
   const T* Axp = blk;
   const T* Axm = blk + 16 * L.nfx;

@@ -12,32 +12,68 @@ __device__ __forceinline__ bool on_cut(const LevelDev& L, int i) { return L.nw >
 
 // Finest-level metrics from vertices: i-face S = (dy, -dx) along (i,j)->(i,j+1), j-face
 // S = (-dy, dx) along (i,j)->(i+1,j), volume = half the cross product of the diagonals.
-__global__ void k_metrics_fine(LevelDev L, const double* x, const double* y) {
+// The vertices are the reference vertices rotated by (cs, sn) = (cos, sin) of the pitch angle
+// about (xc, yc); the grid velocity of the rigid rotation, v = phidot (-(y - yc), x - xc), is
+// linear, so each face's grid volume flux is its midpoint value dotted with S.
+struct Motion { double cs, sn, phidot, xc, yc; int rotate; };
+
+__device__ __forceinline__ void vert(const double* x, const double* y, int k, const Motion& m, double& px, double& py) {
+  if (!m.rotate) {  // fixed grid: the vertices as given
+    px = x[k];
+    py = y[k];
+    return;
+  }
+  const double dx = x[k] - m.xc, dy = y[k] - m.yc;
+  px = m.xc + m.cs * dx - m.sn * dy;
+  py = m.yc + m.sn * dx + m.cs * dy;
+}
+
+__global__ void k_metrics_fine(LevelDev L, const double* x, const double* y, Motion mo) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ni = L.ni, nj = L.nj, V = ni + 1;
+  const int ni = L.ni, V = ni + 1;
+  auto vgx = [&](double, double py) { return -mo.phidot * (py - mo.yc); };
+  auto vgy = [&](double px, double) { return mo.phidot * (px - mo.xc); };
   if (t < L.nfx) {
     const int i = t % (ni + 1), j = t / (ni + 1);
-    const double dx = x[(j + 1) * V + i] - x[j * V + i], dy = y[(j + 1) * V + i] - y[j * V + i];
+    double xa, ya, xb, yb;
+    vert(x, y, j * V + i, mo, xa, ya);
+    vert(x, y, (j + 1) * V + i, mo, xb, yb);
+    const double dx = xb - xa, dy = yb - ya;
     L.sxi[t] = dy;
     L.sxi[L.nfx + t] = -dx;
+    const double mx = 0.5 * (xa + xb), my = 0.5 * (ya + yb);
+    L.vfx[t] = vgx(mx, my) * dy + vgy(mx, my) * (-dx);
   }
   if (t < L.nfe) {
     const int i = t % ni, j = t / ni;
-    const double dx = x[j * V + i + 1] - x[j * V + i], dy = y[j * V + i + 1] - y[j * V + i];
+    double xa, ya, xb, yb;
+    vert(x, y, j * V + i, mo, xa, ya);
+    vert(x, y, j * V + i + 1, mo, xb, yb);
+    const double dx = xb - xa, dy = yb - ya;
     L.seta[t] = -dy;
     L.seta[L.nfe + t] = dx;
+    const double mx = 0.5 * (xa + xb), my = 0.5 * (ya + yb);
+    L.vfe[t] = vgx(mx, my) * (-dy) + vgy(mx, my) * dx;
+    if (j == 0) {
+      L.wvx[i] = vgx(mx, my);
+      L.wvy[i] = vgy(mx, my);
+    }
   }
   if (t < L.n) {
     const int i = t % ni, j = t / ni;
-    const double x00 = x[j * V + i], x10 = x[j * V + i + 1], x11 = x[(j + 1) * V + i + 1], x01 = x[(j + 1) * V + i];
-    const double y00 = y[j * V + i], y10 = y[j * V + i + 1], y11 = y[(j + 1) * V + i + 1], y01 = y[(j + 1) * V + i];
+    double x00, y00, x10, y10, x11, y11, x01, y01, xw0, yw0, xw1, yw1;
+    vert(x, y, j * V + i, mo, x00, y00);
+    vert(x, y, j * V + i + 1, mo, x10, y10);
+    vert(x, y, (j + 1) * V + i + 1, mo, x11, y11);
+    vert(x, y, (j + 1) * V + i, mo, x01, y01);
+    vert(x, y, i, mo, xw0, yw0);
+    vert(x, y, i + 1, mo, xw1, yw1);
     const double d1x = x11 - x00, d1y = y11 - y00, d2x = x01 - x10, d2y = y01 - y10;
     L.vol[t] = 0.5 * (d1x * d2y - d1y * d2x);
     const double cx = 0.25 * (x00 + x10 + x11 + x01), cy = 0.25 * (y00 + y10 + y11 + y01);
-    const double mx = 0.5 * (x[i] + x[i + 1]), my = 0.5 * (y[i] + y[i + 1]);
+    const double mx = 0.5 * (xw0 + xw1), my = 0.5 * (yw0 + yw1);
     L.wdist[t] = sqrt((cx - mx) * (cx - mx) + (cy - my) * (cy - my));
   }
-  (void)nj;
 }
 
 // Coarse metrics by agglomerating 2x2 fine cells: face vectors add, volumes add.
@@ -49,12 +85,18 @@ __global__ void k_agglomerate(LevelDev F, LevelDev C) {
     const int fa = (2 * j) * (F.ni + 1) + 2 * i, fb = (2 * j + 1) * (F.ni + 1) + 2 * i;
     C.sxi[t] = F.sxi[fa] + F.sxi[fb];
     C.sxi[C.nfx + t] = F.sxi[F.nfx + fa] + F.sxi[F.nfx + fb];
+    C.vfx[t] = F.vfx[fa] + F.vfx[fb];
   }
   if (t < C.nfe) {
     const int i = t % ni, j = t / ni;
     const int fa = (2 * j) * F.ni + 2 * i, fb = fa + 1;
     C.seta[t] = F.seta[fa] + F.seta[fb];
     C.seta[C.nfe + t] = F.seta[F.nfe + fa] + F.seta[F.nfe + fb];
+    C.vfe[t] = F.vfe[fa] + F.vfe[fb];
+    if (j == 0) {
+      C.wvx[i] = 0.5 * (F.wvx[2 * i] + F.wvx[2 * i + 1]);
+      C.wvy[i] = 0.5 * (F.wvy[2 * i] + F.wvy[2 * i + 1]);
+    }
   }
   if (t < C.n) {
     const int i = t % ni, j = t / ni;
@@ -175,9 +217,21 @@ __global__ void k_blocks_transpose(const double* a, double* b, int nf) {
 
 }  // namespace
 
-void launch_metrics_fine(const LevelDev& L, const double* x, const double* y, cudaStream_t st) {
+void launch_metrics_fine(const LevelDev& L, const double* x, const double* y, cudaStream_t st, int rotate, double phi,
+                         double phidot, double xc, double yc) {
   const int m = L.nfx > L.nfe ? L.nfx : L.nfe;
-  k_metrics_fine<<<(m + 127) / 128, 128, 0, st>>>(L, x, y);
+  Motion mo{cos(phi), sin(phi), phidot, xc, yc, rotate};
+  k_metrics_fine<<<(m + 127) / 128, 128, 0, st>>>(L, x, y, mo);
+}
+
+// Dual-time source of the finest level: src = c1 u^n + c2 u^(n-1)
+__global__ void k_time_source(double* src, const double* un, const double* unm1, double c1, double c2, int m) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) src[t] = c1 * un[t] + (unm1 ? c2 * unm1[t] : 0.0);
+}
+
+void launch_time_source(double* src, const double* un, const double* unm1, double c1, double c2, int m, cudaStream_t st) {
+  k_time_source<<<(m + 255) / 256, 256, 0, st>>>(src, un, unm1, c1, c2, m);
 }
 
 void launch_agglomerate(const LevelDev& F, const LevelDev& C, cudaStream_t st) {

@@ -81,7 +81,18 @@ def library():
             "fasw_launch_count": (ll, [p]),
             "fasw_profile": (i, [p, i]),
             "fasw_use_graphs": (i, [p, i]),
+            "fasw_set_sweep": (i, [p, i]),
+            "fasw_set_motion": (i, [p, d, d, d, d]),
+            "fasw_dual_time_step": (i, [p, d, i, d, i, dp, C.POINTER(i)]),
             "fasw_kernel_time": (i, [p, i, C.POINTER(ll), C.POINTER(d)]),
+            "fasw_batch_create": (i, [i, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_void_p), i, C.POINTER(Params), p, C.POINTER(p)]),
+            "fasw_batch_destroy": (None, [p]),
+            "fasw_batch_case": (p, [p, i]),
+            "fasw_batch_cycle": (i, [p, i, dp]),
+            "fasw_batch_solve": (i, [p, d, i, dp, dp, C.POINTER(i)]),
+            "fasw_batch_autotune": (i, [p, dp]),
+            "fasw_batch_launch_count": (ll, [p]),
             "fasw_strerror": (C.c_char_p, [i]),
             "fasw_last_cuda_error": (C.c_char_p, []),
         }
@@ -241,6 +252,22 @@ class Solver:
     def launch_count(self) -> int:
         return int(self.lib.fasw_launch_count(self.h))
 
+    def set_motion(self, phi, phidot, xc=0.25, yc=0.0):
+        _check(self.lib.fasw_set_motion(self.h, phi, phidot, xc, yc), "fasw_set_motion")
+
+    def dual_time_step(self, dt, drop, max_cycles, bdf_order=2):
+        hist = np.zeros(max_cycles)
+        nc = C.c_int(0)
+        code = self.lib.fasw_dual_time_step(self.h, dt, bdf_order, drop, max_cycles, hist.ctypes.data, C.byref(nc))
+        if code not in (0, -4, -6):
+            _check(code, "fasw_dual_time_step")
+        return code, nc.value, hist[:nc.value]
+
+    def set_sweep(self, kind):
+        """0 auto, 1 reference (one thread per cell), 2 one CTA, 3 strips of 8 rows, 4 strips of 16."""
+        kinds = {"auto": 0, "reference": 1, "cta": 2, "strips": 3, "strips16": 4}
+        _check(self.lib.fasw_set_sweep(self.h, kinds.get(kind, kind)), "fasw_set_sweep")
+
     def use_graphs(self, enable: bool):
         _check(self.lib.fasw_use_graphs(self.h, 1 if enable else 0), "fasw_use_graphs")
 
@@ -253,3 +280,64 @@ class Solver:
         ms = C.c_double()
         _check(self.lib.fasw_kernel_time(self.h, kernel, C.byref(n), C.byref(ms)), "fasw_kernel_time")
         return n.value, ms.value
+
+
+class Batch:
+    """Many independent cases advanced together (one captured CUDA graph per cycle)."""
+
+    def __init__(self, grids, params_list, stream=None):
+        self.lib = library()
+        n = len(grids)
+        self.grids = grids
+        self._coords = [g.coords() for g in grids]
+        ni = (C.c_int * n)(*[g.ni for g in grids])
+        nj = (C.c_int * n)(*[g.nj for g in grids])
+        nw = (C.c_int * n)(*[g.n_wake for g in grids])
+        xs = (C.c_void_p * n)(*[c[0].ctypes.data for c in self._coords])
+        ys = (C.c_void_p * n)(*[c[1].ctypes.data for c in self._coords])
+        self.params = list(params_list)
+        ps = (Params * n)(*params_list)
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if stream is not None else None
+        _check(self.lib.fasw_batch_create(n, ni, nj, nw, xs, ys, 0, ps, st, C.byref(h)), "fasw_batch_create")
+        self.h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fasw_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def cycle(self, k):
+        norms = np.zeros(self.n)
+        _check(self.lib.fasw_batch_cycle(self.h, k, norms.ctypes.data), "fasw_batch_cycle")
+        return norms
+
+    def solve(self, drop, max_cycles):
+        cyc = np.zeros(self.n, dtype=np.float64)
+        fd = np.zeros(self.n)
+        ncy = C.c_int(0)
+        ci = (C.c_int * self.n)()
+        code = self.lib.fasw_batch_solve(self.h, drop, max_cycles, C.cast(ci, C.c_void_p), fd.ctypes.data,
+                                         C.byref(ncy))
+        if code not in (0, -4, -6):
+            _check(code, "fasw_batch_solve")
+        return code, np.array(list(ci)), fd, ncy.value
+
+    def autotune(self):
+        ch = (C.c_int * self.n)()
+        _check(self.lib.fasw_batch_autotune(self.h, C.cast(ch, C.c_void_p)), "fasw_batch_autotune")
+        return list(ch)
+
+    def get_state(self, k):
+        g = self.grids[k]
+        out = np.zeros((4, g.nj, g.ni))
+        ctx = self.lib.fasw_batch_case(self.h, k)
+        _check(self.lib.fasw_get_state(ctx, self.params[k].nlevels - 1, out.ctypes.data, 0), "fasw_get_state")
+        return out
+
+    def launch_count(self):
+        return int(self.lib.fasw_batch_launch_count(self.h))

@@ -158,3 +158,61 @@ def test_solver_reports_divergence_not_garbage():
     assert code in (0, -4, -6)
     if code == -4:
         assert not np.isfinite(hist[-1]) or hist[-1] > 1e8 * hist[0]
+
+
+def test_graph_replayed_cycles_equal_eager_cycles():
+    """Cycles captured into CUDA graphs (non-default stream) give the same history as eager launches."""
+    import torch
+    import paper_1710_04875_gb300 as P
+    from tests.helpers import pair_params
+    g = make_cgrid(64, 16)
+    _, p = pair_params(nlevels=2, mach=0.8, alpha_deg=1.25)
+    st = torch.cuda.Stream()
+    a = P.Solver(g, p, stream=st.cuda_stream)
+    b = P.Solver(g, p, stream=st.cuda_stream)
+    b.use_graphs(False)
+    ha = [a.fas_cycle(k) for k in range(6)]
+    hb = [b.fas_cycle(k) for k in range(6)]
+    assert ha == hb
+    assert np.array_equal(a.get_state(), b.get_state())
+
+
+@pytest.mark.parametrize("kind", ["reference", "cta", "strips", "strips16"])
+@pytest.mark.parametrize("scheme", ["AW3", "ARK3J"])
+@pytest.mark.parametrize("ni,nj,nw", [(128, 32, 16), (72, 20, 8), (40, 12, 4), (256, 64, 32), (16, 6, 2)])
+def test_sweep_kinds_match_the_oracle(kind, scheme, ni, nj, nw):
+    """Every sweep kernel (one thread per cell, one CTA with transfer blocks, pipelined strips
+    with a partial last strip) applies the same (D+L) D^-1 (D+U) inverse."""
+    g = make_cgrid(ni, nj, n_wake=nw, jitter=0.03, seed=ni + nj, wall_spacing=2e-3 if nj < 64 else 1e-4)
+    o, s = make_pair(g, scheme=scheme, nlevels=1, d_cut=0.5)
+    s.set_sweep(kind)
+    u = perturbed_state(0.8, 1.25, nj, ni, amp=0.05, seed=6)
+    o.set_state(u); s.set_state(u)
+    r = np.random.default_rng(8).standard_normal((4, nj, ni))
+    zo, _ = o.precond_apply(r, 50.0)
+    zg = s.precond_apply(r, 50.0)
+    assert rel_err(zg, zo) < 1e-11
+
+
+def test_mixed_sweep_is_the_fp32_preconditioner():
+    """Mixed precision: the same operator applied in FP32 (loose tolerance)."""
+    g = make_cgrid(128, 32, n_wake=16, jitter=0.03, seed=1)
+    o, s = make_pair(g, nlevels=1, d_cut=0.5, precision="mixed")
+    u = perturbed_state(0.8, 1.25, 32, 128, amp=0.05, seed=6)
+    o.set_state(u); s.set_state(u)
+    r = np.random.default_rng(8).standard_normal((4, 32, 128))
+    zo, _ = o.precond_apply(r, 50.0)
+    zg = s.precond_apply(r, 50.0)
+    assert rel_err(zg, zo) < 1e-3
+
+
+@pytest.mark.parametrize("kind", ["cta", "strips", "strips16"])
+def test_cycle_history_with_fast_sweeps(kind):
+    """Full FAS cycles with the transfer-block sweeps keep the 1e-8 history parity."""
+    g = make_cgrid(128, 32)
+    o, s = make_pair(g, nlevels=3, mach=0.8, alpha_deg=1.25)
+    s.set_sweep(kind)
+    ho = np.array([o.fas_cycle(k) for k in range(25)])
+    hg = np.array([s.fas_cycle(k) for k in range(25)])
+    mask = ho > 1e-12 * ho[0]
+    assert np.all(np.abs(hg - ho)[mask] <= 1e-8 * ho[mask])
