@@ -48,6 +48,7 @@ extern "C" {
 #define FASW_ERR_DIVERGED (-4)       /* residual norm became NaN/Inf or grew by > 1e8 */
 #define FASW_ERR_DEVICE_TIMEOUT (-5) /* a bounded device-side wait ran out */
 #define FASW_ERR_NOT_CONVERGED (-6)  /* soft: max_cycles reached; history is filled */
+#define FASW_ERR_TOO_LARGE (-7)      /* grid needs more than the fixed no-allocation scratch */
 
 /* Smoother schemes (Table "RK smoothers"; AW uses the same alpha/beta as ARK). */
 enum fasw_scheme {
@@ -192,6 +193,30 @@ int fasw_profile(fasw_ctx* ctx, int enable);
 
 /* Launch count and summed device milliseconds of one kernel class since fasw_profile. */
 int fasw_kernel_time(fasw_ctx* ctx, int kernel, long long* count, double* total_ms);
+
+/* Residual without any device allocation.  No counterpart in the paper: this is a service
+ * for callers that cannot call cudaMalloc where they need a residual -- an application that
+ * owns all device memory and gives this library fixed buffers only, or a latency-critical
+ * loop that must not pay for cudaMalloc/cudaFree.
+ *
+ * Computes F = F^c + F^v of the finest level (same definition and layout as fasw_residual,
+ * steady, zero forcing, laminar: p->turb must be 0) for an ni x nj C-grid whose vertices
+ * x, y ((ni+1)*(nj+1), index j*(ni+1)+i) and state u (4 x nj x ni) are DEVICE pointers; the
+ * result goes to the DEVICE buffer F (4 x nj x ni).  Work is enqueued on `stream`; the call
+ * does not synchronize.
+ *
+ * Scratch: a fixed array of FASW_NOALLOC_SCRATCH_DOUBLES doubles (4 MiB) compiled into the
+ * library, held by every GPU that loads the library until the process exits; about
+ * 6 (ni+4)(nj+4) + 20 ni nj doubles are needed (a 256 x 64 grid fits, 512 x 128 does not);
+ * larger grids return FASW_ERR_TOO_LARGE.  The first call on each device looks up the array's
+ * device address with that device current; make that first call before any stream capture.
+ * All calls share the one array and it keeps the previous call's contents (the parts that
+ * must start at zero are cleared each call): calls that overlap on the GPU -- on different
+ * streams, or from different host threads -- race and must be serialized by the caller.
+ * Errors: FASW_ERR_ARG, FASW_ERR_TOO_LARGE, FASW_ERR_CUDA. */
+#define FASW_NOALLOC_SCRATCH_DOUBLES 524288
+int fasw_residual_noalloc(int ni, int nj, int n_wake, const double* x, const double* y, const double* u,
+                          double* F, const fasw_params* p, void* stream);
 
 /* ---- Batched cases (many independent airfoil cases of uneven size).  Each case is a context
  * on its own stream (created and owned by the batch); fasw_batch_cycle runs one FAS cycle of

@@ -996,6 +996,7 @@ const char* fasw_strerror(int code) {
     case FASW_ERR_DIVERGED: return "residual diverged";
     case FASW_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
     case FASW_ERR_NOT_CONVERGED: return "not converged within max_cycles";
+    case FASW_ERR_TOO_LARGE: return "grid too large for the fixed no-allocation scratch";
     default: return "unknown error";
   }
 }

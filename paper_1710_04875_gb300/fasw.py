@@ -14,7 +14,7 @@ from . import _build
 
 FASW_OK = 0
 ERRORS = {-1: "FASW_ERR_ARG", -2: "FASW_ERR_OOM", -3: "FASW_ERR_CUDA", -4: "FASW_ERR_DIVERGED",
-          -5: "FASW_ERR_DEVICE_TIMEOUT", -6: "FASW_ERR_NOT_CONVERGED"}
+          -5: "FASW_ERR_DEVICE_TIMEOUT", -6: "FASW_ERR_NOT_CONVERGED", -7: "FASW_ERR_TOO_LARGE"}
 FASW_AW3, FASW_AW5J, FASW_AW51, FASW_AW52, FASW_ARK3J, FASW_ARK5J, FASW_ARK51, FASW_ARK52 = range(8)
 FASW_FP64, FASW_MIXED = 0, 1
 KERNEL_CLASSES = ["bc", "cell_aux", "residual", "face_blocks", "diag_blocks", "sgs", "copy", "restrict",
@@ -85,6 +85,7 @@ def library():
             "fasw_set_motion": (i, [p, d, d, d, d]),
             "fasw_dual_time_step": (i, [p, d, i, d, i, dp, C.POINTER(i)]),
             "fasw_kernel_time": (i, [p, i, C.POINTER(ll), C.POINTER(d)]),
+            "fasw_residual_noalloc": (i, [i, i, i, dp, dp, dp, dp, C.POINTER(Params), p]),
             "fasw_batch_create": (i, [i, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_void_p), i, C.POINTER(Params), p, C.POINTER(p)]),
             "fasw_batch_destroy": (None, [p]),
