@@ -143,11 +143,14 @@ int fasw_solve_steady(fasw_ctx* ctx, double drop, int max_cycles, double* histor
  * stream; with the legacy default stream (NULL) cycles are always launched individually. */
 int fasw_use_graphs(fasw_ctx* ctx, int enable);
 
-/* How the SGS sweeps run: 0 = automatic (FP64: strip-pipelined multi-CTA sweep; mixed: one-CTA
- * sweep), 1 = one thread per cell applying the LU blocks (reference kernel), 2 = one CTA with
- * precomputed transfer blocks (strips where a hyperplane exceeds 128 cells), 3 = strip-pipelined
- * with 8 rows per strip, 4 = with 16 rows per strip.  All give the same
- * Gauss-Seidel result up to rounding.  Synchronizes the stream; drops captured cycles. */
+/* How the SGS sweeps run: 0 = automatic (FP64: strip-pipelined multi-CTA sweep; mixed:
+ * hyperplane-staged sweep where the level fits, else one-CTA sweep), 1 = one thread per cell
+ * applying the LU blocks (reference kernel), 2 = one CTA with precomputed transfer blocks
+ * (strips where a hyperplane exceeds 128 cells), 3 = strip-pipelined with 8 rows per strip,
+ * 4 = with 16 rows per strip, 5 = hyperplane-staged (mixed precision only, nj <= 128: blocks
+ * stored hyperplane-major and staged through shared memory by cp.async; elsewhere as 0).  All
+ * give the same Gauss-Seidel result up to rounding.  Synchronizes the stream; drops captured
+ * cycles. */
 int fasw_set_sweep(fasw_ctx* ctx, int kind);
 
 /* Eddy viscosity of the finest level (Baldwin-Lomax from the current state); n doubles. */
@@ -207,7 +210,7 @@ int fasw_kernel_time(fasw_ctx* ctx, int kernel, long long* count, double* total_
  *
  * Scratch: a fixed array of FASW_NOALLOC_SCRATCH_DOUBLES doubles (4 MiB) compiled into the
  * library, held by every GPU that loads the library until the process exits; about
- * 6 (ni+4)(nj+4) + 20 ni nj doubles are needed (a 256 x 64 grid fits, 512 x 128 does not);
+ * 7 (ni+4)(nj+4) + 20 ni nj doubles are needed (a 256 x 64 grid fits, 512 x 128 does not);
  * larger grids return FASW_ERR_TOO_LARGE.  The first call on each device looks up the array's
  * device address with that device current; make that first call before any stream capture.
  * All calls share the one array and it keeps the previous call's contents (the parts that
@@ -237,7 +240,9 @@ int fasw_batch_cycle(fasw_batch* batch, int cycle_index, double* norms);
  * FASW_ERR_NOT_CONVERGED or FASW_ERR_DIVERGED (some case diverged). */
 int fasw_batch_solve(fasw_batch* batch, double drop, int max_cycles, int* cycles, double* final_drop, int* ncycles);
 /* Picks the sweep variant (see fasw_set_sweep) by timing whole batch cycles with each candidate
- * (states are saved and restored); choice[k] (nullable) receives the kind used for case k. */
+ * that never waits on another CTA (kinds 5 and 2; strips are excluded because concurrent cases
+ * do not guarantee that all CTAs of a sweep are resident); states are saved and restored;
+ * choice[k] (nullable) receives the kind used for case k. */
 int fasw_batch_autotune(fasw_batch* batch, int* choice);
 long long fasw_batch_launch_count(fasw_batch* batch);
 

@@ -154,6 +154,7 @@ int alloc_level(fasw_ctx* c, LevelDev& L) {
   A(L.src, 4 * n);
   A(L.p, G);
   A(L.q, G);
+  A(L.rinv, G);
   A(L.rt, 2 * n);
   A(L.dts, n);
   A(L.sxi, 2 * nfx);
@@ -175,6 +176,13 @@ int alloc_level(fasw_ctx* c, LevelDev& L) {
   A(L.vfe, nfe);
   A(L.wvx, (size_t)L.ni);
   A(L.wvy, (size_t)L.ni);
+  if (c->mixed && hp_fits(L.ni, L.nj, L.nw)) {
+    const size_t h = hp_floats(L.ni, L.nj);
+    A(L.hpF, 32 * h);
+    A(L.hpB, 32 * h);
+    A(L.hpC, 4 * h);
+    A(L.hpY, 4 * h);
+  }
 #undef A
   CKR(cudaMemsetAsync(L.vfx, 0, nfx * sizeof(double), c->st));
   CKR(cudaMemsetAsync(L.vfe, 0, nfe * sizeof(double), c->st));
@@ -201,13 +209,23 @@ void free_stream(double mach, double alpha_deg, double w[4]) {
 }
 
 // ---- driver steps
+// Sweep kind used on a level: automatic = hyperplane-staged FP32 sweep where the level fits
+// (mixed), else one CTA (mixed) or strips (FP64); a requested kind that does not apply to the
+// level or precision falls back the same way.
+int level_sweep_kind(const fasw_ctx* c, const LevelDev& L) {
+  int k = c->sweep_kind;
+  if (k == SWEEP_AUTO || (k == SWEEP_HP && !(c->mixed && L.hpF)))
+    k = c->mixed ? (L.hpF ? SWEEP_HP : SWEEP_CTA) : SWEEP_STRIPS;
+  return k;
+}
+
 void run_sweep(fasw_ctx* c, const LevelDev& L, int do_update, double alpha, const double* rhs) {
   if (c->sweep_kind == SWEEP_LEGACY) {
     launch_sgs(L, c->sc, c->mixed, do_update, alpha, rhs, nullptr, c->st);
     return;
   }
-  const int kind = c->sweep_kind == SWEEP_AUTO ? (c->mixed ? SWEEP_CTA : SWEEP_STRIPS) : c->sweep_kind;
-  launch_sweep(L, c->mixed, kind, do_update, c->sc.aw, alpha, rhs, c->d_prog, c->d_err, c->spin_limit, c->st);
+  launch_sweep(L, c->mixed, level_sweep_kind(c, L), do_update, c->sc.aw, alpha, rhs, c->d_prog, c->d_err,
+               c->spin_limit, c->st);
 }
 
 void bc_aux(fasw_ctx* c, int l, double cfl, int want_dts) {
@@ -227,7 +245,7 @@ void smooth_step(fasw_ctx* c, int l, double cfl, bool record_norm) {
   c->launches += 2;
   if (c->sweep_kind != SWEEP_LEGACY) {
     Prof p(c, FASW_K_DIAG_BLOCKS);
-    launch_sgs_prep(L, c->mixed, c->st);
+    launch_sgs_prep(L, c->mixed, level_sweep_kind(c, L), c->st);
     ++c->launches;
   }
   for (int i = 1; i <= sc.nstages; ++i) {
@@ -350,6 +368,9 @@ int fasw_create(int ni, int nj, int n_wake, const double* x, const double* y, in
   c->ph.re = p->re;
   c->ph.pr = p->pr;
   c->ph.prt = p->prt;
+  c->ph.inv_re = p->re > 0.0 ? 1.0 / p->re : 0.0;
+  c->ph.inv_pr = p->pr > 0.0 ? 1.0 / p->pr : 0.0;
+  c->ph.inv_prt = p->prt > 0.0 ? 1.0 / p->prt : 0.0;
   c->ph.s_coarse = p->s_coarse;
   c->ph.viscous = p->viscous;
   c->ph.turb = p->turb;
@@ -543,7 +564,7 @@ int fasw_precond_apply(fasw_ctx* c, int l, double cfl, const double* rin, double
   int r = copy_in(c, c->d_tmp2, rin, m, on_device);
   if (r) return r;
   if (c->sweep_kind != SWEEP_LEGACY) {
-    launch_sgs_prep(L, c->mixed, c->st);
+    launch_sgs_prep(L, c->mixed, level_sweep_kind(c, L), c->st);
     ++c->launches;
   }
   run_sweep(c, L, 0, 0.0, c->d_tmp2);
@@ -639,7 +660,7 @@ int fasw_fas_cycle(fasw_ctx* c, int cycle_index, double* res_norm) {
 }
 
 int fasw_set_sweep(fasw_ctx* c, int kind) {
-  if (!c || kind < SWEEP_AUTO || kind > SWEEP_STRIPS16) return FASW_ERR_ARG;
+  if (!c || kind < SWEEP_AUTO || kind > SWEEP_HP) return FASW_ERR_ARG;
   int r = sync(c);
   if (r) return r;
   c->sweep_kind = kind;
@@ -926,14 +947,17 @@ int fasw_batch_solve(fasw_batch* b, double drop, int max_cycles, int* cycles, do
   return diverged ? FASW_ERR_DIVERGED : FASW_ERR_NOT_CONVERGED;
 }
 
-// Autotuner: the sweep variants (one CTA per sweep with transfer blocks; strips of 8 or 16
-// rows) trade SM count against per-step latency, and which wins depends on how full the GPU
-// is, so each candidate is timed on whole batch cycles (all cases concurrently, CUDA events)
-// and the fastest is kept.  The cases' states are saved before and restored after.
+// Autotuner: the sweep variants that never wait on another CTA (the hyperplane-staged FP32
+// sweep and the one-CTA sweep) trade staging depth against per-step work, and which wins
+// depends on how full the GPU is, so each candidate is timed on whole batch cycles (all cases
+// concurrently, CUDA events) and the fastest is kept.  Strip-pipelined sweeps are not
+// candidates here: their CTAs wait on one another, which is safe only while all CTAs of one
+// sweep are resident, and concurrent branches of a batch graph do not guarantee that.
+// The cases' states are saved before and restored after.
 // choice (nullable, ncases): the kind used for case k.
 int fasw_batch_autotune(fasw_batch* b, int* choice) {
   if (!b) return FASW_ERR_ARG;
-  const int kinds[3] = {SWEEP_CTA, SWEEP_STRIPS, SWEEP_STRIPS16};
+  const int kinds[2] = {SWEEP_HP, SWEEP_CTA};
   std::vector<double*> saved(b->cases.size(), nullptr);
   for (size_t k = 0; k < b->cases.size(); ++k) {
     fasw_ctx* c = b->cases[k];

@@ -29,6 +29,7 @@ struct LevelDev {
   double* src;  // 4*n  dual-time history source (finest level)
   double* p;    // Gn   pressure (ghosted)
   double* q;    // Gn   sensor quantity (ghosted)
+  double* rinv; // Gn   1/rho (ghosted), formed once per state by the cell-auxiliary kernel
   double* rt;   // 2*n  Martinelli-corrected radii (xi plane, eta plane)
   double* dts;  // n    local pseudo time step
   double* sxi;  // 2*nfx  i-face area vectors (x plane, y plane), index j*(ni+1)+i
@@ -50,10 +51,18 @@ struct LevelDev {
   double* vfe;        // nfe grid volume flux of the j-faces
   double* wvx;        // ni  grid velocity at the j = 0 face midpoints (moving wall)
   double* wvy;
+  // hyperplane-major FP32 arrays of the staged sweep (mixed precision, levels that fit; else
+  // null): entry h = (i + j) * nj + j.  hpF: G_W, G_S; hpB: H_E, H_N (32 floats per entry);
+  // hpC: D^-1 r (4); hpY: forward result y (4).
+  float* hpF;
+  float* hpB;
+  float* hpC;
+  float* hpY;
 };
 
 struct PhysParams {
   double mach, alpha_deg, re, pr, prt;
+  double inv_re, inv_pr, inv_prt;  // reciprocals of re, pr, prt (set with them by the host)
   double uinf[4];
   double s_coarse;
   int viscous, turb, sensor;

@@ -39,6 +39,7 @@ size_t carve(LevelDev& L, double* base) {
   take(L.u, 4 * (size_t)L.Gn);
   take(L.p, (size_t)L.Gn);
   take(L.q, (size_t)L.Gn);
+  take(L.rinv, (size_t)L.Gn);
   take(L.rt, 2 * (size_t)L.n);
   take(L.dts, (size_t)L.n);
   take(L.sxi, 2 * (size_t)L.nfx);
@@ -98,6 +99,9 @@ extern "C" int fasw_residual_noalloc(int ni, int nj, int n_wake, const double* x
   ph.re = p->re;
   ph.pr = p->pr;
   ph.prt = p->prt;
+  ph.inv_re = p->re > 0.0 ? 1.0 / p->re : 0.0;
+  ph.inv_pr = p->pr > 0.0 ? 1.0 / p->pr : 0.0;
+  ph.inv_prt = p->prt > 0.0 ? 1.0 / p->prt : 0.0;
   ph.s_coarse = p->s_coarse;
   ph.viscous = p->viscous;
   ph.turb = 0;

@@ -4,14 +4,19 @@
 
 namespace fasw {
 
-enum SweepKind { SWEEP_AUTO = 0, SWEEP_LEGACY = 1, SWEEP_CTA = 2, SWEEP_STRIPS = 3, SWEEP_STRIPS16 = 4 };
+enum SweepKind { SWEEP_AUTO = 0, SWEEP_LEGACY = 1, SWEEP_CTA = 2, SWEEP_STRIPS = 3, SWEEP_STRIPS16 = 4, SWEEP_HP = 5 };
 
-void launch_sgs_prep(const LevelDev& L, int mixed, cudaStream_t st);
+// kind: the resolved sweep kind of this level (SWEEP_HP writes the hyperplane-major blocks).
+void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st);
 // Forward and backward sweep of one stage: y = (D+L)^-1 rhs, z = (D+U)^-1 D y into L.yz64 /
 // L.yz32, with the stage update u = u0 - alpha z (AW) or u0 - alpha dt* z (ARK) when
 // do_update.  prog: 2 * sweep_strips(L) flags, err: device error word.
 int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, double alpha, const double* rhs,
                  long long* prog, int* err, long long limit, cudaStream_t st);
 int sweep_strips(const LevelDev& L);
+// Hyperplane-staged FP32 sweep: whether a level fits (rows, shared memory), and the entries
+// (ni + nj - 1) * nj of its hyperplane-major arrays (hpF, hpB: 32 floats each; hpC, hpY: 4).
+bool hp_fits(int ni, int nj, int nw);
+size_t hp_floats(int ni, int nj);
 
 }  // namespace fasw

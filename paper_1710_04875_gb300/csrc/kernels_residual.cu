@@ -6,9 +6,14 @@ namespace fasw {
 
 namespace {
 
-constexpr int TX = 32;   // residual tile: TX x TY cells, (TX+1) x (TY+1) threads
+// Residual tile: TX x TY cells.  Warps 0..TY-1 compute the TX+1 = 32 i-faces of one tile row
+// each, warps TY..2TY compute the TX j-faces of one row of j-faces each (lane 31 idle), so no
+// warp mixes the two kinds of face and a j-face (with the viscous terms) is a thread of its
+// own: on GB300 an SM sub-partition issues one FP64 warp-instruction every few dozen cycles,
+// so the FP64 work of a launch is spread over as many warps and SMs as the grid allows.
+constexpr int TX = 31;
 constexpr int TY = 4;
-constexpr int RES_THREADS = (TX + 1) * (TY + 1);
+constexpr int RES_THREADS = 32 * (2 * TY + 1);
 
 __device__ __forceinline__ int gidx(const LevelDev& L, int i, int j) { return (j + 2) * L.P + (i + 2); }
 __device__ __forceinline__ bool on_cut(const LevelDev& L, int i) { return L.nw > 0 && (i < L.nw || i >= L.ni - L.nw); }
@@ -28,10 +33,17 @@ __device__ __forceinline__ double pressure(const double w[4]) {
 
 // Far-field boundary state by 1-D Riemann invariants along the outward unit normal (nx, ny).
 // vb: normal velocity of the (moving) boundary; in/outflow is decided on the relative velocity.
+// The density follows from the entropy of the upwind side: with s = p/rho^gamma fixed,
+// rho_b = (a_b^2 / (gamma s))^(1/(gamma-1)) = rho_up (a_b / a_up)^(2/(gamma-1)), and for
+// gamma = 1.4 the exponent is the integer 5 (FP64 pow costs about a hundred FP64 instructions
+// on a part whose FP64 issue rate is the bound of this kernel).
+static_assert(GAM == 1.4, "far-field density uses 2/(gamma-1) = 5");
 __device__ void farfield(const double wi[4], const double wf[4], double nx, double ny, double vb, double out[4]) {
-  const double ri = wi[0], ui = wi[1] / ri, vi = wi[2] / ri, pi = pressure(wi);
-  const double rf = wf[0], uf = wf[1] / rf, vf = wf[2] / rf, pf = pressure(wf);
-  const double ai = sqrt(GAM * pi / ri), af = sqrt(GAM * pf / rf);
+  const double ri = wi[0], rri = 1.0 / ri, ui = wi[1] * rri, vi = wi[2] * rri;
+  const double pi = (GAM - 1.0) * (wi[3] - 0.5 * (wi[1] * ui + wi[2] * vi));
+  const double rf = wf[0], rrf = 1.0 / rf, uf = wf[1] * rrf, vf = wf[2] * rrf;
+  const double pf = (GAM - 1.0) * (wf[3] - 0.5 * (wf[1] * uf + wf[2] * vf));
+  const double ai = sqrt(GAM * pi * rri), af = sqrt(GAM * pf * rrf);
   const double vni = ui * nx + vi * ny, vnf = uf * nx + vf * ny;
   if (fabs(vni - vb) >= ai) {
     const double* src = vni - vb > 0.0 ? wi : wf;
@@ -39,27 +51,31 @@ __device__ void farfield(const double wi[4], const double wf[4], double nx, doub
     for (int k = 0; k < 4; ++k) out[k] = src[k];
     return;
   }
-  const double Rp = vni + 2.0 * ai / (GAM - 1.0);
-  const double Rm = vnf - 2.0 * af / (GAM - 1.0);
+  constexpr double k2 = 2.0 / (GAM - 1.0);
+  const double Rp = vni + k2 * ai;
+  const double Rm = vnf - k2 * af;
   const double vnb = 0.5 * (Rp + Rm);
   const double ab = 0.25 * (GAM - 1.0) * (Rp - Rm);
-  double s, ut, vt;
+  double rup, aup, ut, vt;
   if (vnb - vb > 0.0) {
-    s = pi / pow(ri, GAM);
+    rup = ri;
+    aup = ai;
     ut = ui - vni * nx;
     vt = vi - vni * ny;
   } else {
-    s = pf / pow(rf, GAM);
+    rup = rf;
+    aup = af;
     ut = uf - vnf * nx;
     vt = vf - vnf * ny;
   }
-  const double rho = pow(ab * ab / (GAM * s), 1.0 / (GAM - 1.0));
-  const double p = rho * ab * ab / GAM;
+  const double ra = ab / aup, ra2 = ra * ra;
+  const double rho = rup * (ra2 * ra2 * ra);
+  const double p = rho * ab * ab * (1.0 / GAM);
   const double u = ut + vnb * nx, v = vt + vnb * ny;
   out[0] = rho;
   out[1] = rho * u;
   out[2] = rho * v;
-  out[3] = p / (GAM - 1.0) + 0.5 * rho * (u * u + v * v);
+  out[3] = p * (1.0 / (GAM - 1.0)) + 0.5 * rho * (u * u + v * v);
 }
 
 // Boundary value of ghost cell (gi, gj) (two layers on every side; corners excluded):
@@ -170,13 +186,15 @@ __global__ void k_cell_aux(LevelDev L, PhysParams ph, double cfl, int want_dts, 
   } else {
     load4(L, t, w);
   }
-  const double p = pressure(w);
+  const double rr = 1.0 / w[0];
+  const double u = w[1] * rr, v = w[2] * rr;
+  const double p = (GAM - 1.0) * (w[3] - 0.5 * (w[1] * u + w[2] * v));
   L.p[t] = p;
+  L.rinv[t] = rr;
   L.q[t] = ph.sensor ? p / pow(w[0], GAM) : p;
   if (gi < 0 || gi >= L.ni || gj < 0 || gj >= L.nj) return;
   const int i = gi, j = gj, ni = L.ni;
-  const double a = sqrt(GAM * p / w[0]);
-  const double u = w[1] / w[0], v = w[2] / w[0];
+  const double a = sqrt(GAM * p * rr);
   const int fw = j * (ni + 1) + i, fs = j * ni + i;
   const double sx = 0.5 * (L.sxi[fw] + L.sxi[fw + 1]);
   const double sy = 0.5 * (L.sxi[L.nfx + fw] + L.sxi[L.nfx + fw + 1]);
@@ -187,8 +205,11 @@ __global__ void k_cell_aux(LevelDev L, PhysParams ph, double cfl, int want_dts, 
   const double rxi = fabs(u * sx + v * sy - vx) + a * sqrt(sx * sx + sy * sy);
   const double reta = fabs(u * ex + v * ey - ve) + a * sqrt(ex * ex + ey * ey);
   const int c = j * ni + i;
-  L.rt[c] = rxi * (1.0 + pow(reta / rxi, 2.0 / 3.0));
-  L.rt[L.n + c] = reta * (1.0 + pow(rxi / reta, 2.0 / 3.0));
+  // Martinelli scaling: (r_eta/r_xi)^(2/3) = cr^2 with cr the cube root of the ratio, and the
+  // other direction's factor is 1/cr^2 (one cbrt instead of two pow).
+  const double cr = cbrt(reta / rxi), t2 = cr * cr;
+  L.rt[c] = rxi + rxi * t2;
+  L.rt[L.n + c] = reta + reta / t2;
   if (want_dts) L.dts[c] = cfl * L.vol[c] / (rxi + reta);
 }
 
@@ -219,8 +240,8 @@ __device__ void jst_face(const LevelDev& L, int gLL, int gL, int gR, int gRR, do
   load4(L, gR, uR);
   const double pL = L.p[gL], pR = L.p[gR];
   {
-    const double qnL = (uL[1] * sx + uL[2] * sy) / uL[0];
-    const double qnR = (uR[1] * sx + uR[2] * sy) / uR[0];
+    const double qnL = (uL[1] * sx + uL[2] * sy) * L.rinv[gL];
+    const double qnR = (uR[1] * sx + uR[2] * sy) * L.rinv[gR];
     hc[0] = 0.5 * ((uL[0] * qnL - uL[0] * vf) + (uR[0] * qnR - uR[0] * vf));
     hc[1] = 0.5 * (((uL[1] * qnL + pL * sx) - uL[1] * vf) + ((uR[1] * qnR + pR * sx) - uR[1] * vf));
     hc[2] = 0.5 * (((uL[2] * qnL + pL * sy) - uL[2] * vf) + ((uR[2] * qnR + pR * sy) - uR[2] * vf));
@@ -283,19 +304,22 @@ __device__ void visc_face(const LevelDev& L, const PhysParams& ph, int i, int j,
     volR = L.vol[j * ni + i];
     mutf = 0.5 * (L.mut[(j - 1) * ni + i] + L.mut[j * ni + i]);
   }
-  const double volf = 0.5 * (volL + volR);
+  const double rvf = 2.0 / (volL + volR);  // 1 / mean volume
   double wL[4], wR[4];
   const int gL = gidx(L, i, j - 1), gR = gidx(L, i, j);
   load4(L, gL, wL);
   load4(L, gR, wR);
-  const double uL = wL[1] / wL[0], vL = wL[2] / wL[0], uR = wR[1] / wR[0], vR = wR[2] / wR[0];
-  const double hL = GAM / (GAM - 1.0) * L.p[gL] / wL[0], hR = GAM / (GAM - 1.0) * L.p[gR] / wR[0];
-  const double mu = 1.0 / ph.re;
+  const double rL = L.rinv[gL], rR = L.rinv[gR];
+  const double uL = wL[1] * rL, vL = wL[2] * rL, uR = wR[1] * rR, vR = wR[2] * rR;
+  constexpr double cp = GAM / (GAM - 1.0);
+  const double hL = cp * L.p[gL] * rL, hR = cp * L.p[gR] * rR;
+  const double mu = ph.inv_re;
   const double mueff = mu + mutf;
-  const double keff = mu / ph.pr + mutf / ph.prt;
-  const double gux = (uR - uL) * sx / volf, guy = (uR - uL) * sy / volf;
-  const double gvx = (vR - vL) * sx / volf, gvy = (vR - vL) * sy / volf;
-  const double ghx = (hR - hL) * sx / volf, ghy = (hR - hL) * sy / volf;
+  const double keff = mu * ph.inv_pr + mutf * ph.inv_prt;
+  const double sxv = sx * rvf, syv = sy * rvf;
+  const double gux = (uR - uL) * sxv, guy = (uR - uL) * syv;
+  const double gvx = (vR - vL) * sxv, gvy = (vR - vL) * syv;
+  const double ghx = (hR - hL) * sxv, ghy = (hR - hL) * syv;
   const double div = gux + gvy;
   const double txx = mueff * (2.0 * gux - 2.0 / 3.0 * div);
   const double tyy = mueff * (2.0 * gvy - 2.0 / 3.0 * div);
@@ -308,18 +332,30 @@ __device__ void visc_face(const LevelDev& L, const PhysParams& ph, int i, int j,
   hv[3] = uf * fx + vf * fy + keff * (ghx * sx + ghy * sy);
 }
 
+// Deterministic block sum of one double per thread (fixed shuffle tree, then warps in order).
+__device__ double block_sum(double v, double* wsum) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) wsum[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < nw; ++k) s += wsum[k];
+  return s;
+}
+
 // One tile of TX x TY cells: every face of the tile is computed once into shared memory,
 // then each cell assembles F^c and F^v and writes what the mode asks for.
 __global__ void __launch_bounds__(RES_THREADS) k_residual(LevelDev L, PhysParams ph, ResArgs a) {
   __shared__ double xc[4][TY][TX + 1], xd[4][TY][TX + 1];
   __shared__ double ec[4][TY + 1][TX], ed[4][TY + 1][TX];
-  __shared__ double red[RES_THREADS];
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  __shared__ double wsum[RES_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int ni = L.ni, nj = L.nj;
-  const int tid = ty * (TX + 1) + tx;
-  // i-face (i0+tx, j0+ty)
-  if (ty < TY) {
+  if (warp < TY) {  // i-face (i0 + lane, j0 + warp)
+    const int tx = lane, ty = warp;
     const int i = i0 + tx, j = j0 + ty;
     if (i <= ni && j < nj) {
       const int f = j * (ni + 1) + i;
@@ -332,9 +368,8 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(LevelDev L, PhysParams
         xd[k][ty][tx] = hd[k];
       }
     }
-  }
-  // j-face (i0+tx, j0+ty)
-  if (tx < TX) {
+  } else if (lane < TX) {  // j-face (i0 + lane, j0 + warp - TY)
+    const int tx = lane, ty = warp - TY;
     const int i = i0 + tx, j = j0 + ty;
     if (i < ni && j <= nj) {
       const int f = j * ni + i;
@@ -357,22 +392,23 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(LevelDev L, PhysParams
   }
   __syncthreads();
   double nacc = 0.0;
-  if (tx < TX && ty < TY) {
+  if (warp < TY && lane < TX) {  // cell (i0 + lane, j0 + warp)
+    const int tx = lane, ty = warp;
     const int i = i0 + tx, j = j0 + ty;
     if (i < ni && j < nj) {
       const int c = j * ni + i;
       const int n = L.n;
-      const double vol = L.vol[c];
+      const double rvol = 1.0 / L.vol[c];
       const int g = gidx(L, i, j);
       double Fc[4], Fv[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const double fc = (xc[k][ty][tx + 1] - xc[k][ty][tx]) + (ec[k][ty + 1][tx] - ec[k][ty][tx]);
         const double fd = -((xd[k][ty][tx + 1] - xd[k][ty][tx]) + (ed[k][ty + 1][tx] - ed[k][ty][tx]));
-        double fcv = fc / vol + L.a_t * L.u[k * L.Gn + g] + L.src[k * n + c];
+        double fcv = fc * rvol + L.a_t * L.u[k * L.Gn + g] + L.src[k * n + c];
         if (a.mode != RES_FORCING) fcv -= L.s[k * n + c];
         Fc[k] = fcv;
-        Fv[k] = fd / vol;
+        Fv[k] = fd * rvol;
       }
       if (a.want_norm) {
         if (a.norm_all) {
@@ -412,27 +448,17 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(LevelDev L, PhysParams
     }
   }
   if (a.want_norm) {
-    red[tid] = nacc;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int k = 0; k < RES_THREADS; ++k) s += red[k];
-      L.norm_part[blockIdx.y * gridDim.x + blockIdx.x] = s;
-    }
+    const double s = block_sum(nacc, wsum);
+    if (threadIdx.x == 0) L.norm_part[blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
 }
 
 __global__ void k_norm_final(const double* part, int nparts, double count, double* out) {
-  __shared__ double red[256];
+  __shared__ double wsum[8];
   double s = 0.0;
   for (int k = threadIdx.x; k < nparts; k += blockDim.x) s += part[k];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < (int)blockDim.x; ++k) t += red[k];
-    out[0] = sqrt(t / count);
-  }
+  const double t = block_sum(s, wsum);
+  if (threadIdx.x == 0) out[0] = sqrt(t / count);
 }
 
 // ---- Baldwin-Lomax (finest level): vorticity by Green-Gauss, then one thread per i-line.
@@ -440,16 +466,15 @@ __global__ void k_vorticity(LevelDev L) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int ni = L.ni, i = c % ni, j = c / ni;
-  double w[4];
-  load4(L, gidx(L, i, j), w);
-  const double u0 = w[1] / w[0], v0 = w[2] / w[0];
+  const int g0 = gidx(L, i, j);
+  const double u0 = L.u[L.Gn + g0] * L.rinv[g0], v0 = L.u[2 * L.Gn + g0] * L.rinv[g0];
   double fu[4], fv[4];
   const int nb[4][2] = {{i + 1, j}, {i - 1, j}, {i, j + 1}, {i, j - 1}};
+#pragma unroll
   for (int k = 0; k < 4; ++k) {
-    double z[4];
-    load4(L, gidx(L, nb[k][0], nb[k][1]), z);
-    fu[k] = 0.5 * (u0 + z[1] / z[0]);
-    fv[k] = 0.5 * (v0 + z[2] / z[0]);
+    const int g = gidx(L, nb[k][0], nb[k][1]);
+    fu[k] = 0.5 * (u0 + L.u[L.Gn + g] * L.rinv[g]);
+    fv[k] = 0.5 * (v0 + L.u[2 * L.Gn + g] * L.rinv[g]);
   }
   const int fe = j * (ni + 1) + i + 1, fw = j * (ni + 1) + i, fn = (j + 1) * ni + i, fs = j * ni + i;
   const double circ = (fv[0] * L.sxi[fe] - fu[0] * L.sxi[L.nfx + fe]) - (fv[1] * L.sxi[fw] - fu[1] * L.sxi[L.nfx + fw]) +
@@ -457,47 +482,74 @@ __global__ void k_vorticity(LevelDev L) {
   L.omega[c] = fabs(circ / L.vol[c]);
 }
 
+// Baldwin-Lomax along each grid line i = const: one warp per line, lanes over j.  The search
+// for F_max takes the first j of the largest F (as a sequential scan with a strict > would),
+// and the inner/outer crossover is the first j where the inner value reaches the outer one.
 __global__ void k_bl_lines(LevelDev L, PhysParams ph) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L.ni) return;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= L.ni) return;  // whole warps leave together
   const double Aplus = 26.0, Ccp = 1.6, Ckleb = 0.3, Cwk = 0.25, kap = 0.4, Kc = 0.0168;
   const int ni = L.ni, nj = L.nj;
-  const double mu = 1.0 / ph.re;
+  const double mu = ph.inv_re;
   const bool wake = on_cut(L, i);
   const double rhow = L.u[gidx(L, i, 0)];
   const double tauw = mu * L.omega[i];
   const double utr = sqrt(rhow * tauw);
+  const double yplus_scale = utr * ph.re / Aplus;  // y+ / A+ = y * utr / (mu A+)
   const int jsearch = max(1, nj / 2);
-  double Fmax = 0.0, ymax = 0.0, smax = 0.0, smin = 1e300;
-  for (int j = 0; j < jsearch; ++j) {
+  double Fmax = 0.0, smax = 0.0, smin = 1e300;
+  int jmax = 1 << 30;
+  for (int j = lane; j < jsearch; j += 32) {
     const int c = j * ni + i;
     const double y = L.wdist[c];
-    const double damp = wake ? 1.0 : 1.0 - exp(-(utr * y / mu) / Aplus);
+    const double damp = wake ? 1.0 : 1.0 - exp(-y * yplus_scale);
     const double F = y * L.omega[c] * damp;
-    if (F > Fmax) {
+    if (F > Fmax) {  // lanes scan increasing j: keeps the first j of the lane's largest F
       Fmax = F;
-      ymax = y;
+      jmax = j;
     }
     const int g = gidx(L, i, j);
-    const double r = L.u[g], uu = L.u[L.Gn + g] / r, vv = L.u[2 * L.Gn + g] / r;
+    const double rr = L.rinv[g], uu = L.u[L.Gn + g] * rr, vv = L.u[2 * L.Gn + g] * rr;
     const double sp = sqrt(uu * uu + vv * vv);
     smax = fmax(smax, sp);
     smin = fmin(smin, sp);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double F2 = __shfl_xor_sync(0xffffffffu, Fmax, o);
+    const int j2 = __shfl_xor_sync(0xffffffffu, jmax, o);
+    if (F2 > Fmax || (F2 == Fmax && j2 < jmax)) {
+      Fmax = F2;
+      jmax = j2;
+    }
+    smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    smin = fmin(smin, __shfl_xor_sync(0xffffffffu, smin, o));
+  }
+  const double ymax = Fmax > 0.0 ? L.wdist[jmax * ni + i] : 0.0;
   const double udif = wake ? smax - smin : smax;
   const double Fwake = Fmax > 0.0 ? fmin(ymax * Fmax, Cwk * ymax * udif * udif / Fmax) : 0.0;
-  bool outer = wake;
-  for (int j = 0; j < nj; ++j) {
-    const int c = j * ni + i;
-    const double y = L.wdist[c];
-    const double rho = L.u[gidx(L, i, j)];
-    const double fk = ymax > 0.0 ? 1.0 / (1.0 + 5.5 * pow(Ckleb * y / ymax, 6.0)) : 0.0;
-    const double mo = Kc * Ccp * rho * Fwake * fk;
-    const double damp = wake ? 1.0 : 1.0 - exp(-(utr * y / mu) / Aplus);
-    const double l = kap * y * damp;
-    const double mi = rho * l * l * L.omega[c];
-    if (!outer && mi >= mo) outer = true;
-    L.mut[c] = outer ? mo : mi;
+  const double rym = ymax > 0.0 ? Ckleb / ymax : 0.0;
+  int jcross = wake ? 0 : nj;
+  for (int j0 = 0; j0 < nj; j0 += 32) {
+    const int j = j0 + lane;
+    double mo = 0.0, mi = 0.0;
+    if (j < nj) {
+      const int c = j * ni + i;
+      const double y = L.wdist[c];
+      const double rho = L.u[gidx(L, i, j)];
+      const double x = y * rym, x2 = x * x;
+      const double fk = ymax > 0.0 ? 1.0 / (1.0 + 5.5 * (x2 * x2 * x2)) : 0.0;
+      mo = Kc * Ccp * rho * Fwake * fk;
+      const double damp = wake ? 1.0 : 1.0 - exp(-y * yplus_scale);
+      const double l = kap * y * damp;
+      mi = rho * l * l * L.omega[c];
+    }
+    if (jcross == nj) {
+      const unsigned hit = __ballot_sync(0xffffffffu, j < nj && mi >= mo);
+      if (hit) jcross = j0 + __ffs(hit) - 1;
+    }
+    if (j < nj) L.mut[j * ni + i] = j >= jcross ? mo : mi;
   }
 }
 
@@ -505,23 +557,22 @@ __global__ void k_bl_lines(LevelDev L, PhysParams ph) {
 
 void launch_bc(const LevelDev& L, const PhysParams& ph, cudaStream_t st) {
   const int nt = 4 * L.ni + 4 * L.nj;
-  k_bc<<<(nt + 127) / 128, 128, 0, st>>>(L, ph);
+  k_bc<<<(nt + 63) / 64, 64, 0, st>>>(L, ph);
 }
 
 void launch_cell_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st) {
-  k_cell_aux<<<(L.Gn + 255) / 256, 256, 0, st>>>(L, ph, cfl, want_dts, 0);
+  k_cell_aux<<<(L.Gn + 63) / 64, 64, 0, st>>>(L, ph, cfl, want_dts, 0);
 }
 
 void launch_bc_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st) {
-  k_cell_aux<<<(L.Gn + 255) / 256, 256, 0, st>>>(L, ph, cfl, want_dts, 1);
+  k_cell_aux<<<(L.Gn + 63) / 64, 64, 0, st>>>(L, ph, cfl, want_dts, 1);
 }
 
 int residual_blocks(const LevelDev& L) { return ((L.ni + TX - 1) / TX) * ((L.nj + TY - 1) / TY); }
 
 void launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, cudaStream_t st) {
   dim3 grid((L.ni + TX - 1) / TX, (L.nj + TY - 1) / TY);
-  dim3 block(TX + 1, TY + 1);
-  k_residual<<<grid, block, 0, st>>>(L, ph, a);
+  k_residual<<<grid, RES_THREADS, 0, st>>>(L, ph, a);
 }
 
 void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* out, cudaStream_t st) {
@@ -529,8 +580,8 @@ void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* o
 }
 
 void launch_bl(const LevelDev& L, const PhysParams& ph, cudaStream_t st) {
-  k_vorticity<<<(L.n + 255) / 256, 256, 0, st>>>(L);
-  k_bl_lines<<<(L.ni + 63) / 64, 64, 0, st>>>(L, ph);
+  k_vorticity<<<(L.n + 63) / 64, 64, 0, st>>>(L);
+  k_bl_lines<<<(L.ni + 1) / 2, 64, 0, st>>>(L, ph);
 }
 
 }  // namespace fasw

@@ -93,12 +93,11 @@ __device__ double visc_radius(const LevelDev& L, const PhysParams& ph, int i, in
     volR = L.vol[j * ni + i];
     mutf = 0.5 * (L.mut[(j - 1) * ni + i] + L.mut[j * ni + i]);
   }
-  const double volf = 0.5 * (volL + volR);
-  const double mu = 1.0 / ph.re;
-  const double nu = fmax(mu + mutf, GAM * (mu / ph.pr + mutf / ph.prt)) / rho;
+  const double mu = ph.inv_re;
+  const double nu = fmax(mu + mutf, GAM * (mu * ph.inv_pr + mutf * ph.inv_prt)) / rho;
   const int f = j * ni + i;
   const double sx = L.seta[f], sy = L.seta[L.nfe + f];
-  return nu * (sx * sx + sy * sy) / volf;
+  return 2.0 * nu * (sx * sx + sy * sy) / (volL + volR);
 }
 
 template <typename T>
@@ -303,16 +302,16 @@ __global__ void k_sgs_single(LevelDev L, const T* blk, const T* dlu, T* yz, cons
 void launch_face_blocks(const LevelDev& L, const PhysParams& ph, const SchemeParams& sc, int mixed, cudaStream_t st) {
   const int nf = L.nfx + L.nfe;
   if (mixed)
-    k_face_blocks<float><<<(nf + 127) / 128, 128, 0, st>>>(L, ph, L.blk32, float(sc.d_cut));
+    k_face_blocks<float><<<(nf + 63) / 64, 64, 0, st>>>(L, ph, L.blk32, float(sc.d_cut));
   else
-    k_face_blocks<double><<<(nf + 127) / 128, 128, 0, st>>>(L, ph, L.blk64, sc.d_cut);
+    k_face_blocks<double><<<(nf + 63) / 64, 64, 0, st>>>(L, ph, L.blk64, sc.d_cut);
 }
 
 void launch_diag_blocks(const LevelDev& L, const SchemeParams& sc, int mixed, cudaStream_t st) {
   if (mixed)
-    k_diag_blocks<float><<<(L.n + 127) / 128, 128, 0, st>>>(L, L.blk32, L.dlu32, sc.aw, sc.eta);
+    k_diag_blocks<float><<<(L.n + 63) / 64, 64, 0, st>>>(L, L.blk32, L.dlu32, sc.aw, sc.eta);
   else
-    k_diag_blocks<double><<<(L.n + 127) / 128, 128, 0, st>>>(L, L.blk64, L.dlu64, sc.aw, sc.eta);
+    k_diag_blocks<double><<<(L.n + 63) / 64, 64, 0, st>>>(L, L.blk64, L.dlu64, sc.aw, sc.eta);
 }
 
 void launch_sgs(const LevelDev& L, const SchemeParams& sc, int mixed, int do_update, double alpha,

@@ -33,8 +33,10 @@ namespace {
 __device__ __forceinline__ bool on_cut(const LevelDev& L, int i) { return L.nw > 0 && (i < L.nw || i >= L.ni - L.nw); }
 
 // Transfer blocks, entry-major: tb[(blk*16 + e) * n + c], blk 0 = D^-1, 1 = G_W, 2 = G_S,
-// 3 = H_E, 4 = H_N.  Blocks of absent neighbours are zero.
-template <typename T>
+// 3 = H_E, 4 = H_N.  Blocks of absent neighbours are zero.  With HP (FP32 only) blocks 1-4 go
+// to the hyperplane-major arrays of k_sweep_hp instead: entry h = (i + j) * nj + j holds
+// hpF[32h..] = G_W, G_S and hpB[32h..] = H_E, H_N (row-major 4x4 each); D^-1 stays in tb.
+template <typename T, bool HP>
 __global__ void k_sgs_prep(LevelDev L, const T* blk, const T* dlu, T* tb) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
@@ -72,10 +74,12 @@ __global__ void k_sgs_prep(LevelDev L, const T* blk, const T* dlu, T* tb) {
   const bool hasS = j > 0 || on_cut(L, i);
 #pragma unroll
   for (int e = 0; e < 16; ++e) tb[e * n + c] = Di[e];
+  const size_t h = (size_t)(i + j) * nj + j;
   // product helper: out = s * Di * B (B entry-major with stride sb at face f)
   auto prod = [&](int slot, const T* B, int sb, int f, T s, bool present) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 4; ++r) {
+      T row[4];
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
         T acc = T(0);
@@ -84,8 +88,16 @@ __global__ void k_sgs_prep(LevelDev L, const T* blk, const T* dlu, T* tb) {
           for (int k = 0; k < 4; ++k) acc += Di[4 * r + k] * B[(4 * k + cc) * sb + f];
           acc *= s;
         }
-        tb[(slot * 16 + 4 * r + cc) * n + c] = acc;
+        row[cc] = acc;
       }
+      if constexpr (HP) {
+        float* dst = (slot <= 2 ? L.hpF : L.hpB) + 32 * h + ((slot - 1) & 1) * 16 + 4 * r;
+        *reinterpret_cast<float4*>(dst) = make_float4(row[0], row[1], row[2], row[3]);
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) tb[(slot * 16 + 4 * r + cc) * n + c] = row[cc];
+      }
+    }
   };
   prod(1, Axp, L.nfx, fw, cf, hasW);
   prod(2, Aep, L.nfe, fs, cf, hasS);
@@ -452,17 +464,222 @@ __global__ void __launch_bounds__(16 * SH) k_sweep_strips(LevelDev L, const T* t
   }
 }
 
+// ---------------------------------------------------------------- hyperplane-staged, FP32
+// For the FP32 preconditioner the sweep is bound by how fast one SM can bring in the blocks
+// of the next hyperplane (36 floats per cell and direction) and by the per-step barrier, not
+// by arithmetic.  Cells are therefore stored hyperplane-major (entry h = (i+j)*nj + j, see
+// k_sgs_prep<float, true>), so that the data of one step of all rows are contiguous, and
+// each thread (row j, block row q) copies its own 16-byte pieces with cp.async into a
+// per-thread ring of shared memory STAGES steps ahead of use.  The previous hyperplane's
+// vectors are exchanged through shared memory (one barrier per step); row 0 keeps its values
+// for the wake-cut coupling, which in the forward sweep reads the mirror cell processed
+// earlier on the same row, and in the backward sweep the mirror cell processed earlier there.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  const int sz = valid ? 16 : 0;  // 0: zero-fill without reading
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  const int sz = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gsrc), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  const int sz = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gsrc), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ float dot4(const float4 a, const float4 b) {
+  return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w);
+}
+__device__ __forceinline__ void set_comp(float4& v, int q, float x) { reinterpret_cast<float*>(&v)[q] = x; }
+
+// cy = D^-1 rhs per cell, written hyperplane-major (the forward sweep's constant term).
+__global__ void k_hp_cy(LevelDev L, const float* dinv, const double* rhs) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  const int n = L.n, i = c % L.ni, j = c / L.ni;
+  float r[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) r[t] = float(rhs[t * n + c]);
+  float y[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float a = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) a += dinv[(4 * q + t) * n + c] * r[t];
+    y[q] = a;
+  }
+  *reinterpret_cast<float4*>(L.hpC + 4 * ((size_t)(i + j) * L.nj + j)) = make_float4(y[0], y[1], y[2], y[3]);
+}
+
+// Shared memory (float4 units): ring [STAGES][4][nt], exchange [2][njp+1], row 0 [ni],
+// lower-wake G_S rows [nw][4].
+inline size_t hp_smem_bytes(int stages, int nt, int njp, int ni, int nw) {
+  return 16 * ((size_t)stages * 4 * nt + 2 * (size_t)(njp + 1) + (size_t)ni + 4 * (size_t)nw);
+}
+
+template <int STAGES>
+__global__ void __launch_bounds__(512) k_sweep_hp(LevelDev L, int do_update, int aw, double alpha) {
+  extern __shared__ float4 sm4[];
+  const int nt = blockDim.x, tid = threadIdx.x;
+  const int j = tid >> 2, q = tid & 3, njp = nt >> 2;
+  const int ni = L.ni, nj = L.nj, n = L.n, nw = L.nw;
+  const int K = ni + nj - 1;
+  float4* ring = sm4;
+  float4* xb = ring + (size_t)STAGES * 4 * nt;
+  float4* row0 = xb + 2 * (njp + 1);
+  float4* gsm = row0 + ni;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int x = tid; x < 2 * (njp + 1); x += nt) xb[x] = zero4;
+
+  // ---------------- forward: y = D^-1 r + G_W y_W + G_S y_S
+  auto fissue = [&](int k) {
+    float4* slot = ring + (size_t)(k & (STAGES - 1)) * 4 * nt;
+    const int i = k - j;
+    const bool v = k < K && j < nj && i >= 0 && i < ni;
+    const size_t h = v ? (size_t)k * nj + j : 0;
+    cp_async16(&slot[tid], L.hpF + 32 * h + 4 * q, v);
+    cp_async16(&slot[nt + tid], L.hpF + 32 * h + 16 + 4 * q, v);
+    cp_async4(&slot[2 * nt + tid], L.hpC + 4 * h + q, v);
+    cp_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < STAGES; ++k) fissue(k);
+  __syncthreads();
+  for (int k = 0; k < K; ++k) {
+    cp_wait<STAGES - 1>();
+    const float4* slot = ring + (size_t)(k & (STAGES - 1)) * 4 * nt;
+    const float4 gw = slot[tid], gs = slot[nt + tid];
+    const float cy = slot[2 * nt + tid].x;
+    const float4* prev = xb + ((k + 1) & 1) * (njp + 1);
+    float4* cur = xb + (k & 1) * (njp + 1);
+    const int i = k - j;
+    float4 ys = zero4;
+    if (j > 0) {
+      ys = prev[j - 1];
+    } else if (nw > 0 && i >= ni - nw && i < ni) {  // lower-half mirror of the upper wake cell
+      ys = row0[ni - 1 - i];
+    }
+    const float y = cy + (dot4(gw, prev[j]) + dot4(gs, ys));
+    set_comp(cur[j], q, y);
+    if (j < nj && i >= 0 && i < ni) {
+      L.hpY[4 * ((size_t)k * nj + j) + q] = y;
+      if (j == 0) set_comp(row0[i], q, y);
+    }
+    __syncthreads();
+    fissue(k + STAGES);
+  }
+  cp_wait<0>();
+  __threadfence_block();
+
+  // ---------------- backward: z = y + H_E z_E + H_N z_N (+ G_S z_mirror on the lower wake)
+  for (int x = tid; x < 2 * (njp + 1); x += nt) xb[x] = zero4;
+  for (int x = tid; x < 4 * nw; x += nt) {
+    const int i = x >> 2, r = x & 3;  // cell (i, 0) is entry h = i
+    gsm[x] = *reinterpret_cast<const float4*>(L.hpF + 32 * (size_t)i * nj + 16 + 4 * r);
+  }
+  auto bissue = [&](int kk) {
+    float4* slot = ring + (size_t)(kk & (STAGES - 1)) * 4 * nt;
+    const int k = K - 1 - kk, i = k - j;
+    const bool v = kk < K && j < nj && i >= 0 && i < ni;
+    const size_t h = v ? (size_t)k * nj + j : 0;
+    const size_t c = v ? (size_t)j * ni + i : 0;
+    cp_async16(&slot[tid], L.hpB + 32 * h + 4 * q, v);
+    cp_async16(&slot[nt + tid], L.hpB + 32 * h + 16 + 4 * q, v);
+    cp_async4(&slot[2 * nt + tid], L.hpY + 4 * h + q, v);
+    if (do_update) {
+      cp_async8(&slot[3 * nt + tid], L.u0 + (size_t)q * n + c, v);
+      cp_async8(reinterpret_cast<char*>(&slot[3 * nt + tid]) + 8, L.dts + c, v && !aw);
+    }
+    cp_commit();
+  };
+#pragma unroll
+  for (int kk = 0; kk < STAGES; ++kk) bissue(kk);
+  __syncthreads();
+  for (int kk = 0; kk < K; ++kk) {
+    cp_wait<STAGES - 1>();
+    const float4* slot = ring + (size_t)(kk & (STAGES - 1)) * 4 * nt;
+    const float4 he = slot[tid], hn = slot[nt + tid];
+    const float yv = slot[2 * nt + tid].x;
+    const float4* prev = xb + ((kk + 1) & 1) * (njp + 1);
+    float4* cur = xb + (kk & 1) * (njp + 1);
+    const int k = K - 1 - kk, i = k - j;
+    const bool valid = j < nj && i >= 0 && i < ni;
+    float z = yv + (dot4(he, prev[j]) + dot4(hn, prev[j + 1]));
+    if (j == 0 && i < nw && i >= 0) z += dot4(gsm[4 * i + q], row0[ni - 1 - i]);
+    set_comp(cur[j], q, z);
+    if (valid) {
+      if (j == 0) set_comp(row0[i], q, z);
+      const size_t c = (size_t)j * ni + i;
+      if (do_update) {
+        const double2 ud = *reinterpret_cast<const double2*>(&slot[3 * nt + tid]);
+        const double sc = aw ? alpha : alpha * ud.y;
+        L.u[(size_t)q * L.Gn + (j + 2) * L.P + (i + 2)] = ud.x - sc * double(z);
+      } else {
+        L.yz32[(size_t)q * n + c] = z;
+      }
+    }
+    __syncthreads();
+    bissue(kk + STAGES);
+  }
+  cp_wait<0>();
+}
+
 }  // namespace
 
-void launch_sgs_prep(const LevelDev& L, int mixed, cudaStream_t st) {
-  if (mixed)
-    k_sgs_prep<float><<<(L.n + 127) / 128, 128, 0, st>>>(L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
+void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st) {
+  if (mixed && kind == SWEEP_HP && L.hpF)
+    k_sgs_prep<float, true><<<(L.n + 63) / 64, 64, 0, st>>>(L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
+  else if (mixed)
+    k_sgs_prep<float, false><<<(L.n + 63) / 64, 64, 0, st>>>(L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
   else
-    k_sgs_prep<double><<<(L.n + 127) / 128, 128, 0, st>>>(L, L.blk64, L.dlu64, L.tb);
+    k_sgs_prep<double, false><<<(L.n + 63) / 64, 64, 0, st>>>(L, L.blk64, L.dlu64, L.tb);
+}
+
+namespace {
+int hp_threads(int nj) { return 4 * ((nj + 7) / 8 * 8); }
+int hp_stages(int nt) { return nt <= 256 ? 8 : 4; }
+constexpr size_t kHpSmemMax = 227 * 1024;
+}  // namespace
+
+size_t hp_floats(int ni, int nj) { return (size_t)(ni + nj - 1) * nj; }
+
+bool hp_fits(int ni, int nj, int nw) {
+  if (nj > 128) return false;
+  const int nt = hp_threads(nj);
+  return hp_smem_bytes(hp_stages(nt), nt, nt / 4, ni, nw) <= kHpSmemMax;
 }
 
 int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, double alpha, const double* rhs,
                  long long* prog, int* err, long long limit, cudaStream_t st) {
+  if (kind == SWEEP_HP && mixed && L.hpF) {
+    k_hp_cy<<<(L.n + 255) / 256, 256, 0, st>>>(L, reinterpret_cast<const float*>(L.tb), rhs);
+    const int nt = hp_threads(L.nj), stages = hp_stages(nt);
+    const size_t sm = hp_smem_bytes(stages, nt, nt / 4, L.ni, L.nw);
+    if (stages == 8) {
+      static bool attr8 = false;
+      if (!attr8) {
+        cudaFuncSetAttribute(k_sweep_hp<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHpSmemMax);
+        attr8 = true;
+      }
+      k_sweep_hp<8><<<1, nt, sm, st>>>(L, do_update, aw, alpha);
+    } else {
+      static bool attr4 = false;
+      if (!attr4) {
+        cudaFuncSetAttribute(k_sweep_hp<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHpSmemMax);
+        attr4 = true;
+      }
+      k_sweep_hp<4><<<1, nt, sm, st>>>(L, do_update, aw, alpha);
+    }
+    return 0;
+  }
+  if (kind == SWEEP_HP) kind = mixed ? SWEEP_CTA : SWEEP_STRIPS;
   const int cells = L.ni < L.nj ? L.ni : L.nj;  // longest hyperplane
   const bool cta_fits = 4 * cells <= 512;       // one thread slot per cell of a hyperplane
   if ((kind == SWEEP_CTA || (mixed && kind != SWEEP_STRIPS && kind != SWEEP_STRIPS16)) && cta_fits) {

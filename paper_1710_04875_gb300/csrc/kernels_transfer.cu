@@ -246,11 +246,11 @@ void launch_fill_state(const LevelDev& L, const double w[4], cudaStream_t st) {
 void launch_copy_u0(const LevelDev& L, cudaStream_t st) { k_copy_u0<<<(L.n + 255) / 256, 256, 0, st>>>(L); }
 
 void launch_restrict(const LevelDev& F, const LevelDev& C, int restrict_mut, cudaStream_t st) {
-  k_restrict<<<(C.n + 127) / 128, 128, 0, st>>>(F, C, restrict_mut);
+  k_restrict<<<(C.n + 63) / 64, 64, 0, st>>>(F, C, restrict_mut);
 }
 
 void launch_prolong(const LevelDev& F, const LevelDev& C, cudaStream_t st) {
-  k_prolong<<<(F.n + 255) / 256, 256, 0, st>>>(F, C);
+  k_prolong<<<(F.n + 63) / 64, 64, 0, st>>>(F, C);
 }
 
 void launch_pack(const LevelDev& L, const double* in, int to_ghosted, double* out, cudaStream_t st) {

@@ -265,8 +265,9 @@ class Solver:
         return code, nc.value, hist[:nc.value]
 
     def set_sweep(self, kind):
-        """0 auto, 1 reference (one thread per cell), 2 one CTA, 3 strips of 8 rows, 4 strips of 16."""
-        kinds = {"auto": 0, "reference": 1, "cta": 2, "strips": 3, "strips16": 4}
+        """0 auto, 1 reference (one thread per cell), 2 one CTA, 3 strips of 8 rows, 4 strips of 16,
+        5 hyperplane-staged (mixed precision)."""
+        kinds = {"auto": 0, "reference": 1, "cta": 2, "strips": 3, "strips16": 4, "staged": 5}
         _check(self.lib.fasw_set_sweep(self.h, kinds.get(kind, kind)), "fasw_set_sweep")
 
     def use_graphs(self, enable: bool):

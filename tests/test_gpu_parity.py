@@ -133,19 +133,39 @@ def test_rans_cycle_parity_full_size():
     assert rel_err(Fg, Fo) < 1e-9
 
 
-def test_mixed_precision_reaches_the_fp64_fixed_point():
-    """FP32 preconditioner only changes the iteration, not the converged answer."""
+@pytest.mark.parametrize("sweep", ["auto", "staged", "cta"])
+def test_mixed_precision_reaches_the_fp64_fixed_point(sweep):
+    """FP32 preconditioner only changes the iteration, not the converged answer (every FP32
+    sweep kernel)."""
     g = make_cgrid(64, 16)
     import paper_1710_04875_gb300 as P
     from tests.helpers import pair_params
     _, p64 = pair_params(nlevels=2, mach=0.5, alpha_deg=1.0)
     _, p32 = pair_params(nlevels=2, mach=0.5, alpha_deg=1.0, precision="mixed")
     a, b = P.Solver(g, p64), P.Solver(g, p32)
+    b.set_sweep(sweep)
     ca, na, ha = a.solve(1e-10, 400)
     cb, nb, hb = b.solve(1e-10, 400)
     assert ca == 0 and cb == 0
     ua, ub = a.get_state(), b.get_state()
     assert rel_err(ub, ua) < 1e-8
+
+
+@pytest.mark.parametrize("sweep", ["staged", "cta"])
+def test_mixed_ark_stage_update_tracks_fp64(sweep):
+    """ARK stage updates (u0 - alpha dt* z) through the FP32 sweeps: the cycle history follows
+    the FP64 one to FP32 accuracy."""
+    g = make_cgrid(64, 16)
+    import paper_1710_04875_gb300 as P
+    from tests.helpers import pair_params
+    kw = dict(scheme="ARK3J", nlevels=2, mach=0.5, alpha_deg=1.0, cfl=2.0, cfl_ramp=2.0)
+    _, p64 = pair_params(**kw)
+    _, p32 = pair_params(precision="mixed", **kw)
+    a, b = P.Solver(g, p64), P.Solver(g, p32)
+    b.set_sweep(sweep)
+    ha = np.array([a.fas_cycle(k) for k in range(15)])
+    hb = np.array([b.fas_cycle(k) for k in range(15)])
+    assert np.all(np.abs(hb - ha) <= 1e-4 * ha)
 
 
 def test_solver_reports_divergence_not_garbage():
@@ -194,16 +214,34 @@ def test_sweep_kinds_match_the_oracle(kind, scheme, ni, nj, nw):
     assert rel_err(zg, zo) < 1e-11
 
 
-def test_mixed_sweep_is_the_fp32_preconditioner():
-    """Mixed precision: the same operator applied in FP32 (loose tolerance)."""
-    g = make_cgrid(128, 32, n_wake=16, jitter=0.03, seed=1)
+@pytest.mark.parametrize("kind", ["staged", "cta", "strips"])
+@pytest.mark.parametrize("ni,nj,nw", [(128, 32, 16), (72, 20, 8), (16, 6, 2), (256, 64, 32), (128, 128, 16)])
+def test_mixed_sweep_is_the_fp32_preconditioner(kind, ni, nj, nw):
+    """Mixed precision: every FP32 sweep kernel applies the oracle's operator to FP32 accuracy,
+    including partial 8-row groups (nj = 20, 6) and the 128-row staged variant."""
+    g = make_cgrid(ni, nj, n_wake=nw, jitter=0.03, seed=ni + nj, wall_spacing=2e-3 if nj < 64 else 1e-4)
     o, s = make_pair(g, nlevels=1, d_cut=0.5, precision="mixed")
-    u = perturbed_state(0.8, 1.25, 32, 128, amp=0.05, seed=6)
+    s.set_sweep(kind)
+    u = perturbed_state(0.8, 1.25, nj, ni, amp=0.05, seed=6)
     o.set_state(u); s.set_state(u)
-    r = np.random.default_rng(8).standard_normal((4, 32, 128))
+    r = np.random.default_rng(8).standard_normal((4, nj, ni))
     zo, _ = o.precond_apply(r, 50.0)
     zg = s.precond_apply(r, 50.0)
     assert rel_err(zg, zo) < 1e-3
+
+
+def test_staged_and_cta_fp32_sweeps_agree():
+    """The two single-CTA FP32 sweeps differ only by FP32 rounding."""
+    g = make_cgrid(256, 64, n_wake=32, jitter=0.03, seed=5, wall_spacing=1e-4)
+    _, s = make_pair(g, nlevels=1, d_cut=0.5, precision="mixed")
+    u = perturbed_state(0.8, 1.25, 64, 256, amp=0.05, seed=6)
+    s.set_state(u)
+    r = np.random.default_rng(8).standard_normal((4, 64, 256))
+    s.set_sweep("staged")
+    za = s.precond_apply(r, 50.0)
+    s.set_sweep("cta")
+    zb = s.precond_apply(r, 50.0)
+    assert rel_err(za, zb) < 1e-4
 
 
 @pytest.mark.parametrize("kind", ["cta", "strips", "strips16"])
