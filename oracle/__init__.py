@@ -87,6 +87,7 @@ def lib():
             "or_get_mut": (None, [p, i, dp]),
             "or_compute_mut": (None, [p]),
             "or_residual": (None, [p, i, dp, dp, dp]),
+            "or_wall_force": (None, [p, dp, dp]),
             "or_pseudo_dt": (None, [p, i, d, dp]),
             "or_precond_apply": (None, [p, i, d, dp, dp, i, dp]),
             "or_face_blocks": (None, [p, i, dp, dp, dp, dp]),
@@ -232,6 +233,14 @@ class Oracle:
         F = np.zeros((4, nj, ni)); Fc = np.zeros_like(F); Fv = np.zeros_like(F)
         self.L.or_residual(self.h, l, _dp(F), _dp(Fc), _dp(Fv))
         return F, Fc, Fv
+
+    def wall_force(self):
+        """Per-wall-face force on the body (fx, fy), ni entries each (zero on the wake cut), from
+        the residual's own j = 0 face fluxes at the current state (finest level)."""
+        ni = self.grid.ni
+        fx = np.zeros(ni); fy = np.zeros(ni)
+        self.L.or_wall_force(self.h, _dp(fx), _dp(fy))
+        return fx, fy
 
     def pseudo_dt(self, cfl, l=None):
         l = self.finest if l is None else l

@@ -1464,6 +1464,29 @@ void or_residual(void* h, int l, double* F, double* Fc_out, double* Fv_out) {
     }
 }
 
+// Force on the body through each wall face (j = 0 off the wake cut) of the finest level: the
+// discrete momentum flux of the residual's j-face (central part minus dissipation minus the
+// viscous part), with the opposite sign because the face vector points into the fluid.
+// fx, fy: ni entries, zero on the cut.  The lift and drag objectives of the discrete adjoint
+// are built from these (force coefficients from the scheme's own wall fluxes).
+void or_wall_force(void* h, double* fx, double* fy) {
+  Solver* S = static_cast<Solver*>(h);
+  Level& g = S->lev[S->L()];
+  bc_fill(*S, g);
+  for (int i = 0; i < g.ni; ++i) {
+    if (g.cut(i)) {
+      fx[i] = fy[i] = 0.0;
+      continue;
+    }
+    const FaceFlux f = jst_face(*S, g.u[g.G(i, -2)], g.u[g.G(i, -1)], g.u[g.G(i, 0)], g.u[g.G(i, 1)],
+                                g.seta_x[g.FE(i, 0)], g.seta_y[g.FE(i, 0)], g.vfe[g.FE(i, 0)],
+                                rtilde(g, i, -1, 1), rtilde(g, i, 0, 1), true);
+    const V4 v = S->P.viscous ? visc_face(*S, g, i, 0) : V4{};
+    fx[i] = -(f.hc[1] - f.hd[1] - v[1]);
+    fy[i] = -(f.hc[2] - f.hd[2] - v[2]);
+  }
+}
+
 void or_pseudo_dt(void* h, int l, double cfl, double* dts) {
   Solver* S = static_cast<Solver*>(h);
   Level& g = S->lev[l];
