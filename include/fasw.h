@@ -179,6 +179,47 @@ int fasw_set_motion(fasw_ctx* ctx, double phi, double phidot, double xc, double 
 int fasw_dual_time_step(fasw_ctx* ctx, double dt, int bdf_order, double drop, int max_cycles, double* history,
                         int* ncycles);
 
+/* ---- Discrete adjoint of the steady residual on the finest level.  The primal method is the
+ * paper's; the adjoint is the standard one of F(u, X) = 0 with an objective J(u, X):
+ * (dF/du)^T lambda = (dJ/du)^T and dJ/dX = dJ/dX|_u - lambda^T dF/dX.  The eddy viscosity is
+ * frozen at its current value (no dependence of mu_t on u or X); fixed grid, steady (a_t = 0).
+ * Objectives: lift and drag coefficients (which = 0: C_L, 1: C_D) of the force the scheme's own
+ * wall-face fluxes (j = 0 faces off the wake cut: central flux minus dissipation minus viscous
+ * flux) exert on the body, for the free stream of the parameters (rho = 1, |v| = 1, chord 1).
+ * Vectors are 4 x nj x ni, component-major, like the state. */
+
+/* C_L and C_D at the current state.  Synchronizes. */
+int fasw_force_coefficients(fasw_ctx* ctx, double* cl, double* cd);
+/* Assembles J = dF/du at the current state by central differences with relative step h_rel
+ * (step h_rel * max(1, |u|) per unit), perturbing all cells of one colour at a time (a greedy
+ * colouring in which no residual stencil holds two cells of one colour), and the state
+ * gradients of C_L and C_D the same way.  The state is restored.  Synchronizes.
+ * Errors: FASW_ERR_ARG (moving grid, dual-time term set, h_rel <= 0), FASW_ERR_OOM. */
+int fasw_adjoint_jacobian(fasw_ctx* ctx, double h_rel);
+/* out = J v (transpose = 0) or J^T v (transpose != 0) with the assembled J. */
+int fasw_adjoint_apply(fasw_ctx* ctx, const double* v, double* out, int transpose, int on_device);
+/* State gradient dJ/du of objective `which` (as assembled with J). */
+int fasw_adjoint_objective_gradient(fasw_ctx* ctx, int which, double* g, int on_device);
+/* z = P^-T r with the adjoint preconditioner of fasw_adjoint_solve built at pseudo CFL cfl:
+ * P = S^-1 W, W the primal additive-W preconditioner (D+L) D^-1 (D+U), S = eta dt* per cell;
+ * so z = S (D+L)^-T D^T (D+U)^-T r.  Rebuilds the finest level's blocks and dt*. */
+int fasw_adjoint_precond_apply(fasw_ctx* ctx, double cfl, const double* r, double* z, int on_device);
+/* Solves J^T lam = g (g null: the gradient of objective `which`) by restarted GMRES(restart),
+ * right-preconditioned by the transpose of the primal preconditioner in additive-W form
+ * (section 4: flux-vector-split blocks with the eigenvalue cutoff at the parameters' cfl,
+ * symmetric Gauss-Seidel factors, transposed sweeps in i+j order) scaled by eta dt*, to
+ * relative residual tol or max_iters iterations; *iters and *rel_res report both.  Rebuilds
+ * the finest level's preconditioner blocks and dt* at the current state.
+ * Returns FASW_OK or FASW_ERR_NOT_CONVERGED (lam holds the last iterate). */
+int fasw_adjoint_solve(fasw_ctx* ctx, int which, const double* g, double* lam, double tol, int max_iters, int restart,
+                       int* iters, double* rel_res, int on_device);
+/* Shape gradient of objective `which` for nparam vertex fields: vy is nparam x (nj+1) x (ni+1)
+ * y-displacements per unit parameter (index k*(nj+1)*(ni+1) + j*(ni+1) + i);
+ * grad[k] = dJ/dX V_k - lam^T dF/dX V_k, both X-derivatives by central differences of step
+ * h_x along V_k at the current state.  The grid is restored.  grad is host memory. */
+int fasw_adjoint_shape_gradient(fasw_ctx* ctx, int which, const double* lam, int nparam, const double* vy, double h_x,
+                                double* grad, int on_device);
+
 /* Number of kernel launches the context has enqueued since creation (instrumentation). */
 long long fasw_launch_count(fasw_ctx* ctx);
 

@@ -1,0 +1,61 @@
+"""Shape sensitivities through the discrete adjoint, as a torch.autograd.Function.
+
+``ShapeForces.apply(p, ctx)`` returns the lift and drag coefficients of the steady solution on
+the grid deformed by the shape parameters p (a float64 tensor), and its backward pass gives
+dC/dp from the CUDA library's adjoint solves (``fasw_adjoint_*``).  The geometry is supplied by
+the caller: a function ``grid_of(p)`` that returns the deformed C-grid and the vertex fields
+dX/dp (y-displacements per unit parameter), so this module carries no shape parameterization.
+All numerics run in the library; this file only sequences calls and marshals arrays.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from .fasw import Solver
+
+
+class AdjointContext:
+    """Primal and adjoint settings shared by the forward and backward passes."""
+
+    def __init__(self, grid_of, fields, params, drop=1e-12, max_cycles=2000, h_rel=1e-6, h_x=1e-6,
+                 tol=1e-10, max_iters=1500, restart=60, warm_state=None):
+        self.grid_of = grid_of
+        self.fields = np.ascontiguousarray(fields, dtype=np.float64)
+        self.params = params
+        self.drop, self.max_cycles = drop, max_cycles
+        self.h_rel, self.h_x = h_rel, h_x
+        self.tol, self.max_iters, self.restart = tol, max_iters, restart
+        self.warm_state = warm_state
+        self.solver = None
+        self.info = {}
+
+
+class ShapeForces(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, p: torch.Tensor, actx: AdjointContext):
+        grid = actx.grid_of(p.detach().cpu().numpy())
+        s = Solver(grid, actx.params)
+        if actx.warm_state is not None:
+            s.set_state(actx.warm_state)
+        code, nc, hist = s.solve(actx.drop, actx.max_cycles)
+        actx.info["primal"] = (int(code), int(nc), float(hist[-1] / hist[0]) if len(hist) else None)
+        if actx.solver is not None:
+            actx.solver.close()
+        actx.solver = s
+        cl, cd = s.force_coefficients()
+        ctx.actx = actx
+        return torch.tensor([cl, cd], dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, gout: torch.Tensor):
+        a = ctx.actx
+        s = a.solver
+        s.adjoint_jacobian(a.h_rel)
+        grads = []
+        for which in (0, 1):
+            lam, code, it, rr = s.adjoint_solve(which, tol=a.tol, max_iters=a.max_iters, restart=a.restart)
+            a.info[("adjoint", which)] = (int(code), it, rr)
+            grads.append(s.adjoint_shape_gradient(which, lam, a.fields, a.h_x))
+        g = torch.tensor(np.stack(grads), dtype=torch.float64)  # (2, nparam)
+        return gout.to(torch.float64) @ g, None

@@ -1,0 +1,61 @@
+// Discrete adjoint of the steady finest-level residual (kernels_adjoint.cu): the Jacobian
+// dF/du by coloured central differences with the eddy viscosity frozen, its products with
+// vectors and its transpose, and a GMRES solve of the adjoint system preconditioned by the
+// transposed primal AW preconditioner.
+#pragma once
+#include <vector>
+
+#include "fasw_internal.cuh"
+
+namespace fasw {
+
+// Residual stencil slots of cell (i, j): 0 the cell, 1-4 i-2, i-1, i+1, i+2, 5-8 j-2, j-1, j+1,
+// j+2, 9 and 10 the wake-cut mirror cells (ni-1-i, 0) and (ni-1-i, 1).
+constexpr int ADJ_SLOTS = 11;
+
+struct AdjointDev {
+  int ni = 0, nj = 0, n = 0, ncolours = 0;
+  int* nbr = nullptr;      // n * ADJ_SLOTS neighbour cell or -1
+  int* col = nullptr;      // n colours
+  int* rev_ptr = nullptr;  // n + 1: entries (c, s) with nbr[c][s] = d, CSR by d
+  int* rev = nullptr;      // c * ADJ_SLOTS + s
+  double* J = nullptr;     // n * ADJ_SLOTS * 16, block (c, s) row-major dF_c / du_nbr
+  double* g = nullptr;     // 2 * 4n state gradients of C_L, C_D
+  double* ub = nullptr;    // 4n base state
+  double* Fp = nullptr;    // 4n residual scratch (+)
+  double* Fm = nullptr;    // 4n residual scratch (-)
+  double* fw = nullptr;    // 4 * ni wall forces fx+, fy+, fx-, fy-
+  double* parts = nullptr; // reduction partials
+  double* h_parts = nullptr;  // pinned host copy of the reduced values
+  double* kry = nullptr;   // (restart + 2) * 4n Krylov basis and work vectors
+  int restart = 0;
+  bool built = false;      // Jacobian assembled at the current state
+  LevelDev Lp{};           // finest level whose transfer blocks hold the preconditioner
+};
+
+// Host-side stencil, colouring and reverse map; allocates the device arrays (cudaMalloc).
+int adj_setup(AdjointDev& A, int ni, int nj, int nw, std::vector<void*>& allocs, cudaStream_t st);
+// J and the objective gradients at the current state of L (ghosts and auxiliaries are refilled).
+int adj_assemble(AdjointDev& A, const LevelDev& L, const PhysParams& ph, double h_rel, cudaStream_t st,
+                 long long& launches);
+void adj_apply(const AdjointDev& A, const double* v, double* out, int transpose, cudaStream_t st);
+// GMRES(restart) on J^T lam = g, right-preconditioned by the transposed primal AW
+// preconditioner built on L at pseudo CFL cfl (overwrites L's blocks and dt*); returns FASW_OK
+// or FASW_ERR_NOT_CONVERGED; *iters, *relres.
+int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const SchemeParams& sc, double cfl,
+              const double* g, double* lam, double tol, int max_iters, int restart, std::vector<void*>& allocs,
+              cudaStream_t st, int* iters, double* relres, long long& launches);
+// Lift and drag coefficients of the wall force at the current state (ghosts refilled).
+int adj_force_coefficients(AdjointDev& A, const LevelDev& L, const PhysParams& ph, cudaStream_t st, double* cl,
+                           double* cd, long long& launches);
+// Builds the primal AW blocks of L at pseudo CFL cfl (FP64) as the adjoint preconditioner, and
+// applies z = P^-T r with it (scratch: 4n).
+void adj_build_precond(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const SchemeParams& sc, double cfl,
+                       cudaStream_t st, long long& launches);
+void adj_precond(const AdjointDev& A, const double* r, double* scratch, double* z, cudaStream_t st);
+// out = x + a v (device vectors of length m).
+void adj_lincomb(int m, const double* x, double a, const double* v, double* out, cudaStream_t st);
+// Deterministic dot product of two device vectors of length m.
+int adj_dot(AdjointDev& A, const double* a, const double* b, int m, cudaStream_t st, double* out);
+
+}  // namespace fasw

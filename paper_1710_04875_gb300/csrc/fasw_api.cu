@@ -11,6 +11,7 @@
 #include "../../include/fasw.h"
 #include "fasw_internal.cuh"
 #include "fasw_sweep.cuh"
+#include "fasw_adjoint.cuh"
 #include "fasw_transfer.cuh"
 
 using namespace fasw;
@@ -78,6 +79,7 @@ struct fasw_ctx {
   double* d_un = nullptr;       // dual-time history of the finest level (4 x n)
   double* d_unm1 = nullptr;
   int steps_done = 0;
+  AdjointDev adj;               // discrete adjoint of the steady finest level (built on demand)
   int L() const { return (int)lev.size() - 1; }
 };
 
@@ -222,10 +224,11 @@ int level_sweep_kind(const fasw_ctx* c, const LevelDev& L) {
 void run_sweep(fasw_ctx* c, const LevelDev& L, int do_update, double alpha, const double* rhs) {
   if (c->sweep_kind == SWEEP_LEGACY) {
     launch_sgs(L, c->sc, c->mixed, do_update, alpha, rhs, nullptr, c->st);
+    ++c->launches;
     return;
   }
-  launch_sweep(L, c->mixed, level_sweep_kind(c, L), do_update, c->sc.aw, alpha, rhs, c->d_prog, c->d_err,
-               c->spin_limit, c->st);
+  c->launches += launch_sweep(L, c->mixed, level_sweep_kind(c, L), do_update, c->sc.aw, alpha, rhs, c->d_prog,
+                              c->d_err, c->spin_limit, c->st);
 }
 
 void bc_aux(fasw_ctx* c, int l, double cfl, int want_dts) {
@@ -264,7 +267,7 @@ void smooth_step(fasw_ctx* c, int l, double cfl, bool record_norm) {
       ++c->launches;
     }
     { Prof p(c, FASW_K_SGS); run_sweep(c, L, 1, sc.alpha[i - 1], L.rhs); }
-    c->launches += 2;
+    ++c->launches;  // the residual
   }
   // no ghost refill here: every consumer of the ghosts starts with its own fill (bc_aux)
 }
@@ -469,6 +472,7 @@ void fasw_destroy(fasw_ctx* c) {
   for (void* q : c->allocs) cudaFree(q);
   if (c->h_norm) cudaFreeHost(c->h_norm);
   if (c->h_err) cudaFreeHost(c->h_err);
+  if (c->adj.h_parts) cudaFreeHost(c->adj.h_parts);
   delete c;
 }
 
@@ -568,7 +572,6 @@ int fasw_precond_apply(fasw_ctx* c, int l, double cfl, const double* rin, double
     ++c->launches;
   }
   run_sweep(c, L, 0, 0.0, c->d_tmp2);
-  ++c->launches;
   const double* zsrc = L.yz64;
   if (c->mixed) {
     launch_f2d(L.yz32, c->d_tmp, (int)m, c->st);
@@ -657,6 +660,119 @@ int fasw_fas_cycle(fasw_ctx* c, int cycle_index, double* res_norm) {
   if (*c->h_err) return FASW_ERR_DEVICE_TIMEOUT;
   if (res_norm) *res_norm = *c->h_norm;
   return FASW_OK;
+}
+
+// ---- discrete adjoint (steady finest level, eddy viscosity frozen)
+static int adj_ready(fasw_ctx* c) {
+  if (c->adj.n) return FASW_OK;
+  const LevelDev& F = c->lev[c->L()];
+  return adj_setup(c->adj, F.ni, F.nj, F.nw, c->allocs, c->st);
+}
+
+int fasw_force_coefficients(fasw_ctx* c, double* cl, double* cd) {
+  if (!c || !cl || !cd) return FASW_ERR_ARG;
+  int r = adj_ready(c);
+  if (r) return r;
+  return adj_force_coefficients(c->adj, c->lev[c->L()], c->ph, c->st, cl, cd, c->launches);
+}
+
+int fasw_adjoint_jacobian(fasw_ctx* c, double h_rel) {
+  if (!c || !(h_rel > 0.0) || c->ph.moving || c->lev[c->L()].a_t != 0.0) return FASW_ERR_ARG;
+  int r = adj_ready(c);
+  if (r) return r;
+  r = adj_assemble(c->adj, c->lev[c->L()], c->ph, h_rel, c->st, c->launches);
+  if (r) return r;
+  return sync(c);
+}
+
+int fasw_adjoint_apply(fasw_ctx* c, const double* v, double* out, int transpose, int on_device) {
+  if (!c || !v || !out || !c->adj.built) return FASW_ERR_ARG;
+  const size_t m = 4 * (size_t)c->adj.n;
+  int r = copy_in(c, c->d_tmp, v, m, on_device);
+  if (r) return r;
+  adj_apply(c->adj, c->d_tmp, c->d_tmp2, transpose, c->st);
+  ++c->launches;
+  r = copy_out(c, out, c->d_tmp2, m, on_device);
+  if (r) return r;
+  return sync(c);
+}
+
+int fasw_adjoint_objective_gradient(fasw_ctx* c, int which, double* g, int on_device) {
+  if (!c || !g || which < 0 || which > 1 || !c->adj.built) return FASW_ERR_ARG;
+  const size_t m = 4 * (size_t)c->adj.n;
+  int r = copy_out(c, g, c->adj.g + which * m, m, on_device);
+  if (r) return r;
+  return sync(c);
+}
+
+int fasw_adjoint_precond_apply(fasw_ctx* c, double cfl, const double* r, double* z, int on_device) {
+  if (!c || !r || !z || !(cfl > 0.0) || c->ph.moving) return FASW_ERR_ARG;
+  int e = adj_ready(c);
+  if (e) return e;
+  const size_t m = 4 * (size_t)c->adj.n;
+  if ((e = copy_in(c, c->d_tmp, r, m, on_device))) return e;
+  adj_build_precond(c->adj, c->lev[c->L()], c->ph, c->sc, cfl, c->st, c->launches);
+  adj_precond(c->adj, c->d_tmp, c->adj.Fp, c->d_tmp2, c->st);
+  c->launches += 2;
+  if ((e = copy_out(c, z, c->d_tmp2, m, on_device))) return e;
+  return sync(c);
+}
+
+int fasw_adjoint_solve(fasw_ctx* c, int which, const double* g, double* lam, double tol, int max_iters, int restart,
+                       int* iters, double* rel_res, int on_device) {
+  if (!c || !lam || !iters || !rel_res || !c->adj.built || !(tol > 0.0) || max_iters < 1) return FASW_ERR_ARG;
+  if (!g && (which < 0 || which > 1)) return FASW_ERR_ARG;
+  const size_t m = 4 * (size_t)c->adj.n;
+  const double* rhs = c->adj.g + (which < 0 ? 0 : which) * m;
+  if (g) {
+    int r = copy_in(c, c->d_tmp, g, m, on_device);
+    if (r) return r;
+    rhs = c->d_tmp;
+  }
+  const int code = adj_solve(c->adj, c->lev[c->L()], c->ph, c->sc, c->prm.cfl, rhs, c->d_tmp2, tol, max_iters,
+                             restart, c->allocs, c->st, iters, rel_res, c->launches);
+  if (code != FASW_OK && code != FASW_ERR_NOT_CONVERGED) return code;
+  int r = copy_out(c, lam, c->d_tmp2, m, on_device);
+  if (r) return r;
+  r = sync(c);
+  return r ? r : code;
+}
+
+int fasw_adjoint_shape_gradient(fasw_ctx* c, int which, const double* lam, int nparam, const double* vy, double h_x,
+                                double* grad, int on_device) {
+  if (!c || !lam || !vy || !grad || nparam < 1 || which < 0 || which > 1 || !(h_x > 0.0) || c->ph.moving)
+    return FASW_ERR_ARG;
+  int r = adj_ready(c);
+  if (r) return r;
+  LevelDev& F = c->lev[c->L()];
+  const size_t m = 4 * (size_t)F.n, nv = (size_t)(F.ni + 1) * (F.nj + 1);
+  if ((r = copy_in(c, c->d_tmp, lam, m, on_device))) return r;
+  double* ytmp = c->d_tmp3;
+  double* vk = c->d_tmp3 + nv;
+  ResArgs a{};
+  a.mode = RES_FULL;
+  for (int k = 0; k < nparam; ++k) {
+    if ((r = copy_in(c, vk, vy + (size_t)k * nv, nv, on_device))) return r;
+    double cl[2], cd[2];
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      adj_lincomb((int)nv, c->d_y0, sgn == 0 ? h_x : -h_x, vk, ytmp, c->st);
+      launch_metrics_fine(F, c->d_x0, ytmp, c->st);
+      launch_bc_aux(F, c->ph, 1.0, 0, c->st);
+      a.F = sgn == 0 ? c->adj.Fp : c->adj.Fm;
+      launch_residual(F, c->ph, a, c->st);
+      c->launches += 4;
+      if ((r = adj_force_coefficients(c->adj, F, c->ph, c->st, &cl[sgn], &cd[sgn], c->launches))) return r;
+    }
+    adj_lincomb((int)m, c->adj.Fp, -1.0, c->adj.Fm, c->d_tmp2, c->st);  // F+ - F-
+    double dot = 0.0;
+    if ((r = adj_dot(c->adj, c->d_tmp, c->d_tmp2, (int)m, c->st, &dot))) return r;
+    const double dJ = which == 0 ? cl[0] - cl[1] : cd[0] - cd[1];
+    grad[k] = (dJ - dot) / (2.0 * h_x);
+  }
+  launch_metrics_fine(F, c->d_x0, c->d_y0, c->st);
+  launch_bc_aux(F, c->ph, 1.0, 0, c->st);
+  c->launches += 2;
+  return sync(c);
 }
 
 int fasw_set_sweep(fasw_ctx* c, int kind) {

@@ -105,6 +105,8 @@ void launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, 
 int residual_blocks(const LevelDev& L);
 void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* out, cudaStream_t st);
 void launch_bl(const LevelDev& L, const PhysParams& ph, cudaStream_t st);
+// per-wall-face force on the body from the j = 0 face fluxes (ghosts and auxiliaries current)
+void launch_wall_force(const LevelDev& L, const PhysParams& ph, double* fx, double* fy, cudaStream_t st);
 
 // ---- launchers (kernels_sgs.cu)
 void launch_face_blocks(const LevelDev& L, const PhysParams& ph, const SchemeParams& sc, int mixed, cudaStream_t st);

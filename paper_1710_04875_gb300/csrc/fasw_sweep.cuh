@@ -10,7 +10,8 @@ enum SweepKind { SWEEP_AUTO = 0, SWEEP_LEGACY = 1, SWEEP_CTA = 2, SWEEP_STRIPS =
 void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st);
 // Forward and backward sweep of one stage: y = (D+L)^-1 rhs, z = (D+U)^-1 D y into L.yz64 /
 // L.yz32, with the stage update u = u0 - alpha z (AW) or u0 - alpha dt* z (ARK) when
-// do_update.  prog: 2 * sweep_strips(L) flags, err: device error word.
+// do_update.  prog: 2 * sweep_strips(L) flags, err: device error word.  Returns the number of
+// kernels launched.
 int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, double alpha, const double* rhs,
                  long long* prog, int* err, long long limit, cudaStream_t st);
 int sweep_strips(const LevelDev& L);

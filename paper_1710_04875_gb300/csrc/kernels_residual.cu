@@ -146,54 +146,77 @@ __device__ void ghost_state(const LevelDev& L, const PhysParams& ph, int gi, int
   }
 }
 
-// Ghost fill alone: one thread per ghost cell of the two layers (corners untouched).
-__global__ void k_bc(LevelDev L, PhysParams ph) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+// Ghost cell t of the two layers around the domain (corners excluded): rows j = -1, -2, rows
+// j = nj, nj+1, columns i = -1, -2, columns i = ni, ni+1; false past the last one.
+__device__ __forceinline__ bool ghost_of(const LevelDev& L, int t, int& gi, int& gj) {
   const int ni = L.ni, nj = L.nj;
-  int gi, gj;
-  if (t < 2 * ni) {  // rows j = -1, -2
+  if (t < 2 * ni) {
     gi = t % ni;
     gj = -1 - t / ni;
-  } else if (t < 4 * ni) {  // rows j = nj, nj + 1
+  } else if (t < 4 * ni) {
     gi = (t - 2 * ni) % ni;
     gj = nj + (t - 2 * ni) / ni;
-  } else if (t < 4 * ni + 2 * nj) {  // columns i = -1, -2
+  } else if (t < 4 * ni + 2 * nj) {
     gj = (t - 4 * ni) % nj;
     gi = -1 - (t - 4 * ni) / nj;
-  } else if (t < 4 * ni + 4 * nj) {  // columns i = ni, ni + 1
+  } else if (t < 4 * ni + 4 * nj) {
     gj = (t - 4 * ni - 2 * nj) % nj;
     gi = ni + (t - 4 * ni - 2 * nj) / nj;
   } else {
-    return;
+    return false;
   }
+  return true;
+}
+
+// Ghost fill alone: one thread per ghost cell of the two layers.
+__global__ void k_bc(LevelDev L, PhysParams ph) {
+  int gi, gj;
+  if (!ghost_of(L, blockIdx.x * blockDim.x + threadIdx.x, gi, gj)) return;
   double g[4];
   ghost_state(L, ph, gi, gj, g);
   store4(L, gidx(L, gi, gj), g);
 }
 
-// Pressure and sensor quantity on the ghosted domain; Martinelli radii and dt* on the interior.
-// With fill_ghosts, ghost threads first compute and store their boundary value (it depends
-// on interior cells only), so ghost fill and auxiliaries take one launch.
-__global__ void k_cell_aux(LevelDev L, PhysParams ph, double cfl, int want_dts, int fill_ghosts) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= L.Gn) return;
-  const int gi = t % L.P - 2, gj = t / L.P - 2;
-  double w[4];
-  const bool gx = gi < 0 || gi >= L.ni, gy = gj < 0 || gj >= L.nj;
-  if (fill_ghosts && (gx != gy)) {  // ghost, not a corner
-    ghost_state(L, ph, gi, gj, w);
-    store4(L, t, w);
-  } else {
-    load4(L, t, w);
+// Pressure, 1/rho and sensor quantity of one (ghosted) cell.
+__device__ __forceinline__ void cell_thermo(const LevelDev& L, const PhysParams& ph, int g, const double w[4],
+                                            double& rr, double& u, double& v, double& p) {
+  rr = 1.0 / w[0];
+  u = w[1] * rr;
+  v = w[2] * rr;
+  p = (GAM - 1.0) * (w[3] - 0.5 * (w[1] * u + w[2] * v));
+  L.p[g] = p;
+  L.rinv[g] = rr;
+  L.q[g] = ph.sensor ? p / pow(w[0], GAM) : p;
+}
+
+// Auxiliaries: blocks [0, nbi) take the interior cells (pressure, 1/rho, sensor quantity,
+// Martinelli radii, dt*), the blocks after them the ghost cells (with fill_ghosts their
+// boundary value first, which depends on interior cells only; then pressure, 1/rho, sensor).
+// Interior and ghost work never share a warp, so neither path waits on the other's FP64 chain.
+__global__ void k_cell_aux(LevelDev L, PhysParams ph, double cfl, int want_dts, int fill_ghosts, int nbi) {
+  if ((int)blockIdx.x >= nbi) {
+    int gi, gj;
+    if (!ghost_of(L, (blockIdx.x - nbi) * blockDim.x + threadIdx.x, gi, gj)) return;
+    const int g = gidx(L, gi, gj);
+    double w[4];
+    if (fill_ghosts) {
+      ghost_state(L, ph, gi, gj, w);
+      store4(L, g, w);
+    } else {
+      load4(L, g, w);
+    }
+    double rr, u, v, p;
+    cell_thermo(L, ph, g, w, rr, u, v, p);
+    return;
   }
-  const double rr = 1.0 / w[0];
-  const double u = w[1] * rr, v = w[2] * rr;
-  const double p = (GAM - 1.0) * (w[3] - 0.5 * (w[1] * u + w[2] * v));
-  L.p[t] = p;
-  L.rinv[t] = rr;
-  L.q[t] = ph.sensor ? p / pow(w[0], GAM) : p;
-  if (gi < 0 || gi >= L.ni || gj < 0 || gj >= L.nj) return;
-  const int i = gi, j = gj, ni = L.ni;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  const int ni = L.ni, i = c % ni, j = c / ni;
+  const int g = gidx(L, i, j);
+  double w[4];
+  load4(L, g, w);
+  double rr, u, v, p;
+  cell_thermo(L, ph, g, w, rr, u, v, p);
   const double a = sqrt(GAM * p * rr);
   const int fw = j * (ni + 1) + i, fs = j * ni + i;
   const double sx = 0.5 * (L.sxi[fw] + L.sxi[fw + 1]);
@@ -204,7 +227,6 @@ __global__ void k_cell_aux(LevelDev L, PhysParams ph, double cfl, int want_dts, 
   const double ve = 0.5 * (L.vfe[fs] + L.vfe[fs + ni]);
   const double rxi = fabs(u * sx + v * sy - vx) + a * sqrt(sx * sx + sy * sy);
   const double reta = fabs(u * ex + v * ey - ve) + a * sqrt(ex * ex + ey * ey);
-  const int c = j * ni + i;
   // Martinelli scaling: (r_eta/r_xi)^(2/3) = cr^2 with cr the cube root of the ratio, and the
   // other direction's factor is 1/cr^2 (one cbrt instead of two pow).
   const double cr = cbrt(reta / rxi), t2 = cr * cr;
@@ -453,6 +475,29 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(LevelDev L, PhysParams
   }
 }
 
+// Force on the body through each wall face (j = 0 off the wake cut): the residual's own
+// j-face flux (central part minus dissipation minus viscous part) with the opposite sign,
+// since the face vector points into the fluid.  fx, fy: ni entries, zero on the cut.
+__global__ void k_wall_force(LevelDev L, PhysParams ph, double* fx, double* fy) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.ni) return;
+  if (on_cut(L, i)) {
+    fx[i] = fy[i] = 0.0;
+    return;
+  }
+  const double sx = L.seta[i], sy = L.seta[L.nfe + i];
+  double hc[4], hd[4];
+  jst_face(L, gidx(L, i, -2), gidx(L, i, -1), gidx(L, i, 0), gidx(L, i, 1), sx, sy, L.vfe[i], rt_cell(L, i, -1, 1),
+           rt_cell(L, i, 0, 1), ph.s_coarse, hc, hd);
+  if (ph.viscous) {
+    double hv[4];
+    visc_face(L, ph, i, 0, sx, sy, hv);
+    for (int k = 0; k < 4; ++k) hd[k] += hv[k];
+  }
+  fx[i] = -(hc[1] - hd[1]);
+  fy[i] = -(hc[2] - hd[2]);
+}
+
 __global__ void k_norm_final(const double* part, int nparts, double count, double* out) {
   __shared__ double wsum[8];
   double s = 0.0;
@@ -561,11 +606,17 @@ void launch_bc(const LevelDev& L, const PhysParams& ph, cudaStream_t st) {
 }
 
 void launch_cell_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st) {
-  k_cell_aux<<<(L.Gn + 63) / 64, 64, 0, st>>>(L, ph, cfl, want_dts, 0);
+  const int nbi = (L.n + 63) / 64, nbg = (4 * (L.ni + L.nj) + 63) / 64;
+  k_cell_aux<<<nbi + nbg, 64, 0, st>>>(L, ph, cfl, want_dts, 0, nbi);
 }
 
 void launch_bc_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st) {
-  k_cell_aux<<<(L.Gn + 63) / 64, 64, 0, st>>>(L, ph, cfl, want_dts, 1);
+  const int nbi = (L.n + 63) / 64, nbg = (4 * (L.ni + L.nj) + 63) / 64;
+  k_cell_aux<<<nbi + nbg, 64, 0, st>>>(L, ph, cfl, want_dts, 1, nbi);
+}
+
+void launch_wall_force(const LevelDev& L, const PhysParams& ph, double* fx, double* fy, cudaStream_t st) {
+  k_wall_force<<<(L.ni + 63) / 64, 64, 0, st>>>(L, ph, fx, fy);
 }
 
 int residual_blocks(const LevelDev& L) { return ((L.ni + TX - 1) / TX) * ((L.nj + TY - 1) / TY); }

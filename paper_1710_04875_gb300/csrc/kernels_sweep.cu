@@ -518,117 +518,181 @@ __global__ void k_hp_cy(LevelDev L, const float* dinv, const double* rhs) {
   *reinterpret_cast<float4*>(L.hpC + 4 * ((size_t)(i + j) * L.nj + j)) = make_float4(y[0], y[1], y[2], y[3]);
 }
 
-// Shared memory (float4 units): ring [STAGES][4][nt], exchange [2][njp+1], row 0 [ni],
-// lower-wake G_S rows [nw][4].
+// Shared memory: ring of STAGES steps, each [2][nt] float4 block rows + [nt] floats (the
+// thread's D^-1 r or y component); exchange [2][njp+1] float4; row 0 [ni] float4; lower-wake
+// G_S rows [nw][4] float4.
 inline size_t hp_smem_bytes(int stages, int nt, int njp, int ni, int nw) {
-  return 16 * ((size_t)stages * 4 * nt + 2 * (size_t)(njp + 1) + (size_t)ni + 4 * (size_t)nw);
+  return (size_t)stages * 36 * nt + 16 * (2 * (size_t)(njp + 1) + (size_t)ni + 4 * (size_t)nw);
 }
 
+// The sweep proper: y (forward) and z (backward, written over y in hpY).  No FP64 work and
+// no per-cell update inside the recurrence; k_hp_finish applies the stage update afterwards.
+// The step loop is unrolled by the ring depth, so ring slots and exchange buffers are fixed
+// shared-memory offsets, and the global sources advance by one hyperplane per issue.
 template <int STAGES>
-__global__ void __launch_bounds__(512) k_sweep_hp(LevelDev L, int do_update, int aw, double alpha) {
+__global__ void __launch_bounds__(512) k_sweep_hp(LevelDev L) {
+  static_assert((STAGES & (STAGES - 1)) == 0 && STAGES >= 4, "ring depth: power of two, at least 4");
   extern __shared__ float4 sm4[];
   const int nt = blockDim.x, tid = threadIdx.x;
   const int j = tid >> 2, q = tid & 3, njp = nt >> 2;
-  const int ni = L.ni, nj = L.nj, n = L.n, nw = L.nw;
+  const int ni = L.ni, nj = L.nj, nw = L.nw;
   const int K = ni + nj - 1;
+  const int stage_f4 = 2 * nt + nt / 4;  // float4 units per ring stage (nt is a multiple of 32)
   float4* ring = sm4;
-  float4* xb = ring + (size_t)STAGES * 4 * nt;
+  float4* xb = ring + (size_t)STAGES * stage_f4;
   float4* row0 = xb + 2 * (njp + 1);
   float4* gsm = row0 + ni;
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int x = tid; x < 2 * (njp + 1); x += nt) xb[x] = zero4;
 
+  float4* myA = ring + tid;       // block row q of the first block of this thread's cell
+  float4* myB = ring + nt + tid;  // of the second block
+  float* myC = reinterpret_cast<float*>(ring + 2 * nt) + tid;
+  const int cstride = 4 * stage_f4;  // floats per ring stage
+  float4* xj = xb + j;               // exchange entries of this row (buffer 0; buffer 1 at + njp + 1)
+  const int xo = njp + 1;
+
+  // Hyperplane k holds entry (k, j) = k * nj + j.  Padding threads (j >= nj) point at the
+  // array start and only ever zero-fill.
+  const bool rowok = j < nj;
+  const size_t e0 = rowok ? (size_t)j : 0;
+  const size_t s32 = 32 * (size_t)nj, s4 = 4 * (size_t)nj;
+  auto valid_at = [&](int k) { return rowok && (unsigned)(k - j) < (unsigned)ni; };
+
   // ---------------- forward: y = D^-1 r + G_W y_W + G_S y_S
-  auto fissue = [&](int k) {
-    float4* slot = ring + (size_t)(k & (STAGES - 1)) * 4 * nt;
-    const int i = k - j;
-    const bool v = k < K && j < nj && i >= 0 && i < ni;
-    const size_t h = v ? (size_t)k * nj + j : 0;
-    cp_async16(&slot[tid], L.hpF + 32 * h + 4 * q, v);
-    cp_async16(&slot[nt + tid], L.hpF + 32 * h + 16 + 4 * q, v);
-    cp_async4(&slot[2 * nt + tid], L.hpC + 4 * h + q, v);
-    cp_commit();
-  };
+  {
+    const float* bW = L.hpF + 32 * e0 + 4 * q;
+    const float* bC = L.hpC + 4 * e0 + q;
+    const float* iW = bW;
+    const float* iC = bC;
+    int ki = 0;
+    auto issue = [&](int u) {
+      const bool v = valid_at(ki);
+      const float* w = v ? iW : bW;
+      cp_async16(myA + u * stage_f4, w, v);
+      cp_async16(myB + u * stage_f4, w + 16, v);
+      cp_async4(myC + u * cstride, v ? iC : bC, v);
+      cp_commit();
+      ++ki;
+      iW += s32;
+      iC += s4;
+    };
+    // steps 0 .. STAGES-2 in flight; step k refills the slot step k-1 used with step
+    // k + STAGES - 1, right after its own operands are read, so the issue overlaps their latency
 #pragma unroll
-  for (int k = 0; k < STAGES; ++k) fissue(k);
-  __syncthreads();
-  for (int k = 0; k < K; ++k) {
-    cp_wait<STAGES - 1>();
-    const float4* slot = ring + (size_t)(k & (STAGES - 1)) * 4 * nt;
-    const float4 gw = slot[tid], gs = slot[nt + tid];
-    const float cy = slot[2 * nt + tid].x;
-    const float4* prev = xb + ((k + 1) & 1) * (njp + 1);
-    float4* cur = xb + (k & 1) * (njp + 1);
-    const int i = k - j;
-    float4 ys = zero4;
-    if (j > 0) {
-      ys = prev[j - 1];
-    } else if (nw > 0 && i >= ni - nw && i < ni) {  // lower-half mirror of the upper wake cell
-      ys = row0[ni - 1 - i];
-    }
-    const float y = cy + (dot4(gw, prev[j]) + dot4(gs, ys));
-    set_comp(cur[j], q, y);
-    if (j < nj && i >= 0 && i < ni) {
-      L.hpY[4 * ((size_t)k * nj + j) + q] = y;
-      if (j == 0) set_comp(row0[i], q, y);
-    }
+    for (int u = 0; u < STAGES - 1; ++u) issue(u);
     __syncthreads();
-    fissue(k + STAGES);
+    float* pY = L.hpY + 4 * e0 + q;
+    const bool mirror_row = j == 0 && nw > 0;
+    for (int k0 = 0; k0 < K; k0 += STAGES) {
+#pragma unroll
+      for (int u = 0; u < STAGES; ++u) {
+        const int k = k0 + u;
+        if (k < K) {  // uniform
+          cp_wait<STAGES - 2>();
+          const float4 ga = myA[u * stage_f4], gb = myB[u * stage_f4];
+          const float cy = myC[u * cstride];
+          const int pv = ((u + 1) & 1) * xo, cu = (u & 1) * xo;  // k0 is even
+          const float4 yw = xj[pv];
+          float4 ys = zero4;
+          if (j > 0) {
+            ys = xj[pv - 1];
+          } else if (mirror_row && k >= ni - nw && k < ni) {  // row 0, i = k: lower-half mirror
+            ys = row0[ni - 1 - k];
+          }
+          issue((u + STAGES - 1) & (STAGES - 1));
+          const float y = cy + (dot4(ga, yw) + dot4(gb, ys));
+          set_comp(xj[cu], q, y);
+          if (valid_at(k)) {
+            *pY = y;
+            if (j == 0) set_comp(row0[k], q, y);
+          }
+          __syncthreads();
+          pY += s4;
+        }
+      }
+    }
+    cp_wait<0>();
   }
-  cp_wait<0>();
   __threadfence_block();
 
   // ---------------- backward: z = y + H_E z_E + H_N z_N (+ G_S z_mirror on the lower wake)
   for (int x = tid; x < 2 * (njp + 1); x += nt) xb[x] = zero4;
   for (int x = tid; x < 4 * nw; x += nt) {
-    const int i = x >> 2, r = x & 3;  // cell (i, 0) is entry h = i
+    const int i = x >> 2, r = x & 3;  // cell (i, 0) is entry h = i * nj
     gsm[x] = *reinterpret_cast<const float4*>(L.hpF + 32 * (size_t)i * nj + 16 + 4 * r);
   }
-  auto bissue = [&](int kk) {
-    float4* slot = ring + (size_t)(kk & (STAGES - 1)) * 4 * nt;
-    const int k = K - 1 - kk, i = k - j;
-    const bool v = kk < K && j < nj && i >= 0 && i < ni;
-    const size_t h = v ? (size_t)k * nj + j : 0;
-    const size_t c = v ? (size_t)j * ni + i : 0;
-    cp_async16(&slot[tid], L.hpB + 32 * h + 4 * q, v);
-    cp_async16(&slot[nt + tid], L.hpB + 32 * h + 16 + 4 * q, v);
-    cp_async4(&slot[2 * nt + tid], L.hpY + 4 * h + q, v);
-    if (do_update) {
-      cp_async8(&slot[3 * nt + tid], L.u0 + (size_t)q * n + c, v);
-      cp_async8(reinterpret_cast<char*>(&slot[3 * nt + tid]) + 8, L.dts + c, v && !aw);
-    }
-    cp_commit();
-  };
+  __syncthreads();  // the forward's y (same thread) and the shared arrays are in place
+  {
+    const float* bE = L.hpB + 32 * e0 + 4 * q;
+    const float* bY = L.hpY + 4 * e0 + q;
+    const float* iE = bE + s32 * (size_t)(K - 1);
+    const float* iY = bY + s4 * (size_t)(K - 1);
+    int ki = K - 1;
+    auto issue = [&](int u) {
+      const bool v = valid_at(ki);
+      const float* e = v ? iE : bE;
+      cp_async16(myA + u * stage_f4, e, v);
+      cp_async16(myB + u * stage_f4, e + 16, v);
+      cp_async4(myC + u * cstride, v ? iY : bY, v);
+      cp_commit();
+      --ki;
+      iE -= s32;
+      iY -= s4;
+    };
 #pragma unroll
-  for (int kk = 0; kk < STAGES; ++kk) bissue(kk);
-  __syncthreads();
-  for (int kk = 0; kk < K; ++kk) {
-    cp_wait<STAGES - 1>();
-    const float4* slot = ring + (size_t)(kk & (STAGES - 1)) * 4 * nt;
-    const float4 he = slot[tid], hn = slot[nt + tid];
-    const float yv = slot[2 * nt + tid].x;
-    const float4* prev = xb + ((kk + 1) & 1) * (njp + 1);
-    float4* cur = xb + (kk & 1) * (njp + 1);
-    const int k = K - 1 - kk, i = k - j;
-    const bool valid = j < nj && i >= 0 && i < ni;
-    float z = yv + (dot4(he, prev[j]) + dot4(hn, prev[j + 1]));
-    if (j == 0 && i < nw && i >= 0) z += dot4(gsm[4 * i + q], row0[ni - 1 - i]);
-    set_comp(cur[j], q, z);
-    if (valid) {
-      if (j == 0) set_comp(row0[i], q, z);
-      const size_t c = (size_t)j * ni + i;
-      if (do_update) {
-        const double2 ud = *reinterpret_cast<const double2*>(&slot[3 * nt + tid]);
-        const double sc = aw ? alpha : alpha * ud.y;
-        L.u[(size_t)q * L.Gn + (j + 2) * L.P + (i + 2)] = ud.x - sc * double(z);
-      } else {
-        L.yz32[(size_t)q * n + c] = z;
+    for (int u = 0; u < STAGES - 1; ++u) issue(u);
+    __syncthreads();
+    float* pZ = L.hpY + 4 * e0 + q + s4 * (size_t)(K - 1);
+    for (int kk0 = 0; kk0 < K; kk0 += STAGES) {
+#pragma unroll
+      for (int u = 0; u < STAGES; ++u) {
+        const int kk = kk0 + u;
+        if (kk < K) {  // uniform
+          cp_wait<STAGES - 2>();
+          const float4 he = myA[u * stage_f4], hn = myB[u * stage_f4];
+          const float yv = myC[u * cstride];
+          const int pv = ((u + 1) & 1) * xo, cu = (u & 1) * xo;
+          const int k = K - 1 - kk;
+          const float4 ze = xj[pv], zn = xj[pv + 1];
+          float4 gm = zero4, zm = zero4;
+          if (j == 0 && k < nw) {  // row 0, i = k: upper-half mirror
+            gm = gsm[4 * k + q];
+            zm = row0[ni - 1 - k];
+          }
+          issue((u + STAGES - 1) & (STAGES - 1));
+          const float z = yv + (dot4(he, ze) + dot4(hn, zn)) + dot4(gm, zm);
+          set_comp(xj[cu], q, z);
+          if (valid_at(k)) {
+            *pZ = z;
+            if (j == 0) set_comp(row0[k], q, z);
+          }
+          __syncthreads();
+          pZ -= s4;
+        }
       }
     }
-    __syncthreads();
-    bissue(kk + STAGES);
+    cp_wait<0>();
   }
-  cp_wait<0>();
+}
+
+// After the sweep: the stage update u = u^(0) - alpha z (AW) or u^(0) - alpha dt* z (ARK) in
+// FP64, or (no update) z to the natural-layout FP32 vector.
+__global__ void k_hp_finish(LevelDev L, int do_update, int aw, double alpha) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  const int n = L.n, i = c % L.ni, j = c / L.ni;
+  const float4 z = *reinterpret_cast<const float4*>(L.hpY + 4 * ((size_t)(i + j) * L.nj + j));
+  const float zz[4] = {z.x, z.y, z.z, z.w};
+  if (do_update) {
+    const double sc = aw ? alpha : alpha * L.dts[c];
+    const size_t g = (size_t)(j + 2) * L.P + (i + 2);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) L.u[q * (size_t)L.Gn + g] = L.u0[q * (size_t)n + c] - sc * double(zz[q]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) L.yz32[q * (size_t)n + c] = zz[q];
+  }
 }
 
 }  // namespace
@@ -644,7 +708,7 @@ void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st) {
 
 namespace {
 int hp_threads(int nj) { return 4 * ((nj + 7) / 8 * 8); }
-int hp_stages(int nt) { return nt <= 256 ? 8 : 4; }
+int hp_stages(int nt) { return nt <= 256 ? 8 : 4; }  // 512 threads: ring of 4 keeps shared memory < 227 KB
 constexpr size_t kHpSmemMax = 227 * 1024;
 }  // namespace
 
@@ -659,7 +723,7 @@ bool hp_fits(int ni, int nj, int nw) {
 int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, double alpha, const double* rhs,
                  long long* prog, int* err, long long limit, cudaStream_t st) {
   if (kind == SWEEP_HP && mixed && L.hpF) {
-    k_hp_cy<<<(L.n + 255) / 256, 256, 0, st>>>(L, reinterpret_cast<const float*>(L.tb), rhs);
+    k_hp_cy<<<(L.n + 127) / 128, 128, 0, st>>>(L, reinterpret_cast<const float*>(L.tb), rhs);
     const int nt = hp_threads(L.nj), stages = hp_stages(nt);
     const size_t sm = hp_smem_bytes(stages, nt, nt / 4, L.ni, L.nw);
     if (stages == 8) {
@@ -668,16 +732,17 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
         cudaFuncSetAttribute(k_sweep_hp<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHpSmemMax);
         attr8 = true;
       }
-      k_sweep_hp<8><<<1, nt, sm, st>>>(L, do_update, aw, alpha);
+      k_sweep_hp<8><<<1, nt, sm, st>>>(L);
     } else {
       static bool attr4 = false;
       if (!attr4) {
         cudaFuncSetAttribute(k_sweep_hp<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHpSmemMax);
         attr4 = true;
       }
-      k_sweep_hp<4><<<1, nt, sm, st>>>(L, do_update, aw, alpha);
+      k_sweep_hp<4><<<1, nt, sm, st>>>(L);
     }
-    return 0;
+    k_hp_finish<<<(L.n + 63) / 64, 64, 0, st>>>(L, do_update, aw, alpha);
+    return 3;
   }
   if (kind == SWEEP_HP) kind = mixed ? SWEEP_CTA : SWEEP_STRIPS;
   const int cells = L.ni < L.nj ? L.ni : L.nj;  // longest hyperplane
@@ -704,7 +769,7 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
       }
       k_sweep_cta<double><<<1, threads, sm, st>>>(L, L.tb, L.yz64, rhs, do_update, aw, alpha);
     }
-    return 0;
+    return 1;
   }
   // Strips wait on one another: at most ceil(nj / SH) CTAs of 16*SH threads, launched on the
   // library's single stream after the previous kernel has finished, so all of them are
@@ -725,7 +790,7 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
     else
       k_sweep_strips<double, 8><<<nb, 128, 0, st>>>(L, L.tb, L.yz64, rhs, prog, err, limit, do_update, aw, alpha);
   }
-  return 0;
+  return 1;
 }
 
 int sweep_strips(const LevelDev& L) { return (L.nj + 7) / 8; }

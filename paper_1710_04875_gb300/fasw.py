@@ -85,6 +85,13 @@ def library():
             "fasw_set_motion": (i, [p, d, d, d, d]),
             "fasw_dual_time_step": (i, [p, d, i, d, i, dp, C.POINTER(i)]),
             "fasw_kernel_time": (i, [p, i, C.POINTER(ll), C.POINTER(d)]),
+            "fasw_force_coefficients": (i, [p, C.POINTER(d), C.POINTER(d)]),
+            "fasw_adjoint_jacobian": (i, [p, d]),
+            "fasw_adjoint_apply": (i, [p, dp, dp, i, i]),
+            "fasw_adjoint_objective_gradient": (i, [p, i, dp, i]),
+            "fasw_adjoint_solve": (i, [p, i, dp, dp, d, i, i, C.POINTER(i), C.POINTER(d), i]),
+            "fasw_adjoint_precond_apply": (i, [p, d, dp, dp, i]),
+            "fasw_adjoint_shape_gradient": (i, [p, i, dp, i, dp, d, dp, i]),
             "fasw_residual_noalloc": (i, [i, i, i, dp, dp, dp, dp, C.POINTER(Params), p]),
             "fasw_batch_create": (i, [i, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_void_p), i, C.POINTER(Params), p, C.POINTER(p)]),
@@ -282,6 +289,62 @@ class Solver:
         ms = C.c_double()
         _check(self.lib.fasw_kernel_time(self.h, kernel, C.byref(n), C.byref(ms)), "fasw_kernel_time")
         return n.value, ms.value
+
+    # ---- discrete adjoint of the steady finest-level residual
+    def force_coefficients(self):
+        """(C_L, C_D) of the wall-face force at the current state."""
+        cl, cd = C.c_double(), C.c_double()
+        _check(self.lib.fasw_force_coefficients(self.h, C.byref(cl), C.byref(cd)), "fasw_force_coefficients")
+        return cl.value, cd.value
+
+    def adjoint_jacobian(self, h_rel=1e-6):
+        _check(self.lib.fasw_adjoint_jacobian(self.h, h_rel), "fasw_adjoint_jacobian")
+
+    def adjoint_apply(self, v, transpose=False, out=None):
+        v = np.ascontiguousarray(v, dtype=np.float64) if isinstance(v, np.ndarray) else v
+        out = np.zeros(self._shape(self.finest)) if out is None else out
+        vp, vd = _ptr(v)
+        op, od = _ptr(out)
+        assert vd == od, "v and out must both be host or both device"
+        _check(self.lib.fasw_adjoint_apply(self.h, vp, op, 1 if transpose else 0, vd), "fasw_adjoint_apply")
+        return out
+
+    def adjoint_objective_gradient(self, which):
+        out = np.zeros(self._shape(self.finest))
+        _check(self.lib.fasw_adjoint_objective_gradient(self.h, which, out.ctypes.data, 0),
+               "fasw_adjoint_objective_gradient")
+        return out
+
+    def adjoint_precond_apply(self, r, cfl):
+        """z = P^-T r, the adjoint preconditioner (transposed primal AW preconditioner, scaled)."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        z = np.zeros(self._shape(self.finest))
+        _check(self.lib.fasw_adjoint_precond_apply(self.h, cfl, r.ctypes.data, z.ctypes.data, 0),
+               "fasw_adjoint_precond_apply")
+        return z
+
+    def adjoint_solve(self, which=0, g=None, tol=1e-10, max_iters=400, restart=40):
+        """(lam, code, iterations, relative residual) of J^T lam = g (g None: objective which)."""
+        lam = np.zeros(self._shape(self.finest))
+        gp = None
+        if g is not None:
+            g = np.ascontiguousarray(g, dtype=np.float64)
+            gp = g.ctypes.data
+        it, rr = C.c_int(), C.c_double()
+        code = self.lib.fasw_adjoint_solve(self.h, which, gp, lam.ctypes.data, tol, max_iters, restart, C.byref(it),
+                                           C.byref(rr), 0)
+        if code not in (0, -6):
+            _check(code, "fasw_adjoint_solve")
+        return lam, code, it.value, rr.value
+
+    def adjoint_shape_gradient(self, which, lam, fields, h_x=1e-6):
+        """grad[k] = dJ/dX V_k - lam^T dF/dX V_k for y-displacement fields (nparam, nj+1, ni+1)."""
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        V = np.ascontiguousarray(fields, dtype=np.float64)
+        grad = np.zeros(V.shape[0])
+        _check(self.lib.fasw_adjoint_shape_gradient(self.h, which, lam.ctypes.data, V.shape[0], V.ctypes.data, h_x,
+                                                    grad.ctypes.data, 0), "fasw_adjoint_shape_gradient")
+        return grad
 
 
 class Batch:

@@ -1,0 +1,136 @@
+"""GPU discrete adjoint against the oracle's (coloured-difference Jacobian, sparse direct
+transposed solve) and against differences of full GPU solves."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import adjoint as A
+from synth.cgrid import make_cgrid
+from synth.shape import bump_fields, deformed
+from tests.helpers import make_pair, pair_params, perturbed_state, rel_err
+
+pytestmark = pytest.mark.gpu
+
+ALPHA = 1.25
+
+
+def _euler_pair(g, **kw):
+    return make_pair(g, nlevels=2, mach=0.6, alpha_deg=ALPHA, cfl=1e4, **kw)
+
+
+@pytest.mark.parametrize("viscous", [0, 1])
+def test_jacobian_products_match_the_oracle(viscous):
+    g = make_cgrid(64, 16, jitter=0.02, seed=4)
+    o, s = make_pair(g, nlevels=1, mach=0.6, alpha_deg=ALPHA, viscous=viscous, turb=0, re=1e4)
+    u = perturbed_state(0.6, ALPHA, 16, 64, amp=0.03, seed=2)
+    o.set_state(u); s.set_state(u)
+    J, gL, gD = A.jacobian(o, ALPHA)
+    s.adjoint_jacobian(1e-6)
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal((4, 16, 64)); w = rng.standard_normal((4, 16, 64))
+    Jv = s.adjoint_apply(v)
+    JTw = s.adjoint_apply(w, transpose=True)
+    assert rel_err(Jv.ravel(), J @ v.ravel()) < 1e-6
+    assert rel_err(JTw.ravel(), J.T @ w.ravel()) < 1e-6
+    # dot-product test of the GPU's own pair of products
+    a, b = float(np.sum(Jv * w)), float(np.sum(v * JTw))
+    assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))
+    assert rel_err(s.adjoint_objective_gradient(0).ravel(), gL) < 1e-6
+    assert rel_err(s.adjoint_objective_gradient(1).ravel(), gD) < 1e-6
+
+
+def test_adjoint_preconditioner_is_the_transposed_primal_w():
+    """z = S M^-T r with M the primal AW preconditioner: compare with the transpose of the
+    oracle's M^-1 (applied column by column on a tiny grid with a wake cut), S = eta dt*."""
+    ni, nj = 16, 6
+    g = make_cgrid(ni, nj, n_wake=2, jitter=0.03, seed=7)
+    o, s = make_pair(g, nlevels=1, mach=0.6, alpha_deg=ALPHA, d_cut=0.5)
+    u = perturbed_state(0.6, ALPHA, nj, ni, amp=0.04, seed=8)
+    o.set_state(u); s.set_state(u)
+    n = ni * nj
+    Minv = np.zeros((4 * n, 4 * n))
+    for col in range(4 * n):
+        e = np.zeros(4 * n); e[col] = 1.0
+        Minv[:, col] = o.precond_apply(e.reshape(4, nj, ni), 50.0)[0].ravel()
+    r = np.random.default_rng(9).standard_normal((4, nj, ni))
+    S = 0.8 * o.pseudo_dt(50.0).ravel()                 # eta dt*
+    ref = (Minv.T @ r.ravel()) * np.tile(S, 4)
+    z = s.adjoint_precond_apply(r, 50.0)
+    assert rel_err(z.ravel(), ref) < 1e-11
+
+
+def test_force_coefficients_match_the_oracle():
+    g = make_cgrid(64, 16)
+    o, s = _euler_pair(g)
+    u = perturbed_state(0.6, ALPHA, 16, 64, amp=0.03, seed=3)
+    o.set_state(u); s.set_state(u)
+    cl_o, cd_o = A.force_coefficients(*o.wall_force(), ALPHA)
+    cl_g, cd_g = s.force_coefficients()
+    assert abs(cl_g - cl_o) <= 1e-11 * abs(cl_o)
+    assert abs(cd_g - cd_o) <= 1e-11 * max(abs(cd_o), 1e-3)
+
+
+def test_adjoint_solution_and_shape_gradient_match_the_oracle():
+    g = make_cgrid(64, 16)
+    o, s = _euler_pair(g)
+    code, nc, hist = s.solve(1e-13, 800)
+    assert code == 0
+    u = s.get_state()
+    o.set_state(u)
+    V = bump_fields(g, 4)
+    _, p = pair_params(nlevels=2, mach=0.6, alpha_deg=ALPHA, cfl=1e4)
+    po, _ = pair_params(nlevels=2, mach=0.6, alpha_deg=ALPHA, cfl=1e4)
+    dL_o, dD_o, lamL_o, lamD_o = A.shape_gradient(g, po, u, None, V, ALPHA)
+    s.adjoint_jacobian(1e-6)
+    for which, lam_o, d_o in ((0, lamL_o, dL_o), (1, lamD_o, dD_o)):
+        lam, code, it, rr = s.adjoint_solve(which, tol=1e-10, max_iters=1500, restart=60)
+        assert code == 0 and rr <= 1e-10, (code, it, rr)
+        assert rel_err(lam.ravel(), lam_o) < 1e-6
+        grad = s.adjoint_shape_gradient(which, lam, V)
+        assert rel_err(grad, d_o) < 1e-5
+
+
+def test_adjoint_gradient_matches_differences_of_gpu_solves():
+    import paper_1710_04875_gb300 as P
+    g = make_cgrid(64, 16)
+    _, p = pair_params(nlevels=2, mach=0.6, alpha_deg=ALPHA, cfl=1e4)
+    s = P.Solver(g, p)
+    s.solve(1e-13, 800)
+    u = s.get_state()
+    V = bump_fields(g, 4)
+    s.adjoint_jacobian(1e-6)
+    lam, code, _, _ = s.adjoint_solve(0, tol=1e-10, max_iters=1500, restart=60)
+    gradL = s.adjoint_shape_gradient(0, lam, V)
+    h = 1e-5
+    for k in (0, 2):
+        cs = []
+        for sgn in (1, -1):
+            e = np.zeros(4); e[k] = sgn * h
+            sk = P.Solver(deformed(g, e, V), p)
+            sk.set_state(u)
+            sk.solve(1e-13, 800)
+            cs.append(sk.force_coefficients()[0])
+            sk.close()
+        fd = (cs[0] - cs[1]) / (2 * h)
+        assert abs(fd - gradL[k]) <= 1e-3 * abs(gradL[k])   # piecewise-smooth JST residual
+
+
+def test_autograd_function_gives_the_adjoint_gradient():
+    from paper_1710_04875_gb300.adjoint import AdjointContext, ShapeForces
+    g = make_cgrid(64, 16)
+    _, p = pair_params(nlevels=2, mach=0.6, alpha_deg=ALPHA, cfl=1e4)
+    V = bump_fields(g, 4)
+    actx = AdjointContext(lambda q: deformed(g, q, V), V, p, drop=1e-13, max_cycles=800, tol=1e-10,
+                          max_iters=1500, restart=60)
+    q = torch.zeros(4, dtype=torch.float64, requires_grad=True)
+    c = ShapeForces.apply(q, actx)
+    (c[0] + 10.0 * c[1]).backward()
+    s = actx.solver
+    lamL, _, _, _ = s.adjoint_solve(0, tol=1e-10, max_iters=1500, restart=60)
+    lamD, _, _, _ = s.adjoint_solve(1, tol=1e-10, max_iters=1500, restart=60)
+    ref = s.adjoint_shape_gradient(0, lamL, V) + 10.0 * s.adjoint_shape_gradient(1, lamD, V)
+    # the same adjoint systems solved twice to relative residual 1e-10
+    assert rel_err(q.grad.numpy(), ref) < 1e-7
+    assert all(actx.info[("adjoint", w)][0] == 0 for w in (0, 1)), actx.info
+    assert actx.info["primal"][0] == 0
