@@ -197,6 +197,28 @@ def time_cycles(s, stream, flush, steps, k0):
     return ms
 
 
+def measure_adjoint(s, g, n_bumps=16):
+    """Discrete adjoint of the steady RANS workload at its 6-order state (eddy viscosity
+    frozen): Jacobian assembly, the GMRES adjoint solve for C_D, and the shape gradient of C_D
+    for 16 Hicks-Henne bumps, each timed on the host around synchronous library calls."""
+    from synth.shape import bump_fields
+    V = bump_fields(g, n_bumps)
+    t0 = time.perf_counter()
+    s.adjoint_jacobian(1e-6)
+    t_jac = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lam, code, it, rr = s.adjoint_solve(1, tol=1e-8, max_iters=1500, restart=60)
+    t_sol = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    grad = s.adjoint_shape_gradient(1, lam, V)
+    t_grad = time.perf_counter() - t0
+    cl, cd = s.force_coefficients()
+    return {"objective": "C_D", "cl": cl, "cd": cd, "jacobian_s": t_jac, "solve_s": t_sol,
+            "gmres_iterations": it, "relative_residual": rr, "status": int(code), "shape_gradient_s": t_grad,
+            "n_params": n_bumps, "grad_norm": float(np.linalg.norm(grad)),
+            "note": "steady state after the 6-order drop; eddy viscosity frozen; GMRES(60), tol 1e-8"}
+
+
 def measure_batched(P, stream, flush, steps, warmup, precision="mixed"):
     """64 uneven Euler cases (128x32 .. 512x128 cells, seeded M, alpha, thickness) advanced
     together, one captured CUDA graph per cycle; sweep variants chosen by the autotuner."""
@@ -250,6 +272,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.warmup < 3:
@@ -328,6 +351,7 @@ def main():
     # pitching motion (alpha = 2 deg sin(2kt), k = 0.2, 64 steps per period): an implicit-Euler
     # start step and one BDF2 step, each to an 11-order drop in pseudo time
     drops, unsteady = {}, {}
+    adjoint = None
     omega = 0.4
     dt_phys = 2.0 * np.pi / omega / 64
     amp = np.radians(2.0)
@@ -340,13 +364,15 @@ def main():
         dt = time.perf_counter() - t0
         drops[prec] = {"seconds": dt if code == 0 else None, "cycles": nc, "status": int(code),
                        "final_drop": float(hist[-1] / hist[0]) if len(hist) else None}
+        if prec == "fp64" and not args.no_adjoint:
+            adjoint = measure_adjoint(sd, g)
         steps = []
         for step in (1, 2):
             tt = step * dt_phys
             sd.set_motion(-amp * np.sin(omega * tt), -amp * omega * np.cos(omega * tt))
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            c2, n2, h2 = sd.dual_time_step(dt_phys, 1e-11, 400)
+            c2, n2, h2 = sd.dual_time_step(dt_phys, 1e-11, 1000)
             torch.cuda.synchronize()
             steps.append({"kind": "implicit Euler" if step == 1 else "BDF2", "seconds": time.perf_counter() - t0,
                           "cycles": n2, "status": int(c2),
@@ -399,7 +425,7 @@ def main():
             "other_precision": {"precision": "mixed" if args.precision == "fp64" else "fp64",
                                 "value": other_value, "ms_per_step": sum(ms_other) / args.steps},
             "time_to_6_orders": drops, "time_to_11_orders_per_time_step": unsteady,
-            "batched_64_cases": batched, "kernel_share": share,
+            "batched_64_cases": batched, "adjoint": adjoint, "kernel_share": share,
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes + 8},
             "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "cpu_baseline": cpu}

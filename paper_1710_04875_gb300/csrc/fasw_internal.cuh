@@ -11,6 +11,32 @@ constexpr double GAM = 1.4;
 // Ghosted arrays have two ghost layers on every side: cell (i, j), -2 <= i < ni+2,
 // -2 <= j < nj+2, at (j+2)*P + (i+2) with pitch P = ni + 4.  Interior arrays hold
 // cell (i, j) at j*ni + i.  Vector fields are component-major (4 planes).
+// Programmatic dependent launch.  Every kernel of the library starts with pdl_entry(): it waits
+// until the kernel before it on the stream has completed and its writes are visible, then lets
+// the next kernel be launched, so that launch overlaps this kernel's run instead of following
+// its completion.  launch_pdl() launches with the attribute that allows this overlap; without
+// it griddepcontrol.wait returns at once.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KP, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KP>(args)...);
+}
+
 struct LevelDev {
   int ni, nj, nw;
   int P;        // ghost pitch ni + 4

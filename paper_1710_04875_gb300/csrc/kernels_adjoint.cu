@@ -39,6 +39,7 @@ __device__ __forceinline__ int gidx_of(const LevelDev& L, int i, int j) { return
 
 // L.u interior = base state, plus sgn * h at component m of the cells of colour k (k < 0: none).
 __global__ void k_adj_set_state(LevelDev L, const double* ub, const int* col, int k, int m, double h_rel, double sgn) {
+  pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int n = L.n, g = gidx_of(L, c % L.ni, c / L.ni);
@@ -51,6 +52,7 @@ __global__ void k_adj_set_state(LevelDev L, const double* ub, const int* col, in
 }
 
 __global__ void k_adj_get_state(LevelDev L, double* ub) {
+  pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int n = L.n, g = gidx_of(L, c % L.ni, c / L.ni);
@@ -61,6 +63,7 @@ __global__ void k_adj_get_state(LevelDev L, double* ub) {
 // Column m of the block of the unique colour-k dependency of every cell.
 __global__ void k_adj_extract(int n, const int* nbr, const int* col, int k, int m, const double* Fp,
                               const double* Fm, const double* ub, double h_rel, double* J) {
+  pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   for (int s = 0; s < ADJ_SLOTS; ++s) {
@@ -77,6 +80,7 @@ __global__ void k_adj_extract(int n, const int* nbr, const int* col, int k, int 
 // Objective gradients: wall face i depends on cells (i, 0) and (i, 1) only.
 __global__ void k_adj_extract_obj(int ni, int n, const int* col, int k, int m, const double* fw, const double* ub,
                                   double h_rel, double sa, double ca, double* g) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ni) return;
   int x = -1;
@@ -91,6 +95,7 @@ __global__ void k_adj_extract_obj(int ni, int n, const int* col, int k, int m, c
 
 // out = J v
 __global__ void k_jac_mv(int n, const int* nbr, const double* J, const double* v, double* out) {
+  pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -112,6 +117,7 @@ __global__ void k_jac_mv(int n, const int* nbr, const double* J, const double* v
 
 // out = J^T v: every cell d gathers the blocks whose column is d.
 __global__ void k_jac_tmv(int n, const int* rev_ptr, const int* rev, const double* J, const double* v, double* out) {
+  pdl_entry();
   const int d = blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= n) return;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -145,6 +151,7 @@ __device__ __forceinline__ double tbT(const double* tb, int n, int blk, int r, i
 }
 
 __global__ void __launch_bounds__(1024) k_adj_wt(LevelDev L, const double* r, double* a, double* b) {
+  pdl_entry();
   const int ni = L.ni, nj = L.nj, n = L.n, nw = L.nw, K = ni + nj - 1;
   const double* tb = L.tb;
   const int q = threadIdx.x & 3, lane_cell = threadIdx.x >> 2, ncell = blockDim.x >> 2;
@@ -192,6 +199,7 @@ __global__ void __launch_bounds__(1024) k_adj_wt(LevelDev L, const double* r, do
 
 // z = S D^-T b, S = eta dt* = coef * vol (coef of the AW blocks)
 __global__ void k_adj_wt_finish(LevelDev L, const double* b, double* z) {
+  pdl_entry();
   const int d = blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= L.n) return;
   const int n = L.n;
@@ -207,6 +215,7 @@ __global__ void k_adj_wt_finish(LevelDev L, const double* b, double* z) {
 
 // Partial sums of dot(V_v, w) for v < nvec (grid RED_BLOCKS x nvec), then row reduction.
 __global__ void k_multi_dot(const double* V, size_t ld, const double* w, int m, double* parts) {
+  pdl_entry();
   __shared__ double red[256];
   const double* a = V + (size_t)blockIdx.y * ld;
   double s = 0.0;
@@ -221,6 +230,7 @@ __global__ void k_multi_dot(const double* V, size_t ld, const double* w, int m, 
 }
 
 __global__ void k_rows_sum(const double* parts, int nblk, int nvec, double* out) {
+  pdl_entry();
   const int v = threadIdx.x;
   if (v >= nvec) return;
   double s = 0.0;
@@ -230,6 +240,7 @@ __global__ void k_rows_sum(const double* parts, int nblk, int nvec, double* out)
 
 // w -= sum_v coef[v] V_v
 __global__ void k_multi_axpy(const double* V, size_t ld, const double* coef, int nvec, int m, double* w) {
+  pdl_entry();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= m) return;
   double s = w[x];
@@ -239,6 +250,7 @@ __global__ void k_multi_axpy(const double* V, size_t ld, const double* coef, int
 
 // y = a x + b y
 __global__ void k_axpby(int m, double a, const double* x, double b, double* y) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) y[i] = a * x[i] + b * y[i];
 }
@@ -322,7 +334,7 @@ int adj_assemble(AdjointDev& A, const LevelDev& L, const PhysParams& ph, double 
                  long long& launches) {
   const int n = A.n, nb = (n + 127) / 128, nbf = (A.ni + 127) / 128;
   const double al = ph.alpha_deg * M_PI / 180.0, sa = std::sin(al), ca = std::cos(al);
-  k_adj_get_state<<<nb, 128, 0, st>>>(L, A.ub);
+  launch_pdl(k_adj_get_state, nb, 128, 0, st, L, A.ub);
   cudaMemsetAsync(A.g, 0, 8 * (size_t)n * sizeof(double), st);
   ++launches;
   ResArgs a{};
@@ -330,18 +342,18 @@ int adj_assemble(AdjointDev& A, const LevelDev& L, const PhysParams& ph, double 
   for (int k = 0; k < A.ncolours; ++k)
     for (int m = 0; m < 4; ++m) {
       for (int sgn = 0; sgn < 2; ++sgn) {
-        k_adj_set_state<<<nb, 128, 0, st>>>(L, A.ub, A.col, k, m, h_rel, sgn == 0 ? 1.0 : -1.0);
+        launch_pdl(k_adj_set_state, nb, 128, 0, st, L, A.ub, A.col, k, m, h_rel, sgn == 0 ? 1.0 : -1.0);
         launch_bc_aux(L, ph, 1.0, 0, st);
         a.F = sgn == 0 ? A.Fp : A.Fm;
         launch_residual(L, ph, a, st);
         launch_wall_force(L, ph, A.fw + 2 * sgn * A.ni, A.fw + (2 * sgn + 1) * A.ni, st);
         launches += 4;
       }
-      k_adj_extract<<<nb, 128, 0, st>>>(n, A.nbr, A.col, k, m, A.Fp, A.Fm, A.ub, h_rel, A.J);
-      k_adj_extract_obj<<<nbf, 128, 0, st>>>(A.ni, n, A.col, k, m, A.fw, A.ub, h_rel, sa, ca, A.g);
+      launch_pdl(k_adj_extract, nb, 128, 0, st, n, A.nbr, A.col, k, m, A.Fp, A.Fm, A.ub, h_rel, A.J);
+      launch_pdl(k_adj_extract_obj, nbf, 128, 0, st, A.ni, n, A.col, k, m, A.fw, A.ub, h_rel, sa, ca, A.g);
       launches += 2;
     }
-  k_adj_set_state<<<nb, 128, 0, st>>>(L, A.ub, A.col, -1, 0, 0.0, 0.0);
+  launch_pdl(k_adj_set_state, nb, 128, 0, st, L, A.ub, A.col, -1, 0, 0.0, 0.0);
   launch_bc_aux(L, ph, 1.0, 0, st);
   launches += 2;
   A.built = true;
@@ -351,9 +363,9 @@ int adj_assemble(AdjointDev& A, const LevelDev& L, const PhysParams& ph, double 
 void adj_apply(const AdjointDev& A, const double* v, double* out, int transpose, cudaStream_t st) {
   const int nb = (A.n + 127) / 128;
   if (transpose)
-    k_jac_tmv<<<nb, 128, 0, st>>>(A.n, A.rev_ptr, A.rev, A.J, v, out);
+    launch_pdl(k_jac_tmv, nb, 128, 0, st, A.n, A.rev_ptr, A.rev, A.J, v, out);
   else
-    k_jac_mv<<<nb, 128, 0, st>>>(A.n, A.nbr, A.J, v, out);
+    launch_pdl(k_jac_mv, nb, 128, 0, st, A.n, A.nbr, A.J, v, out);
 }
 
 namespace {
@@ -364,15 +376,15 @@ void precond(const AdjointDev& A, const double* r, double* y, double* z, cudaStr
   int threads = 4 * cells;
   threads = threads > 1024 ? 1024 : threads;
   threads = (threads + 31) / 32 * 32;
-  k_adj_wt<<<1, threads, 0, st>>>(A.Lp, r, y, z);
-  k_adj_wt_finish<<<(A.n + 127) / 128, 128, 0, st>>>(A.Lp, z, z);
+  launch_pdl(k_adj_wt, 1, threads, 0, st, A.Lp, r, y, z);
+  launch_pdl(k_adj_wt_finish, (A.n + 127) / 128, 128, 0, st, A.Lp, z, z);
 }
 
 // out[v] = dot(V_v, w), v < nvec (host values, synchronizes)
 int multi_dot(AdjointDev& A, const double* V, size_t ld, int nvec, const double* w, int m, cudaStream_t st,
               double* out) {
-  k_multi_dot<<<dim3(RED_BLOCKS, nvec), 256, 0, st>>>(V, ld, w, m, A.parts);
-  k_rows_sum<<<1, 64, 0, st>>>(A.parts, RED_BLOCKS, nvec, A.parts + RED_BLOCKS * 64 - 64);
+  launch_pdl(k_multi_dot, dim3(RED_BLOCKS, nvec), 256, 0, st, V, ld, w, m, A.parts);
+  launch_pdl(k_rows_sum, 1, 64, 0, st, A.parts, RED_BLOCKS, nvec, A.parts + RED_BLOCKS * 64 - 64);
   if (cudaMemcpyAsync(A.h_parts, A.parts + RED_BLOCKS * 64 - 64, nvec * sizeof(double), cudaMemcpyDeviceToHost,
                       st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
@@ -385,7 +397,7 @@ int multi_dot(AdjointDev& A, const double* V, size_t ld, int nvec, const double*
 
 void adj_lincomb(int m, const double* x, double a, const double* v, double* out, cudaStream_t st) {
   cudaMemcpyAsync(out, x, m * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  k_axpby<<<(m + 255) / 256, 256, 0, st>>>(m, a, v, 1.0, out);
+  launch_pdl(k_axpby, (m + 255) / 256, 256, 0, st, m, a, v, 1.0, out);
 }
 
 int adj_dot(AdjointDev& A, const double* a, const double* b, int m, cudaStream_t st, double* out) {
@@ -462,7 +474,7 @@ int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const Sche
       h2(restart + 1);
   double* d_coef = A.parts + RED_BLOCKS * 64 - 128;  // 64 coefficients
   while (*iters < max_iters) {
-    k_axpby<<<nb, 256, 0, st>>>(m, 1.0 / beta, res, 0.0, V);
+    launch_pdl(k_axpby, nb, 256, 0, st, m, 1.0 / beta, res, 0.0, V);
     std::fill(s.begin(), s.end(), 0.0);
     s[0] = beta;
     int jdone = 0;
@@ -474,7 +486,7 @@ int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const Sche
       for (int pass = 0; pass < 2; ++pass) {
         if ((r = multi_dot(A, V, ld, j + 1, w, m, st, pass == 0 ? h.data() : h2.data()))) return r;
         cudaMemcpyAsync(d_coef, pass == 0 ? h.data() : h2.data(), (j + 1) * sizeof(double), cudaMemcpyHostToDevice, st);
-        k_multi_axpy<<<nb, 256, 0, st>>>(V, ld, d_coef, j + 1, m, w);
+        launch_pdl(k_multi_axpy, nb, 256, 0, st, V, ld, d_coef, j + 1, m, w);
         launches += 3;
       }
       for (int i = 0; i <= j; ++i) H[(size_t)i * restart + j] = h[i] + h2[i];
@@ -482,7 +494,7 @@ int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const Sche
       if ((r = adj_dot(A, w, w, m, st, &hn))) return r;
       hn = std::sqrt(hn);
       H[(size_t)(j + 1) * restart + j] = hn;
-      if (hn > 0.0) k_axpby<<<nb, 256, 0, st>>>(m, 1.0 / hn, w, 0.0, V + (size_t)(j + 1) * ld);
+      if (hn > 0.0) launch_pdl(k_axpby, nb, 256, 0, st, m, 1.0 / hn, w, 0.0, V + (size_t)(j + 1) * ld);
       ++launches;
       for (int i = 0; i < j; ++i) {  // previous rotations
         const double a = H[(size_t)i * restart + j], b = H[(size_t)(i + 1) * restart + j];
@@ -514,12 +526,12 @@ int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const Sche
     for (int i = 0; i < jdone; ++i) yv[i] = -yv[i];  // k_multi_axpy subtracts
     cudaMemsetAsync(w, 0, m * sizeof(double), st);
     cudaMemcpyAsync(d_coef, yv.data(), jdone * sizeof(double), cudaMemcpyHostToDevice, st);
-    k_multi_axpy<<<nb, 256, 0, st>>>(V, ld, d_coef, jdone, m, w);
+    launch_pdl(k_multi_axpy, nb, 256, 0, st, V, ld, d_coef, jdone, m, w);
     precond(A, w, y, t, st);
-    k_axpby<<<nb, 256, 0, st>>>(m, 1.0, t, 1.0, lam);
+    launch_pdl(k_axpby, nb, 256, 0, st, m, 1.0, t, 1.0, lam);
     // true residual g - J^T lam
     adj_apply(A, lam, res, 1, st);
-    k_axpby<<<nb, 256, 0, st>>>(m, 1.0, g, -1.0, res);
+    launch_pdl(k_axpby, nb, 256, 0, st, m, 1.0, g, -1.0, res);
     launches += 5;
     if ((r = adj_dot(A, res, res, m, st, &beta))) return r;
     beta = std::sqrt(beta);

@@ -170,6 +170,7 @@ __device__ __forceinline__ bool ghost_of(const LevelDev& L, int t, int& gi, int&
 
 // Ghost fill alone: one thread per ghost cell of the two layers.
 __global__ void k_bc(LevelDev L, PhysParams ph) {
+  pdl_entry();
   int gi, gj;
   if (!ghost_of(L, blockIdx.x * blockDim.x + threadIdx.x, gi, gj)) return;
   double g[4];
@@ -194,6 +195,7 @@ __device__ __forceinline__ void cell_thermo(const LevelDev& L, const PhysParams&
 // boundary value first, which depends on interior cells only; then pressure, 1/rho, sensor).
 // Interior and ghost work never share a warp, so neither path waits on the other's FP64 chain.
 __global__ void k_cell_aux(LevelDev L, PhysParams ph, double cfl, int want_dts, int fill_ghosts, int nbi) {
+  pdl_entry();
   if ((int)blockIdx.x >= nbi) {
     int gi, gj;
     if (!ghost_of(L, (blockIdx.x - nbi) * blockDim.x + threadIdx.x, gi, gj)) return;
@@ -370,6 +372,7 @@ __device__ double block_sum(double v, double* wsum) {
 // One tile of TX x TY cells: every face of the tile is computed once into shared memory,
 // then each cell assembles F^c and F^v and writes what the mode asks for.
 __global__ void __launch_bounds__(RES_THREADS) k_residual(LevelDev L, PhysParams ph, ResArgs a) {
+  pdl_entry();
   __shared__ double xc[4][TY][TX + 1], xd[4][TY][TX + 1];
   __shared__ double ec[4][TY + 1][TX], ed[4][TY + 1][TX];
   __shared__ double wsum[RES_THREADS / 32];
@@ -479,6 +482,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(LevelDev L, PhysParams
 // j-face flux (central part minus dissipation minus viscous part) with the opposite sign,
 // since the face vector points into the fluid.  fx, fy: ni entries, zero on the cut.
 __global__ void k_wall_force(LevelDev L, PhysParams ph, double* fx, double* fy) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.ni) return;
   if (on_cut(L, i)) {
@@ -499,6 +503,7 @@ __global__ void k_wall_force(LevelDev L, PhysParams ph, double* fx, double* fy) 
 }
 
 __global__ void k_norm_final(const double* part, int nparts, double count, double* out) {
+  pdl_entry();
   __shared__ double wsum[8];
   double s = 0.0;
   for (int k = threadIdx.x; k < nparts; k += blockDim.x) s += part[k];
@@ -508,6 +513,7 @@ __global__ void k_norm_final(const double* part, int nparts, double count, doubl
 
 // ---- Baldwin-Lomax (finest level): vorticity by Green-Gauss, then one thread per i-line.
 __global__ void k_vorticity(LevelDev L) {
+  pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int ni = L.ni, i = c % ni, j = c / ni;
@@ -531,6 +537,7 @@ __global__ void k_vorticity(LevelDev L) {
 // for F_max takes the first j of the largest F (as a sequential scan with a strict > would),
 // and the inner/outer crossover is the first j where the inner value reaches the outer one.
 __global__ void k_bl_lines(LevelDev L, PhysParams ph) {
+  pdl_entry();
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= L.ni) return;  // whole warps leave together
@@ -602,37 +609,37 @@ __global__ void k_bl_lines(LevelDev L, PhysParams ph) {
 
 void launch_bc(const LevelDev& L, const PhysParams& ph, cudaStream_t st) {
   const int nt = 4 * L.ni + 4 * L.nj;
-  k_bc<<<(nt + 63) / 64, 64, 0, st>>>(L, ph);
+  launch_pdl(k_bc, (nt + 63) / 64, 64, 0, st, L, ph);
 }
 
 void launch_cell_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st) {
   const int nbi = (L.n + 63) / 64, nbg = (4 * (L.ni + L.nj) + 63) / 64;
-  k_cell_aux<<<nbi + nbg, 64, 0, st>>>(L, ph, cfl, want_dts, 0, nbi);
+  launch_pdl(k_cell_aux, nbi + nbg, 64, 0, st, L, ph, cfl, want_dts, 0, nbi);
 }
 
 void launch_bc_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st) {
   const int nbi = (L.n + 63) / 64, nbg = (4 * (L.ni + L.nj) + 63) / 64;
-  k_cell_aux<<<nbi + nbg, 64, 0, st>>>(L, ph, cfl, want_dts, 1, nbi);
+  launch_pdl(k_cell_aux, nbi + nbg, 64, 0, st, L, ph, cfl, want_dts, 1, nbi);
 }
 
 void launch_wall_force(const LevelDev& L, const PhysParams& ph, double* fx, double* fy, cudaStream_t st) {
-  k_wall_force<<<(L.ni + 63) / 64, 64, 0, st>>>(L, ph, fx, fy);
+  launch_pdl(k_wall_force, (L.ni + 63) / 64, 64, 0, st, L, ph, fx, fy);
 }
 
 int residual_blocks(const LevelDev& L) { return ((L.ni + TX - 1) / TX) * ((L.nj + TY - 1) / TY); }
 
 void launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, cudaStream_t st) {
   dim3 grid((L.ni + TX - 1) / TX, (L.nj + TY - 1) / TY);
-  k_residual<<<grid, RES_THREADS, 0, st>>>(L, ph, a);
+  launch_pdl(k_residual, grid, RES_THREADS, 0, st, L, ph, a);
 }
 
 void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* out, cudaStream_t st) {
-  k_norm_final<<<1, 256, 0, st>>>(L.norm_part, nparts, (double)ncomp_cells, out);
+  launch_pdl(k_norm_final, 1, 256, 0, st, L.norm_part, nparts, (double)ncomp_cells, out);
 }
 
 void launch_bl(const LevelDev& L, const PhysParams& ph, cudaStream_t st) {
-  k_vorticity<<<(L.n + 63) / 64, 64, 0, st>>>(L);
-  k_bl_lines<<<(L.ni + 1) / 2, 64, 0, st>>>(L, ph);
+  launch_pdl(k_vorticity, (L.n + 63) / 64, 64, 0, st, L);
+  launch_pdl(k_bl_lines, (L.ni + 1) / 2, 64, 0, st, L, ph);
 }
 
 }  // namespace fasw

@@ -102,6 +102,7 @@ __device__ double visc_radius(const LevelDev& L, const PhysParams& ph, int i, in
 
 template <typename T>
 __global__ void k_face_blocks(LevelDev L, PhysParams ph, T* blk, T d) {
+  pdl_entry();
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   const int ni = L.ni;
   if (f >= L.nfx + L.nfe) return;
@@ -160,6 +161,7 @@ __global__ void k_face_blocks(LevelDev L, PhysParams ph, T* blk, T d) {
 // diagonal, U on and above with the reciprocal of its diagonal stored on the diagonal).
 template <typename T>
 __global__ void k_diag_blocks(LevelDev L, const T* blk, T* dlu, int aw, double eta) {
+  pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int ni = L.ni, i = c % ni, j = c / ni;
@@ -242,6 +244,7 @@ __device__ __forceinline__ void matvec_acc(const T* B, int stride, int f, const 
 template <typename T>
 __global__ void k_sgs_single(LevelDev L, const T* blk, const T* dlu, T* yz, const double* r_in,
                              int do_update, int aw, double alpha) {
+  pdl_entry();
   const int ni = L.ni, nj = L.nj, n = L.n;
   const T* Axp = blk;
   const T* Axm = blk + 16 * L.nfx;
@@ -302,25 +305,25 @@ __global__ void k_sgs_single(LevelDev L, const T* blk, const T* dlu, T* yz, cons
 void launch_face_blocks(const LevelDev& L, const PhysParams& ph, const SchemeParams& sc, int mixed, cudaStream_t st) {
   const int nf = L.nfx + L.nfe;
   if (mixed)
-    k_face_blocks<float><<<(nf + 63) / 64, 64, 0, st>>>(L, ph, L.blk32, float(sc.d_cut));
+    launch_pdl(k_face_blocks<float>, (nf + 63) / 64, 64, 0, st, L, ph, L.blk32, float(sc.d_cut));
   else
-    k_face_blocks<double><<<(nf + 63) / 64, 64, 0, st>>>(L, ph, L.blk64, sc.d_cut);
+    launch_pdl(k_face_blocks<double>, (nf + 63) / 64, 64, 0, st, L, ph, L.blk64, sc.d_cut);
 }
 
 void launch_diag_blocks(const LevelDev& L, const SchemeParams& sc, int mixed, cudaStream_t st) {
   if (mixed)
-    k_diag_blocks<float><<<(L.n + 63) / 64, 64, 0, st>>>(L, L.blk32, L.dlu32, sc.aw, sc.eta);
+    launch_pdl(k_diag_blocks<float>, (L.n + 63) / 64, 64, 0, st, L, L.blk32, L.dlu32, sc.aw, sc.eta);
   else
-    k_diag_blocks<double><<<(L.n + 63) / 64, 64, 0, st>>>(L, L.blk64, L.dlu64, sc.aw, sc.eta);
+    launch_pdl(k_diag_blocks<double>, (L.n + 63) / 64, 64, 0, st, L, L.blk64, L.dlu64, sc.aw, sc.eta);
 }
 
 void launch_sgs(const LevelDev& L, const SchemeParams& sc, int mixed, int do_update, double alpha,
                 const double* r_in, double* z_out, cudaStream_t st) {
   const int threads = 128;
   if (mixed) {
-    k_sgs_single<float><<<1, threads, 0, st>>>(L, L.blk32, L.dlu32, L.yz32, r_in, do_update, sc.aw, alpha);
+    launch_pdl(k_sgs_single<float>, 1, threads, 0, st, L, L.blk32, L.dlu32, L.yz32, r_in, do_update, sc.aw, alpha);
   } else {
-    k_sgs_single<double><<<1, threads, 0, st>>>(L, L.blk64, L.dlu64, L.yz64, r_in, do_update, sc.aw, alpha);
+    launch_pdl(k_sgs_single<double>, 1, threads, 0, st, L, L.blk64, L.dlu64, L.yz64, r_in, do_update, sc.aw, alpha);
   }
   (void)z_out;
 }

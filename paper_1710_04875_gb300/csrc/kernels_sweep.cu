@@ -38,6 +38,7 @@ __device__ __forceinline__ bool on_cut(const LevelDev& L, int i) { return L.nw >
 // hpF[32h..] = G_W, G_S and hpB[32h..] = H_E, H_N (row-major 4x4 each); D^-1 stays in tb.
 template <typename T, bool HP>
 __global__ void k_sgs_prep(LevelDev L, const T* blk, const T* dlu, T* tb) {
+  pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int ni = L.ni, nj = L.nj, n = L.n, i = c % ni, j = c / ni;
@@ -123,6 +124,7 @@ struct CtaPre {
 
 template <typename T>
 __global__ void __launch_bounds__(512) k_sweep_cta(LevelDev L, const T* tb, T* yz, const double* rhs, int do_update, int aw, double alpha) {
+  pdl_entry();
   extern __shared__ unsigned char smem_raw[];
   T* buf = reinterpret_cast<T*>(smem_raw);  // 2 x ni x 4
   const int ni = L.ni, nj = L.nj, n = L.n;
@@ -276,6 +278,7 @@ template <typename T, int SH>  // SH rows per strip
 __global__ void __launch_bounds__(16 * SH) k_sweep_strips(LevelDev L, const T* tb, T* yz, const double* rhs,
                                                            long long* prog, int* err, long long limit,
                                                            int do_update, int aw, double alpha) {
+  pdl_entry();
   __shared__ T buf[2][SH][4];
   __shared__ T ring[RING][4];
   __shared__ int abort_flag;
@@ -501,6 +504,7 @@ __device__ __forceinline__ void set_comp(float4& v, int q, float x) { reinterpre
 
 // cy = D^-1 rhs per cell, written hyperplane-major (the forward sweep's constant term).
 __global__ void k_hp_cy(LevelDev L, const float* dinv, const double* rhs) {
+  pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int n = L.n, i = c % L.ni, j = c / L.ni;
@@ -531,6 +535,7 @@ inline size_t hp_smem_bytes(int stages, int nt, int njp, int ni, int nw) {
 // shared-memory offsets, and the global sources advance by one hyperplane per issue.
 template <int STAGES>
 __global__ void __launch_bounds__(512) k_sweep_hp(LevelDev L) {
+  pdl_entry();
   static_assert((STAGES & (STAGES - 1)) == 0 && STAGES >= 4, "ring depth: power of two, at least 4");
   extern __shared__ float4 sm4[];
   const int nt = blockDim.x, tid = threadIdx.x;
@@ -679,6 +684,7 @@ __global__ void __launch_bounds__(512) k_sweep_hp(LevelDev L) {
 // After the sweep: the stage update u = u^(0) - alpha z (AW) or u^(0) - alpha dt* z (ARK) in
 // FP64, or (no update) z to the natural-layout FP32 vector.
 __global__ void k_hp_finish(LevelDev L, int do_update, int aw, double alpha) {
+  pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int n = L.n, i = c % L.ni, j = c / L.ni;
@@ -699,11 +705,11 @@ __global__ void k_hp_finish(LevelDev L, int do_update, int aw, double alpha) {
 
 void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st) {
   if (mixed && kind == SWEEP_HP && L.hpF)
-    k_sgs_prep<float, true><<<(L.n + 63) / 64, 64, 0, st>>>(L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
+    launch_pdl(k_sgs_prep<float, true>, (L.n + 63) / 64, 64, 0, st, L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
   else if (mixed)
-    k_sgs_prep<float, false><<<(L.n + 63) / 64, 64, 0, st>>>(L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
+    launch_pdl(k_sgs_prep<float, false>, (L.n + 63) / 64, 64, 0, st, L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
   else
-    k_sgs_prep<double, false><<<(L.n + 63) / 64, 64, 0, st>>>(L, L.blk64, L.dlu64, L.tb);
+    launch_pdl(k_sgs_prep<double, false>, (L.n + 63) / 64, 64, 0, st, L, L.blk64, L.dlu64, L.tb);
 }
 
 namespace {
@@ -723,7 +729,7 @@ bool hp_fits(int ni, int nj, int nw) {
 int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, double alpha, const double* rhs,
                  long long* prog, int* err, long long limit, cudaStream_t st) {
   if (kind == SWEEP_HP && mixed && L.hpF) {
-    k_hp_cy<<<(L.n + 127) / 128, 128, 0, st>>>(L, reinterpret_cast<const float*>(L.tb), rhs);
+    launch_pdl(k_hp_cy, (L.n + 127) / 128, 128, 0, st, L, reinterpret_cast<const float*>(L.tb), rhs);
     const int nt = hp_threads(L.nj), stages = hp_stages(nt);
     const size_t sm = hp_smem_bytes(stages, nt, nt / 4, L.ni, L.nw);
     if (stages == 8) {
@@ -732,16 +738,16 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
         cudaFuncSetAttribute(k_sweep_hp<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHpSmemMax);
         attr8 = true;
       }
-      k_sweep_hp<8><<<1, nt, sm, st>>>(L);
+      launch_pdl(k_sweep_hp<8>, 1, nt, sm, st, L);
     } else {
       static bool attr4 = false;
       if (!attr4) {
         cudaFuncSetAttribute(k_sweep_hp<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHpSmemMax);
         attr4 = true;
       }
-      k_sweep_hp<4><<<1, nt, sm, st>>>(L);
+      launch_pdl(k_sweep_hp<4>, 1, nt, sm, st, L);
     }
-    k_hp_finish<<<(L.n + 63) / 64, 64, 0, st>>>(L, do_update, aw, alpha);
+    launch_pdl(k_hp_finish, (L.n + 63) / 64, 64, 0, st, L, do_update, aw, alpha);
     return 3;
   }
   if (kind == SWEEP_HP) kind = mixed ? SWEEP_CTA : SWEEP_STRIPS;
@@ -758,7 +764,7 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
         cudaFuncSetAttribute(k_sweep_cta<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_f = true;
       }
-      k_sweep_cta<float><<<1, threads, sm, st>>>(L, reinterpret_cast<const float*>(L.tb), L.yz32, rhs, do_update, aw,
+      launch_pdl(k_sweep_cta<float>, 1, threads, sm, st, L, reinterpret_cast<const float*>(L.tb), L.yz32, rhs, do_update, aw,
                                                  alpha);
     } else {
       const size_t sm = 2 * (size_t)L.ni * 4 * sizeof(double);
@@ -767,7 +773,7 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
         cudaFuncSetAttribute(k_sweep_cta<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_d = true;
       }
-      k_sweep_cta<double><<<1, threads, sm, st>>>(L, L.tb, L.yz64, rhs, do_update, aw, alpha);
+      launch_pdl(k_sweep_cta<double>, 1, threads, sm, st, L, L.tb, L.yz64, rhs, do_update, aw, alpha);
     }
     return 1;
   }
@@ -779,16 +785,16 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
   cudaMemsetAsync(prog, 0, 2 * (size_t)nb * sizeof(long long), st);
   if (sh == 16) {
     if (mixed)
-      k_sweep_strips<float, 16><<<nb, 256, 0, st>>>(L, reinterpret_cast<const float*>(L.tb), L.yz32, rhs, prog, err,
+      launch_pdl(k_sweep_strips<float, 16>, nb, 256, 0, st, L, reinterpret_cast<const float*>(L.tb), L.yz32, rhs, prog, err,
                                                     limit, do_update, aw, alpha);
     else
-      k_sweep_strips<double, 16><<<nb, 256, 0, st>>>(L, L.tb, L.yz64, rhs, prog, err, limit, do_update, aw, alpha);
+      launch_pdl(k_sweep_strips<double, 16>, nb, 256, 0, st, L, L.tb, L.yz64, rhs, prog, err, limit, do_update, aw, alpha);
   } else {
     if (mixed)
-      k_sweep_strips<float, 8><<<nb, 128, 0, st>>>(L, reinterpret_cast<const float*>(L.tb), L.yz32, rhs, prog, err,
+      launch_pdl(k_sweep_strips<float, 8>, nb, 128, 0, st, L, reinterpret_cast<const float*>(L.tb), L.yz32, rhs, prog, err,
                                                    limit, do_update, aw, alpha);
     else
-      k_sweep_strips<double, 8><<<nb, 128, 0, st>>>(L, L.tb, L.yz64, rhs, prog, err, limit, do_update, aw, alpha);
+      launch_pdl(k_sweep_strips<double, 8>, nb, 128, 0, st, L, L.tb, L.yz64, rhs, prog, err, limit, do_update, aw, alpha);
   }
   return 1;
 }

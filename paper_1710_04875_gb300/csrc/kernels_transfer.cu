@@ -29,6 +29,7 @@ __device__ __forceinline__ void vert(const double* x, const double* y, int k, co
 }
 
 __global__ void k_metrics_fine(LevelDev L, const double* x, const double* y, Motion mo) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int ni = L.ni, V = ni + 1;
   auto vgx = [&](double, double py) { return -mo.phidot * (py - mo.yc); };
@@ -78,6 +79,7 @@ __global__ void k_metrics_fine(LevelDev L, const double* x, const double* y, Mot
 
 // Coarse metrics by agglomerating 2x2 fine cells: face vectors add, volumes add.
 __global__ void k_agglomerate(LevelDev F, LevelDev C) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int ni = C.ni;
   if (t < C.nfx) {
@@ -106,6 +108,7 @@ __global__ void k_agglomerate(LevelDev F, LevelDev C) {
 }
 
 __global__ void k_fill_state(LevelDev L, double w0, double w1, double w2, double w3) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= L.Gn) return;
   L.u[t] = w0;
@@ -115,6 +118,7 @@ __global__ void k_fill_state(LevelDev L, double w0, double w1, double w2, double
 }
 
 __global__ void k_copy_u0(LevelDev L) {
+  pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int i = c % L.ni, j = c / L.ni;
@@ -126,6 +130,7 @@ __global__ void k_copy_u0(LevelDev L) {
 // Volume-weighted agglomeration restriction of the state and of the FAS residual (rhs),
 // and of the eddy viscosity when requested; the coarse state starts at u~.
 __global__ void k_restrict(LevelDev F, LevelDev C, int restrict_mut) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= C.n) return;
   const int I = t % C.ni, J = t / C.ni;
@@ -174,6 +179,7 @@ __device__ __forceinline__ double coarse_delta(const LevelDev& C, int I, int J, 
 // Bilinear prolongation of the correction: 9/16, 3/16, 3/16, 1/16 of the coarse cell
 // containing the fine cell and its three nearest coarse neighbours.
 __global__ void k_prolong(LevelDev F, LevelDev C) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= F.n) return;
   const int i = t % F.ni, j = t / F.ni;
@@ -190,6 +196,7 @@ __global__ void k_prolong(LevelDev F, LevelDev C) {
 }
 
 __global__ void k_pack(LevelDev L, const double* in, int to_ghosted, double* out) {
+  pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int g = gidx(L, c % L.ni, c / L.ni);
@@ -203,12 +210,14 @@ __global__ void k_pack(LevelDev L, const double* in, int to_ghosted, double* out
 }
 
 __global__ void k_f2d(const float* a, double* b, int m) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < m) b[t] = double(a[t]);
 }
 
 // entry-major (e * nf + f) -> face-major (f * 16 + e)
 __global__ void k_blocks_transpose(const double* a, double* b, int nf) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nf * 16) return;
   const int f = t / 16, e = t % 16;
@@ -221,46 +230,47 @@ void launch_metrics_fine(const LevelDev& L, const double* x, const double* y, cu
                          double phidot, double xc, double yc) {
   const int m = L.nfx > L.nfe ? L.nfx : L.nfe;
   Motion mo{cos(phi), sin(phi), phidot, xc, yc, rotate};
-  k_metrics_fine<<<(m + 127) / 128, 128, 0, st>>>(L, x, y, mo);
+  launch_pdl(k_metrics_fine, (m + 127) / 128, 128, 0, st, L, x, y, mo);
 }
 
 // Dual-time source of the finest level: src = c1 u^n + c2 u^(n-1)
 __global__ void k_time_source(double* src, const double* un, const double* unm1, double c1, double c2, int m) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < m) src[t] = c1 * un[t] + (unm1 ? c2 * unm1[t] : 0.0);
 }
 
 void launch_time_source(double* src, const double* un, const double* unm1, double c1, double c2, int m, cudaStream_t st) {
-  k_time_source<<<(m + 255) / 256, 256, 0, st>>>(src, un, unm1, c1, c2, m);
+  launch_pdl(k_time_source, (m + 255) / 256, 256, 0, st, src, un, unm1, c1, c2, m);
 }
 
 void launch_agglomerate(const LevelDev& F, const LevelDev& C, cudaStream_t st) {
   const int m = C.nfx > C.nfe ? C.nfx : C.nfe;
-  k_agglomerate<<<(m + 127) / 128, 128, 0, st>>>(F, C);
+  launch_pdl(k_agglomerate, (m + 127) / 128, 128, 0, st, F, C);
 }
 
 void launch_fill_state(const LevelDev& L, const double w[4], cudaStream_t st) {
-  k_fill_state<<<(L.Gn + 255) / 256, 256, 0, st>>>(L, w[0], w[1], w[2], w[3]);
+  launch_pdl(k_fill_state, (L.Gn + 255) / 256, 256, 0, st, L, w[0], w[1], w[2], w[3]);
 }
 
-void launch_copy_u0(const LevelDev& L, cudaStream_t st) { k_copy_u0<<<(L.n + 255) / 256, 256, 0, st>>>(L); }
+void launch_copy_u0(const LevelDev& L, cudaStream_t st) { launch_pdl(k_copy_u0, (L.n + 255) / 256, 256, 0, st, L); }
 
 void launch_restrict(const LevelDev& F, const LevelDev& C, int restrict_mut, cudaStream_t st) {
-  k_restrict<<<(C.n + 63) / 64, 64, 0, st>>>(F, C, restrict_mut);
+  launch_pdl(k_restrict, (C.n + 63) / 64, 64, 0, st, F, C, restrict_mut);
 }
 
 void launch_prolong(const LevelDev& F, const LevelDev& C, cudaStream_t st) {
-  k_prolong<<<(F.n + 63) / 64, 64, 0, st>>>(F, C);
+  launch_pdl(k_prolong, (F.n + 63) / 64, 64, 0, st, F, C);
 }
 
 void launch_pack(const LevelDev& L, const double* in, int to_ghosted, double* out, cudaStream_t st) {
-  k_pack<<<(L.n + 255) / 256, 256, 0, st>>>(L, in, to_ghosted, out);
+  launch_pdl(k_pack, (L.n + 255) / 256, 256, 0, st, L, in, to_ghosted, out);
 }
 
-void launch_f2d(const float* a, double* b, int m, cudaStream_t st) { k_f2d<<<(m + 255) / 256, 256, 0, st>>>(a, b, m); }
+void launch_f2d(const float* a, double* b, int m, cudaStream_t st) { launch_pdl(k_f2d, (m + 255) / 256, 256, 0, st, a, b, m); }
 
 void launch_blocks_transpose(const double* a, double* b, int nf, cudaStream_t st) {
-  k_blocks_transpose<<<(nf * 16 + 255) / 256, 256, 0, st>>>(a, b, nf);
+  launch_pdl(k_blocks_transpose, (nf * 16 + 255) / 256, 256, 0, st, a, b, nf);
 }
 
 }  // namespace fasw
