@@ -257,7 +257,8 @@ def measure_batched(P, stream, flush, steps, warmup, precision="mixed"):
     b.close()
     return {"cases": len(grids), "cells": cells, "precision": precision, "value": value, "unit": METRIC,
             "ms_per_cycle": sum(ms) / steps,
-            "sweep_choice": {"staged": choice.count(5), "cta": choice.count(2)},
+            "sweep_choice": {"staged8": choice.count(7), "staged4": choice.count(6), "staged": choice.count(5),
+                             "cta": choice.count(2)},
             "time_to_6_orders": {"seconds": dt, "cycles_run": ncy, "status": int(code),
                                  "cases_converged": int((cyc > 0).sum()), "cases_diverged": int((cyc == -2).sum()),
                                  "median_cycles": float(np.median(cyc[cyc > 0])) if (cyc > 0).any() else None}}

@@ -148,9 +148,9 @@ int fasw_use_graphs(fasw_ctx* ctx, int enable);
  * applying the LU blocks (reference kernel), 2 = one CTA with precomputed transfer blocks
  * (strips where a hyperplane exceeds 128 cells), 3 = strip-pipelined with 8 rows per strip,
  * 4 = with 16 rows per strip, 5 = hyperplane-staged (mixed precision only, nj <= 128: blocks
- * stored hyperplane-major and staged through shared memory by cp.async; elsewhere as 0).  All
- * give the same Gauss-Seidel result up to rounding.  Synchronizes the stream; drops captured
- * cycles. */
+ * stored hyperplane-major and staged through shared memory by cp.async; elsewhere as 0), 6 / 7 =
+ * hyperplane-staged with a staging ring of 4 / 8 steps.  All give the same Gauss-Seidel result
+ * up to rounding.  Synchronizes the stream; drops captured cycles. */
 int fasw_set_sweep(fasw_ctx* ctx, int kind);
 
 /* Eddy viscosity of the finest level (Baldwin-Lomax from the current state); n doubles. */
@@ -206,13 +206,15 @@ int fasw_adjoint_objective_gradient(fasw_ctx* ctx, int which, double* g, int on_
 int fasw_adjoint_precond_apply(fasw_ctx* ctx, double cfl, const double* r, double* z, int on_device);
 /* Solves J^T lam = g (g null: the gradient of objective `which`) by restarted GMRES(restart),
  * right-preconditioned by the transpose of the primal preconditioner in additive-W form
- * (section 4: flux-vector-split blocks with the eigenvalue cutoff at the parameters' cfl,
+ * (section 4: flux-vector-split blocks with the eigenvalue cutoff at pseudo CFL cfl, <= 0: the
+ * parameters' cfl; the linear adjoint has no nonlinear stability limit, so cfl can be far
+ * above the primal's,
  * symmetric Gauss-Seidel factors, transposed sweeps in i+j order) scaled by eta dt*, to
  * relative residual tol or max_iters iterations; *iters and *rel_res report both.  Rebuilds
  * the finest level's preconditioner blocks and dt* at the current state.
  * Returns FASW_OK or FASW_ERR_NOT_CONVERGED (lam holds the last iterate). */
 int fasw_adjoint_solve(fasw_ctx* ctx, int which, const double* g, double* lam, double tol, int max_iters, int restart,
-                       int* iters, double* rel_res, int on_device);
+                       double cfl, int* iters, double* rel_res, int on_device);
 /* Shape gradient of objective `which` for nparam vertex fields: vy is nparam x (nj+1) x (ni+1)
  * y-displacements per unit parameter (index k*(nj+1)*(ni+1) + j*(ni+1) + i);
  * grad[k] = dJ/dX V_k - lam^T dF/dX V_k, both X-derivatives by central differences of step
@@ -280,10 +282,12 @@ int fasw_batch_cycle(fasw_batch* batch, int cycle_index, double* norms);
  * final_drop[k] = its last finite norm ratio, *ncycles = cycles run.  Returns FASW_OK,
  * FASW_ERR_NOT_CONVERGED or FASW_ERR_DIVERGED (some case diverged). */
 int fasw_batch_solve(fasw_batch* batch, double drop, int max_cycles, int* cycles, double* final_drop, int* ncycles);
-/* Picks the sweep variant (see fasw_set_sweep) by timing whole batch cycles with each candidate
- * that never waits on another CTA (kinds 5 and 2; strips are excluded because concurrent cases
- * do not guarantee that all CTAs of a sweep are resident); states are saved and restored;
- * choice[k] (nullable) receives the kind used for case k. */
+/* Picks the sweep variant (see fasw_set_sweep) of every case among those that never wait on
+ * another CTA (kinds 7, 6 and 2; strips are excluded because concurrent cases do not guarantee
+ * that all CTAs of a sweep are resident), one grid shape (ni, nj) at a time, by timing whole
+ * batch cycles (states are saved and restored); results are cached per shape and precision for
+ * the process, so a batch whose shapes are all cached is not timed again.  choice[k] (nullable)
+ * receives the kind used for case k. */
 int fasw_batch_autotune(fasw_batch* batch, int* choice);
 long long fasw_batch_launch_count(fasw_batch* batch);
 

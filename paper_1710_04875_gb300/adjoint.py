@@ -19,13 +19,13 @@ class AdjointContext:
     """Primal and adjoint settings shared by the forward and backward passes."""
 
     def __init__(self, grid_of, fields, params, drop=1e-12, max_cycles=2000, h_rel=1e-6, h_x=1e-6,
-                 tol=1e-10, max_iters=1500, restart=60, warm_state=None):
+                 tol=1e-10, max_iters=1500, restart=60, cfl=0.0, warm_state=None):
         self.grid_of = grid_of
         self.fields = np.ascontiguousarray(fields, dtype=np.float64)
         self.params = params
         self.drop, self.max_cycles = drop, max_cycles
         self.h_rel, self.h_x = h_rel, h_x
-        self.tol, self.max_iters, self.restart = tol, max_iters, restart
+        self.tol, self.max_iters, self.restart, self.cfl = tol, max_iters, restart, cfl
         self.warm_state = warm_state
         self.solver = None
         self.info = {}
@@ -54,7 +54,7 @@ class ShapeForces(torch.autograd.Function):
         s.adjoint_jacobian(a.h_rel)
         grads = []
         for which in (0, 1):
-            lam, code, it, rr = s.adjoint_solve(which, tol=a.tol, max_iters=a.max_iters, restart=a.restart)
+            lam, code, it, rr = s.adjoint_solve(which, tol=a.tol, max_iters=a.max_iters, restart=a.restart, cfl=a.cfl)
             a.info[("adjoint", which)] = (int(code), it, rr)
             grads.append(s.adjoint_shape_gradient(which, lam, a.fields, a.h_x))
         g = torch.tensor(np.stack(grads), dtype=torch.float64)  # (2, nparam)

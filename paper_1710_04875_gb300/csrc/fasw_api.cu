@@ -6,6 +6,9 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "../../include/fasw.h"
@@ -216,7 +219,7 @@ void free_stream(double mach, double alpha_deg, double w[4]) {
 // level or precision falls back the same way.
 int level_sweep_kind(const fasw_ctx* c, const LevelDev& L) {
   int k = c->sweep_kind;
-  if (k == SWEEP_AUTO || (k == SWEEP_HP && !(c->mixed && L.hpF)))
+  if (k == SWEEP_AUTO || (is_hp(k) && !(c->mixed && L.hpF)))
     k = c->mixed ? (L.hpF ? SWEEP_HP : SWEEP_CTA) : SWEEP_STRIPS;
   return k;
 }
@@ -719,7 +722,7 @@ int fasw_adjoint_precond_apply(fasw_ctx* c, double cfl, const double* r, double*
 }
 
 int fasw_adjoint_solve(fasw_ctx* c, int which, const double* g, double* lam, double tol, int max_iters, int restart,
-                       int* iters, double* rel_res, int on_device) {
+                       double cfl, int* iters, double* rel_res, int on_device) {
   if (!c || !lam || !iters || !rel_res || !c->adj.built || !(tol > 0.0) || max_iters < 1) return FASW_ERR_ARG;
   if (!g && (which < 0 || which > 1)) return FASW_ERR_ARG;
   const size_t m = 4 * (size_t)c->adj.n;
@@ -729,8 +732,9 @@ int fasw_adjoint_solve(fasw_ctx* c, int which, const double* g, double* lam, dou
     if (r) return r;
     rhs = c->d_tmp;
   }
-  const int code = adj_solve(c->adj, c->lev[c->L()], c->ph, c->sc, c->prm.cfl, rhs, c->d_tmp2, tol, max_iters,
-                             restart, c->allocs, c->st, iters, rel_res, c->launches);
+  const double pcfl = cfl > 0.0 ? cfl : c->prm.cfl;
+  const int code = adj_solve(c->adj, c->lev[c->L()], c->ph, c->sc, pcfl, rhs, c->d_tmp2, tol, max_iters, restart,
+                             c->allocs, c->st, iters, rel_res, c->launches);
   if (code != FASW_OK && code != FASW_ERR_NOT_CONVERGED) return code;
   int r = copy_out(c, lam, c->d_tmp2, m, on_device);
   if (r) return r;
@@ -776,7 +780,7 @@ int fasw_adjoint_shape_gradient(fasw_ctx* c, int which, const double* lam, int n
 }
 
 int fasw_set_sweep(fasw_ctx* c, int kind) {
-  if (!c || kind < SWEEP_AUTO || kind > SWEEP_HP) return FASW_ERR_ARG;
+  if (!c || kind < SWEEP_AUTO || kind > SWEEP_HP8) return FASW_ERR_ARG;
   int r = sync(c);
   if (r) return r;
   c->sweep_kind = kind;
@@ -1063,63 +1067,121 @@ int fasw_batch_solve(fasw_batch* b, double drop, int max_cycles, int* cycles, do
   return diverged ? FASW_ERR_DIVERGED : FASW_ERR_NOT_CONVERGED;
 }
 
-// Autotuner: the sweep variants that never wait on another CTA (the hyperplane-staged FP32
-// sweep and the one-CTA sweep) trade staging depth against per-step work, and which wins
-// depends on how full the GPU is, so each candidate is timed on whole batch cycles (all cases
-// concurrently, CUDA events) and the fastest is kept.  Strip-pipelined sweeps are not
-// candidates here: their CTAs wait on one another, which is safe only while all CTAs of one
-// sweep are resident, and concurrent branches of a batch graph do not guarantee that.
-// The cases' states are saved before and restored after.
+// Autotuner.  Candidates are the sweep variants whose CTAs never wait on one another (strip
+// sweeps are not candidates: their CTAs wait on each other, which is safe only while all CTAs
+// of one sweep are resident, and concurrent branches of a batch graph do not guarantee that):
+// the hyperplane-staged FP32 sweep with a ring of 8 or 4 steps and the one-CTA sweep.  Which
+// wins depends on the grid shape and on how full the GPU is, so the tuner times whole batch
+// cycles (all cases concurrently, CUDA events, states saved and restored) and improves the
+// choice one grid shape (ni, nj) at a time, keeping a change only when the batch gets faster.
+// Results are cached per (ni, nj, precision) for the process: a later batch whose shapes are
+// all cached takes them without timing.
+namespace {
+struct TuneKey {
+  int ni, nj, mixed;
+  bool operator<(const TuneKey& o) const {
+    return ni != o.ni ? ni < o.ni : nj != o.nj ? nj < o.nj : mixed < o.mixed;
+  }
+};
+std::map<TuneKey, int> g_tune_cache;
+std::mutex g_tune_mutex;
+
+TuneKey key_of(fasw_ctx* c) {
+  const LevelDev& F = c->lev[c->L()];
+  return TuneKey{F.ni, F.nj, c->mixed};
+}
+}  // namespace
+
+// Times `reps` batch cycles with kinds[k] on case k (after one capturing cycle); states restored.
+static int batch_time(fasw_batch* b, const std::vector<int>& kinds, const std::vector<double*>& saved, int reps,
+                      cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  for (size_t k = 0; k < b->cases.size(); ++k) {
+    b->cases[k]->sweep_kind = kinds[k];
+    drop_graphs(b->cases[k]);
+  }
+  batch_drop_graphs(b);
+  int r = fasw_batch_cycle(b, 0, nullptr);  // capture + warm-up
+  if (r) return r;
+  CKR(cudaEventRecord(e0, b->st));
+  for (int rep = 0; rep < reps; ++rep)
+    if ((r = fasw_batch_cycle(b, 0, nullptr))) return r;
+  CKR(cudaEventRecord(e1, b->st));
+  CKR(cudaEventSynchronize(e1));
+  CKR(cudaEventElapsedTime(ms, e0, e1));
+  for (size_t k = 0; k < b->cases.size(); ++k) {  // restore the states
+    fasw_ctx* c = b->cases[k];
+    launch_pack(c->lev[c->L()], saved[k], 1, nullptr, c->st);
+    launch_bc(c->lev[c->L()], c->ph, c->st);
+    CKR(cudaStreamSynchronize(c->st));
+  }
+  return FASW_OK;
+}
+
 // choice (nullable, ncases): the kind used for case k.
 int fasw_batch_autotune(fasw_batch* b, int* choice) {
   if (!b) return FASW_ERR_ARG;
-  const int kinds[2] = {SWEEP_HP, SWEEP_CTA};
-  std::vector<double*> saved(b->cases.size(), nullptr);
-  for (size_t k = 0; k < b->cases.size(); ++k) {
-    fasw_ctx* c = b->cases[k];
-    saved[k] = c->d_tmp2;  // 4 x n of the finest level
-    launch_pack(c->lev[c->L()], nullptr, 0, saved[k], c->st);
-    CKR(cudaStreamSynchronize(c->st));
+  const size_t nc = b->cases.size();
+  std::vector<int> kinds(nc, SWEEP_HP);
+  std::map<TuneKey, std::vector<size_t>> groups;
+  for (size_t k = 0; k < nc; ++k) groups[key_of(b->cases[k])].push_back(k);
+  bool all_cached = true;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    for (auto& gk : groups) {
+      auto it = g_tune_cache.find(gk.first);
+      if (it == g_tune_cache.end()) {
+        all_cached = false;
+        continue;
+      }
+      for (size_t k : gk.second) kinds[k] = it->second;
+    }
   }
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  int best = SWEEP_CTA;
-  float best_ms = 1e30f;
-  for (int kind : kinds) {
-    for (fasw_ctx* c : b->cases) {
-      c->sweep_kind = kind;
-      drop_graphs(c);
-    }
-    batch_drop_graphs(b);
-    int r = fasw_batch_cycle(b, 0, nullptr);  // capture + warm-up
-    if (r) return r;
-    cudaEventRecord(e0, b->st);
-    for (int rep = 0; rep < 2; ++rep) {
-      r = fasw_batch_cycle(b, 0, nullptr);
-      if (r) return r;
-    }
-    cudaEventRecord(e1, b->st);
-    CKR(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = kind;
-    }
-    for (size_t k = 0; k < b->cases.size(); ++k) {  // restore the states
+  if (!all_cached) {
+    std::vector<double*> saved(nc, nullptr);
+    for (size_t k = 0; k < nc; ++k) {
       fasw_ctx* c = b->cases[k];
-      launch_pack(c->lev[c->L()], saved[k], 1, nullptr, c->st);
-      launch_bc(c->lev[c->L()], c->ph, c->st);
+      saved[k] = c->d_tmp2;  // 4 x n of the finest level
+      launch_pack(c->lev[c->L()], nullptr, 0, saved[k], c->st);
       CKR(cudaStreamSynchronize(c->st));
     }
+    cudaEvent_t e0, e1;
+    CKR(cudaEventCreate(&e0));
+    CKR(cudaEventCreate(&e1));
+    const int reps = 3;
+    float best = 0.f;
+    int r = batch_time(b, kinds, saved, reps, e0, e1, &best);
+    const int cand[3] = {SWEEP_HP8, SWEEP_HP4, SWEEP_CTA};
+    // larger shapes first: they dominate the batch time
+    std::vector<std::pair<TuneKey, std::vector<size_t>>> order(groups.begin(), groups.end());
+    std::sort(order.begin(), order.end(), [](const auto& x, const auto& y) {
+      return (long long)x.first.ni * x.first.nj * x.second.size() > (long long)y.first.ni * y.first.nj * y.second.size();
+    });
+    for (size_t gi = 0; gi < order.size() && r == FASW_OK; ++gi) {
+      const std::vector<size_t>& members = order[gi].second;
+      const int cur = kinds[members[0]];
+      int keep = cur;
+      for (int k : cand) {
+        if (k == cur || r) continue;
+        for (size_t m : members) kinds[m] = k;
+        float ms = 0.f;
+        r = batch_time(b, kinds, saved, reps, e0, e1, &ms);
+        if (r == FASW_OK && ms < 0.99f * best) {
+          best = ms;
+          keep = k;
+        }
+        for (size_t m : members) kinds[m] = keep;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r) return r;
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    for (auto& gk : groups) g_tune_cache[gk.first] = kinds[gk.second[0]];
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  for (size_t k = 0; k < b->cases.size(); ++k) {
-    b->cases[k]->sweep_kind = best;
+  for (size_t k = 0; k < nc; ++k) {
+    b->cases[k]->sweep_kind = kinds[k];
     drop_graphs(b->cases[k]);
-    if (choice) choice[k] = best;
+    if (choice) choice[k] = kinds[k];
   }
   batch_drop_graphs(b);
   return FASW_OK;

@@ -704,7 +704,7 @@ __global__ void k_hp_finish(LevelDev L, int do_update, int aw, double alpha) {
 }  // namespace
 
 void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st) {
-  if (mixed && kind == SWEEP_HP && L.hpF)
+  if (mixed && is_hp(kind) && L.hpF)
     launch_pdl(k_sgs_prep<float, true>, (L.n + 63) / 64, 64, 0, st, L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
   else if (mixed)
     launch_pdl(k_sgs_prep<float, false>, (L.n + 63) / 64, 64, 0, st, L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
@@ -728,9 +728,11 @@ bool hp_fits(int ni, int nj, int nw) {
 
 int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, double alpha, const double* rhs,
                  long long* prog, int* err, long long limit, cudaStream_t st) {
-  if (kind == SWEEP_HP && mixed && L.hpF) {
+  if (is_hp(kind) && mixed && L.hpF) {
     launch_pdl(k_hp_cy, (L.n + 127) / 128, 128, 0, st, L, reinterpret_cast<const float*>(L.tb), rhs);
-    const int nt = hp_threads(L.nj), stages = hp_stages(nt);
+    const int nt = hp_threads(L.nj);
+    int stages = kind == SWEEP_HP4 ? 4 : kind == SWEEP_HP8 ? 8 : hp_stages(nt);
+    if (hp_smem_bytes(stages, nt, nt / 4, L.ni, L.nw) > kHpSmemMax) stages = 4;  // hp_fits checked 4 or 8
     const size_t sm = hp_smem_bytes(stages, nt, nt / 4, L.ni, L.nw);
     if (stages == 8) {
       static bool attr8 = false;
@@ -750,7 +752,7 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
     launch_pdl(k_hp_finish, (L.n + 63) / 64, 64, 0, st, L, do_update, aw, alpha);
     return 3;
   }
-  if (kind == SWEEP_HP) kind = mixed ? SWEEP_CTA : SWEEP_STRIPS;
+  if (is_hp(kind)) kind = mixed ? SWEEP_CTA : SWEEP_STRIPS;
   const int cells = L.ni < L.nj ? L.ni : L.nj;  // longest hyperplane
   const bool cta_fits = 4 * cells <= 512;       // one thread slot per cell of a hyperplane
   if ((kind == SWEEP_CTA || (mixed && kind != SWEEP_STRIPS && kind != SWEEP_STRIPS16)) && cta_fits) {

@@ -89,7 +89,7 @@ def library():
             "fasw_adjoint_jacobian": (i, [p, d]),
             "fasw_adjoint_apply": (i, [p, dp, dp, i, i]),
             "fasw_adjoint_objective_gradient": (i, [p, i, dp, i]),
-            "fasw_adjoint_solve": (i, [p, i, dp, dp, d, i, i, C.POINTER(i), C.POINTER(d), i]),
+            "fasw_adjoint_solve": (i, [p, i, dp, dp, d, i, i, d, C.POINTER(i), C.POINTER(d), i]),
             "fasw_adjoint_precond_apply": (i, [p, d, dp, dp, i]),
             "fasw_adjoint_shape_gradient": (i, [p, i, dp, i, dp, d, dp, i]),
             "fasw_residual_noalloc": (i, [i, i, i, dp, dp, dp, dp, C.POINTER(Params), p]),
@@ -273,8 +273,9 @@ class Solver:
 
     def set_sweep(self, kind):
         """0 auto, 1 reference (one thread per cell), 2 one CTA, 3 strips of 8 rows, 4 strips of 16,
-        5 hyperplane-staged (mixed precision)."""
-        kinds = {"auto": 0, "reference": 1, "cta": 2, "strips": 3, "strips16": 4, "staged": 5}
+        5 hyperplane-staged (mixed precision), 6 / 7 staged with a ring of 4 / 8 steps."""
+        kinds = {"auto": 0, "reference": 1, "cta": 2, "strips": 3, "strips16": 4, "staged": 5, "staged4": 6,
+                 "staged8": 7}
         _check(self.lib.fasw_set_sweep(self.h, kinds.get(kind, kind)), "fasw_set_sweep")
 
     def use_graphs(self, enable: bool):
@@ -323,16 +324,17 @@ class Solver:
                "fasw_adjoint_precond_apply")
         return z
 
-    def adjoint_solve(self, which=0, g=None, tol=1e-10, max_iters=400, restart=40):
-        """(lam, code, iterations, relative residual) of J^T lam = g (g None: objective which)."""
+    def adjoint_solve(self, which=0, g=None, tol=1e-10, max_iters=400, restart=40, cfl=0.0):
+        """(lam, code, iterations, relative residual) of J^T lam = g (g None: objective which);
+        cfl: pseudo CFL of the preconditioner (<= 0: the parameters')."""
         lam = np.zeros(self._shape(self.finest))
         gp = None
         if g is not None:
             g = np.ascontiguousarray(g, dtype=np.float64)
             gp = g.ctypes.data
         it, rr = C.c_int(), C.c_double()
-        code = self.lib.fasw_adjoint_solve(self.h, which, gp, lam.ctypes.data, tol, max_iters, restart, C.byref(it),
-                                           C.byref(rr), 0)
+        code = self.lib.fasw_adjoint_solve(self.h, which, gp, lam.ctypes.data, tol, max_iters, restart, cfl,
+                                           C.byref(it), C.byref(rr), 0)
         if code not in (0, -6):
             _check(code, "fasw_adjoint_solve")
         return lam, code, it.value, rr.value

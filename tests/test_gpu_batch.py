@@ -36,9 +36,27 @@ def test_batch_solve_and_autotune():
     gs, ps = zip(*[_case(*c) for c in CASES])
     b = P.fasw.Batch(list(gs), list(ps))
     choice = b.autotune()
-    assert all(c in (2, 5) for c in choice)
+    assert all(c in (2, 5, 6, 7) for c in choice)
     code, cycles, drops, ncy = b.solve(1e-3, 120)
     assert code == 0 and np.all(cycles > 0) and np.all(drops <= 1e-3)
     ref = P.Solver(gs[0], ps[0])
     c0, n0, h0 = ref.solve(1e-3, 120)
     assert abs(n0 - cycles[0]) <= 1
+
+
+def test_autotune_choices_are_cached_per_shape():
+    """A second batch with the same grid shapes takes the cached choices without timing, and
+    cases of one shape share one choice."""
+    import time
+    gs, ps = zip(*[_case(*c) for c in CASES])
+    b1 = P.fasw.Batch(list(gs), list(ps))
+    c1 = b1.autotune()
+    b2 = P.fasw.Batch(list(gs), list(ps))
+    t0 = time.perf_counter()
+    c2 = b2.autotune()
+    assert list(c1) == list(c2)
+    assert time.perf_counter() - t0 < 1.0
+    shapes = {}
+    for g, c in zip(gs, c1):
+        shapes.setdefault((g.ni, g.nj), set()).add(c)
+    assert all(len(v) == 1 for v in shapes.values())

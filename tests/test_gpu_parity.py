@@ -214,7 +214,7 @@ def test_sweep_kinds_match_the_oracle(kind, scheme, ni, nj, nw):
     assert rel_err(zg, zo) < 1e-11
 
 
-@pytest.mark.parametrize("kind", ["staged", "cta", "strips"])
+@pytest.mark.parametrize("kind", ["staged", "staged4", "staged8", "cta", "strips"])
 @pytest.mark.parametrize("ni,nj,nw", [(128, 32, 16), (72, 20, 8), (16, 6, 2), (256, 64, 32), (128, 128, 16)])
 def test_mixed_sweep_is_the_fp32_preconditioner(kind, ni, nj, nw):
     """Mixed precision: every FP32 sweep kernel applies the oracle's operator to FP32 accuracy,
