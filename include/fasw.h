@@ -200,18 +200,17 @@ int fasw_adjoint_jacobian(fasw_ctx* ctx, double h_rel);
 int fasw_adjoint_apply(fasw_ctx* ctx, const double* v, double* out, int transpose, int on_device);
 /* State gradient dJ/du of objective `which` (as assembled with J). */
 int fasw_adjoint_objective_gradient(fasw_ctx* ctx, int which, double* g, int on_device);
-/* z = P^-T r with the adjoint preconditioner of fasw_adjoint_solve built at pseudo CFL cfl:
- * P = S^-1 W, W the primal additive-W preconditioner (D+L) D^-1 (D+U), S = eta dt* per cell;
- * so z = S (D+L)^-T D^T (D+U)^-T r.  Rebuilds the finest level's blocks and dt*. */
-int fasw_adjoint_precond_apply(fasw_ctx* ctx, double cfl, const double* r, double* z, int on_device);
+/* Adjoint preconditioner, built at pseudo CFL cfl at the current state: P = S^-1 W, W the primal
+ * additive-W preconditioner (D+L) D^-1 (D+U) (section 4), S = eta dt* per cell.  steps = 0:
+ * z = P^-T r = S (D+L)^-T D^T (D+U)^-T r; steps > 0: z = that many steps from zero of the
+ * transposed primal stage loop x_i = x_0 + (alpha_i / eta) P^-T (r - J^T x_{i-1}) (needs
+ * fasw_adjoint_jacobian first).  Rebuilds the finest level's preconditioner blocks and dt*. */
+int fasw_adjoint_precond_apply(fasw_ctx* ctx, double cfl, int steps, const double* r, double* z, int on_device);
 /* Solves J^T lam = g (g null: the gradient of objective `which`) by restarted GMRES(restart),
- * right-preconditioned by the transpose of the primal preconditioner in additive-W form
- * (section 4: flux-vector-split blocks with the eigenvalue cutoff at pseudo CFL cfl, <= 0: the
- * parameters' cfl; the linear adjoint has no nonlinear stability limit, so cfl can be far
- * above the primal's,
- * symmetric Gauss-Seidel factors, transposed sweeps in i+j order) scaled by eta dt*, to
- * relative residual tol or max_iters iterations; *iters and *rel_res report both.  Rebuilds
- * the finest level's preconditioner blocks and dt* at the current state.
+ * restart <= 251, to relative residual tol or max_iters iterations; *iters and *rel_res report
+ * both.  Right preconditioner: four steps of the transposed primal stage loop of
+ * fasw_adjoint_precond_apply, built at pseudo CFL cfl (<= 0: the parameters' cfl).  Rebuilds
+ * the finest level's preconditioner blocks and dt*.
  * Returns FASW_OK or FASW_ERR_NOT_CONVERGED (lam holds the last iterate). */
 int fasw_adjoint_solve(fasw_ctx* ctx, int which, const double* g, double* lam, double tol, int max_iters, int restart,
                        double cfl, int* iters, double* rel_res, int on_device);

@@ -30,7 +30,15 @@ struct AdjointDev {
   double* kry = nullptr;   // (restart + 2) * 4n Krylov basis and work vectors
   int restart = 0;
   bool built = false;      // Jacobian assembled at the current state
-  LevelDev Lp{};           // finest level whose transfer blocks hold the preconditioner
+  LevelDev Lp{};           // level whose transfer blocks hold the preconditioner
+  double* mgs = nullptr;   // smoother work vectors (4n each): residual, preconditioner scratch
+  double* mgy = nullptr;   // and output
+  double* mgt = nullptr;
+  double* mgz = nullptr;   // start vector of a smoothing step
+  // stage coefficients of the smoother: c_i = alpha_i / eta of the primal AW scheme (the primal
+  // step u - alpha_i W^-1 dt* r is u - (alpha_i / eta) P^-1 r), set with the preconditioner
+  double stage_c[5] = {1.0, 0.0, 0.0, 0.0, 0.0};
+  int nstages = 1;
 };
 
 // Host-side stencil, colouring and reverse map; allocates the device arrays (cudaMalloc).
@@ -39,9 +47,9 @@ int adj_setup(AdjointDev& A, int ni, int nj, int nw, std::vector<void*>& allocs,
 int adj_assemble(AdjointDev& A, const LevelDev& L, const PhysParams& ph, double h_rel, cudaStream_t st,
                  long long& launches);
 void adj_apply(const AdjointDev& A, const double* v, double* out, int transpose, cudaStream_t st);
-// GMRES(restart) on J^T lam = g, right-preconditioned by the transposed primal AW
-// preconditioner built on L at pseudo CFL cfl (overwrites L's blocks and dt*); returns FASW_OK
-// or FASW_ERR_NOT_CONVERGED; *iters, *relres.
+// GMRES(restart) on J^T lam = g, right-preconditioned by steps of the transposed primal stage
+// loop with the transposed AW preconditioner built on L at pseudo CFL cfl (overwrites L's
+// blocks and dt*); returns FASW_OK or FASW_ERR_NOT_CONVERGED; *iters, *relres.
 int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const SchemeParams& sc, double cfl,
               const double* g, double* lam, double tol, int max_iters, int restart, std::vector<void*>& allocs,
               cudaStream_t st, int* iters, double* relres, long long& launches);
@@ -53,6 +61,9 @@ int adj_force_coefficients(AdjointDev& A, const LevelDev& L, const PhysParams& p
 void adj_build_precond(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const SchemeParams& sc, double cfl,
                        cudaStream_t st, long long& launches);
 void adj_precond(const AdjointDev& A, const double* r, double* scratch, double* z, cudaStream_t st);
+// z = P^-T r (steps <= 0) or z = `steps` transposed stage-loop steps from zero; the
+// preconditioner must be built.
+void adj_steps_apply(AdjointDev& A, int steps, const double* r, double* z, cudaStream_t st);
 // out = x + a v (device vectors of length m).
 void adj_lincomb(int m, const double* x, double a, const double* v, double* out, cudaStream_t st);
 // Deterministic dot product of two device vectors of length m.

@@ -708,14 +708,15 @@ int fasw_adjoint_objective_gradient(fasw_ctx* c, int which, double* g, int on_de
   return sync(c);
 }
 
-int fasw_adjoint_precond_apply(fasw_ctx* c, double cfl, const double* r, double* z, int on_device) {
-  if (!c || !r || !z || !(cfl > 0.0) || c->ph.moving) return FASW_ERR_ARG;
+int fasw_adjoint_precond_apply(fasw_ctx* c, double cfl, int steps, const double* r, double* z, int on_device) {
+  if (!c || !r || !z || !(cfl > 0.0) || steps < 0 || c->ph.moving) return FASW_ERR_ARG;
+  if (steps > 0 && !c->adj.built) return FASW_ERR_ARG;
   int e = adj_ready(c);
   if (e) return e;
   const size_t m = 4 * (size_t)c->adj.n;
   if ((e = copy_in(c, c->d_tmp, r, m, on_device))) return e;
   adj_build_precond(c->adj, c->lev[c->L()], c->ph, c->sc, cfl, c->st, c->launches);
-  adj_precond(c->adj, c->d_tmp, c->adj.Fp, c->d_tmp2, c->st);
+  adj_steps_apply(c->adj, steps, c->d_tmp, c->d_tmp2, c->st);
   c->launches += 2;
   if ((e = copy_out(c, z, c->d_tmp2, m, on_device))) return e;
   return sync(c);

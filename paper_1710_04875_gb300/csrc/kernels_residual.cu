@@ -11,9 +11,12 @@ namespace {
 // warp mixes the two kinds of face and a j-face (with the viscous terms) is a thread of its
 // own: on GB300 an SM sub-partition issues one FP64 warp-instruction every few dozen cycles,
 // so the FP64 work of a launch is spread over as many warps and SMs as the grid allows.
+// Tile height 4 where that still gives at least half as many blocks as SMs, else 1: a coarse
+// level then spreads over four times as many SMs for 1.6 times the j-face work (its j-faces are
+// computed by both neighbouring tiles).
 constexpr int TX = 31;
-constexpr int TY = 4;
-constexpr int RES_THREADS = 32 * (2 * TY + 1);
+constexpr int res_threads(int ty) { return 32 * (2 * ty + 1); }
+inline int res_ty(const LevelDev& L) { return ((L.ni + TX - 1) / TX) * ((L.nj + 3) / 4) >= 76 ? 4 : 1; }
 
 __device__ __forceinline__ int gidx(const LevelDev& L, int i, int j) { return (j + 2) * L.P + (i + 2); }
 __device__ __forceinline__ bool on_cut(const LevelDev& L, int i) { return L.nw > 0 && (i < L.nw || i >= L.ni - L.nw); }
@@ -371,11 +374,12 @@ __device__ double block_sum(double v, double* wsum) {
 
 // One tile of TX x TY cells: every face of the tile is computed once into shared memory,
 // then each cell assembles F^c and F^v and writes what the mode asks for.
-__global__ void __launch_bounds__(RES_THREADS) k_residual(LevelDev L, PhysParams ph, ResArgs a) {
+template <int TY>
+__global__ void __launch_bounds__(res_threads(TY)) k_residual(LevelDev L, PhysParams ph, ResArgs a) {
   pdl_entry();
   __shared__ double xc[4][TY][TX + 1], xd[4][TY][TX + 1];
   __shared__ double ec[4][TY + 1][TX], ed[4][TY + 1][TX];
-  __shared__ double wsum[RES_THREADS / 32];
+  __shared__ double wsum[2 * TY + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int ni = L.ni, nj = L.nj;
@@ -626,11 +630,19 @@ void launch_wall_force(const LevelDev& L, const PhysParams& ph, double* fx, doub
   launch_pdl(k_wall_force, (L.ni + 63) / 64, 64, 0, st, L, ph, fx, fy);
 }
 
-int residual_blocks(const LevelDev& L) { return ((L.ni + TX - 1) / TX) * ((L.nj + TY - 1) / TY); }
+int residual_blocks(const LevelDev& L) {
+  const int ty = res_ty(L);
+  return ((L.ni + TX - 1) / TX) * ((L.nj + ty - 1) / ty);
+}
 
 void launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, cudaStream_t st) {
-  dim3 grid((L.ni + TX - 1) / TX, (L.nj + TY - 1) / TY);
-  launch_pdl(k_residual, grid, RES_THREADS, 0, st, L, ph, a);
+  if (res_ty(L) == 4) {
+    dim3 grid((L.ni + TX - 1) / TX, (L.nj + 3) / 4);
+    launch_pdl(k_residual<4>, grid, res_threads(4), 0, st, L, ph, a);
+  } else {
+    dim3 grid((L.ni + TX - 1) / TX, L.nj);
+    launch_pdl(k_residual<1>, grid, res_threads(1), 0, st, L, ph, a);
+  }
 }
 
 void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* out, cudaStream_t st) {

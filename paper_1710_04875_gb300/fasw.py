@@ -90,7 +90,7 @@ def library():
             "fasw_adjoint_apply": (i, [p, dp, dp, i, i]),
             "fasw_adjoint_objective_gradient": (i, [p, i, dp, i]),
             "fasw_adjoint_solve": (i, [p, i, dp, dp, d, i, i, d, C.POINTER(i), C.POINTER(d), i]),
-            "fasw_adjoint_precond_apply": (i, [p, d, dp, dp, i]),
+            "fasw_adjoint_precond_apply": (i, [p, d, i, dp, dp, i]),
             "fasw_adjoint_shape_gradient": (i, [p, i, dp, i, dp, d, dp, i]),
             "fasw_residual_noalloc": (i, [i, i, i, dp, dp, dp, dp, C.POINTER(Params), p]),
             "fasw_batch_create": (i, [i, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(C.c_void_p),
@@ -316,11 +316,13 @@ class Solver:
                "fasw_adjoint_objective_gradient")
         return out
 
-    def adjoint_precond_apply(self, r, cfl):
-        """z = P^-T r, the adjoint preconditioner (transposed primal AW preconditioner, scaled)."""
+    def adjoint_precond_apply(self, r, cfl, steps=0):
+        """z = P^-T r, the transposed primal AW preconditioner scaled by eta dt* (steps 0), or that
+        many steps of the transposed primal stage loop from zero (the GMRES preconditioner)."""
         r = np.ascontiguousarray(r, dtype=np.float64)
         z = np.zeros(self._shape(self.finest))
-        _check(self.lib.fasw_adjoint_precond_apply(self.h, cfl, r.ctypes.data, z.ctypes.data, 0),
+        _check(self.lib.fasw_adjoint_precond_apply(self.h, cfl, int(steps), r.ctypes.data, z.ctypes.data,
+                                                   0),
                "fasw_adjoint_precond_apply")
         return z
 

@@ -60,6 +60,24 @@ def test_adjoint_preconditioner_is_the_transposed_primal_w():
     assert rel_err(z.ravel(), ref) < 1e-11
 
 
+def test_adjoint_smoother_is_the_transposed_stage_loop():
+    """One smoothing step of the adjoint preconditioner equals the transposed AW3 stage loop
+    x_i = x_0 + (alpha_i / eta) P^-T (r - J^T x_{i-1}) assembled here from the library's own
+    J^T and P^-T products."""
+    g = make_cgrid(64, 16)
+    _, s = _euler_pair(g)
+    u = perturbed_state(0.6, ALPHA, 16, 64, amp=0.03, seed=4)
+    s.set_state(u)
+    s.adjoint_jacobian(1e-6)
+    r = np.random.default_rng(11).standard_normal((4, 16, 64))
+    cfl = 1e4
+    x = np.zeros_like(r)
+    for a in (0.1481, 2.0 / 5.0, 1.0):                      # AW3 stage coefficients (eta = 0.8)
+        x = a / 0.8 * s.adjoint_precond_apply(r - s.adjoint_apply(x, transpose=True), cfl)
+    z = s.adjoint_precond_apply(r, cfl, steps=1)
+    assert rel_err(z, x) < 1e-12
+
+
 def test_force_coefficients_match_the_oracle():
     g = make_cgrid(64, 16)
     o, s = _euler_pair(g)
