@@ -197,6 +197,27 @@ def time_cycles(s, stream, flush, steps, k0):
     return ms
 
 
+def measure_c3(P, stream, flush, steps, warmup):
+    """W-cycle device time on the 512 x 128 C-grid of the pitching case (thin-layer RANS with
+    Baldwin-Lomax, M 0.8, Re 1e6, 4 levels), FP64 and mixed precision, from the free stream."""
+    from synth.cases import config_c3
+    c = config_c3()
+    g = c.grid()
+    out = {"cells": g.ni * g.nj}
+    for prec in ("fp64", "mixed"):
+        p = P.default_params(scheme="AW3", nlevels=4, gamma_cycle=2, viscous=1, turb=1, sensor=1, mach=c.mach,
+                             alpha_deg=0.0, re=c.reynolds, eta=0.8, d_cut=0.5, cfl=100.0, cfl_ramp=20.0,
+                             ramp_cycles=2, precision=prec)
+        s = P.Solver(g, p, stream=stream.cuda_stream)
+        for k in range(warmup):
+            s.fas_cycle(k)
+        ms = time_cycles(s, stream, flush, steps, warmup)
+        out[prec] = {"ms_per_cycle": sum(ms) / len(ms), "value": g.ni * g.nj * len(ms) / (sum(ms) / 1e3) / 1e6,
+                     "unit": METRIC}
+        s.close()
+    return out
+
+
 def measure_adjoint(s, g, n_bumps=16):
     """Discrete adjoint of the steady RANS workload at its 6-order state (eddy viscosity
     frozen): Jacobian assembly, the GMRES adjoint solve for C_D, and the shape gradient of C_D
@@ -326,6 +347,9 @@ def main():
     other_value = world * ncell * args.steps / (sum(ms_other) / 1e3) / 1e6
     sm.close()
 
+    # the 512x128 pitching-airfoil grid (M 0.8, Re 1e6): W-cycle throughput of both precisions
+    c3 = measure_c3(P, stream, flush, min(args.steps, 10), args.warmup)
+
     # per-kernel device time over a second pass of the same number of cycles
     s.profile(True)
     for k in range(args.steps):
@@ -427,7 +451,7 @@ def main():
             "other_precision": {"precision": "mixed" if args.precision == "fp64" else "fp64",
                                 "value": other_value, "ms_per_step": sum(ms_other) / args.steps},
             "time_to_6_orders": drops, "time_to_11_orders_per_time_step": unsteady,
-            "batched_64_cases": batched, "adjoint": adjoint, "kernel_share": share,
+            "batched_64_cases": batched, "c3_512x128": c3, "adjoint": adjoint, "kernel_share": share,
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes + 8},
             "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "cpu_baseline": cpu}
