@@ -51,6 +51,21 @@ def level_visits(nlevels, gamma):
     return v
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (the slowest rank's time); x itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(ncell, steps, world, tot_ms):
+    """Mcell-iter/s of the whole job: every rank's cells and cycles over the slowest rank's time."""
+    return world * ncell * steps / (tot_ms / 1e3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -331,13 +346,10 @@ def main():
         ms = time_cycles(s, stream, flush, args.steps, args.warmup)
     launches = (s.launch_count() - l0) // max(args.steps, 1) * args.steps
     torch.cuda.synchronize()
-    tot_ms = float(sum(ms))
+    tot_ms = max_over_ranks(float(sum(ms)), dist, "cuda")
     if dist:
-        t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
         dist.barrier()
-    value = world * ncell * args.steps / (tot_ms / 1e3) / 1e6
+    value = whole_job_value(ncell, args.steps, world, tot_ms)
 
     # same measurement with the mixed-precision preconditioner (FP32 blocks / sweeps)
     sm = P.Solver(g, gpu_params(P, "mixed" if args.precision == "fp64" else "fp64"), stream=stream.cuda_stream)
