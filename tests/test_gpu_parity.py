@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 from synth.cgrid import make_cgrid, make_rect_grid
-from tests.helpers import make_pair, perturbed_state, rel_err
+from tests.helpers import make_pair, pair_params, perturbed_state, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -131,6 +131,30 @@ def test_rans_cycle_parity_full_size():
     Fo, _, _ = o.residual()
     Fg, _, _ = s.residual()
     assert rel_err(Fg, Fo) < 1e-9
+
+
+@pytest.mark.parametrize("precision,tol_norm,tol_f", [("fp64", 1e-10, 1e-9), ("mixed", 1e-3, 1e-2)])
+def test_pitching_grid_cycle_parity_full_size(precision, tol_norm, tol_f):
+    """The 512x128 C-grid of the pitching case (thin-layer RANS, Baldwin-Lomax, M 0.8, Re 1e6,
+    4-level W-cycles) in the launch configuration the benchmark times: two cycles from the free
+    stream against the FP64 oracle.  The mixed form differs from FP64 only through its FP32
+    preconditioner, so its residual follows the oracle's to FP32 accuracy."""
+    from synth.cases import config_c3
+    c = config_c3()
+    g = c.grid()
+    po, _ = pair_params(nlevels=4, gamma_cycle=2, viscous=1, turb=1, mach=c.mach, alpha_deg=0.0, re=c.reynolds,
+                        cfl=100.0)
+    _, pg = pair_params(nlevels=4, gamma_cycle=2, viscous=1, turb=1, mach=c.mach, alpha_deg=0.0, re=c.reynolds,
+                        cfl=100.0, precision=precision)
+    import paper_1710_04875_gb300 as P
+    o, s = O.Oracle(g, po), P.Solver(g, pg)
+    for k in range(2):
+        no = o.fas_cycle(k)
+        ng = s.fas_cycle(k)
+        assert abs(ng - no) <= tol_norm * abs(no), k
+    Fo, _, _ = o.residual()
+    Fg, _, _ = s.residual()
+    assert rel_err(Fg, Fo) < tol_f
 
 
 @pytest.mark.parametrize("sweep", ["auto", "staged", "cta"])
