@@ -221,6 +221,48 @@ int fasw_adjoint_solve(fasw_ctx* ctx, int which, const double* g, double* lam, d
 int fasw_adjoint_shape_gradient(fasw_ctx* ctx, int which, const double* lam, int nparam, const double* vy, double h_x,
                                 double* grad, int on_device);
 
+/* ---- Discrete adjoint of dual time stepping (section 6: implicit Euler for the first step,
+ * BDF2 after) on a rigidly pitching grid.  Level n = 1..N places the grid at rotation
+ * phi(t_n) = -amp sin(omega t_n) about (xc, yc) (angle of attack alpha + amp sin(omega t)),
+ * t_n = n dt, and solves F^n(u^n) = R(u^n; X^n)/vol + a_n u^n + b_n u^(n-1) + c_n u^(n-2) = 0
+ * in pseudo time (fasw_dual_time_step).  Objective: J = (1/N) sum_n C(u^n, X^n), C the lift
+ * (which = 0) or drag (1) coefficient.  Adjoint, backwards from n = N:
+ *   (dF^n/du^n)^T lam^n = (1/N) dC^n/du^n - b_(n+1) lam^(n+1) - c_(n+2) lam^(n+2),
+ * each solved like fasw_adjoint_solve; the shape gradient with the initial state held fixed is
+ * sum_n [(1/N) dC^n/dX - lam^n . dF^n/dX] dX^n/dp and the initial-state sensitivity
+ * dJ/du^0 = -(b_1 lam^1 + c_2 lam^2).  The eddy viscosity is frozen at each level's value.
+ *
+ * Checkpointing: the reverse sweep needs u^N, ..., u^1 in that order.  With `snapshots` stored
+ * levels (each u^m and u^(m-1)) besides u^0, the states are recomputed from stored levels by
+ * the binomial schedule of Griewank and Walther (fewest recomputed physical steps);
+ * snapshots >= N - 1 stores every level once.  Recomputation is bit-identical to the first
+ * sweep (the library's kernels are deterministic), so the result does not depend on it. */
+
+/* The schedule alone (host code; no GPU needed).  Actions (ops[k], args[k]), k < *nactions, on
+ * a working state that holds one time level: 0 advance to level arg, 1 store the current level,
+ * 2 restore stored level arg (0 = the initial state), 3 adjoint step of level arg (the current
+ * one), 4 free the slot of level arg.  capacity = 0 only reports *nactions.
+ * *forward_steps: physical steps run, the initial sweep included.
+ * Errors: FASW_ERR_ARG (nsteps < 1 or > 65536, snapshots < 0, too small a capacity). */
+int fasw_checkpoint_schedule(int nsteps, int snapshots, int* ops, int* args, int capacity, int* nactions,
+                             long long* forward_steps);
+
+/* The unsteady adjoint run from the context's current state u^0 on the grid at rest (no
+ * motion set, no dual-time step taken).  vy: nparam x (nj+1) x (ni+1) y-displacement fields of
+ * the grid at rest (as fasw_adjoint_shape_gradient), nparam >= 0; h_rel, h_x: difference
+ * steps of the Jacobian and of the X-derivatives.  Pseudo-time solves: drop, max_cycles;
+ * adjoint solves: tol, max_iters, restart, cfl (as fasw_adjoint_solve).
+ * Outputs: *objective = J; grad[nparam] (host); g0 = dJ/du^0 (4 x nj x ni, host or device per
+ * on_device; may be NULL); stats (may be NULL) = {physical steps run, recomputed steps, total
+ * GMRES iterations, pseudo-time cycles} as doubles, then the largest adjoint relative residual.
+ * On return the context holds u^0 again on the grid at rest, with no time term.
+ * Returns FASW_OK, FASW_ERR_NOT_CONVERGED (a pseudo-time or adjoint solve hit its limit; all
+ * outputs are still filled), FASW_ERR_DIVERGED, FASW_ERR_ARG, FASW_ERR_OOM or FASW_ERR_CUDA. */
+int fasw_unsteady_adjoint(fasw_ctx* ctx, double amp, double omega, double xc, double yc, double dt, int nsteps,
+                          int bdf_order, double drop, int max_cycles, int snapshots, int which, int nparam,
+                          const double* vy, double h_rel, double h_x, double tol, int max_iters, int restart,
+                          double cfl, double* objective, double* grad, double* g0, int on_device, double* stats);
+
 /* Number of kernel launches the context has enqueued since creation (instrumentation). */
 long long fasw_launch_count(fasw_ctx* ctx);
 

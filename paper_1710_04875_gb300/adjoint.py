@@ -59,3 +59,25 @@ class ShapeForces(torch.autograd.Function):
             grads.append(s.adjoint_shape_gradient(which, lam, a.fields, a.h_x))
         g = torch.tensor(np.stack(grads), dtype=torch.float64)  # (2, nparam)
         return gout.to(torch.float64) @ g, None
+
+
+def pitching_gradient(solver: Solver, fields, amp, omega, dt, nsteps, which=1, xc=0.25, yc=0.0, snapshots=None,
+                      drop=1e-10, max_cycles=500, h_rel=1e-6, h_x=1e-6, tol=1e-10, max_iters=400, restart=40,
+                      cfl=0.0):
+    """Time-averaged C_L (which 0) or C_D (1) over nsteps dual-time steps of the pitching motion
+    alpha + amp sin(omega t), started from the steady solution that `solver` holds on the grid at
+    rest, and its total derivative with respect to the amplitudes of the y-displacement fields:
+    the unsteady adjoint (initial state held fixed) plus the initial state's own dependence on
+    the shape, through one steady adjoint solve with right-hand side dJ/du^0.
+    Returns (J, gradient, info)."""
+    J, grad, g0, code, stats = solver.unsteady_adjoint(
+        amp, omega, dt, nsteps, fields, which=which, xc=xc, yc=yc, drop=drop, max_cycles=max_cycles,
+        snapshots=snapshots, h_rel=h_rel, h_x=h_x, tol=tol, max_iters=max_iters, restart=restart, cfl=cfl)
+    solver.adjoint_jacobian(h_rel)
+    nu, code0, it0, rr0 = solver.adjoint_solve(which, g=g0, tol=tol, max_iters=max_iters, restart=restart, cfl=cfl)
+    # -nu . dR/dX V: the shape gradient with lam = nu minus its explicit objective part (lam = 0)
+    V = np.ascontiguousarray(fields, dtype=np.float64)
+    steady = solver.adjoint_shape_gradient(which, nu, V, h_x) - solver.adjoint_shape_gradient(which, 0.0 * nu, V, h_x)
+    info = dict(stats, unsteady_status=int(code), steady_status=int(code0), steady_iterations=it0,
+                steady_relative_residual=rr0)
+    return J, grad + steady, info

@@ -66,6 +66,8 @@ void adj_precond(const AdjointDev& A, const double* r, double* scratch, double* 
 void adj_steps_apply(AdjointDev& A, int steps, const double* r, double* z, cudaStream_t st);
 // out = x + a v (device vectors of length m).
 void adj_lincomb(int m, const double* x, double a, const double* v, double* out, cudaStream_t st);
+// y = a x + b y (device vectors of length m; y is read even when b = 0).
+void adj_axpby(int m, double a, const double* x, double b, double* y, cudaStream_t st);
 // Deterministic dot product of two device vectors of length m.
 int adj_dot(AdjointDev& A, const double* a, const double* b, int m, cudaStream_t st, double* out);
 

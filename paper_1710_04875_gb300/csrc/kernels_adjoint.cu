@@ -430,6 +430,10 @@ void adj_lincomb(int m, const double* x, double a, const double* v, double* out,
   launch_pdl(k_axpby, (m + 255) / 256, 256, 0, st, m, a, v, 1.0, out);
 }
 
+void adj_axpby(int m, double a, const double* x, double b, double* y, cudaStream_t st) {
+  launch_pdl(k_axpby, (m + 255) / 256, 256, 0, st, m, a, x, b, y);
+}
+
 int adj_dot(AdjointDev& A, const double* a, const double* b, int m, cudaStream_t st, double* out) {
   return multi_dot(A, a, 0, 1, b, m, st, out);
 }

@@ -92,6 +92,9 @@ def library():
             "fasw_adjoint_solve": (i, [p, i, dp, dp, d, i, i, d, C.POINTER(i), C.POINTER(d), i]),
             "fasw_adjoint_precond_apply": (i, [p, d, i, dp, dp, i]),
             "fasw_adjoint_shape_gradient": (i, [p, i, dp, i, dp, d, dp, i]),
+            "fasw_checkpoint_schedule": (i, [i, i, dp, dp, i, C.POINTER(i), C.POINTER(ll)]),
+            "fasw_unsteady_adjoint": (i, [p, d, d, d, d, d, i, i, d, i, i, i, i, dp, d, d, d, i, i, d, C.POINTER(d),
+                                          dp, dp, i, dp]),
             "fasw_residual_noalloc": (i, [i, i, i, dp, dp, dp, dp, C.POINTER(Params), p]),
             "fasw_batch_create": (i, [i, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_void_p), i, C.POINTER(Params), p, C.POINTER(p)]),
@@ -349,6 +352,49 @@ class Solver:
         _check(self.lib.fasw_adjoint_shape_gradient(self.h, which, lam.ctypes.data, V.shape[0], V.ctypes.data, h_x,
                                                     grad.ctypes.data, 0), "fasw_adjoint_shape_gradient")
         return grad
+
+
+    def unsteady_adjoint(self, amp, omega, dt, nsteps, fields=None, which=1, xc=0.25, yc=0.0, bdf_order=2,
+                         drop=1e-10, max_cycles=500, snapshots=None, h_rel=1e-6, h_x=1e-6, tol=1e-10, max_iters=400,
+                         restart=40, cfl=0.0):
+        """Adjoint of nsteps dual-time steps of the pitching motion alpha + amp sin(omega t) from the
+        current state (grid at rest): (J, dJ/dp with u^0 fixed, dJ/du^0, code, stats) with J the
+        time-averaged C_L (which 0) or C_D (1), p the amplitudes of the y-displacement fields
+        (nparam, nj+1, ni+1), and stats = {forward_steps, recomputed_steps, gmres_iterations,
+        cycles, worst_relative_residual}.  snapshots: stored time levels for the reverse sweep
+        (None: every level)."""
+        V = np.zeros((0,)) if fields is None else np.ascontiguousarray(fields, dtype=np.float64)
+        nparam = 0 if fields is None else V.shape[0]
+        snaps = nsteps if snapshots is None else int(snapshots)
+        J = C.c_double()
+        grad = np.zeros(max(nparam, 1))
+        g0 = np.zeros(self._shape(self.finest))
+        st = np.zeros(5)
+        code = self.lib.fasw_unsteady_adjoint(self.h, amp, omega, xc, yc, dt, nsteps, bdf_order, drop, max_cycles,
+                                              snaps, which, nparam, V.ctypes.data if nparam else None, h_rel, h_x,
+                                              tol, max_iters, restart, cfl, C.byref(J), grad.ctypes.data,
+                                              g0.ctypes.data, 0, st.ctypes.data)
+        if code not in (0, -6):
+            _check(code, "fasw_unsteady_adjoint")
+        stats = {"forward_steps": int(st[0]), "recomputed_steps": int(st[1]), "gmres_iterations": int(st[2]),
+                 "cycles": int(st[3]), "worst_relative_residual": float(st[4])}
+        return J.value, grad[:nparam], g0, code, stats
+
+
+def checkpoint_schedule(nsteps, snapshots):
+    """(actions, forward_steps) of the binomial checkpoint schedule for the reverse sweep of the
+    unsteady adjoint: actions are (op, level) pairs, op 0 advance to, 1 store, 2 restore,
+    3 adjoint step, 4 free (host code; no GPU needed)."""
+    lib = library()
+    n = C.c_int()
+    fs = C.c_longlong()
+    _check(lib.fasw_checkpoint_schedule(nsteps, snapshots, None, None, 0, C.byref(n), C.byref(fs)),
+           "fasw_checkpoint_schedule")
+    ops = np.zeros(n.value, dtype=np.int32)
+    args = np.zeros(n.value, dtype=np.int32)
+    _check(lib.fasw_checkpoint_schedule(nsteps, snapshots, ops.ctypes.data, args.ctypes.data, n.value, C.byref(n),
+                                        C.byref(fs)), "fasw_checkpoint_schedule")
+    return list(zip(ops.tolist(), args.tolist())), fs.value
 
 
 class Batch:
