@@ -19,7 +19,7 @@ class AdjointContext:
     """Primal and adjoint settings shared by the forward and backward passes."""
 
     def __init__(self, grid_of, fields, params, drop=1e-12, max_cycles=2000, h_rel=1e-6, h_x=1e-6,
-                 tol=1e-10, max_iters=1500, restart=60, cfl=0.0, warm_state=None):
+                 tol=1e-10, max_iters=1500, restart=250, cfl=0.0, warm_state=None):
         self.grid_of = grid_of
         self.fields = np.ascontiguousarray(fields, dtype=np.float64)
         self.params = params
@@ -62,7 +62,7 @@ class ShapeForces(torch.autograd.Function):
 
 
 def pitching_gradient(solver: Solver, fields, amp, omega, dt, nsteps, which=1, xc=0.25, yc=0.0, snapshots=None,
-                      drop=1e-10, max_cycles=500, h_rel=1e-6, h_x=1e-6, tol=1e-10, max_iters=400, restart=40,
+                      drop=1e-10, max_cycles=500, h_rel=1e-6, h_x=1e-6, tol=1e-10, max_iters=400, restart=250,
                       cfl=0.0):
     """Time-averaged C_L (which 0) or C_D (1) over nsteps dual-time steps of the pitching motion
     alpha + amp sin(omega t), started from the steady solution that `solver` holds on the grid at

@@ -329,9 +329,11 @@ class Solver:
                "fasw_adjoint_precond_apply")
         return z
 
-    def adjoint_solve(self, which=0, g=None, tol=1e-10, max_iters=400, restart=40, cfl=0.0):
+    def adjoint_solve(self, which=0, g=None, tol=1e-10, max_iters=400, restart=250, cfl=0.0):
         """(lam, code, iterations, relative residual) of J^T lam = g (g None: objective which);
-        cfl: pseudo CFL of the preconditioner (<= 0: the parameters')."""
+        cfl: pseudo CFL of the preconditioner (<= 0: the parameters').  restart (<= 251) is the
+        Krylov basis length, (restart + 5) x 4n doubles of device memory: short restarts stall on
+        thin-layer RANS adjoints (stretched wall cells), a basis of a few hundred does not."""
         lam = np.zeros(self._shape(self.finest))
         gp = None
         if g is not None:
@@ -356,7 +358,7 @@ class Solver:
 
     def unsteady_adjoint(self, amp, omega, dt, nsteps, fields=None, which=1, xc=0.25, yc=0.0, bdf_order=2,
                          drop=1e-10, max_cycles=500, snapshots=None, h_rel=1e-6, h_x=1e-6, tol=1e-10, max_iters=400,
-                         restart=40, cfl=0.0):
+                         restart=250, cfl=0.0):
         """Adjoint of nsteps dual-time steps of the pitching motion alpha + amp sin(omega t) from the
         current state (grid at rest): (J, dJ/dp with u^0 fixed, dJ/du^0, code, stats) with J the
         time-averaged C_L (which 0) or C_D (1), p the amplitudes of the y-displacement fields
