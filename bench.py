@@ -253,7 +253,26 @@ def measure_adjoint(s, g, n_bumps=16):
             "gmres_iterations": it, "relative_residual": rr, "status": int(code), "shape_gradient_s": t_grad,
             "n_params": n_bumps, "grad_norm": float(np.linalg.norm(grad)),
             "note": "steady state after the 6-order drop; eddy viscosity frozen; GMRES(250), tol 1e-8, "
-                    "preconditioned by 4 transposed stage-loop steps"}
+                    "preconditioned by 3 transposed stage-loop steps"}
+
+
+def adjoint_profile(P, iters=30):
+    """One adjoint GMRES(250) solve of C_D with a fixed count of iterations on the workload grid
+    (FP64, thin-layer RANS, frozen eddy viscosity) at a smoothly perturbed free stream, so that
+    a kernel-filtered ncu launch list of this process shows the adjoint's kernels only."""
+    g = workload_grid()
+    s = P.Solver(g, gpu_params(P, "fp64"))
+    u = s.get_state()
+    jj, ii = np.meshgrid(np.arange(g.nj), np.arange(g.ni), indexing="ij")
+    u = u * (1.0 + 0.02 * np.sin(2 * np.pi * ii / g.ni) * np.cos(np.pi * jj / g.nj))[None]
+    s.set_state(np.ascontiguousarray(u))
+    s.adjoint_jacobian(1e-6)
+    t0 = time.perf_counter()
+    lam, code, it, rr = s.adjoint_solve(1, tol=1e-14, max_iters=iters, restart=250)
+    t = time.perf_counter() - t0
+    s.close()
+    return {"adjoint_profile": WORKLOAD["name"], "gmres_iterations": it, "seconds": t,
+            "ms_per_iteration": 1e3 * t / max(it, 1), "relative_residual": rr}
 
 
 def measure_unsteady_adjoint(P, stream, nsteps=128, snapshots=8, n_bumps=16):
@@ -340,6 +359,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-unsteady-adjoint", action="store_true")
+    ap.add_argument("--adjoint-profile", action="store_true",
+                    help="only one 30-iteration adjoint GMRES solve on the workload grid (for ncu launch lists)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.warmup < 3:
@@ -350,6 +371,10 @@ def main():
 
     import torch
     import paper_1710_04875_gb300 as P
+
+    if args.adjoint_profile:
+        print(json.dumps(adjoint_profile(P)), flush=True)
+        return
 
     dist = None
     if world > 1:

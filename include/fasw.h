@@ -206,9 +206,13 @@ int fasw_adjoint_objective_gradient(fasw_ctx* ctx, int which, double* g, int on_
  * transposed primal stage loop x_i = x_0 + (alpha_i / eta) P^-T (r - J^T x_{i-1}) (needs
  * fasw_adjoint_jacobian first).  Rebuilds the finest level's preconditioner blocks and dt*. */
 int fasw_adjoint_precond_apply(fasw_ctx* ctx, double cfl, int steps, const double* r, double* z, int on_device);
+/* Smoothing steps per application of the adjoint GMRES preconditioner (1..16; 3 by default):
+ * more steps cost more transposed sweeps per Krylov iteration and save iterations.  Host only. */
+int fasw_adjoint_set_precond_steps(fasw_ctx* ctx, int steps);
 /* Solves J^T lam = g (g null: the gradient of objective `which`) by restarted GMRES(restart),
  * restart <= 251, to relative residual tol or max_iters iterations; *iters and *rel_res report
- * both.  Right preconditioner: four steps of the transposed primal stage loop of
+ * both.  Right preconditioner: three (or the number set above) steps of the transposed primal
+ * stage loop of
  * fasw_adjoint_precond_apply, built at pseudo CFL cfl (<= 0: the parameters' cfl).  Rebuilds
  * the finest level's preconditioner blocks and dt*.
  * Returns FASW_OK or FASW_ERR_NOT_CONVERGED (lam holds the last iterate). */

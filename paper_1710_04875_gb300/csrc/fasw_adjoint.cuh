@@ -35,10 +35,15 @@ struct AdjointDev {
   double* mgy = nullptr;   // and output
   double* mgt = nullptr;
   double* mgz = nullptr;   // start vector of a smoothing step
+  double* tbt = nullptr;   // 80n transfer blocks of the transposed couplings (D' = I, G'_W, G'_S, H'_E, H'_N)
+  long long* prog = nullptr;  // strip progress flags and device error word of the sweep (the
+  int* err = nullptr;         // context's), and the bound of its waits
+  long long spin_limit = 0;
   // stage coefficients of the smoother: c_i = alpha_i / eta of the primal AW scheme (the primal
   // step u - alpha_i W^-1 dt* r is u - (alpha_i / eta) P^-1 r), set with the preconditioner
   double stage_c[5] = {1.0, 0.0, 0.0, 0.0, 0.0};
   int nstages = 1;
+  int smooth_steps = 3;    // smoothing steps per application of the GMRES preconditioner
 };
 
 // Host-side stencil, colouring and reverse map; allocates the device arrays (cudaMalloc).

@@ -670,7 +670,17 @@ int fasw_fas_cycle(fasw_ctx* c, int cycle_index, double* res_norm) {
 static int adj_ready(fasw_ctx* c) {
   if (c->adj.n) return FASW_OK;
   const LevelDev& F = c->lev[c->L()];
+  c->adj.prog = c->d_prog;
+  c->adj.err = c->d_err;
+  c->adj.spin_limit = c->spin_limit;
   return adj_setup(c->adj, F.ni, F.nj, F.nw, c->allocs, c->st);
+}
+
+// FASW_ERR_DEVICE_TIMEOUT when a bounded wait of the sweeps ran out (device error word set).
+static int adj_err_check(fasw_ctx* c) {
+  CKR(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CKR(cudaStreamSynchronize(c->st));
+  return *c->h_err ? FASW_ERR_DEVICE_TIMEOUT : FASW_OK;
 }
 
 int fasw_force_coefficients(fasw_ctx* c, double* cl, double* cd) {
@@ -719,8 +729,15 @@ int fasw_adjoint_precond_apply(fasw_ctx* c, double cfl, int steps, const double*
   adj_build_precond(c->adj, c->lev[c->L()], c->ph, c->sc, cfl, c->st, c->launches);
   adj_steps_apply(c->adj, steps, c->d_tmp, c->d_tmp2, c->st);
   c->launches += 2;
+  if ((e = adj_err_check(c))) return e;
   if ((e = copy_out(c, z, c->d_tmp2, m, on_device))) return e;
   return sync(c);
+}
+
+int fasw_adjoint_set_precond_steps(fasw_ctx* c, int steps) {
+  if (!c || steps < 1 || steps > 16) return FASW_ERR_ARG;
+  c->adj.smooth_steps = steps;
+  return FASW_OK;
 }
 
 int fasw_adjoint_solve(fasw_ctx* c, int which, const double* g, double* lam, double tol, int max_iters, int restart,
@@ -738,7 +755,9 @@ int fasw_adjoint_solve(fasw_ctx* c, int which, const double* g, double* lam, dou
   const int code = adj_solve(c->adj, c->lev[c->L()], c->ph, c->sc, pcfl, rhs, c->d_tmp2, tol, max_iters, restart,
                              c->allocs, c->st, iters, rel_res, c->launches);
   if (code != FASW_OK && code != FASW_ERR_NOT_CONVERGED) return code;
-  int r = copy_out(c, lam, c->d_tmp2, m, on_device);
+  int r = adj_err_check(c);
+  if (r) return r;
+  r = copy_out(c, lam, c->d_tmp2, m, on_device);
   if (r) return r;
   r = sync(c);
   return r ? r : code;
@@ -982,6 +1001,7 @@ int fasw_unsteady_adjoint(fasw_ctx* c, double amp, double omega, double xc, doub
                     c->launches);
       if (r == FASW_ERR_NOT_CONVERGED) soft = true;
       else if (r) return fail(r);
+      if ((r = adj_err_check(c))) return fail(r);
       gm_iters += it;
       worst = std::max(worst, rr);
       const double t = n * dt;

@@ -146,60 +146,44 @@ __global__ void k_jac_tmv(int n, const int* rev_ptr, const int* rev, const doubl
 // a = (I - H_U)^-T r (forward, i+j order), b = (I - G_L)^-T a (backward), z = S D^-T b.
 // H_U^T couples d to its west and south cells (their H_E, H_N) and, on the upper wake, to its
 // mirror (its G_S); G_L^T couples d to its east and north cells (their G_W, G_S) and, on the
-// lower wake, to its mirror.  One CTA, 4 threads per cell (component q), one barrier per
-// hyperplane.
+// lower wake, to its mirror.  That is the primal sweep's own dependence pattern, so the two
+// triangular solves run in the primal's FP64 strip-pipelined sweep on transfer blocks built for
+// the transposed couplings:
+//   D' = I, G'_W(d) = H_E(w)^T, G'_S(d) = H_N(s)^T (on the wake cut: G_S(mirror)^T),
+//   H'_E(d) = G_W(e)^T, H'_N(d) = G_S(n)^T,
+// with w, s, e, n the west, south, east and north cells (zero blocks where there is none).
 __device__ __forceinline__ double tbT(const double* tb, int n, int blk, int r, int q, int c) {
   return tb[(blk * 16 + 4 * r + q) * n + c];  // entry (r, q) of block blk of cell c
 }
 
-__global__ void __launch_bounds__(1024) k_adj_wt(LevelDev L, const double* r, double* a, double* b) {
+__global__ void k_adj_tb_transpose(LevelDev L, double* tbt) {
   pdl_entry();
-  const int ni = L.ni, nj = L.nj, n = L.n, nw = L.nw, K = ni + nj - 1;
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = L.n, ni = L.ni, nj = L.nj, nw = L.nw;
+  if (d >= n) return;
+  const int i = d % ni, j = d / ni;
   const double* tb = L.tb;
-  const int q = threadIdx.x & 3, lane_cell = threadIdx.x >> 2, ncell = blockDim.x >> 2;
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int kk = 0; kk < K; ++kk) {
-      const int k = pass == 0 ? kk : K - 1 - kk;
-      const int ilo = max(0, k - nj + 1), ihi = min(k, ni - 1);
-      for (int i = ilo + lane_cell; i <= ihi; i += ncell) {
-        const int j = k - i, d = j * ni + i;
-        if (pass == 0) {
-          double acc = r[q * n + d];
-          if (i > 0) {
-            const int c = d - 1;
-            for (int rr = 0; rr < 4; ++rr) acc += tbT(tb, n, 3, rr, q, c) * a[rr * n + c];
-          }
-          if (j > 0) {
-            const int c = d - ni;
-            for (int rr = 0; rr < 4; ++rr) acc += tbT(tb, n, 4, rr, q, c) * a[rr * n + c];
-          } else if (nw > 0 && i >= ni - nw) {
-            const int c = ni - 1 - i;
-            for (int rr = 0; rr < 4; ++rr) acc += tbT(tb, n, 2, rr, q, c) * a[rr * n + c];
-          }
-          a[q * n + d] = acc;
-        } else {
-          double acc = a[q * n + d];
-          if (i < ni - 1) {
-            const int c = d + 1;
-            for (int rr = 0; rr < 4; ++rr) acc += tbT(tb, n, 1, rr, q, c) * b[rr * n + c];
-          }
-          if (j < nj - 1) {
-            const int c = d + ni;
-            for (int rr = 0; rr < 4; ++rr) acc += tbT(tb, n, 2, rr, q, c) * b[rr * n + c];
-          }
-          if (j == 0 && nw > 0 && i < nw) {
-            const int c = ni - 1 - i;
-            for (int rr = 0; rr < 4; ++rr) acc += tbT(tb, n, 2, rr, q, c) * b[rr * n + c];
-          }
-          b[q * n + d] = acc;
-        }
-      }
-      __syncthreads();
-    }
+  // source (block, cell) of each transposed block; cell -1: zero block
+  int src_blk[5] = {0, 3, 4, 1, 2}, src_cell[5] = {-1, -1, -1, -1, -1};
+  if (i > 0) src_cell[1] = d - 1;
+  if (j > 0) {
+    src_cell[2] = d - ni;
+  } else if (nw > 0 && (i < nw || i >= ni - nw)) {
+    src_blk[2] = 2;
+    src_cell[2] = ni - 1 - i;
+  }
+  if (i < ni - 1) src_cell[3] = d + 1;
+  if (j < nj - 1) src_cell[4] = d + ni;
+  for (int r = 0; r < 4; ++r)
+    for (int q = 0; q < 4; ++q) tbt[(4 * r + q) * n + d] = r == q ? 1.0 : 0.0;
+  for (int k = 1; k < 5; ++k) {
+    const int c = src_cell[k];
+    for (int r = 0; r < 4; ++r)
+      for (int q = 0; q < 4; ++q)
+        tbt[(k * 16 + 4 * r + q) * n + d] = c < 0 ? 0.0 : tbT(tb, n, src_blk[k], q, r, c);
   }
 }
 
-// z = S D^-T b, S = eta dt* = coef * vol (coef of the AW blocks)
 __global__ void k_adj_wt_finish(LevelDev L, const double* b, double* z) {
   pdl_entry();
   const int d = blockIdx.x * blockDim.x + threadIdx.x;
@@ -322,7 +306,8 @@ int adj_setup(AdjointDev& A, int ni, int nj, int nw, std::vector<void*>& allocs,
       (r = adj_alloc(allocs, &A.Fp, 4 * (size_t)n)) || (r = adj_alloc(allocs, &A.Fm, 4 * (size_t)n)) ||
       (r = adj_alloc(allocs, &A.fw, 4 * (size_t)ni)) || (r = adj_alloc(allocs, &A.parts, PARTS)) ||
       (r = adj_alloc(allocs, &A.mgs, 4 * (size_t)n)) || (r = adj_alloc(allocs, &A.mgy, 4 * (size_t)n)) ||
-      (r = adj_alloc(allocs, &A.mgt, 4 * (size_t)n)) || (r = adj_alloc(allocs, &A.mgz, 4 * (size_t)n)))
+      (r = adj_alloc(allocs, &A.mgt, 4 * (size_t)n)) || (r = adj_alloc(allocs, &A.mgz, 4 * (size_t)n)) ||
+      (r = adj_alloc(allocs, &A.tbt, 80 * (size_t)n)))
     return r;
   if (cudaMallocHost(&A.h_parts, MAXV * sizeof(double)) != cudaSuccess) return FASW_ERR_OOM;
   cudaMemcpyAsync(A.nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice, st);
@@ -374,14 +359,14 @@ void adj_apply(const AdjointDev& A, const double* v, double* out, int transpose,
 
 namespace {
 
-// z = P^-T r (y: scratch of 4n)
+// z = P^-T r (y: scratch of 4n): both triangular solves in one strip-pipelined FP64 sweep on
+// the transposed transfer blocks (into y), then z = S D^-T y.
 void precond(const AdjointDev& A, const double* r, double* y, double* z, cudaStream_t st) {
-  int cells = A.ni < A.nj ? A.ni : A.nj;
-  int threads = 4 * cells;
-  threads = threads > 1024 ? 1024 : threads;
-  threads = (threads + 31) / 32 * 32;
-  launch_pdl(k_adj_wt, 1, threads, 0, st, A.Lp, r, y, z);
-  launch_pdl(k_adj_wt_finish, (A.n + 127) / 128, 128, 0, st, A.Lp, z, z);
+  LevelDev T = A.Lp;
+  T.tb = A.tbt;
+  T.yz64 = y;
+  launch_sweep(T, 0, SWEEP_STRIPS, 0, 1, 0.0, r, A.prog, A.err, A.spin_limit, st);
+  launch_pdl(k_adj_wt_finish, (A.n + 127) / 128, 128, 0, st, A.Lp, (const double*)y, z);
 }
 
 // One smoothing step on J^T x = r from x (in place): the transposed primal stage loop,
@@ -400,11 +385,10 @@ void smooth_step(AdjointDev& A, const double* r, double* x, cudaStream_t st) {
   }
 }
 
-// x = M^-1 r: SMOOTH_STEPS smoothing steps from zero.  As a stationary iteration these steps
-// are not convergent on their own (the primal's stability also rests on its beta blending of
-// the dissipative part, and on multigrid), but as a GMRES preconditioner they cut the Krylov
-// iterations of the Euler adjoint from about 530 (one P^-T per iteration) to about 60.
-constexpr int SMOOTH_STEPS = 4;
+// x = M^-1 r: A.smooth_steps smoothing steps from zero (3 unless set otherwise).  As a
+// stationary iteration these steps are not convergent on their own (the primal's stability also
+// rests on its beta blending of the dissipative part, and on multigrid), but as a GMRES
+// preconditioner they cut the Krylov iterations several-fold against one P^-T per iteration.
 void steps_apply(AdjointDev& A, int steps, const double* r, double* x, cudaStream_t st) {
   cudaMemsetAsync(x, 0, 4 * (size_t)A.n * sizeof(double), st);
   for (int it = 0; it < steps; ++it) smooth_step(A, r, x, st);
@@ -468,7 +452,8 @@ void adj_build_precond(AdjointDev& A, const LevelDev& L, const PhysParams& ph, c
   launch_face_blocks(L, ph, aw, 0, st);
   launch_diag_blocks(L, aw, 0, st);
   launch_sgs_prep(L, 0, SWEEP_STRIPS, st);
-  launches += 4;
+  launch_pdl(k_adj_tb_transpose, (A.n + 127) / 128, 128, 0, st, L, A.tbt);
+  launches += 5;
   A.Lp = L;
   A.nstages = sc.nstages;
   for (int i = 0; i < 5; ++i) A.stage_c[i] = i < sc.nstages ? sc.alpha[i] / sc.eta : 0.0;
@@ -491,7 +476,7 @@ int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const Sche
   adj_build_precond(A, L, ph, sc, cfl, st, launches);
   auto apply_m = [&](const double* rr, double* yy, double* zz) {  // zz = M^-1 rr
     (void)yy;
-    steps_apply(A, SMOOTH_STEPS, rr, zz, st);
+    steps_apply(A, A.smooth_steps, rr, zz, st);
   };
   const int m = 4 * A.n;
   if (restart < 1 || restart > MAXV - 5) return FASW_ERR_ARG;

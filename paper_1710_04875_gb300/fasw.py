@@ -91,6 +91,7 @@ def library():
             "fasw_adjoint_objective_gradient": (i, [p, i, dp, i]),
             "fasw_adjoint_solve": (i, [p, i, dp, dp, d, i, i, d, C.POINTER(i), C.POINTER(d), i]),
             "fasw_adjoint_precond_apply": (i, [p, d, i, dp, dp, i]),
+            "fasw_adjoint_set_precond_steps": (i, [p, i]),
             "fasw_adjoint_shape_gradient": (i, [p, i, dp, i, dp, d, dp, i]),
             "fasw_checkpoint_schedule": (i, [i, i, dp, dp, i, C.POINTER(i), C.POINTER(ll)]),
             "fasw_unsteady_adjoint": (i, [p, d, d, d, d, d, i, i, d, i, i, i, i, dp, d, d, d, i, i, d, C.POINTER(d),
@@ -328,6 +329,10 @@ class Solver:
                                                    0),
                "fasw_adjoint_precond_apply")
         return z
+
+    def adjoint_set_precond_steps(self, steps):
+        """Smoothing steps of the transposed stage loop per GMRES preconditioner application."""
+        _check(self.lib.fasw_adjoint_set_precond_steps(self.h, int(steps)), "fasw_adjoint_set_precond_steps")
 
     def adjoint_solve(self, which=0, g=None, tol=1e-10, max_iters=400, restart=250, cfl=0.0):
         """(lam, code, iterations, relative residual) of J^T lam = g (g None: objective which);

@@ -60,6 +60,24 @@ def test_adjoint_preconditioner_is_the_transposed_primal_w():
     assert rel_err(z.ravel(), ref) < 1e-11
 
 
+@pytest.mark.parametrize("ni,nj,nw,viscous", [(72, 20, 8, 0), (128, 32, 16, 1)])
+def test_adjoint_preconditioner_transposes_the_primal_sweep_on_several_strips(ni, nj, nw, viscous):
+    """<S M^-T r, v> = <r, M^-1 S v> with M^-1 the primal's own FP64 preconditioner sweep, on
+    grids whose transposed sweep runs in several pipelined row strips with a ragged last strip
+    and a wake cut: pins the transposed transfer blocks, including the wake-cut mirror blocks."""
+    g = make_cgrid(ni, nj, n_wake=nw, jitter=0.03, seed=5, wall_spacing=1e-3)
+    _, s = make_pair(g, nlevels=1, mach=0.6, alpha_deg=ALPHA, viscous=viscous, re=1e4, d_cut=0.5)
+    s.set_state(perturbed_state(0.6, ALPHA, nj, ni, amp=0.04, seed=6))
+    rng = np.random.default_rng(12)
+    r = rng.standard_normal((4, nj, ni)); v = rng.standard_normal((4, nj, ni))
+    cfl = 50.0
+    z = s.adjoint_precond_apply(r, cfl)
+    S = 0.8 * s.pseudo_dt(cfl)
+    w = s.precond_apply(S[None] * v, cfl)
+    a, b = float(np.sum(z * v)), float(np.sum(r * w))
+    assert abs(a - b) <= 1e-12 * np.linalg.norm(z) * np.linalg.norm(v)
+
+
 def test_adjoint_smoother_is_the_transposed_stage_loop():
     """One smoothing step of the adjoint preconditioner equals the transposed AW3 stage loop
     x_i = x_0 + (alpha_i / eta) P^-T (r - J^T x_{i-1}) assembled here from the library's own
