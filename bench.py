@@ -285,7 +285,7 @@ def measure_unsteady_adjoint(P, stream, nsteps=128, snapshots=8, n_bumps=16):
     g = make_cgrid(128, 32, wall_spacing=2e-3)
     p = P.default_params(scheme="AW3", nlevels=3, gamma_cycle=1, mach=0.6, alpha_deg=0.0, cfl=1e4)
     s = P.Solver(g, p, stream=stream.cuda_stream)
-    code, nc, hist = s.solve(1e-12, 2000)
+    code, nc, hist = s.solve(1e-10, 3000)
     omega = 0.4
     dt = 2.0 * np.pi / omega / 64
     t0 = time.perf_counter()
