@@ -27,7 +27,7 @@ struct AdjointDev {
   double* fw = nullptr;    // 4 * ni wall forces fx+, fy+, fx-, fy-
   double* parts = nullptr; // reduction partials
   double* h_parts = nullptr;  // pinned host copy of the reduced values
-  double* kry = nullptr;   // (restart + 2) * 4n Krylov basis and work vectors
+  double* kry = nullptr;   // (2 restart + 5) * 4n: Krylov basis V, preconditioned basis Z, work vectors
   int restart = 0;
   bool built = false;      // Jacobian assembled at the current state
   LevelDev Lp{};           // level whose transfer blocks hold the preconditioner
@@ -36,6 +36,15 @@ struct AdjointDev {
   double* mgt = nullptr;
   double* mgz = nullptr;   // start vector of a smoothing step
   double* tbt = nullptr;   // 80n transfer blocks of the transposed couplings (D' = I, G'_W, G'_S, H'_E, H'_N)
+  // FP32 transposed sweep (contexts in mixed precision): the transposed blocks in FP32, entry-major
+  // (80n) and, where the level fits the hyperplane-staged sweep, hyperplane-major
+  bool fp32 = false;
+  float* tb32 = nullptr;
+  float* yz32 = nullptr;
+  float* hpF = nullptr;
+  float* hpB = nullptr;
+  float* hpC = nullptr;
+  float* hpY = nullptr;
   long long* prog = nullptr;  // strip progress flags and device error word of the sweep (the
   int* err = nullptr;         // context's), and the bound of its waits
   long long spin_limit = 0;
@@ -46,15 +55,18 @@ struct AdjointDev {
   int smooth_steps = 3;    // smoothing steps per application of the GMRES preconditioner
 };
 
-// Host-side stencil, colouring and reverse map; allocates the device arrays (cudaMalloc).
+// Host-side stencil, colouring and reverse map; allocates the device arrays (cudaMalloc), with
+// the FP32 sweep arrays when A.fp32 is set.
 int adj_setup(AdjointDev& A, int ni, int nj, int nw, std::vector<void*>& allocs, cudaStream_t st);
 // J and the objective gradients at the current state of L (ghosts and auxiliaries are refilled).
 int adj_assemble(AdjointDev& A, const LevelDev& L, const PhysParams& ph, double h_rel, cudaStream_t st,
                  long long& launches);
 void adj_apply(const AdjointDev& A, const double* v, double* out, int transpose, cudaStream_t st);
-// GMRES(restart) on J^T lam = g, right-preconditioned by steps of the transposed primal stage
-// loop with the transposed AW preconditioner built on L at pseudo CFL cfl (overwrites L's
-// blocks and dt*); returns FASW_OK or FASW_ERR_NOT_CONVERGED; *iters, *relres.
+// Flexible GMRES(restart) on J^T lam = g, right-preconditioned by steps of the transposed
+// primal stage loop with the transposed AW preconditioner built on L at pseudo CFL cfl
+// (overwrites L's blocks and dt*); the preconditioned basis vectors are kept, so an FP32
+// preconditioner does not limit the attainable residual.  Returns FASW_OK or
+// FASW_ERR_NOT_CONVERGED; *iters, *relres.
 int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const SchemeParams& sc, double cfl,
               const double* g, double* lam, double tol, int max_iters, int restart, std::vector<void*>& allocs,
               cudaStream_t st, int* iters, double* relres, long long& launches);

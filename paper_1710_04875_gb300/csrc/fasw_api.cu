@@ -670,6 +670,7 @@ int fasw_fas_cycle(fasw_ctx* c, int cycle_index, double* res_norm) {
 static int adj_ready(fasw_ctx* c) {
   if (c->adj.n) return FASW_OK;
   const LevelDev& F = c->lev[c->L()];
+  c->adj.fp32 = c->mixed != 0;
   c->adj.prog = c->d_prog;
   c->adj.err = c->d_err;
   c->adj.spin_limit = c->spin_limit;

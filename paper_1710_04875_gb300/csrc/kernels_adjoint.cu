@@ -199,6 +199,40 @@ __global__ void k_adj_wt_finish(LevelDev L, const double* b, double* z) {
   }
 }
 
+// FP32 copies of the transposed transfer blocks for the FP32 sweeps: entry-major (all five
+// blocks; D' = I is what k_hp_cy reads) and, with hpF, hyperplane-major G'_W, G'_S | H'_E, H'_N
+// (entry h = (i + j) nj + j, 16 floats per block, row-major).
+__global__ void k_adj_tb_lower(int ni, int nj, const double* tbt, float* tb32, float* hpF, float* hpB) {
+  pdl_entry();
+  const int n = ni * nj;
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n) return;
+  for (int e = 0; e < 80; ++e) tb32[(size_t)e * n + d] = float(tbt[(size_t)e * n + d]);
+  if (!hpF) return;
+  const int i = d % ni, j = d / ni;
+  const size_t h = (size_t)(i + j) * nj + j;
+  for (int k = 1; k < 5; ++k) {
+    float* dst = (k <= 2 ? hpF : hpB) + 32 * h + ((k - 1) & 1) * 16;
+    for (int e = 0; e < 16; ++e) dst[e] = float(tbt[(size_t)(k * 16 + e) * n + d]);
+  }
+}
+
+// z = S D^-T b for the FP32 sweep's output b.
+__global__ void k_adj_wt_finish32(LevelDev L, const float* b, double* z) {
+  pdl_entry();
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= L.n) return;
+  const int n = L.n;
+  const double sc = L.coef[d] * L.vol[d];
+  double bd[4];
+  for (int t = 0; t < 4; ++t) bd[t] = double(b[t * n + d]);
+  for (int q = 0; q < 4; ++q) {
+    double s = 0.0;
+    for (int t = 0; t < 4; ++t) s += tbT(L.tb, n, 0, t, q, d) * bd[t];
+    z[q * n + d] = sc * s;
+  }
+}
+
 // Partial sums of dot(V_v, w) for v < nvec (grid RED_BLOCKS x nvec), then row reduction.
 __global__ void k_multi_dot(const double* V, size_t ld, const double* w, int m, double* parts) {
   pdl_entry();
@@ -309,6 +343,15 @@ int adj_setup(AdjointDev& A, int ni, int nj, int nw, std::vector<void*>& allocs,
       (r = adj_alloc(allocs, &A.mgt, 4 * (size_t)n)) || (r = adj_alloc(allocs, &A.mgz, 4 * (size_t)n)) ||
       (r = adj_alloc(allocs, &A.tbt, 80 * (size_t)n)))
     return r;
+  if (A.fp32) {
+    if ((r = adj_alloc(allocs, &A.tb32, 80 * (size_t)n)) || (r = adj_alloc(allocs, &A.yz32, 4 * (size_t)n))) return r;
+    if (hp_fits(ni, nj, nw)) {
+      const size_t h = hp_floats(ni, nj);
+      if ((r = adj_alloc(allocs, &A.hpF, 32 * h)) || (r = adj_alloc(allocs, &A.hpB, 32 * h)) ||
+          (r = adj_alloc(allocs, &A.hpC, 4 * h)) || (r = adj_alloc(allocs, &A.hpY, 4 * h)))
+        return r;
+    }
+  }
   if (cudaMallocHost(&A.h_parts, MAXV * sizeof(double)) != cudaSuccess) return FASW_ERR_OOM;
   cudaMemcpyAsync(A.nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(A.col, col.data(), col.size() * sizeof(int), cudaMemcpyHostToDevice, st);
@@ -363,6 +406,17 @@ namespace {
 // the transposed transfer blocks (into y), then z = S D^-T y.
 void precond(const AdjointDev& A, const double* r, double* y, double* z, cudaStream_t st) {
   LevelDev T = A.Lp;
+  if (A.fp32) {  // FP32 transfer blocks: the hyperplane-staged sweep where the level fits, else strips
+    T.tb = reinterpret_cast<double*>(A.tb32);
+    T.yz32 = A.yz32;
+    T.hpF = A.hpF;
+    T.hpB = A.hpB;
+    T.hpC = A.hpC;
+    T.hpY = A.hpY;
+    launch_sweep(T, 1, A.hpF ? SWEEP_HP : SWEEP_STRIPS, 0, 1, 0.0, r, A.prog, A.err, A.spin_limit, st);
+    launch_pdl(k_adj_wt_finish32, (A.n + 127) / 128, 128, 0, st, A.Lp, (const float*)A.yz32, z);
+    return;
+  }
   T.tb = A.tbt;
   T.yz64 = y;
   launch_sweep(T, 0, SWEEP_STRIPS, 0, 1, 0.0, r, A.prog, A.err, A.spin_limit, st);
@@ -454,6 +508,10 @@ void adj_build_precond(AdjointDev& A, const LevelDev& L, const PhysParams& ph, c
   launch_sgs_prep(L, 0, SWEEP_STRIPS, st);
   launch_pdl(k_adj_tb_transpose, (A.n + 127) / 128, 128, 0, st, L, A.tbt);
   launches += 5;
+  if (A.fp32) {
+    launch_pdl(k_adj_tb_lower, (A.n + 127) / 128, 128, 0, st, A.ni, A.nj, (const double*)A.tbt, A.tb32, A.hpF, A.hpB);
+    ++launches;
+  }
   A.Lp = L;
   A.nstages = sc.nstages;
   for (int i = 0; i < 5; ++i) A.stage_c[i] = i < sc.nstages ? sc.alpha[i] / sc.eta : 0.0;
@@ -474,23 +532,21 @@ int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const Sche
               const double* g, double* lam, double tol, int max_iters, int restart, std::vector<void*>& allocs,
               cudaStream_t st, int* iters, double* relres, long long& launches) {
   adj_build_precond(A, L, ph, sc, cfl, st, launches);
-  auto apply_m = [&](const double* rr, double* yy, double* zz) {  // zz = M^-1 rr
-    (void)yy;
+  auto apply_m = [&](const double* rr, double* zz) {  // zz = M^-1 rr
     steps_apply(A, A.smooth_steps, rr, zz, st);
   };
   const int m = 4 * A.n;
   if (restart < 1 || restart > MAXV - 5) return FASW_ERR_ARG;
   if (A.restart < restart) {
-    int r = adj_alloc(allocs, &A.kry, (size_t)(restart + 5) * m);
+    int r = adj_alloc(allocs, &A.kry, (size_t)(2 * restart + 5) * m);
     if (r) return r;
     A.restart = restart;
   }
   const size_t ld = m;
   double* V = A.kry;                                  // restart + 1 vectors
-  double* w = A.kry + (size_t)(A.restart + 1) * ld;   // work
-  double* t = w + ld;
-  double* y = t + ld;                                 // preconditioner scratch
-  double* res = y + ld;
+  double* Z = A.kry + (size_t)(A.restart + 1) * ld;   // restart preconditioned vectors
+  double* w = Z + (size_t)A.restart * ld;             // work
+  double* res = w + ld;
   const int nb = (m + 255) / 256;
   cudaMemsetAsync(lam, 0, m * sizeof(double), st);
   cudaMemcpyAsync(res, g, m * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -512,8 +568,9 @@ int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const Sche
     int jdone = 0;
     bool conv = false;
     for (int j = 0; j < restart && *iters < max_iters; ++j) {
-      apply_m(V + (size_t)j * ld, y, t);          // t = M^-1 v_j
-      adj_apply(A, t, w, 1, st);                   // w = J^T t
+      double* zj = Z + (size_t)j * ld;
+      apply_m(V + (size_t)j * ld, zj);            // z_j = M^-1 v_j
+      adj_apply(A, zj, w, 1, st);                  // w = J^T z_j
       launches += 3;
       for (int pass = 0; pass < 2; ++pass) {
         if ((r = multi_dot(A, V, ld, j + 1, w, m, st, pass == 0 ? h.data() : h2.data()))) return r;
@@ -548,7 +605,7 @@ int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const Sche
         break;
       }
     }
-    // y = H^-1 s (upper triangular), lam += M^-1 V y
+    // y = H^-1 s (upper triangular), lam += Z y
     std::vector<double> yv(jdone);
     for (int i = jdone - 1; i >= 0; --i) {
       double acc = s[i];
@@ -556,11 +613,8 @@ int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const Sche
       yv[i] = acc / H[(size_t)i * restart + i];
     }
     for (int i = 0; i < jdone; ++i) yv[i] = -yv[i];  // k_multi_axpy subtracts
-    cudaMemsetAsync(w, 0, m * sizeof(double), st);
     cudaMemcpyAsync(d_coef, yv.data(), jdone * sizeof(double), cudaMemcpyHostToDevice, st);
-    launch_pdl(k_multi_axpy, nb, 256, 0, st, V, ld, d_coef, jdone, m, w);
-    apply_m(w, y, t);
-    launch_pdl(k_axpby, nb, 256, 0, st, m, 1.0, t, 1.0, lam);
+    launch_pdl(k_multi_axpy, nb, 256, 0, st, Z, ld, d_coef, jdone, m, lam);
     // true residual g - J^T lam
     adj_apply(A, lam, res, 1, st);
     launch_pdl(k_axpby, nb, 256, 0, st, m, 1.0, g, -1.0, res);

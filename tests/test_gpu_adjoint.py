@@ -127,6 +127,42 @@ def test_adjoint_solution_and_shape_gradient_match_the_oracle():
         assert rel_err(grad, d_o) < 1e-5
 
 
+@pytest.mark.parametrize("case", ["euler_64x16", "rans_256x64"])
+def test_mixed_precision_adjoint_solves_the_same_system(case):
+    """A mixed-precision context preconditions the adjoint GMRES with FP32 transposed sweeps
+    (hyperplane-staged); flexible GMRES keeps the preconditioned vectors, so the adjoint reaches
+    the same tolerance and the same lambda as the FP64 context (same Jacobian: both are
+    differences of the FP64 residual, with the same frozen eddy viscosity).  The second case is
+    the stiff 256x64 RANS workload at its 6-order state."""
+    import paper_1710_04875_gb300 as P
+    if case == "euler_64x16":
+        g = make_cgrid(64, 16)
+        kw = dict(nlevels=2, mach=0.6, alpha_deg=ALPHA, cfl=1e4)
+        drop = 1e-12
+    else:
+        g = make_cgrid(256, 64, wall_spacing=1e-5)
+        kw = dict(nlevels=4, gamma_cycle=2, viscous=1, turb=1, mach=0.5, alpha_deg=0.0, re=1e7, cfl=100.0)
+        drop = 1e-6
+    _, p64 = pair_params(**kw)
+    _, p32 = pair_params(precision="mixed", **kw)
+    s = P.Solver(g, p64)
+    code, nc, hist = s.solve(drop, 1500)
+    assert code == 0
+    u = s.get_state()
+    s.close()
+    out = []
+    for prm in (p64, p32):
+        s = P.Solver(g, prm)
+        s.set_state(u)
+        s.get_mut()                  # Baldwin-Lomax at u, frozen for the adjoint (zero for Euler)
+        s.adjoint_jacobian(1e-6)
+        lam, code, it, rr = s.adjoint_solve(1, tol=1e-9, max_iters=3000, restart=250)
+        assert code == 0 and rr <= 1e-9, (prm.precision, code, it, rr)
+        out.append(lam)
+        s.close()
+    assert rel_err(out[1], out[0]) < 1e-6
+
+
 def test_adjoint_gradient_matches_differences_of_gpu_solves():
     import paper_1710_04875_gb300 as P
     g = make_cgrid(64, 16)
