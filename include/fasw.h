@@ -206,15 +206,35 @@ int fasw_adjoint_objective_gradient(fasw_ctx* ctx, int which, double* g, int on_
  * transposed primal stage loop x_i = x_0 + (alpha_i / eta) P^-T (r - J^T x_{i-1}) (needs
  * fasw_adjoint_jacobian first).  Rebuilds the finest level's preconditioner blocks and dt*. */
 int fasw_adjoint_precond_apply(fasw_ctx* ctx, double cfl, int steps, const double* r, double* z, int on_device);
+/* Preconditioner of the adjoint GMRES (the Jacobian must be assembled again after a change):
+ *   0: steps of the primal stage loop run on J^T, x_i = x_0 + (alpha_i/eta) P^-T (r - J^T x_(i-1));
+ *   1: steps of the exact transpose of the primal's linearised smoothing step (section 4: the
+ *      stage loop with the dissipative part F^v blended by beta_i, so J = J^c + J^v is assembled
+ *      in two parts);
+ *   2 (default): the exact transpose of the primal's linearised FAS cycle (section 3: nu1
+ *      smoothing steps per level visit, volume-weighted residual restriction R, gamma coarse
+ *      cycles, bilinear prolongation P): C^T v = R^T r + S^T (v - J^T R^T r), r = A^T P^T v, with
+ *      the coarse Jacobians taken at the volume-weighted restriction of the state; one level
+ *      reduces it to kind 1 with one step.
+ * The adjoint iteration with kind 2 has the primal FAS iteration's convergence rate (the two
+ * iteration matrices are transposes up to similarity). Host only. */
+int fasw_adjoint_set_precond(fasw_ctx* ctx, int kind);
+/* z = M r with the linear operator of a preconditioner kind (1: the linearised smoothing step,
+ * as many steps as set below; 2: the linearised FAS cycle), as a solver of J (transpose = 0) or
+ * its transpose (transpose != 0), built at pseudo CFL cfl at the current state after
+ * fasw_adjoint_jacobian (kind 2 needs the cycle selected when the Jacobian was assembled).
+ * Rebuilds every level's preconditioner blocks and dt*. */
+int fasw_adjoint_cycle_apply(fasw_ctx* ctx, double cfl, int kind, int transpose, const double* r, double* z,
+                             int on_device);
 /* Smoothing steps per application of the adjoint GMRES preconditioner (1..16; 3 by default):
  * more steps cost more transposed sweeps per Krylov iteration and save iterations.  Host only. */
 int fasw_adjoint_set_precond_steps(fasw_ctx* ctx, int steps);
 /* Solves J^T lam = g (g null: the gradient of objective `which`) by restarted GMRES(restart),
  * restart <= 251, to relative residual tol or max_iters iterations; *iters and *rel_res report
- * both.  Right preconditioner: three (or the number set above) steps of the transposed primal
- * stage loop of
- * fasw_adjoint_precond_apply, built at pseudo CFL cfl (<= 0: the parameters' cfl).  Rebuilds
- * the finest level's preconditioner blocks and dt*.
+ * both.  Flexible GMRES, right-preconditioned by the preconditioner set above (by default the
+ * transposed linearised FAS cycle; kinds 0 and 1 take three steps unless set otherwise), built
+ * at pseudo CFL cfl (<= 0: the parameters' cfl).  Rebuilds the preconditioner blocks and dt* of
+ * the levels it uses.
  * Returns FASW_OK or FASW_ERR_NOT_CONVERGED (lam holds the last iterate). */
 int fasw_adjoint_solve(fasw_ctx* ctx, int which, const double* g, double* lam, double tol, int max_iters, int restart,
                        double cfl, int* iters, double* rel_res, int on_device);

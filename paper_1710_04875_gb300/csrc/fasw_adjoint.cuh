@@ -13,6 +13,15 @@ namespace fasw {
 // j+2, 9 and 10 the wake-cut mirror cells (ni-1-i, 0) and (ni-1-i, 1).
 constexpr int ADJ_SLOTS = 11;
 
+struct AdjointMG;  // transposed linear FAS cycle: coarse levels, transfer maps, work vectors
+
+// Preconditioners of the adjoint GMRES (fasw_adjoint_set_precond).
+enum AdjPrecond {
+  ADJ_STAGE_LOOP = 0,     // steps of the stage loop run on J^T (x_i = x_0 + c_i P^-T (r - J^T x_(i-1)))
+  ADJ_SMOOTHER_T = 1,     // steps of the exact transpose of the primal's linearised smoothing step
+  ADJ_FAS_CYCLE_T = 2     // the exact transpose of the primal's linearised FAS cycle
+};
+
 struct AdjointDev {
   int ni = 0, nj = 0, n = 0, ncolours = 0;
   int* nbr = nullptr;      // n * ADJ_SLOTS neighbour cell or -1
@@ -20,6 +29,10 @@ struct AdjointDev {
   int* rev_ptr = nullptr;  // n + 1: entries (c, s) with nbr[c][s] = d, CSR by d
   int* rev = nullptr;      // c * ADJ_SLOTS + s
   double* J = nullptr;     // n * ADJ_SLOTS * 16, block (c, s) row-major dF_c / du_nbr
+  double* Jv = nullptr;    // the same for the dissipative part F^v (JST dissipation + viscous flux)
+  double* Fvp = nullptr;   // 4n F^v scratch (+, -)
+  double* Fvm = nullptr;
+  bool finest = true;      // objective gradients only on the finest level
   double* g = nullptr;     // 2 * 4n state gradients of C_L, C_D
   double* ub = nullptr;    // 4n base state
   double* Fp = nullptr;    // 4n residual scratch (+)
@@ -51,7 +64,11 @@ struct AdjointDev {
   // stage coefficients of the smoother: c_i = alpha_i / eta of the primal AW scheme (the primal
   // step u - alpha_i W^-1 dt* r is u - (alpha_i / eta) P^-1 r), set with the preconditioner
   double stage_c[5] = {1.0, 0.0, 0.0, 0.0, 0.0};
+  double stage_b[5] = {1.0, 1.0, 1.0, 1.0, 1.0};  // beta_i: blending of the dissipative part
   int nstages = 1;
+  int precond_kind = ADJ_FAS_CYCLE_T;
+  AdjointMG* mg = nullptr;  // owned (adj_release)
+  double* mgw = nullptr;    // work vectors of the linearised smoothing step and its transpose (8 x 4n)
   int smooth_steps = 3;    // smoothing steps per application of the GMRES preconditioner
 };
 
@@ -67,9 +84,26 @@ void adj_apply(const AdjointDev& A, const double* v, double* out, int transpose,
 // (overwrites L's blocks and dt*); the preconditioned basis vectors are kept, so an FP32
 // preconditioner does not limit the attainable residual.  Returns FASW_OK or
 // FASW_ERR_NOT_CONVERGED; *iters, *relres.
-int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const SchemeParams& sc, double cfl,
-              const double* g, double* lam, double tol, int max_iters, int restart, std::vector<void*>& allocs,
-              cudaStream_t st, int* iters, double* relres, long long& launches);
+// lev: the context's levels (the coarse ones are used by ADJ_FAS_CYCLE_T).
+int adj_solve(AdjointDev& A, const std::vector<LevelDev>& lev, const PhysParams& ph, const SchemeParams& sc,
+              double cfl, const double* g, double* lam, double tol, int max_iters, int restart,
+              std::vector<void*>& allocs, cudaStream_t st, int* iters, double* relres, long long& launches);
+// Coarse levels of the transposed FAS cycle: per-level adjoint data (stencils, colourings,
+// Jacobians) and the prolongation maps; lev is the context's level list (0 = coarsest,
+// lev.back() = the finest, whose data is A itself).  Allocates once.
+int adj_mg_setup(AdjointDev& A, const std::vector<LevelDev>& lev, int gamma, int nu1, std::vector<void*>& allocs,
+                 cudaStream_t st);
+// Jacobians of every coarse level at the volume-weighted restriction of the finest state (the
+// linearisation point of the FAS coarse operators); overwrites the coarse states.
+int adj_mg_assemble(AdjointDev& A, const std::vector<LevelDev>& lev, const PhysParams& ph, int turb, double h_rel,
+                    cudaStream_t st, long long& launches);
+// z = C r (transpose = 0: the primal's linearised FAS cycle as a linear solver for J) or
+// z = C^T r (transpose != 0); Jacobians and preconditioners of all levels must be current.
+void adj_mg_apply(AdjointDev& A, int transpose, const double* r, double* z, cudaStream_t st);
+// z = S r or S^T r for the linearised smoothing step (steps of it) of the finest level.
+void adj_smoother_apply(AdjointDev& A, int steps, int transpose, const double* r, double* z, cudaStream_t st);
+// Host memory and the coarse levels of A.
+void adj_release(AdjointDev& A);
 // Lift and drag coefficients of the wall force at the current state (ghosts refilled).
 int adj_force_coefficients(AdjointDev& A, const LevelDev& L, const PhysParams& ph, cudaStream_t st, double* cl,
                            double* cd, long long& launches);
@@ -77,6 +111,9 @@ int adj_force_coefficients(AdjointDev& A, const LevelDev& L, const PhysParams& p
 // applies z = P^-T r with it (scratch: 4n).
 void adj_build_precond(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const SchemeParams& sc, double cfl,
                        cudaStream_t st, long long& launches);
+// The same for every coarse level of the transposed FAS cycle (lev as in adj_mg_setup).
+void adj_mg_build_precond(AdjointDev& A, const std::vector<LevelDev>& lev, const PhysParams& ph,
+                          const SchemeParams& sc, double cfl, cudaStream_t st, long long& launches);
 void adj_precond(const AdjointDev& A, const double* r, double* scratch, double* z, cudaStream_t st);
 // z = P^-T r (steps <= 0) or z = `steps` transposed stage-loop steps from zero; the
 // preconditioner must be built.

@@ -476,7 +476,7 @@ void fasw_destroy(fasw_ctx* c) {
   for (void* q : c->allocs) cudaFree(q);
   if (c->h_norm) cudaFreeHost(c->h_norm);
   if (c->h_err) cudaFreeHost(c->h_err);
-  if (c->adj.h_parts) cudaFreeHost(c->adj.h_parts);
+  adj_release(c->adj);
   delete c;
 }
 
@@ -677,6 +677,18 @@ static int adj_ready(fasw_ctx* c) {
   return adj_setup(c->adj, F.ni, F.nj, F.nw, c->allocs, c->st);
 }
 
+// The finest level's Jacobian and, for the transposed FAS cycle, those of the coarse levels at
+// the restricted state.
+static int adj_assemble_all(fasw_ctx* c, double h_rel) {
+  int r = adj_assemble(c->adj, c->lev[c->L()], c->ph, h_rel, c->st, c->launches);
+  if (r) return r;
+  if (c->adj.precond_kind == ADJ_FAS_CYCLE_T && c->L() > 0) {
+    if ((r = adj_mg_setup(c->adj, c->lev, c->prm.gamma_cycle, c->prm.nu1, c->allocs, c->st))) return r;
+    if ((r = adj_mg_assemble(c->adj, c->lev, c->ph, c->prm.turb, h_rel, c->st, c->launches))) return r;
+  }
+  return FASW_OK;
+}
+
 // FASW_ERR_DEVICE_TIMEOUT when a bounded wait of the sweeps ran out (device error word set).
 static int adj_err_check(fasw_ctx* c) {
   CKR(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -695,7 +707,7 @@ int fasw_adjoint_jacobian(fasw_ctx* c, double h_rel) {
   if (!c || !(h_rel > 0.0) || c->ph.moving || c->lev[c->L()].a_t != 0.0) return FASW_ERR_ARG;
   int r = adj_ready(c);
   if (r) return r;
-  r = adj_assemble(c->adj, c->lev[c->L()], c->ph, h_rel, c->st, c->launches);
+  r = adj_assemble_all(c, h_rel);
   if (r) return r;
   return sync(c);
 }
@@ -741,6 +753,33 @@ int fasw_adjoint_set_precond_steps(fasw_ctx* c, int steps) {
   return FASW_OK;
 }
 
+int fasw_adjoint_set_precond(fasw_ctx* c, int kind) {
+  if (!c || kind < ADJ_STAGE_LOOP || kind > ADJ_FAS_CYCLE_T) return FASW_ERR_ARG;
+  if (kind != c->adj.precond_kind) c->adj.built = false;  // the cycle needs the coarse Jacobians
+  c->adj.precond_kind = kind;
+  return FASW_OK;
+}
+
+int fasw_adjoint_cycle_apply(fasw_ctx* c, double cfl, int kind, int transpose, const double* r, double* z,
+                             int on_device) {
+  if (!c || !r || !z || !(cfl > 0.0) || (kind != 1 && kind != 2) || !c->adj.built) return FASW_ERR_ARG;
+  if (kind == 2 && c->L() > 0 && !c->adj.mg) return FASW_ERR_ARG;
+  const size_t m = 4 * (size_t)c->adj.n;
+  int e = copy_in(c, c->d_tmp, r, m, on_device);
+  if (e) return e;
+  adj_build_precond(c->adj, c->lev[c->L()], c->ph, c->sc, cfl, c->st, c->launches);
+  if (kind == 2) {
+    adj_mg_build_precond(c->adj, c->lev, c->ph, c->sc, cfl, c->st, c->launches);
+    adj_mg_apply(c->adj, transpose, c->d_tmp, c->d_tmp2, c->st);
+  } else {
+    adj_smoother_apply(c->adj, c->adj.smooth_steps, transpose, c->d_tmp, c->d_tmp2, c->st);
+  }
+  ++c->launches;
+  if ((e = adj_err_check(c))) return e;
+  if ((e = copy_out(c, z, c->d_tmp2, m, on_device))) return e;
+  return sync(c);
+}
+
 int fasw_adjoint_solve(fasw_ctx* c, int which, const double* g, double* lam, double tol, int max_iters, int restart,
                        double cfl, int* iters, double* rel_res, int on_device) {
   if (!c || !lam || !iters || !rel_res || !c->adj.built || !(tol > 0.0) || max_iters < 1) return FASW_ERR_ARG;
@@ -753,7 +792,7 @@ int fasw_adjoint_solve(fasw_ctx* c, int which, const double* g, double* lam, dou
     rhs = c->d_tmp;
   }
   const double pcfl = cfl > 0.0 ? cfl : c->prm.cfl;
-  const int code = adj_solve(c->adj, c->lev[c->L()], c->ph, c->sc, pcfl, rhs, c->d_tmp2, tol, max_iters, restart,
+  const int code = adj_solve(c->adj, c->lev, c->ph, c->sc, pcfl, rhs, c->d_tmp2, tol, max_iters, restart,
                              c->allocs, c->st, iters, rel_res, c->launches);
   if (code != FASW_OK && code != FASW_ERR_NOT_CONVERGED) return code;
   int r = adj_err_check(c);
@@ -990,7 +1029,7 @@ int fasw_unsteady_adjoint(fasw_ctx* c, double amp, double omega, double xc, doub
         launch_bl(F, c->ph, c->st);
         c->launches += 2;
       }
-      if ((r = adj_assemble(c->adj, F, c->ph, h_rel, c->st, c->launches))) return fail(r);
+      if ((r = adj_assemble_all(c, h_rel))) return fail(r);
       cudaMemsetAsync(rhs, 0, m * sizeof(double), c->st);
       adj_axpby((int)m, w, c->adj.g + (size_t)which * m, 1.0, rhs, c->st);
       if (n + 1 <= nsteps) adj_axpby((int)m, -b1, lam1, 1.0, rhs, c->st);
@@ -998,7 +1037,7 @@ int fasw_unsteady_adjoint(fasw_ctx* c, double amp, double omega, double xc, doub
       c->launches += 1 + (n + 1 <= nsteps) + (n + 2 <= nsteps);
       int it = 0;
       double rr = 0.0;
-      r = adj_solve(c->adj, F, c->ph, c->sc, pcfl, rhs, lamn, tol, max_iters, restart, c->allocs, c->st, &it, &rr,
+      r = adj_solve(c->adj, c->lev, c->ph, c->sc, pcfl, rhs, lamn, tol, max_iters, restart, c->allocs, c->st, &it, &rr,
                     c->launches);
       if (r == FASW_ERR_NOT_CONVERGED) soft = true;
       else if (r) return fail(r);

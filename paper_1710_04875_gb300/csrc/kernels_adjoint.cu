@@ -341,7 +341,9 @@ int adj_setup(AdjointDev& A, int ni, int nj, int nw, std::vector<void*>& allocs,
       (r = adj_alloc(allocs, &A.fw, 4 * (size_t)ni)) || (r = adj_alloc(allocs, &A.parts, PARTS)) ||
       (r = adj_alloc(allocs, &A.mgs, 4 * (size_t)n)) || (r = adj_alloc(allocs, &A.mgy, 4 * (size_t)n)) ||
       (r = adj_alloc(allocs, &A.mgt, 4 * (size_t)n)) || (r = adj_alloc(allocs, &A.mgz, 4 * (size_t)n)) ||
-      (r = adj_alloc(allocs, &A.tbt, 80 * (size_t)n)))
+      (r = adj_alloc(allocs, &A.tbt, 80 * (size_t)n)) ||
+      (r = adj_alloc(allocs, &A.Jv, (size_t)n * ADJ_SLOTS * 16)) || (r = adj_alloc(allocs, &A.Fvp, 4 * (size_t)n)) ||
+      (r = adj_alloc(allocs, &A.Fvm, 4 * (size_t)n)) || (r = adj_alloc(allocs, &A.mgw, 32 * (size_t)n)))
     return r;
   if (A.fp32) {
     if ((r = adj_alloc(allocs, &A.tb32, 80 * (size_t)n)) || (r = adj_alloc(allocs, &A.yz32, 4 * (size_t)n))) return r;
@@ -358,6 +360,7 @@ int adj_setup(AdjointDev& A, int ni, int nj, int nw, std::vector<void*>& allocs,
   cudaMemcpyAsync(A.rev_ptr, rev_ptr.data(), rev_ptr.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(A.rev, rev.data(), rev.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(A.J, 0, (size_t)n * ADJ_SLOTS * 16 * sizeof(double), st);
+  cudaMemsetAsync(A.Jv, 0, (size_t)n * ADJ_SLOTS * 16 * sizeof(double), st);
   // the host vectors above are freed on return: wait for the copies
   return cudaStreamSynchronize(st) == cudaSuccess ? FASW_OK : FASW_ERR_CUDA;
 }
@@ -377,13 +380,22 @@ int adj_assemble(AdjointDev& A, const LevelDev& L, const PhysParams& ph, double 
         launch_pdl(k_adj_set_state, nb, 128, 0, st, L, A.ub, A.col, k, m, h_rel, sgn == 0 ? 1.0 : -1.0);
         launch_bc_aux(L, ph, 1.0, 0, st);
         a.F = sgn == 0 ? A.Fp : A.Fm;
+        a.Fv = sgn == 0 ? A.Fvp : A.Fvm;
         launch_residual(L, ph, a, st);
-        launch_wall_force(L, ph, A.fw + 2 * sgn * A.ni, A.fw + (2 * sgn + 1) * A.ni, st);
-        launches += 4;
+        launches += 3;
+        if (A.finest) {
+          launch_wall_force(L, ph, A.fw + 2 * sgn * A.ni, A.fw + (2 * sgn + 1) * A.ni, st);
+          ++launches;
+        }
       }
       launch_pdl(k_adj_extract, nb, 128, 0, st, n, A.nbr, A.col, k, m, A.Fp, A.Fm, A.ub, h_rel, A.J);
-      launch_pdl(k_adj_extract_obj, nbf, 128, 0, st, A.ni, n, A.col, k, m, A.fw, A.ub, h_rel, sa, ca, A.g);
+      launch_pdl(k_adj_extract, nb, 128, 0, st, n, A.nbr, A.col, k, m, (const double*)A.Fvp, (const double*)A.Fvm,
+                 (const double*)A.ub, h_rel, A.Jv);
       launches += 2;
+      if (A.finest) {
+        launch_pdl(k_adj_extract_obj, nbf, 128, 0, st, A.ni, n, A.col, k, m, A.fw, A.ub, h_rel, sa, ca, A.g);
+        ++launches;
+      }
     }
   launch_pdl(k_adj_set_state, nb, 128, 0, st, L, A.ub, A.col, -1, 0, 0.0, 0.0);
   launch_bc_aux(L, ph, 1.0, 0, st);
@@ -514,7 +526,10 @@ void adj_build_precond(AdjointDev& A, const LevelDev& L, const PhysParams& ph, c
   }
   A.Lp = L;
   A.nstages = sc.nstages;
-  for (int i = 0; i < 5; ++i) A.stage_c[i] = i < sc.nstages ? sc.alpha[i] / sc.eta : 0.0;
+  for (int i = 0; i < 5; ++i) {
+    A.stage_c[i] = i < sc.nstages ? sc.alpha[i] / sc.eta : 0.0;
+    A.stage_b[i] = i < sc.nstages ? sc.beta[i] : 1.0;
+  }
 }
 
 void adj_precond(const AdjointDev& A, const double* r, double* scratch, double* z, cudaStream_t st) {
@@ -528,12 +543,431 @@ void adj_steps_apply(AdjointDev& A, int steps, const double* r, double* z, cudaS
     steps_apply(A, steps, r, z, st);
 }
 
-int adj_solve(AdjointDev& A, const LevelDev& L, const PhysParams& ph, const SchemeParams& sc, double cfl,
-              const double* g, double* lam, double tol, int max_iters, int restart, std::vector<void*>& allocs,
-              cudaStream_t st, int* iters, double* relres, long long& launches) {
-  adj_build_precond(A, L, ph, sc, cfl, st, launches);
+namespace {
+
+// ---------------------------------------------------------------- transposed smoother and cycle
+// The primal's smoothing step, linearised at a converged state, is a linear solver for J x = b
+// (x from 0; c_i = alpha_i / eta, P^-1 t = W^-1 (eta dt* t), J = J^c + J^v with J^v the
+// Jacobian of the dissipative part F^v, whose stage value is blended with beta_i as in the
+// primal's stage residual):
+//   f_i = beta_i J^v x_(i-1) + (1 - beta_i) f_(i-1),   x_i = c_i P^-1 (b - J^c x_(i-1) - f_i).
+// Its transpose is this recurrence run backwards (reverse mode), with P^-T, J^T and J^v^T.
+// The linearised FAS cycle on level l (nu1 smoothing steps, residual restriction R, gamma
+// coarse cycles on J_(l-1) from zero, bilinear prolongation P of the correction) is
+//   x1 = S b,  x = x1 + P A_(l-1) R (b - J x1),   A = C_(l-1) (gamma 1) or 2C - C J C (gamma 2),
+// and its transpose C^T v = R^T r + S^T (v - J^T R^T r) with r = A^T P^T v.
+
+__global__ void k_lc(int m, double a0, const double* x0, double a1, const double* x1, double a2, const double* x2,
+                     double a3, const double* x3, double* out) {
+  pdl_entry();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  double s = a0 * x0[t];
+  if (x1) s += a1 * x1[t];
+  if (x2) s += a2 * x2[t];
+  if (x3) s += a3 * x3[t];
+  out[t] = s;
+}
+
+// out = eta dt* t per cell (eta dt* = coef vol)
+__global__ void k_scale_dts(int n, const double* coef, const double* vol, const double* t, double* out) {
+  pdl_entry();
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n) return;
+  const double s = coef[d] * vol[d];
+  for (int k = 0; k < 4; ++k) out[(size_t)k * n + d] = s * t[(size_t)k * n + d];
+}
+
+// out[o] = sum over entries e of row o: w[e] in[idx[e]], all four components
+__global__ void k_csr_apply(int nout, int nin, const int* ptr, const int* idx, const double* w, const double* in,
+                            double* out) {
+  pdl_entry();
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int e = ptr[o]; e < ptr[o + 1]; ++e) {
+    const int c = idx[e];
+    for (int k = 0; k < 4; ++k) s[k] += w[e] * in[(size_t)k * nin + c];
+  }
+  for (int k = 0; k < 4; ++k) out[(size_t)k * nout + o] = s[k];
+}
+
+// residual restriction of the FAS cycle: volume-weighted average of the four children
+__global__ void k_restrict_res(LevelDev F, LevelDev C, const double* in, double* out) {
+  pdl_entry();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= C.n) return;
+  const int I = t % C.ni, J = t / C.ni;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q = 0; q < 4; ++q) {
+    const int fc = (2 * J + (q >> 1)) * F.ni + 2 * I + (q & 1);
+    const double w = F.vol[fc];
+    for (int k = 0; k < 4; ++k) s[k] += w * in[(size_t)k * F.n + fc];
+  }
+  for (int k = 0; k < 4; ++k) out[(size_t)k * C.n + t] = s[k] / C.vol[t];
+}
+
+// its transpose: child c of coarse cell t receives vol_c / vol_t of it
+__global__ void k_restrict_res_T(LevelDev F, LevelDev C, const double* in, double* out) {
+  pdl_entry();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= F.n) return;
+  const int t = (c / F.ni / 2) * C.ni + (c % F.ni) / 2;
+  const double w = F.vol[c] / C.vol[t];
+  for (int k = 0; k < 4; ++k) out[(size_t)k * F.n + c] = w * in[(size_t)k * C.n + t];
+}
+
+}  // namespace
+
+struct TransferMap {
+  int* fptr = nullptr;  // fine-major: the coarse cells (and weights) each fine cell reads
+  int* fidx = nullptr;
+  double* fw = nullptr;
+  int* cptr = nullptr;  // coarse-major: the same entries grouped by coarse cell (the transpose)
+  int* cidx = nullptr;
+  double* cw = nullptr;
+};
+
+struct AdjointMG {
+  int L = 0, gamma = 1, nu1 = 1;
+  std::vector<AdjointDev> lv;          // coarse levels 0 .. L-1 (the finest is the outer AdjointDev)
+  std::vector<LevelDev> lev;           // the context's levels (volumes and sizes)
+  std::vector<TransferMap> pm;         // pm[l]: prolongation from level l-1 to level l
+  std::vector<std::vector<double*>> wk;  // per level: 8 work vectors of 4 n_l
+};
+
+namespace {
+
+AdjointDev& level_of(AdjointDev& A, int l) { return l == A.mg->L ? A : A.mg->lv[l]; }
+
+// The prolongation of k_prolong as a matrix: fine cell (i, j) takes 9/16, 3/16, 3/16, 1/16 of
+// the coarse cells (I, J), (I2, J), (I, J2), (I2, J2), I = i/2, I2 = I -+ 1 by the parity of i
+// (likewise J), a coarse index outside the grid standing for the clamped cell, or below the
+// wake cut for the mirror cell of row 0.
+int build_prolong_map(const LevelDev& F, const LevelDev& C, TransferMap& T, std::vector<void*>& allocs,
+                      cudaStream_t st) {
+  const int nf = F.n, nc = C.n;
+  auto target = [&](int I, int J) {
+    int Ic = std::min(std::max(I, 0), C.ni - 1);
+    int Jc;
+    if (J < 0) {
+      if (C.nw > 0 && (Ic < C.nw || Ic >= C.ni - C.nw)) Ic = C.ni - 1 - Ic;
+      Jc = 0;
+    } else {
+      Jc = std::min(J, C.nj - 1);
+    }
+    return Jc * C.ni + Ic;
+  };
+  std::vector<int> fptr(nf + 1, 0), fidx;
+  std::vector<double> fw;
+  for (int c = 0; c < nf; ++c) {
+    const int i = c % F.ni, j = c / F.ni, I = i / 2, J = j / 2;
+    const int I2 = (i % 2 == 0) ? I - 1 : I + 1, J2 = (j % 2 == 0) ? J - 1 : J + 1;
+    const int tg[4] = {target(I, J), target(I2, J), target(I, J2), target(I2, J2)};
+    const double wt[4] = {9.0 / 16.0, 3.0 / 16.0, 3.0 / 16.0, 1.0 / 16.0};
+    const int start = (int)fidx.size();
+    for (int q = 0; q < 4; ++q) {
+      bool merged = false;
+      for (int e = start; e < (int)fidx.size(); ++e)
+        if (fidx[e] == tg[q]) {
+          fw[e] += wt[q];
+          merged = true;
+        }
+      if (!merged) {
+        fidx.push_back(tg[q]);
+        fw.push_back(wt[q]);
+      }
+    }
+    fptr[c + 1] = (int)fidx.size();
+  }
+  const int ne = (int)fidx.size();
+  std::vector<int> cptr(nc + 1, 0), cidx(ne);
+  std::vector<double> cw(ne);
+  for (int e = 0; e < ne; ++e) ++cptr[fidx[e] + 1];
+  for (int t = 0; t < nc; ++t) cptr[t + 1] += cptr[t];
+  std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+  for (int c = 0; c < nf; ++c)  // fine cells in increasing order: a fixed summation order
+    for (int e = fptr[c]; e < fptr[c + 1]; ++e) {
+      const int k = fill[fidx[e]]++;
+      cidx[k] = c;
+      cw[k] = fw[e];
+    }
+  int r;
+  if ((r = adj_alloc(allocs, &T.fptr, fptr.size())) || (r = adj_alloc(allocs, &T.fidx, (size_t)ne)) ||
+      (r = adj_alloc(allocs, &T.fw, (size_t)ne)) || (r = adj_alloc(allocs, &T.cptr, cptr.size())) ||
+      (r = adj_alloc(allocs, &T.cidx, (size_t)ne)) || (r = adj_alloc(allocs, &T.cw, (size_t)ne)))
+    return r;
+  cudaMemcpyAsync(T.fptr, fptr.data(), fptr.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(T.fidx, fidx.data(), ne * sizeof(int), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(T.fw, fw.data(), ne * sizeof(double), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(T.cptr, cptr.data(), cptr.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(T.cidx, cidx.data(), ne * sizeof(int), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(T.cw, cw.data(), ne * sizeof(double), cudaMemcpyHostToDevice, st);
+  return cudaStreamSynchronize(st) == cudaSuccess ? FASW_OK : FASW_ERR_CUDA;  // host vectors die here
+}
+
+void lc(int m, double a0, const double* x0, double a1, const double* x1, double a2, const double* x2, double a3,
+        const double* x3, double* out, cudaStream_t st) {
+  launch_pdl(k_lc, (m + 255) / 256, 256, 0, st, m, a0, x0, a1, x1, a2, x2, a3, x3, out);
+}
+
+void jac(const AdjointDev& A, const double* blocks, const double* v, double* out, int transpose, cudaStream_t st) {
+  const int nb = (A.n + 127) / 128;
+  if (transpose)
+    launch_pdl(k_jac_tmv, nb, 128, 0, st, A.n, A.rev_ptr, A.rev, blocks, v, out);
+  else
+    launch_pdl(k_jac_mv, nb, 128, 0, st, A.n, A.nbr, blocks, v, out);
+}
+
+// x = c P^-1 t (forward: the level's own FP64 blocks; scratch s)
+void precond_fwd(const AdjointDev& A, double c, const double* t, double* s, double* x, cudaStream_t st) {
+  launch_pdl(k_scale_dts, (A.n + 127) / 128, 128, 0, st, A.n, (const double*)A.Lp.coef, (const double*)A.Lp.vol, t,
+             s);
+  LevelDev T = A.Lp;
+  T.yz64 = x;
+  launch_sweep(T, 0, SWEEP_STRIPS, 0, 1, 0.0, s, A.prog, A.err, A.spin_limit, st);
+  const int m = 4 * A.n;
+  lc(m, c, x, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, x, st);
+}
+
+// x = S b: one linearised smoothing step from zero.  Work: A.mgw vectors 0-3.
+void smooth_fwd(AdjointDev& A, const double* b, double* x, cudaStream_t st) {
+  const int m = 4 * A.n;
+  double* f = A.mgw;
+  double* t = A.mgw + (size_t)m;
+  double* jv = A.mgw + 2 * (size_t)m;
+  double* jx = A.mgw + 3 * (size_t)m;
+  for (int i = 0; i < A.nstages; ++i) {
+    const double be = A.stage_b[i], c = A.stage_c[i];
+    if (i == 0) {  // x_0 = 0: f_1 = 0, t = b
+      precond_fwd(A, c, b, t, x, st);
+      continue;
+    }
+    jac(A, A.Jv, x, jv, 0, st);
+    if (i == 1)
+      lc(m, be, jv, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, f, st);
+    else
+      lc(m, be, jv, 1.0 - be, f, 0.0, nullptr, 0.0, nullptr, f, st);
+    jac(A, A.J, x, jx, 0, st);
+    lc(m, 1.0, b, -1.0, jx, 1.0, jv, -1.0, f, t, st);  // b - J^c x - f
+    precond_fwd(A, c, t, jx, x, st);
+  }
+}
+
+// out = S^T v (reverse of smooth_fwd).  Work: A.mgw vectors 0-4, A.mgy.
+void smooth_T(AdjointDev& A, const double* v, double* out, cudaStream_t st) {
+  const int m = 4 * A.n;
+  double* xb = A.mgw;
+  double* fb = A.mgw + (size_t)m;
+  double* w = A.mgw + 2 * (size_t)m;
+  double* s = A.mgw + 3 * (size_t)m;
+  double* tmp = A.mgw + 4 * (size_t)m;
+  cudaMemcpyAsync(xb, v, m * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  for (int i = A.nstages - 1; i >= 0; --i) {
+    const double be = A.stage_b[i], c = A.stage_c[i];
+    precond(A, xb, A.mgy, w, st);
+    lc(m, c, w, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, w, st);  // w = c P^-T xbar_i
+    if (i == A.nstages - 1) {
+      cudaMemcpyAsync(out, w, m * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      lc(m, -1.0, w, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, fb, st);  // fbar_s = -w
+    } else {
+      lc(m, 1.0, out, 1.0, w, 0.0, nullptr, 0.0, nullptr, out, st);
+      lc(m, 1.0, fb, -1.0, w, 0.0, nullptr, 0.0, nullptr, fb, st);
+    }
+    if (i == 0) break;  // x_0 = 0 is no input
+    // xbar_(i-1) = -J^T w + J^v^T (w + beta_i fbar_i);  fbar_(i-1) = (1 - beta_i) fbar_i
+    lc(m, 1.0, w, be, fb, 0.0, nullptr, 0.0, nullptr, s, st);
+    jac(A, A.Jv, s, tmp, 1, st);
+    jac(A, A.J, w, xb, 1, st);
+    lc(m, -1.0, xb, 1.0, tmp, 0.0, nullptr, 0.0, nullptr, xb, st);
+    lc(m, 1.0 - be, fb, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, fb, st);
+  }
+}
+
+// `steps` smoothing steps as a solver of J x = b from zero (transpose: of J^T), x_k = x_(k-1) +
+// S (b - J x_(k-1)); out = sum_k S^T y_k with y_0 = v, y_(k+1) = y_k - J^T S^T y_k.
+// Work: A.mgw vectors 5-7 (plus those of the single step).
+void smooth_steps(AdjointDev& A, int steps, int transpose, const double* v, double* out, cudaStream_t st) {
+  const int m = 4 * A.n;
+  double* y = A.mgw + 5 * (size_t)m;
+  double* mv = A.mgw + 6 * (size_t)m;
+  double* jt = A.mgw + 7 * (size_t)m;
+  if (steps <= 1) {
+    if (transpose)
+      smooth_T(A, v, out, st);
+    else
+      smooth_fwd(A, v, out, st);
+    return;
+  }
+  cudaMemcpyAsync(y, v, m * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(out, 0, m * sizeof(double), st);
+  for (int k = 0; k < steps; ++k) {
+    if (transpose) {
+      smooth_T(A, y, mv, st);
+      lc(m, 1.0, out, 1.0, mv, 0.0, nullptr, 0.0, nullptr, out, st);
+      if (k + 1 < steps) {
+        jac(A, A.J, mv, jt, 1, st);
+        lc(m, 1.0, y, -1.0, jt, 0.0, nullptr, 0.0, nullptr, y, st);
+      }
+    } else {  // y = b - J x, x += S y
+      if (k > 0) {
+        jac(A, A.J, out, jt, 0, st);
+        lc(m, 1.0, v, -1.0, jt, 0.0, nullptr, 0.0, nullptr, y, st);
+      }
+      smooth_fwd(A, y, mv, st);
+      lc(m, 1.0, out, 1.0, mv, 0.0, nullptr, 0.0, nullptr, out, st);
+    }
+  }
+}
+
+// out = C_l v (transpose = 0) or C_l^T v, recursively over the coarse levels.
+void mg_cycle(AdjointDev& A, int l, int transpose, const double* v, double* out, cudaStream_t st) {
+  AdjointMG& G = *A.mg;
+  AdjointDev& Al = level_of(A, l);
+  if (l == 0) {
+    smooth_steps(Al, G.nu1, transpose, v, out, st);
+    return;
+  }
+  AdjointDev& Ac = level_of(A, l - 1);
+  const LevelDev &F = G.lev[l], &Cl = G.lev[l - 1];
+  const int mf = 4 * F.n, mc = 4 * Cl.n;
+  double** wc = G.wk[l - 1].data();
+  double** wf = G.wk[l].data();
+  double *xH = wc[0], *t = wc[1], *u = wc[2], *rH = wc[3], *jt = wc[4];
+  double *rb = wf[5], *x1 = wf[6], *sm = wf[7];
+  const TransferMap& T = G.pm[l];
+  if (transpose) {
+    launch_pdl(k_csr_apply, (Cl.n + 127) / 128, 128, 0, st, Cl.n, F.n, (const int*)T.cptr, (const int*)T.cidx,
+               (const double*)T.cw, v, xH);  // P^T v
+    if (G.gamma == 1) {
+      mg_cycle(A, l - 1, 1, xH, rH, st);
+    } else {  // (2C - C J C)^T = 2C^T - C^T J^T C^T
+      mg_cycle(A, l - 1, 1, xH, t, st);
+      jac(Ac, Ac.J, t, jt, 1, st);
+      lc(mc, 1.0, xH, -1.0, jt, 0.0, nullptr, 0.0, nullptr, u, st);
+      mg_cycle(A, l - 1, 1, u, rH, st);
+      lc(mc, 1.0, rH, 1.0, t, 0.0, nullptr, 0.0, nullptr, rH, st);
+    }
+    launch_pdl(k_restrict_res_T, (F.n + 127) / 128, 128, 0, st, F, Cl, (const double*)rH, rb);  // R^T
+    jac(Al, Al.J, rb, x1, 1, st);
+    lc(mf, 1.0, v, -1.0, x1, 0.0, nullptr, 0.0, nullptr, x1, st);
+    smooth_steps(Al, G.nu1, 1, x1, sm, st);
+    lc(mf, 1.0, rb, 1.0, sm, 0.0, nullptr, 0.0, nullptr, out, st);
+  } else {
+    smooth_steps(Al, G.nu1, 0, v, x1, st);
+    jac(Al, Al.J, x1, rb, 0, st);
+    lc(mf, 1.0, v, -1.0, rb, 0.0, nullptr, 0.0, nullptr, rb, st);  // b - J x1
+    launch_pdl(k_restrict_res, (Cl.n + 127) / 128, 128, 0, st, F, Cl, (const double*)rb, rH);
+    if (G.gamma == 1) {
+      mg_cycle(A, l - 1, 0, rH, xH, st);
+    } else {
+      mg_cycle(A, l - 1, 0, rH, t, st);
+      jac(Ac, Ac.J, t, jt, 0, st);
+      lc(mc, 1.0, rH, -1.0, jt, 0.0, nullptr, 0.0, nullptr, u, st);
+      mg_cycle(A, l - 1, 0, u, xH, st);
+      lc(mc, 1.0, xH, 1.0, t, 0.0, nullptr, 0.0, nullptr, xH, st);
+    }
+    launch_pdl(k_csr_apply, (F.n + 127) / 128, 128, 0, st, F.n, Cl.n, (const int*)T.fptr, (const int*)T.fidx,
+               (const double*)T.fw, (const double*)xH, sm);  // P x_H
+    lc(mf, 1.0, x1, 1.0, sm, 0.0, nullptr, 0.0, nullptr, out, st);
+  }
+}
+
+}  // namespace
+
+int adj_mg_setup(AdjointDev& A, const std::vector<LevelDev>& lev, int gamma, int nu1, std::vector<void*>& allocs,
+                 cudaStream_t st) {
+  const int L = (int)lev.size() - 1;
+  if (A.mg && A.mg->L == L) return FASW_OK;
+  if (A.mg) return FASW_ERR_ARG;
+  AdjointMG* G = new AdjointMG;
+  G->L = L;
+  G->gamma = gamma == 2 ? 2 : 1;
+  G->nu1 = nu1 < 1 ? 1 : nu1;
+  G->lev = lev;
+  G->lv.resize(L);
+  G->pm.resize(L + 1);
+  G->wk.resize(L + 1);
+  A.mg = G;
+  int r;
+  for (int l = 0; l < L; ++l) {
+    AdjointDev& C = G->lv[l];
+    C.finest = false;
+    C.fp32 = A.fp32;
+    C.prog = A.prog;
+    C.err = A.err;
+    C.spin_limit = A.spin_limit;
+    if ((r = adj_setup(C, lev[l].ni, lev[l].nj, lev[l].nw, allocs, st))) return r;
+  }
+  for (int l = 1; l <= L; ++l)
+    if ((r = build_prolong_map(lev[l], lev[l - 1], G->pm[l], allocs, st))) return r;
+  for (int l = 0; l <= L; ++l) {
+    G->wk[l].assign(8, nullptr);
+    for (int k = 0; k < 8; ++k)
+      if ((r = adj_alloc(allocs, &G->wk[l][k], 4 * (size_t)lev[l].n))) return r;
+  }
+  return FASW_OK;
+}
+
+int adj_mg_assemble(AdjointDev& A, const std::vector<LevelDev>& lev, const PhysParams& ph, int turb, double h_rel,
+                    cudaStream_t st, long long& launches) {
+  if (!A.mg) return FASW_ERR_ARG;
+  const int L = A.mg->L;
+  for (int l = L; l >= 1; --l) {
+    launch_restrict(lev[l], lev[l - 1], turb, st);
+    ++launches;
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    // The forcing is constant in the differences but enters their rounding; what the last
+    // primal cycle left there must not make the Jacobian depend on history (the primal
+    // recomputes it every cycle).
+    cudaMemsetAsync(lev[l].s, 0, 4 * (size_t)lev[l].n * sizeof(double), st);
+    int r = adj_assemble(A.mg->lv[l], lev[l], ph, h_rel, st, launches);
+    if (r) return r;
+  }
+  return FASW_OK;
+}
+
+void adj_mg_build_precond(AdjointDev& A, const std::vector<LevelDev>& lev, const PhysParams& ph,
+                          const SchemeParams& sc, double cfl, cudaStream_t st, long long& launches) {
+  if (!A.mg) return;
+  for (int l = 0; l < A.mg->L; ++l) adj_build_precond(A.mg->lv[l], lev[l], ph, sc, cfl, st, launches);
+}
+
+void adj_mg_apply(AdjointDev& A, int transpose, const double* r, double* z, cudaStream_t st) {
+  if (A.mg)
+    mg_cycle(A, A.mg->L, transpose, r, z, st);
+  else
+    smooth_steps(A, 1, transpose, r, z, st);
+}
+
+void adj_smoother_apply(AdjointDev& A, int steps, int transpose, const double* r, double* z, cudaStream_t st) {
+  smooth_steps(A, steps, transpose, r, z, st);
+}
+
+void adj_release(AdjointDev& A) {
+  if (A.h_parts) cudaFreeHost(A.h_parts);
+  A.h_parts = nullptr;
+  if (A.mg) {
+    for (auto& C : A.mg->lv) adj_release(C);
+    delete A.mg;
+    A.mg = nullptr;
+  }
+}
+
+int adj_solve(AdjointDev& A, const std::vector<LevelDev>& lev, const PhysParams& ph, const SchemeParams& sc,
+              double cfl, const double* g, double* lam, double tol, int max_iters, int restart,
+              std::vector<void*>& allocs, cudaStream_t st, int* iters, double* relres, long long& launches) {
+  adj_build_precond(A, lev.back(), ph, sc, cfl, st, launches);
+  const bool cycle = A.precond_kind == ADJ_FAS_CYCLE_T && A.mg;
+  if (cycle) adj_mg_build_precond(A, lev, ph, sc, cfl, st, launches);
   auto apply_m = [&](const double* rr, double* zz) {  // zz = M^-1 rr
-    steps_apply(A, A.smooth_steps, rr, zz, st);
+    if (cycle)
+      mg_cycle(A, A.mg->L, 1, rr, zz, st);
+    else if (A.precond_kind == ADJ_SMOOTHER_T || A.precond_kind == ADJ_FAS_CYCLE_T)
+      smooth_steps(A, A.smooth_steps, 1, rr, zz, st);
+    else
+      steps_apply(A, A.smooth_steps, rr, zz, st);
   };
   const int m = 4 * A.n;
   if (restart < 1 || restart > MAXV - 5) return FASW_ERR_ARG;

@@ -92,6 +92,8 @@ def library():
             "fasw_adjoint_solve": (i, [p, i, dp, dp, d, i, i, d, C.POINTER(i), C.POINTER(d), i]),
             "fasw_adjoint_precond_apply": (i, [p, d, i, dp, dp, i]),
             "fasw_adjoint_set_precond_steps": (i, [p, i]),
+            "fasw_adjoint_set_precond": (i, [p, i]),
+            "fasw_adjoint_cycle_apply": (i, [p, d, i, i, dp, dp, i]),
             "fasw_adjoint_shape_gradient": (i, [p, i, dp, i, dp, d, dp, i]),
             "fasw_checkpoint_schedule": (i, [i, i, dp, dp, i, C.POINTER(i), C.POINTER(ll)]),
             "fasw_unsteady_adjoint": (i, [p, d, d, d, d, d, i, i, d, i, i, i, i, dp, d, d, d, i, i, d, C.POINTER(d),
@@ -333,6 +335,25 @@ class Solver:
     def adjoint_set_precond_steps(self, steps):
         """Smoothing steps of the transposed stage loop per GMRES preconditioner application."""
         _check(self.lib.fasw_adjoint_set_precond_steps(self.h, int(steps)), "fasw_adjoint_set_precond_steps")
+
+    ADJOINT_PRECONDITIONERS = {"stage_loop": 0, "smoother": 1, "cycle": 2}
+
+    def adjoint_set_precond(self, kind):
+        """Adjoint GMRES preconditioner: "stage_loop" (the stage loop run on J^T), "smoother" (the
+        transposed linearised smoothing step) or "cycle" (the transposed linearised FAS cycle, the
+        default).  Assemble the Jacobian again afterwards."""
+        _check(self.lib.fasw_adjoint_set_precond(self.h, self.ADJOINT_PRECONDITIONERS[kind]),
+               "fasw_adjoint_set_precond")
+
+    def adjoint_cycle_apply(self, r, cfl, kind="cycle", transpose=True):
+        """z = M r for the linear operator of the linearised smoothing step ("smoother") or FAS
+        cycle ("cycle") as a solver of J, or its transpose (a solver of J^T)."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        z = np.zeros(self._shape(self.finest))
+        _check(self.lib.fasw_adjoint_cycle_apply(self.h, cfl, self.ADJOINT_PRECONDITIONERS[kind],
+                                                 1 if transpose else 0, r.ctypes.data, z.ctypes.data, 0),
+               "fasw_adjoint_cycle_apply")
+        return z
 
     def adjoint_solve(self, which=0, g=None, tol=1e-10, max_iters=400, restart=250, cfl=0.0):
         """(lam, code, iterations, relative residual) of J^T lam = g (g None: objective which);
