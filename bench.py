@@ -252,8 +252,44 @@ def measure_adjoint(s, g, n_bumps=16):
     return {"objective": "C_D", "cl": cl, "cd": cd, "jacobian_s": t_jac, "solve_s": t_sol,
             "gmres_iterations": it, "relative_residual": rr, "status": int(code), "shape_gradient_s": t_grad,
             "n_params": n_bumps, "grad_norm": float(np.linalg.norm(grad)),
-            "note": "steady state after the 6-order drop; eddy viscosity frozen; GMRES(250), tol 1e-8, "
-                    "preconditioned by 3 transposed stage-loop steps"}
+            "note": "steady state after the 6-order drop; eddy viscosity frozen; flexible GMRES(250), tol 1e-8, "
+                    "preconditioned by the transposed linearised W-cycle"}
+
+
+def measure_c5(P, n_bumps=16):
+    """The 1024x256 RANS sensitivity case (wall spacing 1e-5, M 0.75, Re 6.5e6, alpha 0, 5-level
+    W-cycles of AW3, mixed precision): time to a 6-order drop from the free stream, then the
+    C_D adjoint (eddy viscosity frozen) to a 6-order drop and the shape gradient for 16
+    Hicks-Henne bumps; host-timed around the synchronous library calls."""
+    from synth.shape import bump_fields
+    g = make_cgrid(1024, 256, n_wake=128, wall_spacing=1e-5)
+    p = P.default_params(scheme="AW3", nlevels=5, gamma_cycle=2, viscous=1, turb=1, sensor=1, mach=0.75,
+                         alpha_deg=0.0, re=6.5e6, eta=0.8, d_cut=0.5, cfl=100.0, cfl_ramp=20.0, ramp_cycles=2,
+                         precision="mixed")
+    s = P.Solver(g, p)
+    t0 = time.perf_counter()
+    code, nc, hist = s.solve(1e-6, 3000)
+    t_primal = time.perf_counter() - t0
+    out = {"workload": "rans_1024x256_c5", "cells": g.ni * g.nj, "levels": 5, "precision": "mixed",
+           "primal_status": int(code), "primal_cycles": nc, "primal_s": t_primal,
+           "primal_drop": float(hist[-1] / hist[0]) if len(hist) else None}
+    if code != 0:
+        s.close()
+        return out
+    V = bump_fields(g, n_bumps)
+    t0 = time.perf_counter()
+    s.adjoint_jacobian(1e-6)
+    out["jacobian_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lam, acode, it, rr = s.adjoint_solve(1, tol=1e-6, max_iters=1500, restart=250)
+    out.update(adjoint_status=int(acode), gmres_iterations=it, relative_residual=rr,
+               adjoint_s=time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    grad = s.adjoint_shape_gradient(1, lam, V)
+    out.update(shape_gradient_s=time.perf_counter() - t0, n_params=n_bumps, cd=s.force_coefficients()[1],
+               grad=[float(x) for x in grad])
+    s.close()
+    return out
 
 
 def adjoint_profile(P, iters=30):
@@ -363,6 +399,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-unsteady-adjoint", action="store_true")
+    ap.add_argument("--c5", action="store_true",
+                    help="only the 1024x256 RANS shape-sensitivity case (steady solve, adjoint, 16 bump gradients)")
     ap.add_argument("--adjoint-profile", action="store_true",
                     help="only one 30-iteration adjoint GMRES solve on the workload grid (for ncu launch lists)")
     args = ap.parse_args()
@@ -378,6 +416,9 @@ def main():
 
     if args.adjoint_profile:
         print(json.dumps(adjoint_profile(P)), flush=True)
+        return
+    if args.c5:
+        print(json.dumps(measure_c5(P)), flush=True)
         return
 
     dist = None
