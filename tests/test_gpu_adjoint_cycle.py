@@ -112,7 +112,8 @@ def test_transposed_smoother_and_cycle_are_exact_transposes(precision):
 
 def test_cycle_preconditioned_adjoint_solves_the_rans_workload():
     """The 256x64 RANS workload at its 6-order state: the adjoint preconditioned by the
-    transposed W-cycle and by the stage loop on J^T reach the same lambda."""
+    transposed W-cycle and by the stage loop on J^T reach the same lambda, and the drag
+    gradient of upper and lower bumps has the antisymmetry of the symmetric section."""
     import paper_1710_04875_gb300 as P
     g = make_cgrid(256, 64, wall_spacing=1e-5)
     kw = dict(nlevels=4, gamma_cycle=2, viscous=1, turb=1, mach=0.5, alpha_deg=0.0, re=1e7, cfl=100.0)
@@ -128,4 +129,9 @@ def test_cycle_preconditioned_adjoint_solves_the_rans_workload():
         assert code == 0 and rr <= 1e-9, (kind, code, it, rr)
         out[kind] = (lam, it)
     assert rel_err(out["cycle"][0], out["stage_loop"][0]) < 1e-6
+    # the section is symmetric and alpha = 0: a bump raising the upper surface changes the drag
+    # as the same bump lowering the lower surface, i.e. dC_D/dp_upper = -dC_D/dp_lower
+    from synth.shape import bump_fields
+    grad = s.adjoint_shape_gradient(1, out["cycle"][0], bump_fields(g, 16))
+    assert np.abs(grad[:8] + grad[8:]).max() <= 1e-4 * np.abs(grad).max(), grad
     s.close()
