@@ -149,8 +149,9 @@ int fasw_use_graphs(fasw_ctx* ctx, int enable);
  * (strips where a hyperplane exceeds 128 cells), 3 = strip-pipelined with 8 rows per strip,
  * 4 = with 16 rows per strip, 5 = hyperplane-staged (mixed precision only, nj <= 128: blocks
  * stored hyperplane-major and staged through shared memory by cp.async; elsewhere as 0), 6 / 7 =
- * hyperplane-staged with a staging ring of 4 / 8 steps.  All give the same Gauss-Seidel result
- * up to rounding.  Synchronizes the stream; drops captured cycles. */
+ * hyperplane-staged with a staging ring of 4 / 8 steps, 8 = strip-pipelined with 4 rows per
+ * strip.  All give the same Gauss-Seidel result up to rounding.  Synchronizes the stream; drops
+ * captured cycles. */
 int fasw_set_sweep(fasw_ctx* ctx, int kind);
 
 /* Eddy viscosity of the finest level (Baldwin-Lomax from the current state); n doubles. */

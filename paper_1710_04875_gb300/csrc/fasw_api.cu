@@ -430,7 +430,7 @@ int fasw_create(int ni, int nj, int n_wake, const double* x, const double* y, in
   *c->h_err = 0;
   if (p->spin_limit > 0) c->spin_limit = p->spin_limit;
   {
-    const int nstrips = (nj + 7) / 8 + 1;
+    const int nstrips = (nj + 3) / 4 + 1;  // strips of 4 rows at most
     if ((r = dalloc(c, &c->d_prog, 2 * (size_t)nstrips)) != FASW_OK || (r = dalloc(c, &c->d_err, 1)) != FASW_OK) {
       fasw_destroy(c);
       return r;
@@ -1089,7 +1089,7 @@ int fasw_unsteady_adjoint(fasw_ctx* c, double amp, double omega, double xc, doub
 extern "C" {
 
 int fasw_set_sweep(fasw_ctx* c, int kind) {
-  if (!c || kind < SWEEP_AUTO || kind > SWEEP_HP8) return FASW_ERR_ARG;
+  if (!c || kind < SWEEP_AUTO || kind > SWEEP_STRIPS4) return FASW_ERR_ARG;
   int r = sync(c);
   if (r) return r;
   c->sweep_kind = kind;

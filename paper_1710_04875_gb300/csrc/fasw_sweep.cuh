@@ -5,10 +5,11 @@
 namespace fasw {
 
 // SWEEP_HP: hyperplane-staged FP32 sweep with the default ring depth; SWEEP_HP4 / SWEEP_HP8: with a
-// ring of 4 / 8 steps (where 8 does not fit in shared memory, 4).
+// ring of 4 / 8 steps (where 8 does not fit in shared memory, 4).  SWEEP_STRIPS / STRIPS16 /
+// STRIPS4: pipelined strips of 8 / 16 / 4 rows.
 enum SweepKind {
   SWEEP_AUTO = 0, SWEEP_LEGACY = 1, SWEEP_CTA = 2, SWEEP_STRIPS = 3, SWEEP_STRIPS16 = 4,
-  SWEEP_HP = 5, SWEEP_HP4 = 6, SWEEP_HP8 = 7
+  SWEEP_HP = 5, SWEEP_HP4 = 6, SWEEP_HP8 = 7, SWEEP_STRIPS4 = 8
 };
 inline bool is_hp(int kind) { return kind == SWEEP_HP || kind == SWEEP_HP4 || kind == SWEEP_HP8; }
 

@@ -755,7 +755,8 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
   if (is_hp(kind)) kind = mixed ? SWEEP_CTA : SWEEP_STRIPS;
   const int cells = L.ni < L.nj ? L.ni : L.nj;  // longest hyperplane
   const bool cta_fits = 4 * cells <= 512;       // one thread slot per cell of a hyperplane
-  if ((kind == SWEEP_CTA || (mixed && kind != SWEEP_STRIPS && kind != SWEEP_STRIPS16)) && cta_fits) {
+  const bool strips = kind == SWEEP_STRIPS || kind == SWEEP_STRIPS16 || kind == SWEEP_STRIPS4;
+  if ((kind == SWEEP_CTA || (mixed && !strips)) && cta_fits) {
     int threads = 4 * cells;
     threads = threads < 64 ? 64 : threads;
     threads = (threads + 31) / 32 * 32;
@@ -782,10 +783,16 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
   // Strips wait on one another: at most ceil(nj / SH) CTAs of 16*SH threads, launched on the
   // library's single stream after the previous kernel has finished, so all of them are
   // resident at once on the 152 SMs; every wait is bounded in any case.
-  const int sh = kind == SWEEP_STRIPS16 ? 16 : 8;
+  const int sh = kind == SWEEP_STRIPS16 ? 16 : kind == SWEEP_STRIPS4 ? 4 : 8;
   const int nb = (L.nj + sh - 1) / sh;
   cudaMemsetAsync(prog, 0, 2 * (size_t)nb * sizeof(long long), st);
-  if (sh == 16) {
+  if (sh == 4) {
+    if (mixed)
+      launch_pdl(k_sweep_strips<float, 4>, nb, 64, 0, st, L, reinterpret_cast<const float*>(L.tb), L.yz32, rhs, prog, err,
+                                                   limit, do_update, aw, alpha);
+    else
+      launch_pdl(k_sweep_strips<double, 4>, nb, 64, 0, st, L, L.tb, L.yz64, rhs, prog, err, limit, do_update, aw, alpha);
+  } else if (sh == 16) {
     if (mixed)
       launch_pdl(k_sweep_strips<float, 16>, nb, 256, 0, st, L, reinterpret_cast<const float*>(L.tb), L.yz32, rhs, prog, err,
                                                     limit, do_update, aw, alpha);
@@ -801,6 +808,6 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
   return 1;
 }
 
-int sweep_strips(const LevelDev& L) { return (L.nj + 7) / 8; }
+int sweep_strips(const LevelDev& L) { return (L.nj + 3) / 4; }  // the most strips any kind uses
 
 }  // namespace fasw

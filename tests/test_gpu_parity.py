@@ -221,7 +221,7 @@ def test_graph_replayed_cycles_equal_eager_cycles():
     assert np.array_equal(a.get_state(), b.get_state())
 
 
-@pytest.mark.parametrize("kind", ["reference", "cta", "strips", "strips16"])
+@pytest.mark.parametrize("kind", ["reference", "cta", "strips", "strips16", "strips4"])
 @pytest.mark.parametrize("scheme", ["AW3", "ARK3J"])
 @pytest.mark.parametrize("ni,nj,nw", [(128, 32, 16), (72, 20, 8), (40, 12, 4), (256, 64, 32), (16, 6, 2)])
 def test_sweep_kinds_match_the_oracle(kind, scheme, ni, nj, nw):
