@@ -216,7 +216,8 @@ int fasw_adjoint_precond_apply(fasw_ctx* ctx, double cfl, int steps, const doubl
  *      smoothing steps per level visit, volume-weighted residual restriction R, gamma coarse
  *      cycles, bilinear prolongation P): C^T v = R^T r + S^T (v - J^T R^T r), r = A^T P^T v, with
  *      the coarse Jacobians taken at the volume-weighted restriction of the state; one level
- *      reduces it to kind 1 with one step.
+ *      reduces it to kind 1 with one step;
+ *   3: kind 2 with one coarse cycle per level visit (a V-cycle) whatever the primal's gamma.
  * The adjoint iteration with kind 2 has the primal FAS iteration's convergence rate (the two
  * iteration matrices are transposes up to similarity). Host only. */
 int fasw_adjoint_set_precond(fasw_ctx* ctx, int kind);

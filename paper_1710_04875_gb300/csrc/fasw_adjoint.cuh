@@ -19,7 +19,8 @@ struct AdjointMG;  // transposed linear FAS cycle: coarse levels, transfer maps,
 enum AdjPrecond {
   ADJ_STAGE_LOOP = 0,     // steps of the stage loop run on J^T (x_i = x_0 + c_i P^-T (r - J^T x_(i-1)))
   ADJ_SMOOTHER_T = 1,     // steps of the exact transpose of the primal's linearised smoothing step
-  ADJ_FAS_CYCLE_T = 2     // the exact transpose of the primal's linearised FAS cycle
+  ADJ_FAS_CYCLE_T = 2,    // the exact transpose of the primal's linearised FAS cycle
+  ADJ_FAS_VCYCLE_T = 3    // the same with one coarse cycle per level (V) whatever the primal's gamma
 };
 
 struct AdjointDev {

@@ -682,8 +682,10 @@ static int adj_ready(fasw_ctx* c) {
 static int adj_assemble_all(fasw_ctx* c, double h_rel) {
   int r = adj_assemble(c->adj, c->lev[c->L()], c->ph, h_rel, c->st, c->launches);
   if (r) return r;
-  if (c->adj.precond_kind == ADJ_FAS_CYCLE_T && c->L() > 0) {
-    if ((r = adj_mg_setup(c->adj, c->lev, c->prm.gamma_cycle, c->prm.nu1, c->allocs, c->st))) return r;
+  const int kind = c->adj.precond_kind;
+  if ((kind == ADJ_FAS_CYCLE_T || kind == ADJ_FAS_VCYCLE_T) && c->L() > 0) {
+    const int gamma = kind == ADJ_FAS_VCYCLE_T ? 1 : c->prm.gamma_cycle;
+    if ((r = adj_mg_setup(c->adj, c->lev, gamma, c->prm.nu1, c->allocs, c->st))) return r;
     if ((r = adj_mg_assemble(c->adj, c->lev, c->ph, c->prm.turb, h_rel, c->st, c->launches))) return r;
   }
   return FASW_OK;
@@ -754,7 +756,7 @@ int fasw_adjoint_set_precond_steps(fasw_ctx* c, int steps) {
 }
 
 int fasw_adjoint_set_precond(fasw_ctx* c, int kind) {
-  if (!c || kind < ADJ_STAGE_LOOP || kind > ADJ_FAS_CYCLE_T) return FASW_ERR_ARG;
+  if (!c || kind < ADJ_STAGE_LOOP || kind > ADJ_FAS_VCYCLE_T) return FASW_ERR_ARG;
   if (kind != c->adj.precond_kind) c->adj.built = false;  // the cycle needs the coarse Jacobians
   c->adj.precond_kind = kind;
   return FASW_OK;

@@ -878,7 +878,10 @@ void mg_cycle(AdjointDev& A, int l, int transpose, const double* v, double* out,
 int adj_mg_setup(AdjointDev& A, const std::vector<LevelDev>& lev, int gamma, int nu1, std::vector<void*>& allocs,
                  cudaStream_t st) {
   const int L = (int)lev.size() - 1;
-  if (A.mg && A.mg->L == L) return FASW_OK;
+  if (A.mg && A.mg->L == L) {
+    A.mg->gamma = gamma == 2 ? 2 : 1;
+    return FASW_OK;
+  }
   if (A.mg) return FASW_ERR_ARG;
   AdjointMG* G = new AdjointMG;
   G->L = L;
@@ -959,12 +962,12 @@ int adj_solve(AdjointDev& A, const std::vector<LevelDev>& lev, const PhysParams&
               double cfl, const double* g, double* lam, double tol, int max_iters, int restart,
               std::vector<void*>& allocs, cudaStream_t st, int* iters, double* relres, long long& launches) {
   adj_build_precond(A, lev.back(), ph, sc, cfl, st, launches);
-  const bool cycle = A.precond_kind == ADJ_FAS_CYCLE_T && A.mg;
+  const bool cycle = (A.precond_kind == ADJ_FAS_CYCLE_T || A.precond_kind == ADJ_FAS_VCYCLE_T) && A.mg;
   if (cycle) adj_mg_build_precond(A, lev, ph, sc, cfl, st, launches);
   auto apply_m = [&](const double* rr, double* zz) {  // zz = M^-1 rr
     if (cycle)
       mg_cycle(A, A.mg->L, 1, rr, zz, st);
-    else if (A.precond_kind == ADJ_SMOOTHER_T || A.precond_kind == ADJ_FAS_CYCLE_T)
+    else if (A.precond_kind != ADJ_STAGE_LOOP)
       smooth_steps(A, A.smooth_steps, 1, rr, zz, st);
     else
       steps_apply(A, A.smooth_steps, rr, zz, st);

@@ -336,12 +336,13 @@ class Solver:
         """Smoothing steps of the transposed stage loop per GMRES preconditioner application."""
         _check(self.lib.fasw_adjoint_set_precond_steps(self.h, int(steps)), "fasw_adjoint_set_precond_steps")
 
-    ADJOINT_PRECONDITIONERS = {"stage_loop": 0, "smoother": 1, "cycle": 2}
+    ADJOINT_PRECONDITIONERS = {"stage_loop": 0, "smoother": 1, "cycle": 2, "vcycle": 3}
 
     def adjoint_set_precond(self, kind):
         """Adjoint GMRES preconditioner: "stage_loop" (the stage loop run on J^T), "smoother" (the
-        transposed linearised smoothing step) or "cycle" (the transposed linearised FAS cycle, the
-        default).  Assemble the Jacobian again afterwards."""
+        transposed linearised smoothing step), "cycle" (the transposed linearised FAS cycle, the
+        default) or "vcycle" (the same with one coarse cycle per level).  Assemble the Jacobian
+        again afterwards."""
         _check(self.lib.fasw_adjoint_set_precond(self.h, self.ADJOINT_PRECONDITIONERS[kind]),
                "fasw_adjoint_set_precond")
 
