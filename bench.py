@@ -292,6 +292,38 @@ def measure_c5(P, n_bumps=16):
     return out
 
 
+def measure_c5_unsteady(P, n_bumps=16):
+    """The unsteady part of the sensitivity case: the pitching motion of the 512x128 RANS case
+    (M 0.8, Re 1e6, alpha = 2 deg sin(2kt), k = 0.2, 64 steps per period) over two periods (128
+    levels), each level to a 3-order pseudo-time drop, every level stored; time-averaged C_D
+    and its shape gradient for 16 bumps with the steady start's own adjoint (eddy viscosity
+    frozen per level), mixed precision.  Host-timed around the synchronous library calls."""
+    from synth.cases import config_c3
+    from synth.shape import bump_fields
+    from paper_1710_04875_gb300.adjoint import pitching_gradient
+    c = config_c3()
+    g = c.grid()
+    p = P.default_params(scheme="AW3", nlevels=4, gamma_cycle=2, viscous=1, turb=1, sensor=1, mach=c.mach,
+                         alpha_deg=0.0, re=c.reynolds, eta=0.8, d_cut=0.5, cfl=100.0, cfl_ramp=20.0, ramp_cycles=2,
+                         precision="mixed")
+    s = P.Solver(g, p)
+    t0 = time.perf_counter()
+    code, nc, hist = s.solve(1e-6, 2000)
+    t_steady = time.perf_counter() - t0
+    omega = 0.4
+    dt = 2.0 * np.pi / omega / 64
+    t0 = time.perf_counter()
+    J, grad, info = pitching_gradient(s, bump_fields(g, n_bumps), np.radians(2.0), omega, dt, 128, which=1,
+                                      snapshots=None, drop=1e-3, max_cycles=400, tol=1e-6, max_iters=1500,
+                                      restart=250)
+    t = time.perf_counter() - t0
+    s.close()
+    return {"workload": "rans_512x128_pitching_2_periods", "cells": g.ni * g.nj, "time_levels": 128,
+            "precision": "mixed", "steady_start_status": int(code), "steady_start_cycles": nc,
+            "steady_start_s": t_steady, "J": J, "seconds": t, "seconds_per_time_level": t / 128,
+            "grad": [float(x) for x in grad], **info}
+
+
 def adjoint_profile(P, iters=30):
     """One adjoint GMRES(250) solve of C_D with a fixed count of iterations on the workload grid
     (FP64, thin-layer RANS, frozen eddy viscosity) at a smoothly perturbed free stream, so that
@@ -401,6 +433,8 @@ def main():
     ap.add_argument("--no-unsteady-adjoint", action="store_true")
     ap.add_argument("--c5", action="store_true",
                     help="only the 1024x256 RANS shape-sensitivity case (steady solve, adjoint, 16 bump gradients)")
+    ap.add_argument("--c5-unsteady", action="store_true",
+                    help="only the two-period unsteady adjoint of the pitching 512x128 RANS case (minutes)")
     ap.add_argument("--adjoint-profile", action="store_true",
                     help="only one 30-iteration adjoint GMRES solve on the workload grid (for ncu launch lists)")
     args = ap.parse_args()
@@ -419,6 +453,9 @@ def main():
         return
     if args.c5:
         print(json.dumps(measure_c5(P)), flush=True)
+        return
+    if args.c5_unsteady:
+        print(json.dumps(measure_c5_unsteady(P)), flush=True)
         return
 
     dist = None
