@@ -352,7 +352,9 @@ int fasw_batch_solve(fasw_batch* batch, double drop, int max_cycles, int* cycles
 /* Picks the sweep variant (see fasw_set_sweep) of every case among those that never wait on
  * another CTA (kinds 7, 6 and 2; strips are excluded because concurrent cases do not guarantee
  * that all CTAs of a sweep are resident), one grid shape (ni, nj) at a time, by timing whole
- * batch cycles (states are saved and restored); results are cached per shape and precision for
+ * batch cycles (states are saved and restored; each candidate against the incumbent timed beside
+ * it, the faster of two timings each, a switch must gain 2 %); results are cached per shape and
+ * precision for
  * the process, so a batch whose shapes are all cached is not timed again.  choice[k] (nullable)
  * receives the kind used for case k. */
 int fasw_batch_autotune(fasw_batch* batch, int* choice);

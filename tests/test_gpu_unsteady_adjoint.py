@@ -53,6 +53,28 @@ def test_unsteady_adjoint_matches_the_oracle(euler_case):
     s.close()
 
 
+def test_laminar_unsteady_adjoint_matches_the_oracle():
+    """Thin-layer viscous flux on the pitching no-slip wall (moving-wall ghosts, grid velocities in
+    the viscous terms): three levels against the oracle."""
+    import paper_1710_04875_gb300 as P
+    g = make_cgrid(64, 16, wall_spacing=5e-3)
+    kw = dict(nlevels=2, viscous=1, turb=0, mach=0.5, alpha_deg=0.0, re=5e3, cfl=1e3)
+    po, pg = pair_params(**kw)
+    u0 = _steady(g, po)
+    V = bump_fields(g, 2)
+    N = 3
+    Jo, go, g0o, _ = U.gradient(g, po, u0, V, AMP, OMEGA, XC, YC, DT, N, DROP, CYCLES, 1)
+    s = P.Solver(g, pg)
+    s.set_state(u0)
+    Jg, gg, g0g, code, st = s.unsteady_adjoint(AMP, OMEGA, DT, N, V, which=1, xc=XC, yc=YC, drop=DROP,
+                                               max_cycles=CYCLES, tol=1e-11, max_iters=600, restart=250)
+    assert code == 0, st
+    assert abs(Jg - Jo) <= 1e-9 * abs(Jo)
+    assert rel_err(gg, go) < 1e-6, (gg, go)
+    assert rel_err(g0g, g0o) < 1e-6
+    s.close()
+
+
 def test_checkpointed_reverse_sweep_is_bit_identical(euler_case):
     """Binomial checkpointing with one and with two stored levels recomputes states exactly
     (deterministic kernels), so the adjoint equals the store-every-level run bit for bit; the

@@ -111,3 +111,41 @@ def test_adjoint_matches_finite_differences_of_unsteady_solves(case):
     Jp, _ = U.forward(g, p, u0 + hp * d, AMP, OMEGA, XC, YC, DT, N, DROP, CYCLES, 1)
     Jm, _ = U.forward(g, p, u0 - hp * d, AMP, OMEGA, XC, YC, DT, N, DROP, CYCLES, 1)
     assert abs((Jp - Jm) / (2 * hp) - np.sum(g0 * d)) <= 1e-3 * abs(np.sum(g0 * d))
+
+
+def test_laminar_adjoint_equals_tangent():
+    """The same identity with the thin-layer viscous flux on the moving no-slip wall."""
+    g = make_cgrid(32, 8, n_wake=4, wall_spacing=5e-3)
+    p = O.make_params("AW3", nlevels=2, viscous=1, turb=0, sensor=1, mach=0.5, alpha_deg=0.0, re=5e3, cfl=1e3)
+    o = O.Oracle(g, p)
+    for k in range(300):
+        o.fas_cycle(k)
+    u0 = o.get_state()
+    V = bump_fields(g, 2)
+    n = 3
+    J, grad, g0, _ = U.gradient(g, p, u0, V, AMP, OMEGA, XC, YC, DT, n, DROP, CYCLES, 1)
+    _, states = U.forward(g, p, u0, AMP, OMEGA, XC, YC, DT, n, DROP, CYCLES, 1)
+    e = np.zeros(2)
+    e[0] = 1e-6
+    du = {0: np.zeros(u0.size)}
+    dJ = 0.0
+    for m in range(1, n + 1):
+        phi, phidot = U.pitch(m * DT, AMP, OMEGA)
+        a, b, c = U.time_coefficients(m, DT)
+        on = O.Oracle(g, p)
+        on.set_motion(phi, phidot, XC, YC)
+        on.set_state(states[m])
+        on.set_time_source(a, None)
+        Jn, _, gD = jacobian(on, 0.0)
+        F, C = [], []
+        for sgn in (1.0, -1.0):
+            ok = O.Oracle(deformed(g, sgn * e, V), p)
+            ok.set_motion(phi, phidot, XC, YC)
+            ok.set_state(states[m])
+            F.append(ok.residual()[0].ravel())
+            C.append(force_coefficients(*ok.wall_force(), 0.0)[1])
+        rhs = -(F[0] - F[1]) / 2e-6 - b * du[m - 1] - (c * du[m - 2] if m >= 2 else 0.0)
+        du[m] = spla.spsolve(Jn.tocsc(), rhs)
+        dJ += ((C[0] - C[1]) / 2e-6 + gD @ du[m]) / n
+    assert abs(dJ - grad[0]) <= 1e-9 * max(abs(grad[0]), 1.0), (dJ, grad[0])
+
