@@ -81,3 +81,63 @@ def pitching_gradient(solver: Solver, fields, amp, omega, dt, nsteps, which=1, x
     info = dict(stats, unsteady_status=int(code), steady_status=int(code0), steady_iterations=it0,
                 steady_relative_residual=rr0)
     return J, grad + steady, info
+
+
+class PitchingContext:
+    """Settings of the pitching objective: motion alpha + amp sin(omega t) for nsteps dual-time
+    steps of size dt from the steady state, objective `which` (0 C_L, 1 C_D) averaged over the
+    steps, shape from grid_of(p) / fields as for ShapeForces."""
+
+    def __init__(self, grid_of, fields, params, amp, omega, dt, nsteps, which=1, xc=0.25, yc=0.0, snapshots=None,
+                 steady_drop=1e-12, steady_cycles=3000, drop=1e-10, max_cycles=500, tol=1e-10, max_iters=600,
+                 restart=250):
+        self.grid_of = grid_of
+        self.fields = np.ascontiguousarray(fields, dtype=np.float64)
+        self.params = params
+        self.amp, self.omega, self.dt, self.nsteps = amp, omega, dt, nsteps
+        self.which, self.xc, self.yc, self.snapshots = which, xc, yc, snapshots
+        self.steady_drop, self.steady_cycles = steady_drop, steady_cycles
+        self.drop, self.max_cycles = drop, max_cycles
+        self.tol, self.max_iters, self.restart = tol, max_iters, restart
+        self.info = {}
+
+
+def _steady_solver(actx, p):
+    s = Solver(actx.grid_of(p.detach().cpu().numpy()), actx.params)
+    code, nc, hist = s.solve(actx.steady_drop, actx.steady_cycles)
+    actx.info["steady"] = (int(code), int(nc))
+    return s
+
+
+class PitchingForces(torch.autograd.Function):
+    """Time-averaged lift or drag of the pitching motion as a function of the shape parameters
+    p; the forward pass runs the steady start and the dual-time steps, the backward pass the
+    unsteady adjoint (fasw_unsteady_adjoint) and the steady start's own adjoint."""
+
+    @staticmethod
+    def forward(ctx, p: torch.Tensor, actx: PitchingContext):
+        s = _steady_solver(actx, p)
+        J = 0.0
+        for n in range(1, actx.nsteps + 1):
+            t = n * actx.dt
+            s.set_motion(-actx.amp * np.sin(actx.omega * t), -actx.amp * actx.omega * np.cos(actx.omega * t),
+                         actx.xc, actx.yc)
+            s.dual_time_step(actx.dt, actx.drop, actx.max_cycles)
+            J += s.force_coefficients()[actx.which] / actx.nsteps
+        s.close()
+        ctx.actx = actx
+        ctx.save_for_backward(p)
+        return torch.tensor(J, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, gout: torch.Tensor):
+        a = ctx.actx
+        (p,) = ctx.saved_tensors
+        s = _steady_solver(a, p)
+        J, grad, info = pitching_gradient(s, a.fields, a.amp, a.omega, a.dt, a.nsteps, which=a.which, xc=a.xc,
+                                          yc=a.yc, snapshots=a.snapshots, drop=a.drop, max_cycles=a.max_cycles,
+                                          tol=a.tol, max_iters=a.max_iters, restart=a.restart)
+        s.close()
+        a.info["adjoint"] = info
+        a.info["J_backward"] = J
+        return gout.to(torch.float64) * torch.tensor(grad, dtype=torch.float64), None

@@ -133,3 +133,27 @@ def test_total_pitching_gradient_matches_differences_of_full_solves(euler_case):
               - _unsteady_objective(P, deformed(g, -e, V), pg, N, 1)) / (2 * h)
         # JST switches make the residual piecewise smooth; an O(1) error shows far above this
         assert abs(fd - grad[k]) <= 1e-3 * abs(grad[k]), (k, fd, grad[k])
+
+
+def test_pitching_forces_autograd():
+    """torch.autograd.Function around the pitching objective: the forward value is the time
+    average of the dual-time steps, the backward gradient the unsteady adjoint's."""
+    import torch
+    import paper_1710_04875_gb300 as P
+    from paper_1710_04875_gb300.adjoint import PitchingContext, PitchingForces, pitching_gradient
+    g = make_cgrid(64, 16, wall_spacing=2e-3)
+    _, pg = pair_params(nlevels=2, mach=0.6, alpha_deg=0.0, cfl=1e4)
+    V = bump_fields(g, 2)
+    N = 3
+    actx = PitchingContext(lambda q: deformed(g, q, V), V, pg, AMP, OMEGA, DT, N, which=1, drop=DROP,
+                           max_cycles=CYCLES, tol=1e-11)
+    p = torch.zeros(2, dtype=torch.float64, requires_grad=True)
+    J = PitchingForces.apply(p, actx)
+    J.backward()
+    s = P.Solver(g, pg)
+    s.solve(actx.steady_drop, actx.steady_cycles)
+    Jr, gr, _ = pitching_gradient(s, V, AMP, OMEGA, DT, N, which=1, drop=DROP, max_cycles=CYCLES, tol=1e-11)
+    s.close()
+    assert abs(float(J) - Jr) <= 1e-12 * abs(Jr)
+    assert rel_err(p.grad.numpy(), gr) < 1e-12
+
