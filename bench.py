@@ -38,9 +38,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # algorithmic FP64 flops per cell and launch, counted from the kernels (FMA = 2)
 FLOPS_PER_CELL = {"sgs": 230.0, "residual": 310.0, "face_blocks": 380.0, "diag_blocks": 100.0}
 # DRAM bytes per cell of one FP64 strip-sweep launch (dram__bytes_read.sum + write, cold caches):
-# 767 KB for the 1,024 cells of a 64x16 level (profiles/sweep_strips_fp64_rans_256x64_level64x16.md);
+# 11.6 MB for the 16,384 cells of the finest 256x64 level (profiles/sweep_strips_fp64_dram_rans_256x64.md);
 # the traffic is the transfer blocks and vectors of each cell, so it scales with the cells
-SWEEP_DRAM_BYTES_PER_CELL = 767e3 / 1024
+SWEEP_DRAM_BYTES_PER_CELL = 11.6e6 / 16384
 
 
 def level_visits(nlevels, gamma):
@@ -599,7 +599,7 @@ def main():
         traffic = SWEEP_DRAM_BYTES_PER_CELL * cells_per_launch if dom == "sgs" else None
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "traffic_source": "ncu dram bytes of one 64x16-level launch, scaled by cells" if traffic else None,
+                "traffic_source": "ncu dram bytes of a finest-level launch (708 B/cell), scaled by cells" if traffic else None,
                 "avg_launch_ms": avg_ms,
                 "launches_per_cycle": n_l / args.steps, "cells_per_launch": cells_per_launch,
                 "flops_per_cell": FLOPS_PER_CELL[dom],
