@@ -252,9 +252,15 @@ def measure_adjoint(s, g, n_bumps=16):
     t0 = time.perf_counter()
     grad = s.adjoint_shape_gradient(1, lam, V)
     t_grad = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gx, gy = s.adjoint_vertex_gradient(1, lam)
+    t_vert = time.perf_counter() - t0
+    via = np.array([np.sum(gy * V[k]) for k in range(n_bumps)])
     cl, cd = s.force_coefficients()
     return {"objective": "C_D", "cl": cl, "cd": cd, "jacobian_s": t_jac, "solve_s": t_sol,
             "gmres_iterations": it, "relative_residual": rr, "status": int(code), "shape_gradient_s": t_grad,
+            "vertex_gradient_s": t_vert,
+            "vertex_vs_shape_gradient": float(np.abs(via - grad).max() / max(np.abs(grad).max(), 1e-300)),
             "n_params": n_bumps, "grad_norm": float(np.linalg.norm(grad)),
             "note": "steady state after the 6-order drop; eddy viscosity frozen; flexible GMRES(250), tol 1e-8, "
                     "preconditioned by the transposed linearised W-cycle"}

@@ -154,7 +154,8 @@ int fasw_use_graphs(fasw_ctx* ctx, int enable);
  * captured cycles. */
 int fasw_set_sweep(fasw_ctx* ctx, int kind);
 
-/* Eddy viscosity of the finest level (Baldwin-Lomax from the current state); n doubles. */
+/* Eddy viscosity of the finest level (Baldwin-Lomax from the current state); n doubles.  A
+ * laminar context (turb = 0) keeps a zero eddy viscosity in its own residual. */
 int fasw_get_mut(fasw_ctx* ctx, double* mut, int on_device);
 
 /* Dual time stepping, eq. (nonlin-eq): set a_t (3/(2 dt) for BDF2, 1/dt for implicit Euler;
@@ -246,6 +247,18 @@ int fasw_adjoint_solve(fasw_ctx* ctx, int which, const double* g, double* lam, d
  * h_x along V_k at the current state.  The grid is restored.  grad is host memory. */
 int fasw_adjoint_shape_gradient(fasw_ctx* ctx, int which, const double* lam, int nparam, const double* vy, double h_x,
                                 double* grad, int on_device);
+
+/* The transposed product (dF/dX)^T lam with the objective's explicit part: for every vertex
+ * coordinate, gx/gy = dJ/dX - lam^T dF/dX ((nj+1) x (ni+1) each, index j*(ni+1) + i), by central
+ * differences over colour groups of vertices, each vertex moved by h_x times the shortest grid
+ * edge at it (a wall vertex of a stretched grid moves by a small part of its first cell; a fixed
+ * step would be a large part of it and the differences nonlinear) (a greedy colouring in which no cell
+ * residual and no wall-face force depends on two vertices of one colour: a vertex reaches the
+ * 6 x 6 cells around it, the cells that see those across the wake cut, and the wall faces next
+ * to it).  Contracting with any vertex displacement field V gives that field's shape gradient
+ * (fasw_adjoint_shape_gradient computes the same per field).  Fixed grid.  The grid is restored. */
+int fasw_adjoint_vertex_gradient(fasw_ctx* ctx, int which, const double* lam, double h_x, double* gx, double* gy,
+                                 int on_device);
 
 /* ---- Discrete adjoint of dual time stepping (section 6: implicit Euler for the first step,
  * BDF2 after) on a rigidly pitching grid.  Level n = 1..N places the grid at rotation

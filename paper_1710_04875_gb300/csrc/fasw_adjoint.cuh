@@ -69,6 +69,13 @@ struct AdjointDev {
   int nstages = 1;
   int precond_kind = ADJ_FAS_CYCLE_T;
   AdjointMG* mg = nullptr;  // owned (adj_release)
+  // (dF/dX)^T lam by coloured differences over vertices (adj_vertex_setup)
+  int nvcolours = 0;
+  int* vcol = nullptr;      // (nj+1)(ni+1) vertex colours
+  int* vinfl_ptr = nullptr; // CSR: the cells (index < n) and wall faces (n + i) each vertex reaches
+  int* vinfl = nullptr;
+  double* vx = nullptr;     // 2 x (nj+1)(ni+1) perturbed vertex coordinates
+  double* vlen = nullptr;   // (nj+1)(ni+1) shortest edge at each vertex (scale of its step)
   double* mgw = nullptr;    // work vectors of the linearised smoothing step and its transpose (8 x 4n)
   int smooth_steps = 3;    // smoothing steps per application of the GMRES preconditioner
 };
@@ -103,6 +110,22 @@ int adj_mg_assemble(AdjointDev& A, const std::vector<LevelDev>& lev, const PhysP
 void adj_mg_apply(AdjointDev& A, int transpose, const double* r, double* z, cudaStream_t st);
 // z = S r or S^T r for the linearised smoothing step (steps of it) of the finest level.
 void adj_smoother_apply(AdjointDev& A, int steps, int transpose, const double* r, double* z, cudaStream_t st);
+// Vertex colouring for the vertex gradient: every vertex reaches the cells whose residual
+// depends on it (a box of 6 x 6 cells around it, and across the wake cut the cells that see the
+// box through their ghosts) and the wall faces whose force does; no cell or face is reached by
+// two vertices of one colour.  Allocates once.
+int adj_vertex_setup(AdjointDev& A, int nw, std::vector<void*>& allocs, cudaStream_t st);
+// The shortest grid edge at every vertex (A.vlen): each vertex moves by h_rel times it, so that a
+// wall vertex of a stretched grid is moved by a small fraction of its first cell.
+void adj_vertex_lengths(const AdjointDev& A, const double* x0, const double* y0, cudaStream_t st);
+// Per vertex of colour k, direction dir: g[v] = (dC_which - lam . dF) / (2 h_rel len_v) over the
+// cells and wall faces it reaches (dF = F+ - F-, dC from the wall forces fw+ / fw-).
+void adj_vertex_accumulate(const AdjointDev& A, int k, int which, double sa, double ca, const double* lam,
+                           const double* Fp, const double* Fm, const double* fw, double h_rel, double* g,
+                           cudaStream_t st);
+// xo, yo = x0, y0 moved by +-h_rel len_v in x (dir 0) or y (dir 1) at the vertices of colour k.
+void adj_vertex_perturb(const AdjointDev& A, int k, int dir, double h, const double* x0, const double* y0,
+                        double* xo, double* yo, cudaStream_t st);
 // Host memory and the coarse levels of A.
 void adj_release(AdjointDev& A);
 // Lift and drag coefficients of the wall force at the current state (ghosts refilled).

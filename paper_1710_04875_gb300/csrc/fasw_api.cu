@@ -1090,6 +1090,47 @@ int fasw_unsteady_adjoint(fasw_ctx* c, double amp, double omega, double xc, doub
 
 extern "C" {
 
+int fasw_adjoint_vertex_gradient(fasw_ctx* c, int which, const double* lam, double h_x, double* gx, double* gy,
+                                 int on_device) {
+  if (!c || !lam || !gx || !gy || which < 0 || which > 1 || !(h_x > 0.0) || c->ph.moving) return FASW_ERR_ARG;
+  int r = adj_ready(c);
+  if (r) return r;
+  LevelDev& F = c->lev[c->L()];
+  AdjointDev& A = c->adj;
+  if ((r = adj_vertex_setup(A, F.nw, c->allocs, c->st))) return r;
+  adj_vertex_lengths(A, c->d_x0, c->d_y0, c->st);
+  ++c->launches;
+  const size_t m = 4 * (size_t)F.n, nv = (size_t)(F.ni + 1) * (F.nj + 1);
+  if ((r = copy_in(c, c->d_tmp, lam, m, on_device))) return r;
+  double* xo = A.vx;
+  double* yo = A.vx + nv;
+  double* g = c->d_tmp3;  // gx, then gy
+  LevelDev Fz = F;
+  Fz.a_t = 0.0;  // the time term does not depend on X
+  ResArgs a{};
+  a.mode = RES_FULL;
+  const double al = c->ph.alpha_deg * M_PI / 180.0, sa = std::sin(al), ca = std::cos(al);
+  for (int k = 0; k < A.nvcolours; ++k)
+    for (int dir = 0; dir < 2; ++dir) {
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        adj_vertex_perturb(A, k, dir, sgn == 0 ? h_x : -h_x, c->d_x0, c->d_y0, xo, yo, c->st);
+        launch_metrics_fine(Fz, xo, yo, c->st);
+        launch_bc_aux(Fz, c->ph, 1.0, 0, c->st);
+        a.F = sgn == 0 ? A.Fp : A.Fm;
+        launch_residual(Fz, c->ph, a, c->st);
+        launch_wall_force(Fz, c->ph, A.fw + 2 * sgn * A.ni, A.fw + (2 * sgn + 1) * A.ni, c->st);
+        c->launches += 5;
+      }
+      adj_vertex_accumulate(A, k, which, sa, ca, c->d_tmp, A.Fp, A.Fm, A.fw, h_x, g + dir * nv, c->st);
+      ++c->launches;
+    }
+  launch_metrics_fine(F, c->d_x0, c->d_y0, c->st);
+  launch_bc_aux(F, c->ph, 1.0, 0, c->st);
+  c->launches += 2;
+  if ((r = copy_out(c, gx, g, nv, on_device)) || (r = copy_out(c, gy, g + nv, nv, on_device))) return r;
+  return sync(c);
+}
+
 int fasw_set_sweep(fasw_ctx* c, int kind) {
   if (!c || kind < SWEEP_AUTO || kind > SWEEP_STRIPS4) return FASW_ERR_ARG;
   int r = sync(c);
@@ -1132,6 +1173,8 @@ int fasw_get_mut(fasw_ctx* c, double* mut, int on_device) {
   c->launches += 2;
   int r = copy_out(c, mut, c->lev[Lf].mut, (size_t)c->lev[Lf].n, on_device);
   if (r) return r;
+  if (!c->prm.turb)  // a laminar context's residual must not see the eddy viscosity
+    CKR(cudaMemsetAsync(c->lev[Lf].mut, 0, (size_t)c->lev[Lf].n * sizeof(double), c->st));
   return sync(c);
 }
 

@@ -875,6 +875,136 @@ void mg_cycle(AdjointDev& A, int l, int transpose, const double* v, double* out,
 
 }  // namespace
 
+// ---------------------------------------------------------------- vertex gradient
+namespace {
+
+__global__ void k_vertex_lengths(int ni, int nj, const double* x, const double* y, double* len) {
+  pdl_entry();
+  const int V = ni + 1;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V * (nj + 1)) return;
+  const int I = v % V, J = v / V;
+  double best = 1e300;
+  const int nb[4][2] = {{I - 1, J}, {I + 1, J}, {I, J - 1}, {I, J + 1}};
+  for (int q = 0; q < 4; ++q) {
+    const int a = nb[q][0], b = nb[q][1];
+    if (a < 0 || a > ni || b < 0 || b > nj) continue;
+    const double dx = x[b * V + a] - x[v], dy = y[b * V + a] - y[v];
+    const double d = sqrt(dx * dx + dy * dy);
+    if (d > 0.0 && d < best) best = d;  // coincident wake-cut vertices have no length between them
+  }
+  len[v] = best < 1e300 ? best : 1.0;
+}
+
+__global__ void k_vertex_perturb(int nv, const int* col, int k, int dir, double h, const double* len,
+                                 const double* x0, const double* y0, double* xo, double* yo) {
+  pdl_entry();
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const double d = col[v] == k ? h * len[v] : 0.0;
+  xo[v] = x0[v] + (dir == 0 ? d : 0.0);
+  yo[v] = y0[v] + (dir == 1 ? d : 0.0);
+}
+
+__global__ void k_vertex_accum(int nv, int n, int ni, const int* col, int k, const int* ptr, const int* idx,
+                               int which, double sa, double ca, const double* lam, const double* Fp,
+                               const double* Fm, const double* fw, double h, const double* len, double* g) {
+  pdl_entry();
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv || col[v] != k) return;
+  double dl = 0.0, dc = 0.0;
+  for (int e = ptr[v]; e < ptr[v + 1]; ++e) {
+    const int t = idx[e];
+    if (t < n) {
+      for (int q = 0; q < 4; ++q) dl += lam[(size_t)q * n + t] * (Fp[(size_t)q * n + t] - Fm[(size_t)q * n + t]);
+    } else {
+      const int i = t - n;
+      const double dfx = fw[i] - fw[2 * ni + i], dfy = fw[ni + i] - fw[3 * ni + i];
+      dc += which == 0 ? 2.0 * (-dfx * sa + dfy * ca) : 2.0 * (dfx * ca + dfy * sa);
+    }
+  }
+  g[v] = (dc - dl) / (2.0 * h * len[v]);
+}
+
+}  // namespace
+
+int adj_vertex_setup(AdjointDev& A, int nw, std::vector<void*>& allocs, cudaStream_t st) {
+  if (A.vcol) return FASW_OK;
+  const int ni = A.ni, nj = A.nj, n = A.n, V = ni + 1, nv = (ni + 1) * (nj + 1);
+  auto on_cut = [&](int i) { return nw > 0 && (i < nw || i >= ni - nw); };
+  std::vector<std::vector<int>> infl(nv);
+  for (int J = 0; J <= nj; ++J)
+    for (int I = 0; I <= ni; ++I) {
+      std::vector<int>& t = infl[J * V + I];
+      for (int j = std::max(0, J - 3); j <= std::min(nj - 1, J + 2); ++j)
+        for (int i = std::max(0, I - 3); i <= std::min(ni - 1, I + 2); ++i) {
+          t.push_back(j * ni + i);
+          if (j <= 2 && on_cut(i))  // cells on the other side of the cut see this cell through ghosts
+            for (int jj = 0; jj <= std::min(2, nj - 1); ++jj)
+              for (int d = -2; d <= 2; ++d) {
+                const int m = ni - 1 - i + d;
+                if (m >= 0 && m < ni) t.push_back(jj * ni + m);
+              }
+        }
+      if (J <= 3)
+        for (int i = std::max(0, I - 3); i <= std::min(ni - 1, I + 2); ++i)
+          if (!on_cut(i)) t.push_back(n + i);  // wall faces
+      std::sort(t.begin(), t.end());
+      t.erase(std::unique(t.begin(), t.end()), t.end());
+    }
+  // greedy colouring: no target reached by two vertices of one colour
+  std::vector<std::vector<int>> reached_by(n + ni);
+  std::vector<int> col(nv, -1);
+  int ncol = 0;
+  std::vector<char> used;
+  for (int v = 0; v < nv; ++v) {
+    used.assign(ncol + 1, 0);
+    for (int t : infl[v])
+      for (int u : reached_by[t]) used[col[u]] = 1;
+    int c = 0;
+    while (c < ncol && used[c]) ++c;
+    col[v] = c;
+    if (c == ncol) ++ncol;
+    for (int t : infl[v]) reached_by[t].push_back(v);
+  }
+  std::vector<int> ptr(nv + 1, 0), idx;
+  for (int v = 0; v < nv; ++v) {
+    idx.insert(idx.end(), infl[v].begin(), infl[v].end());
+    ptr[v + 1] = (int)idx.size();
+  }
+  int r;
+  if ((r = adj_alloc(allocs, &A.vcol, (size_t)nv)) || (r = adj_alloc(allocs, &A.vinfl_ptr, ptr.size())) ||
+      (r = adj_alloc(allocs, &A.vinfl, idx.size())) || (r = adj_alloc(allocs, &A.vx, 2 * (size_t)nv)) ||
+      (r = adj_alloc(allocs, &A.vlen, (size_t)nv)))
+    return r;
+  cudaMemcpyAsync(A.vcol, col.data(), nv * sizeof(int), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(A.vinfl_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(A.vinfl, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  A.nvcolours = ncol;
+  return cudaStreamSynchronize(st) == cudaSuccess ? FASW_OK : FASW_ERR_CUDA;  // host vectors die here
+}
+
+void adj_vertex_lengths(const AdjointDev& A, const double* x0, const double* y0, cudaStream_t st) {
+  const int nv = (A.ni + 1) * (A.nj + 1);
+  launch_pdl(k_vertex_lengths, (nv + 127) / 128, 128, 0, st, A.ni, A.nj, x0, y0, A.vlen);
+}
+
+void adj_vertex_perturb(const AdjointDev& A, int k, int dir, double h, const double* x0, const double* y0,
+                        double* xo, double* yo, cudaStream_t st) {
+  const int nv = (A.ni + 1) * (A.nj + 1);
+  launch_pdl(k_vertex_perturb, (nv + 127) / 128, 128, 0, st, nv, (const int*)A.vcol, k, dir, h,
+             (const double*)A.vlen, x0, y0, xo, yo);
+}
+
+void adj_vertex_accumulate(const AdjointDev& A, int k, int which, double sa, double ca, const double* lam,
+                           const double* Fp, const double* Fm, const double* fw, double h_rel, double* g,
+                           cudaStream_t st) {
+  const int nv = (A.ni + 1) * (A.nj + 1);
+  launch_pdl(k_vertex_accum, (nv + 127) / 128, 128, 0, st, nv, A.n, A.ni, (const int*)A.vcol, k,
+             (const int*)A.vinfl_ptr, (const int*)A.vinfl, which, sa, ca, lam, Fp, Fm, fw, h_rel,
+             (const double*)A.vlen, g);
+}
+
 int adj_mg_setup(AdjointDev& A, const std::vector<LevelDev>& lev, int gamma, int nu1, std::vector<void*>& allocs,
                  cudaStream_t st) {
   const int L = (int)lev.size() - 1;

@@ -93,6 +93,7 @@ def library():
             "fasw_adjoint_precond_apply": (i, [p, d, i, dp, dp, i]),
             "fasw_adjoint_set_precond_steps": (i, [p, i]),
             "fasw_adjoint_set_precond": (i, [p, i]),
+            "fasw_adjoint_vertex_gradient": (i, [p, i, dp, d, dp, dp, i]),
             "fasw_adjoint_cycle_apply": (i, [p, d, i, i, dp, dp, i]),
             "fasw_adjoint_shape_gradient": (i, [p, i, dp, i, dp, d, dp, i]),
             "fasw_checkpoint_schedule": (i, [i, i, dp, dp, i, C.POINTER(i), C.POINTER(ll)]),
@@ -372,6 +373,18 @@ class Solver:
         if code not in (0, -6):
             _check(code, "fasw_adjoint_solve")
         return lam, code, it.value, rr.value
+
+    def adjoint_vertex_gradient(self, which, lam, h_x=1e-6):
+        """(gx, gy), each (nj+1, ni+1): dJ/dX - lam^T dF/dX for every vertex coordinate, the
+        transposed product (dF/dX)^T lam with the objective's explicit part; h_x is the difference
+        step relative to the shortest grid edge at each vertex."""
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        ni, nj, _ = self.dims(self.finest)
+        gx = np.zeros((nj + 1, ni + 1))
+        gy = np.zeros((nj + 1, ni + 1))
+        _check(self.lib.fasw_adjoint_vertex_gradient(self.h, which, lam.ctypes.data, h_x, gx.ctypes.data,
+                                                     gy.ctypes.data, 0), "fasw_adjoint_vertex_gradient")
+        return gx, gy
 
     def adjoint_shape_gradient(self, which, lam, fields, h_x=1e-6):
         """grad[k] = dJ/dX V_k - lam^T dF/dX V_k for y-displacement fields (nparam, nj+1, ni+1)."""

@@ -163,6 +163,36 @@ def test_mixed_precision_adjoint_solves_the_same_system(case):
     assert rel_err(out[1], out[0]) < 1e-6
 
 
+@pytest.mark.parametrize("viscous", [0, 1])
+def test_vertex_gradient_is_the_transposed_grid_derivative(viscous):
+    """(dF/dX)^T lam with the objective's part, for every vertex, contracted with a displacement
+    field in x and y, equals central differences of the oracle's residual and wall force over
+    the displaced grids (any lam: the identity is linear)."""
+    from synth.cgrid import CGrid
+    g = make_cgrid(64, 16, wall_spacing=5e-3, jitter=0.02, seed=3)
+    o, s = make_pair(g, nlevels=1, mach=0.6, alpha_deg=ALPHA, viscous=viscous, turb=0, re=5e3)
+    u = perturbed_state(0.6, ALPHA, 16, 64, amp=0.03, seed=5)
+    o.set_state(u); s.set_state(u)
+    lam = np.random.default_rng(17).standard_normal((4, 16, 64))
+    gx, gy = s.adjoint_vertex_gradient(1, lam)
+    V = bump_fields(g, 4)
+    DX, DY = V[0] - 0.5 * V[3], V[1] + 0.3 * V[2]
+    pred = float(np.sum(gx * DX) + np.sum(gy * DY))
+    h = 1e-6
+    vals = []
+    for sgn in (1.0, -1.0):
+        gs = CGrid(g.ni, g.nj, g.n_wake, g.x + sgn * h * DX, g.y + sgn * h * DY, dict(g.meta))
+        os_ = O.Oracle(gs, o.params)
+        os_.set_state(u)
+        vals.append((os_.residual()[0].ravel(), A.force_coefficients(*os_.wall_force(), ALPHA)[1]))
+    fd = (vals[0][1] - vals[1][1]) / (2 * h) - lam.ravel() @ (vals[0][0] - vals[1][0]) / (2 * h)
+    assert abs(pred - fd) <= 1e-6 * abs(fd), (pred, fd)
+    # the same contraction of the y part is the library's per-field shape gradient
+    ref = s.adjoint_shape_gradient(1, lam, V)
+    via = np.array([np.sum(gy * V[k]) for k in range(4)])
+    assert rel_err(via, ref) < 1e-6
+
+
 def test_adjoint_gradient_matches_differences_of_gpu_solves():
     import paper_1710_04875_gb300 as P
     g = make_cgrid(64, 16)
