@@ -41,7 +41,7 @@ struct AdjointDev {
   double* fw = nullptr;    // 4 * ni wall forces fx+, fy+, fx-, fy-
   double* parts = nullptr; // reduction partials
   double* h_parts = nullptr;  // pinned host copy of the reduced values
-  double* kry = nullptr;   // (2 restart + 5) * 4n: Krylov basis V, preconditioned basis Z, work vectors
+  double* kry = nullptr;   // (2 restart + 7) * 4n: Krylov basis V, preconditioned basis Z, work vectors
   int restart = 0;
   bool built = false;      // Jacobian assembled at the current state
   LevelDev Lp{};           // level whose transfer blocks hold the preconditioner

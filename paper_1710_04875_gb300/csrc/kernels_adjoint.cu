@@ -1094,18 +1094,10 @@ int adj_solve(AdjointDev& A, const std::vector<LevelDev>& lev, const PhysParams&
   adj_build_precond(A, lev.back(), ph, sc, cfl, st, launches);
   const bool cycle = (A.precond_kind == ADJ_FAS_CYCLE_T || A.precond_kind == ADJ_FAS_VCYCLE_T) && A.mg;
   if (cycle) adj_mg_build_precond(A, lev, ph, sc, cfl, st, launches);
-  auto apply_m = [&](const double* rr, double* zz) {  // zz = M^-1 rr
-    if (cycle)
-      mg_cycle(A, A.mg->L, 1, rr, zz, st);
-    else if (A.precond_kind != ADJ_STAGE_LOOP)
-      smooth_steps(A, A.smooth_steps, 1, rr, zz, st);
-    else
-      steps_apply(A, A.smooth_steps, rr, zz, st);
-  };
   const int m = 4 * A.n;
   if (restart < 1 || restart > MAXV - 5) return FASW_ERR_ARG;
   if (A.restart < restart) {
-    int r = adj_alloc(allocs, &A.kry, (size_t)(2 * restart + 5) * m);
+    int r = adj_alloc(allocs, &A.kry, (size_t)(2 * restart + 7) * m);
     if (r) return r;
     A.restart = restart;
   }
@@ -1114,6 +1106,44 @@ int adj_solve(AdjointDev& A, const std::vector<LevelDev>& lev, const PhysParams&
   double* Z = A.kry + (size_t)(A.restart + 1) * ld;   // restart preconditioned vectors
   double* w = Z + (size_t)A.restart * ld;             // work
   double* res = w + ld;
+  double* gin = res + ld;                             // input and output of the captured cycle
+  double* gout = gin + ld;
+  // The transposed cycle is the same launch sequence every iteration: captured once into a CUDA
+  // graph that reads gin and writes gout (not on the legacy default stream, where capture is not
+  // possible; an eager cycle first, so that one-time kernel attributes are set outside capture).
+  cudaGraphExec_t gexec = nullptr;
+  if (cycle && st != nullptr) {
+    cudaMemsetAsync(gin, 0, ld * sizeof(double), st);
+    mg_cycle(A, A.mg->L, 1, gin, gout, st);
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      mg_cycle(A, A.mg->L, 1, gin, gout, st);
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamEndCapture(st, &graph) == cudaSuccess && graph) {
+        if (cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) gexec = nullptr;
+        cudaGraphDestroy(graph);
+      }
+    }
+    cudaGetLastError();  // a failed capture leaves the eager path
+  }
+  struct GraphGuard {
+    cudaGraphExec_t& g;
+    ~GraphGuard() {
+      if (g) cudaGraphExecDestroy(g);
+    }
+  } guard{gexec};
+  auto apply_m = [&](const double* rr, double* zz) {  // zz = M^-1 rr
+    if (gexec) {
+      cudaMemcpyAsync(gin, rr, ld * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      cudaGraphLaunch(gexec, st);
+      cudaMemcpyAsync(zz, gout, ld * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    } else if (cycle) {
+      mg_cycle(A, A.mg->L, 1, rr, zz, st);
+    } else if (A.precond_kind != ADJ_STAGE_LOOP) {
+      smooth_steps(A, A.smooth_steps, 1, rr, zz, st);
+    } else {
+      steps_apply(A, A.smooth_steps, rr, zz, st);
+    }
+  };
   const int nb = (m + 255) / 256;
   cudaMemsetAsync(lam, 0, m * sizeof(double), st);
   cudaMemcpyAsync(res, g, m * sizeof(double), cudaMemcpyDeviceToDevice, st);
