@@ -266,7 +266,7 @@ def measure_adjoint(s, g, n_bumps=16):
                     "preconditioned by the transposed linearised W-cycle"}
 
 
-def measure_c5(P, n_bumps=16):
+def measure_c5(P, stream=None, n_bumps=16):
     """The 1024x256 RANS sensitivity case (wall spacing 1e-5, M 0.75, Re 6.5e6, alpha 0, 5-level
     W-cycles of AW3, mixed precision): time to a 6-order drop from the free stream, then the
     C_D adjoint (eddy viscosity frozen) to a 6-order drop and the shape gradient for 16
@@ -276,7 +276,7 @@ def measure_c5(P, n_bumps=16):
     p = P.default_params(scheme="AW3", nlevels=5, gamma_cycle=2, viscous=1, turb=1, sensor=1, mach=0.75,
                          alpha_deg=0.0, re=6.5e6, eta=0.8, d_cut=0.5, cfl=100.0, cfl_ramp=20.0, ramp_cycles=2,
                          precision="mixed")
-    s = P.Solver(g, p)
+    s = P.Solver(g, p, stream=stream.cuda_stream if stream is not None else None)
     t0 = time.perf_counter()
     code, nc, hist = s.solve(1e-6, 3000)
     t_primal = time.perf_counter() - t0
@@ -296,8 +296,17 @@ def measure_c5(P, n_bumps=16):
                adjoint_s=time.perf_counter() - t0)
     t0 = time.perf_counter()
     grad = s.adjoint_shape_gradient(1, lam, V)
-    out.update(shape_gradient_s=time.perf_counter() - t0, n_params=n_bumps, cd=s.force_coefficients()[1],
-               grad=[float(x) for x in grad])
+    t_grad = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gx, gy = s.adjoint_vertex_gradient(1, lam)
+    t_vert = time.perf_counter() - t0
+    via = np.array([np.sum(gy * V[k]) for k in range(n_bumps)])
+    half = n_bumps // 2
+    out.update(shape_gradient_s=t_grad, vertex_gradient_s=t_vert, n_params=n_bumps, cd=s.force_coefficients()[1],
+               grad=[float(x) for x in grad],
+               vertex_vs_shape_gradient=float(np.abs(via - grad).max() / max(np.abs(grad).max(), 1e-300)),
+               upper_lower_antisymmetry=float(np.abs(grad[:half] + grad[half:2 * half]).max()
+                                              / max(np.abs(grad).max(), 1e-300)))
     s.close()
     return out
 
@@ -578,6 +587,7 @@ def main():
                              "density residual at the stop of each precision"}
     batched = None if args.no_batched else measure_batched(P, stream, flush, args.steps, args.warmup)
     unsteady_adjoint = None if (args.no_adjoint or args.no_unsteady_adjoint) else measure_unsteady_adjoint(P, stream)
+    c5 = None if args.no_adjoint else measure_c5(P, stream)
 
     if rank != 0:
         if dist:
@@ -626,7 +636,7 @@ def main():
                                 "value": other_value, "ms_per_step": sum(ms_other) / args.steps},
             "time_to_6_orders": drops, "time_to_11_orders_per_time_step": unsteady, "precision_gap": precision_gap,
             "batched_64_cases": batched, "c3_512x128": c3, "adjoint": adjoint,
-            "unsteady_adjoint": unsteady_adjoint, "kernel_share": share,
+            "unsteady_adjoint": unsteady_adjoint, "c5_1024x256": c5, "kernel_share": share,
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes + 8},
             "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "cpu_baseline": cpu}
