@@ -75,8 +75,26 @@ def test_laminar_unsteady_adjoint_matches_the_oracle():
     s.close()
 
 
+def test_implicit_euler_unsteady_adjoint_matches_the_oracle(euler_case):
+    """bdf_order 1: implicit Euler on every level (no second history term in the adjoint)."""
+    import paper_1710_04875_gb300 as P
+    g, po, pg, u0, V = euler_case
+    N = 3
+    po1 = O.make_params("AW3", nlevels=2, mach=0.6, alpha_deg=0.0, cfl=1e4, bdf_order=1)
+    Jo, go, g0o, _ = U.gradient(g, po1, u0, V, AMP, OMEGA, XC, YC, DT, N, DROP, CYCLES, 1)
+    s = P.Solver(g, pg)
+    s.set_state(u0)
+    Jg, gg, g0g, code, st = s.unsteady_adjoint(AMP, OMEGA, DT, N, V, which=1, xc=XC, yc=YC, bdf_order=1,
+                                               drop=DROP, max_cycles=CYCLES, tol=1e-11, max_iters=400, restart=60)
+    assert code == 0, st
+    assert abs(Jg - Jo) <= 1e-9 * abs(Jo)
+    assert rel_err(gg, go) < 1e-6
+    assert rel_err(g0g, g0o) < 1e-6
+    s.close()
+
+
 def test_checkpointed_reverse_sweep_is_bit_identical(euler_case):
-    """Binomial checkpointing with one and with two stored levels recomputes states exactly
+    """Binomial checkpointing with no, one and two stored levels recomputes states exactly
     (deterministic kernels), so the adjoint equals the store-every-level run bit for bit; the
     recomputed step count is the binomial optimum."""
     import paper_1710_04875_gb300 as P
@@ -86,7 +104,7 @@ def test_checkpointed_reverse_sweep_is_bit_identical(euler_case):
     s.set_state(u0)
     kw = dict(which=0, xc=XC, yc=YC, drop=1e-10, max_cycles=CYCLES, tol=1e-10, max_iters=400, restart=60)
     ref = s.unsteady_adjoint(AMP, OMEGA, DT, N, V, **kw)
-    for snaps in (1, 2):
+    for snaps in (0, 1, 2):
         out = s.unsteady_adjoint(AMP, OMEGA, DT, N, V, snapshots=snaps, **kw)
         assert out[0] == ref[0]
         assert np.array_equal(out[1], ref[1])
