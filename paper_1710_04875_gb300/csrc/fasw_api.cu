@@ -1,28 +1,30 @@
 // C ABI and host-side driver: level allocation, the AW / ARK stage loop (sections 4.1-4.2
-// of arXiv 1710.04875), the FAS V/W cycle (section 3) and the steady solve loop.
-// Every arithmetic step runs in the kernels of the other translation units.
+// of arXiv 1710.04875), the FAS V/W cycle (section 3), the steady solve loop and dual time
+// stepping (section 6).  Every arithmetic step runs in the kernels of the other translation
+// units; the adjoint entry points are in fasw_adjoint_api.cu, batches in fasw_batch.cu.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
 #include <algorithm>
-#include <map>
-#include <mutex>
 #include <vector>
 
-#include "../../include/fasw.h"
-#include "fasw_internal.cuh"
-#include "fasw_sweep.cuh"
-#include "fasw_adjoint.cuh"
+#include "fasw_ctx.cuh"
 #include "fasw_transfer.cuh"
-#include "fasw_checkpoint.cuh"
 
 using namespace fasw;
 
-namespace {
-
+namespace fasw {
 thread_local std::string g_last_cuda_error;
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda_error = cudaGetErrorString(e);
+  return FASW_ERR_CUDA;
+}
+}  // namespace fasw
+
+namespace {
 
 // Table "RK smoothers" (section 4.1); the W methods use the same coefficients, the
 // 5-stage ARK51/ARK52 alphas take the ARK5J betas, and the ARK5J beta row is read as
@@ -35,59 +37,9 @@ const Coef kCoef[4] = {
     {5, {0.0695, 0.1602, 0.2898, 0.5060, 1.0}, {1.0, 0.0, 0.56, 0.0, 0.44}},
 };
 
-int cuda_fail(cudaError_t e) {
-  g_last_cuda_error = cudaGetErrorString(e);
-  return FASW_ERR_CUDA;
-}
-
-#define CKR(expr)                             \
-  do {                                        \
-    cudaError_t e_ = (expr);                  \
-    if (e_ != cudaSuccess) return cuda_fail(e_); \
-  } while (0)
-
 }  // namespace
 
-struct fasw_ctx {
-  fasw_params prm{};
-  PhysParams ph{};
-  SchemeParams sc{};
-  std::vector<LevelDev> lev;
-  std::vector<void*> allocs;
-  cudaStream_t st = nullptr;
-  int mixed = 0;
-  double* d_norm = nullptr;
-  double* h_norm = nullptr;    // pinned
-  double* d_tmp = nullptr;     // 4 * n_finest scratch for host copies
-  double* d_tmp2 = nullptr;
-  double* d_tmp3 = nullptr;
-  long long launches = 0;
-  // optional per-kernel-class timing with CUDA events on the context's stream
-  int profiling = 0;
-  struct Pending { int id; cudaEvent_t a, b; };
-  std::vector<Pending> pending;
-  std::vector<cudaEvent_t> event_pool;
-  long long prof_count[FASW_NKERNELS] = {};
-  double prof_ms[FASW_NKERNELS] = {};
-  // captured FAS cycles, one per pseudo CFL value (ramp and full)
-  struct CycleGraph { double cfl; cudaGraphExec_t exec; long long kernels; };
-  std::vector<CycleGraph> graphs;
-  int use_graphs = 1;
-  int sweep_kind = SWEEP_AUTO;
-  long long spin_limit = 1LL << 22;
-  long long* d_prog = nullptr;  // strip progress flags
-  int* d_err = nullptr;         // device error word (bounded waits)
-  int* h_err = nullptr;         // pinned copy
-  double* d_x0 = nullptr;       // reference vertices (the grid at rest)
-  double* d_y0 = nullptr;
-  double* d_un = nullptr;       // dual-time history of the finest level (4 x n)
-  double* d_unm1 = nullptr;
-  int steps_done = 0;
-  AdjointDev adj;               // discrete adjoint of the steady finest level (built on demand)
-  int L() const { return (int)lev.size() - 1; }
-};
-
-namespace {
+namespace fasw {
 
 template <typename T>
 int dalloc(fasw_ctx* c, T** p, size_t count) {
@@ -323,7 +275,50 @@ int sync(fasw_ctx* c) {
   return FASW_OK;
 }
 
-}  // namespace
+
+void enqueue_cycle(fasw_ctx* c, double cfl) {
+  const int Lf = c->L();
+  if (c->prm.turb) {
+    bc_aux(c, Lf, cfl, 0);
+    { Prof p(c, FASW_K_BL); launch_bl(c->lev[Lf], c->ph, c->st); }
+    c->launches += 2;
+  }
+  fas_cycle_rec(c, Lf, cfl, true);
+  cudaMemcpyAsync(c->h_norm, c->d_norm, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+}
+
+// The launch sequence of a cycle depends only on c*, so each distinct c* is captured once
+// into a CUDA graph and replayed (no per-kernel launch overhead).  Not used while profiling
+// or on the legacy default stream, where capture is not possible.
+int run_cycle(fasw_ctx* c, double cfl) {
+  if (!c->use_graphs || c->profiling || c->st == nullptr) {
+    enqueue_cycle(c, cfl);
+    return FASW_OK;
+  }
+  for (auto& g : c->graphs)
+    if (g.cfl == cfl) {
+      CKR(cudaGraphLaunch(g.exec, c->st));
+      c->launches += g.kernels;
+      return FASW_OK;
+    }
+  const long long before = c->launches;
+  CKR(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+  enqueue_cycle(c, cfl);
+  cudaGraph_t graph = nullptr;
+  CKR(cudaStreamEndCapture(c->st, &graph));
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const long long k = c->launches - before;
+  c->graphs.push_back({cfl, exec, k});
+  CKR(cudaGraphLaunch(exec, c->st));
+  return FASW_OK;
+}
+
+}  // namespace fasw
+
 
 extern "C" {
 
@@ -613,47 +608,6 @@ int fasw_smooth(fasw_ctx* c, int l, int nsteps, double cfl) {
   return sync(c);
 }
 
-static void enqueue_cycle(fasw_ctx* c, double cfl) {
-  const int Lf = c->L();
-  if (c->prm.turb) {
-    bc_aux(c, Lf, cfl, 0);
-    { Prof p(c, FASW_K_BL); launch_bl(c->lev[Lf], c->ph, c->st); }
-    c->launches += 2;
-  }
-  fas_cycle_rec(c, Lf, cfl, true);
-  cudaMemcpyAsync(c->h_norm, c->d_norm, sizeof(double), cudaMemcpyDeviceToHost, c->st);
-  cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
-}
-
-// The launch sequence of a cycle depends only on c*, so each distinct c* is captured once
-// into a CUDA graph and replayed (no per-kernel launch overhead).  Not used while profiling
-// or on the legacy default stream, where capture is not possible.
-static int run_cycle(fasw_ctx* c, double cfl) {
-  if (!c->use_graphs || c->profiling || c->st == nullptr) {
-    enqueue_cycle(c, cfl);
-    return FASW_OK;
-  }
-  for (auto& g : c->graphs)
-    if (g.cfl == cfl) {
-      CKR(cudaGraphLaunch(g.exec, c->st));
-      c->launches += g.kernels;
-      return FASW_OK;
-    }
-  const long long before = c->launches;
-  CKR(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-  enqueue_cycle(c, cfl);
-  cudaGraph_t graph = nullptr;
-  CKR(cudaStreamEndCapture(c->st, &graph));
-  cudaGraphExec_t exec = nullptr;
-  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return cuda_fail(e);
-  const long long k = c->launches - before;
-  c->graphs.push_back({cfl, exec, k});
-  CKR(cudaGraphLaunch(exec, c->st));
-  return FASW_OK;
-}
-
 int fasw_fas_cycle(fasw_ctx* c, int cycle_index, double* res_norm) {
   if (!c) return FASW_ERR_ARG;
   const double cfl = cycle_index < c->prm.ramp_cycles ? std::fmin(c->prm.cfl, c->prm.cfl_ramp) : c->prm.cfl;
@@ -664,471 +618,6 @@ int fasw_fas_cycle(fasw_ctx* c, int cycle_index, double* res_norm) {
   if (*c->h_err) return FASW_ERR_DEVICE_TIMEOUT;
   if (res_norm) *res_norm = *c->h_norm;
   return FASW_OK;
-}
-
-// ---- discrete adjoint (steady finest level, eddy viscosity frozen)
-static int adj_ready(fasw_ctx* c) {
-  if (c->adj.n) return FASW_OK;
-  const LevelDev& F = c->lev[c->L()];
-  c->adj.fp32 = c->mixed != 0;
-  c->adj.prog = c->d_prog;
-  c->adj.err = c->d_err;
-  c->adj.spin_limit = c->spin_limit;
-  return adj_setup(c->adj, F.ni, F.nj, F.nw, c->allocs, c->st);
-}
-
-// The finest level's Jacobian and, for the transposed FAS cycle, those of the coarse levels at
-// the restricted state.
-static int adj_assemble_all(fasw_ctx* c, double h_rel) {
-  int r = adj_assemble(c->adj, c->lev[c->L()], c->ph, h_rel, c->st, c->launches);
-  if (r) return r;
-  const int kind = c->adj.precond_kind;
-  if ((kind == ADJ_FAS_CYCLE_T || kind == ADJ_FAS_VCYCLE_T) && c->L() > 0) {
-    const int gamma = kind == ADJ_FAS_VCYCLE_T ? 1 : c->prm.gamma_cycle;
-    if ((r = adj_mg_setup(c->adj, c->lev, gamma, c->prm.nu1, c->allocs, c->st))) return r;
-    if ((r = adj_mg_assemble(c->adj, c->lev, c->ph, c->prm.turb, h_rel, c->st, c->launches))) return r;
-  }
-  return FASW_OK;
-}
-
-// FASW_ERR_DEVICE_TIMEOUT when a bounded wait of the sweeps ran out (device error word set).
-static int adj_err_check(fasw_ctx* c) {
-  CKR(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-  CKR(cudaStreamSynchronize(c->st));
-  return *c->h_err ? FASW_ERR_DEVICE_TIMEOUT : FASW_OK;
-}
-
-int fasw_force_coefficients(fasw_ctx* c, double* cl, double* cd) {
-  if (!c || !cl || !cd) return FASW_ERR_ARG;
-  int r = adj_ready(c);
-  if (r) return r;
-  return adj_force_coefficients(c->adj, c->lev[c->L()], c->ph, c->st, cl, cd, c->launches);
-}
-
-int fasw_adjoint_jacobian(fasw_ctx* c, double h_rel) {
-  if (!c || !(h_rel > 0.0) || c->ph.moving || c->lev[c->L()].a_t != 0.0) return FASW_ERR_ARG;
-  int r = adj_ready(c);
-  if (r) return r;
-  r = adj_assemble_all(c, h_rel);
-  if (r) return r;
-  return sync(c);
-}
-
-int fasw_adjoint_apply(fasw_ctx* c, const double* v, double* out, int transpose, int on_device) {
-  if (!c || !v || !out || !c->adj.built) return FASW_ERR_ARG;
-  const size_t m = 4 * (size_t)c->adj.n;
-  int r = copy_in(c, c->d_tmp, v, m, on_device);
-  if (r) return r;
-  adj_apply(c->adj, c->d_tmp, c->d_tmp2, transpose, c->st);
-  ++c->launches;
-  r = copy_out(c, out, c->d_tmp2, m, on_device);
-  if (r) return r;
-  return sync(c);
-}
-
-int fasw_adjoint_objective_gradient(fasw_ctx* c, int which, double* g, int on_device) {
-  if (!c || !g || which < 0 || which > 1 || !c->adj.built) return FASW_ERR_ARG;
-  const size_t m = 4 * (size_t)c->adj.n;
-  int r = copy_out(c, g, c->adj.g + which * m, m, on_device);
-  if (r) return r;
-  return sync(c);
-}
-
-int fasw_adjoint_precond_apply(fasw_ctx* c, double cfl, int steps, const double* r, double* z, int on_device) {
-  if (!c || !r || !z || !(cfl > 0.0) || steps < 0 || c->ph.moving) return FASW_ERR_ARG;
-  if (steps > 0 && !c->adj.built) return FASW_ERR_ARG;
-  int e = adj_ready(c);
-  if (e) return e;
-  const size_t m = 4 * (size_t)c->adj.n;
-  if ((e = copy_in(c, c->d_tmp, r, m, on_device))) return e;
-  adj_build_precond(c->adj, c->lev[c->L()], c->ph, c->sc, cfl, c->st, c->launches);
-  adj_steps_apply(c->adj, steps, c->d_tmp, c->d_tmp2, c->st);
-  c->launches += 2;
-  if ((e = adj_err_check(c))) return e;
-  if ((e = copy_out(c, z, c->d_tmp2, m, on_device))) return e;
-  return sync(c);
-}
-
-int fasw_adjoint_set_precond_steps(fasw_ctx* c, int steps) {
-  if (!c || steps < 1 || steps > 16) return FASW_ERR_ARG;
-  c->adj.smooth_steps = steps;
-  return FASW_OK;
-}
-
-int fasw_adjoint_set_precond(fasw_ctx* c, int kind) {
-  if (!c || kind < ADJ_STAGE_LOOP || kind > ADJ_FAS_VCYCLE_T) return FASW_ERR_ARG;
-  if (kind != c->adj.precond_kind) c->adj.built = false;  // the cycle needs the coarse Jacobians
-  c->adj.precond_kind = kind;
-  return FASW_OK;
-}
-
-int fasw_adjoint_cycle_apply(fasw_ctx* c, double cfl, int kind, int transpose, const double* r, double* z,
-                             int on_device) {
-  if (!c || !r || !z || !(cfl > 0.0) || (kind != 1 && kind != 2) || !c->adj.built) return FASW_ERR_ARG;
-  if (kind == 2 && c->L() > 0 && !c->adj.mg) return FASW_ERR_ARG;
-  const size_t m = 4 * (size_t)c->adj.n;
-  int e = copy_in(c, c->d_tmp, r, m, on_device);
-  if (e) return e;
-  adj_build_precond(c->adj, c->lev[c->L()], c->ph, c->sc, cfl, c->st, c->launches);
-  if (kind == 2) {
-    adj_mg_build_precond(c->adj, c->lev, c->ph, c->sc, cfl, c->st, c->launches);
-    adj_mg_apply(c->adj, transpose, c->d_tmp, c->d_tmp2, c->st);
-  } else {
-    adj_smoother_apply(c->adj, c->adj.smooth_steps, transpose, c->d_tmp, c->d_tmp2, c->st);
-  }
-  ++c->launches;
-  if ((e = adj_err_check(c))) return e;
-  if ((e = copy_out(c, z, c->d_tmp2, m, on_device))) return e;
-  return sync(c);
-}
-
-int fasw_adjoint_solve(fasw_ctx* c, int which, const double* g, double* lam, double tol, int max_iters, int restart,
-                       double cfl, int* iters, double* rel_res, int on_device) {
-  if (!c || !lam || !iters || !rel_res || !c->adj.built || !(tol > 0.0) || max_iters < 1) return FASW_ERR_ARG;
-  if (!g && (which < 0 || which > 1)) return FASW_ERR_ARG;
-  const size_t m = 4 * (size_t)c->adj.n;
-  const double* rhs = c->adj.g + (which < 0 ? 0 : which) * m;
-  if (g) {
-    int r = copy_in(c, c->d_tmp, g, m, on_device);
-    if (r) return r;
-    rhs = c->d_tmp;
-  }
-  const double pcfl = cfl > 0.0 ? cfl : c->prm.cfl;
-  const int code = adj_solve(c->adj, c->lev, c->ph, c->sc, pcfl, rhs, c->d_tmp2, tol, max_iters, restart,
-                             c->allocs, c->st, iters, rel_res, c->launches);
-  if (code != FASW_OK && code != FASW_ERR_NOT_CONVERGED) return code;
-  int r = adj_err_check(c);
-  if (r) return r;
-  r = copy_out(c, lam, c->d_tmp2, m, on_device);
-  if (r) return r;
-  r = sync(c);
-  return r ? r : code;
-}
-
-}  // extern "C"
-
-namespace {
-
-// For one vertex field vk (device, (nj+1) x (ni+1) y-displacements of the grid at rest):
-// *dC = C(X + h vk) - C(X - h vk) of objective `which` and *dot = lam . (F(X + h vk) - F(X - h vk))
-// at the current state, the grid rotated by (phi, phidot) about (xc, yc) when rotate != 0.
-// F leaves out the time term (it does not depend on X).  The caller restores the metrics.
-int shape_term(fasw_ctx* c, int which, const double* d_lam, const double* vk, double h_x, int rotate, double phi,
-               double phidot, double xc, double yc, double* dC, double* dot) {
-  LevelDev F = c->lev[c->L()];
-  F.a_t = 0.0;
-  const size_t m = 4 * (size_t)F.n, nv = (size_t)(F.ni + 1) * (F.nj + 1);
-  double* ytmp = c->d_tmp3;
-  ResArgs a{};
-  a.mode = RES_FULL;
-  double cl[2], cd[2];
-  for (int sgn = 0; sgn < 2; ++sgn) {
-    adj_lincomb((int)nv, c->d_y0, sgn == 0 ? h_x : -h_x, vk, ytmp, c->st);
-    launch_metrics_fine(F, c->d_x0, ytmp, c->st, rotate, phi, phidot, xc, yc);
-    launch_bc_aux(F, c->ph, 1.0, 0, c->st);
-    a.F = sgn == 0 ? c->adj.Fp : c->adj.Fm;
-    launch_residual(F, c->ph, a, c->st);
-    c->launches += 4;
-    int r = adj_force_coefficients(c->adj, F, c->ph, c->st, &cl[sgn], &cd[sgn], c->launches);
-    if (r) return r;
-  }
-  adj_lincomb((int)m, c->adj.Fp, -1.0, c->adj.Fm, c->d_tmp2, c->st);  // F+ - F-
-  *dC = which == 0 ? cl[0] - cl[1] : cd[0] - cd[1];
-  return adj_dot(c->adj, d_lam, c->d_tmp2, (int)m, c->st, dot);
-}
-
-}  // namespace
-
-extern "C" {
-
-int fasw_adjoint_shape_gradient(fasw_ctx* c, int which, const double* lam, int nparam, const double* vy, double h_x,
-                                double* grad, int on_device) {
-  if (!c || !lam || !vy || !grad || nparam < 1 || which < 0 || which > 1 || !(h_x > 0.0) || c->ph.moving)
-    return FASW_ERR_ARG;
-  int r = adj_ready(c);
-  if (r) return r;
-  LevelDev& F = c->lev[c->L()];
-  const size_t m = 4 * (size_t)F.n, nv = (size_t)(F.ni + 1) * (F.nj + 1);
-  if ((r = copy_in(c, c->d_tmp, lam, m, on_device))) return r;
-  double* vk = c->d_tmp3 + nv;
-  for (int k = 0; k < nparam; ++k) {
-    if ((r = copy_in(c, vk, vy + (size_t)k * nv, nv, on_device))) return r;
-    double dJ = 0.0, dot = 0.0;
-    if ((r = shape_term(c, which, c->d_tmp, vk, h_x, 0, 0.0, 0.0, 0.0, 0.0, &dJ, &dot))) return r;
-    grad[k] = (dJ - dot) / (2.0 * h_x);
-  }
-  launch_metrics_fine(F, c->d_x0, c->d_y0, c->st);
-  launch_bc_aux(F, c->ph, 1.0, 0, c->st);
-  c->launches += 2;
-  return sync(c);
-}
-
-}  // extern "C"
-
-namespace {
-
-// (a_n, b_n, c_n) of F^n = R/vol + a_n u^n + b_n u^(n-1) + c_n u^(n-2): implicit Euler for
-// the first step, BDF2 after (section 6), as fasw_dual_time_step takes them.
-void time_coefficients(int n, double dt, int bdf_order, double* a, double* b, double* cc) {
-  if (n <= 1 || bdf_order == 1) {
-    *a = 1.0 / dt, *b = -1.0 / dt, *cc = 0.0;
-  } else {
-    *a = 1.5 / dt, *b = -2.0 / dt, *cc = 0.5 / dt;
-  }
-}
-
-// Device buffers of one unsteady adjoint run, freed on every return.
-struct RunBuffers {
-  std::vector<void*> mem;
-  ~RunBuffers() {
-    for (void* p : mem) cudaFree(p);
-  }
-  int get(double** p, size_t count) {
-    void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, (count ? count : 1) * sizeof(double));
-    if (e != cudaSuccess) {
-      g_last_cuda_error = cudaGetErrorString(e);
-      return FASW_ERR_OOM;
-    }
-    mem.push_back(q);
-    *p = static_cast<double*>(q);
-    return FASW_OK;
-  }
-};
-
-// Puts the context back to u0 on the grid at rest with no time term.
-void unsteady_reset(fasw_ctx* c, const double* u0) {
-  LevelDev& F = c->lev[c->L()];
-  if (c->ph.moving) drop_graphs(c);
-  c->ph.moving = 0;
-  const int nl = (int)c->lev.size();
-  launch_metrics_fine(F, c->d_x0, c->d_y0, c->st);
-  for (int l = nl - 2; l >= 0; --l) launch_agglomerate(c->lev[l + 1], c->lev[l], c->st);
-  if (F.a_t != 0.0) drop_graphs(c);
-  for (auto& L : c->lev) L.a_t = 0.0;
-  cudaMemsetAsync(F.src, 0, 4 * (size_t)F.n * sizeof(double), c->st);
-  if (u0) {
-    launch_pack(F, u0, 1, nullptr, c->st);
-    launch_bc(F, c->ph, c->st);
-  }
-  c->launches += nl + (u0 ? 2 : 0);
-  c->steps_done = 0;
-  c->adj.built = false;
-}
-
-}  // namespace
-
-extern "C" {
-
-int fasw_unsteady_adjoint(fasw_ctx* c, double amp, double omega, double xc, double yc, double dt, int nsteps,
-                          int bdf_order, double drop, int max_cycles, int snapshots, int which, int nparam,
-                          const double* vy, double h_rel, double h_x, double tol, int max_iters, int restart,
-                          double cfl, double* objective, double* grad, double* g0, int on_device, double* stats) {
-  if (!c || !objective || !(dt > 0.0) || nsteps < 1 || (bdf_order != 1 && bdf_order != 2) || max_cycles < 1 ||
-      snapshots < 0 || which < 0 || which > 1 || nparam < 0 || (nparam > 0 && (!vy || !grad)) || !(h_rel > 0.0) ||
-      !(h_x > 0.0) || !(tol > 0.0) || max_iters < 1 || restart < 1 || c->ph.moving || c->steps_done != 0 ||
-      c->lev[c->L()].a_t != 0.0)
-    return FASW_ERR_ARG;
-  std::vector<CkAction> plan;
-  long long fsteps = 0;
-  int r = checkpoint_schedule(nsteps, snapshots, plan, &fsteps);
-  if (r) return r;
-  if ((r = adj_ready(c))) return r;
-  if ((r = sync(c))) return r;
-  LevelDev& F = c->lev[c->L()];
-  const size_t m = 4 * (size_t)F.n, nv = (size_t)(F.ni + 1) * (F.nj + 1);
-  const int S = std::min(snapshots, nsteps - 1);
-  RunBuffers buf;
-  double *u0 = nullptr, *slots = nullptr, *lam = nullptr, *rhs = nullptr, *V = nullptr;
-  if ((r = buf.get(&u0, m)) || (r = buf.get(&slots, 2 * m * (size_t)std::max(S, 1))) || (r = buf.get(&lam, 3 * m)) ||
-      (r = buf.get(&rhs, m)) || (r = buf.get(&V, nv * (size_t)std::max(nparam, 1))))
-    return r;
-  if (nparam > 0 && (r = copy_in(c, V, vy, nv * (size_t)nparam, on_device))) return r;
-  launch_pack(F, nullptr, 0, u0, c->st);
-  cudaMemsetAsync(lam, 0, 3 * m * sizeof(double), c->st);
-  ++c->launches;
-  double* lam1 = lam;          // lam^(n+1)
-  double* lam2 = lam + m;      // lam^(n+2)
-  double* lamn = lam + 2 * m;  // lam^n
-  std::vector<int> slot_of(nsteps + 1, -1);
-  std::vector<int> free_slots;
-  for (int k = S - 1; k >= 0; --k) free_slots.push_back(k);
-  const double w = 1.0 / nsteps;
-  const double pcfl = cfl > 0.0 ? cfl : c->prm.cfl;
-  std::vector<double> gacc(nparam, 0.0);
-  double J = 0.0, worst = 0.0;
-  long long gm_iters = 0, cycles = 0;
-  int pos = 0, reached = 0;
-  bool soft = false;
-  auto motion = [&](int n) {
-    const double t = n * dt;
-    return fasw_set_motion(c, -amp * std::sin(omega * t), -amp * omega * std::cos(omega * t), xc, yc);
-  };
-  auto fail = [&](int code) {
-    unsteady_reset(c, u0);
-    sync(c);
-    return code;
-  };
-  for (const CkAction& act : plan) {
-    if (act.op == CK_ADVANCE) {
-      for (int n = pos + 1; n <= act.arg; ++n) {
-        if ((r = motion(n))) return fail(r);
-        int nc = 0;
-        r = fasw_dual_time_step(c, dt, bdf_order, drop, max_cycles, nullptr, &nc);
-        cycles += nc;
-        if (r == FASW_ERR_NOT_CONVERGED) soft = true;
-        else if (r) return fail(r);
-        if (n > reached) {  // the first sweep: the objective
-          double cl = 0.0, cd = 0.0;
-          if ((r = adj_force_coefficients(c->adj, F, c->ph, c->st, &cl, &cd, c->launches))) return fail(r);
-          J += w * (which == 0 ? cl : cd);
-          reached = n;
-        }
-      }
-      pos = act.arg;
-    } else if (act.op == CK_STORE) {
-      if (free_slots.empty() || act.arg < 1 || act.arg > nsteps) return fail(FASW_ERR_ARG);  // not a valid plan
-      const int k = free_slots.back();
-      free_slots.pop_back();
-      slot_of[act.arg] = k;
-      double* s = slots + 2 * m * (size_t)k;
-      cudaMemcpyAsync(s, c->d_un, m * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-      cudaMemcpyAsync(s + m, c->d_unm1, m * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-    } else if (act.op == CK_FREE) {
-      if (act.arg < 1 || act.arg > nsteps || slot_of[act.arg] < 0) return fail(FASW_ERR_ARG);
-      free_slots.push_back(slot_of[act.arg]);
-      slot_of[act.arg] = -1;
-    } else if (act.op == CK_RESTORE) {
-      if (act.arg == 0) {
-        launch_pack(F, u0, 1, nullptr, c->st);
-        c->steps_done = 0;
-      } else {
-        if (act.arg < 1 || act.arg > nsteps || slot_of[act.arg] < 0) return fail(FASW_ERR_ARG);
-        const double* s = slots + 2 * m * (size_t)slot_of[act.arg];
-        launch_pack(F, s, 1, nullptr, c->st);
-        cudaMemcpyAsync(c->d_un, s, m * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-        cudaMemcpyAsync(c->d_unm1, s + m, m * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-        c->steps_done = act.arg;
-      }
-      launch_bc(F, c->ph, c->st);
-      c->launches += 2;
-      pos = act.arg;
-    } else {  // CK_CONSUME: adjoint step of level n = pos
-      const int n = act.arg;
-      if (n != pos || n < 1) return fail(FASW_ERR_ARG);
-      double a_n, b_n, c_n, a1, b1, c1, a2, b2, c2;
-      time_coefficients(n, dt, bdf_order, &a_n, &b_n, &c_n);
-      time_coefficients(n + 1, dt, bdf_order, &a1, &b1, &c1);
-      time_coefficients(n + 2, dt, bdf_order, &a2, &b2, &c2);
-      if ((r = motion(n))) return fail(r);
-      if (F.a_t != a_n) {
-        drop_graphs(c);
-        for (auto& L : c->lev) L.a_t = a_n;
-      }
-      cudaMemsetAsync(F.src, 0, m * sizeof(double), c->st);
-      if (c->prm.turb) {  // eddy viscosity frozen at its value for u^n
-        launch_bc_aux(F, c->ph, 1.0, 0, c->st);
-        launch_bl(F, c->ph, c->st);
-        c->launches += 2;
-      }
-      if ((r = adj_assemble_all(c, h_rel))) return fail(r);
-      cudaMemsetAsync(rhs, 0, m * sizeof(double), c->st);
-      adj_axpby((int)m, w, c->adj.g + (size_t)which * m, 1.0, rhs, c->st);
-      if (n + 1 <= nsteps) adj_axpby((int)m, -b1, lam1, 1.0, rhs, c->st);
-      if (n + 2 <= nsteps) adj_axpby((int)m, -c2, lam2, 1.0, rhs, c->st);
-      c->launches += 1 + (n + 1 <= nsteps) + (n + 2 <= nsteps);
-      int it = 0;
-      double rr = 0.0;
-      r = adj_solve(c->adj, c->lev, c->ph, c->sc, pcfl, rhs, lamn, tol, max_iters, restart, c->allocs, c->st, &it, &rr,
-                    c->launches);
-      if (r == FASW_ERR_NOT_CONVERGED) soft = true;
-      else if (r) return fail(r);
-      if ((r = adj_err_check(c))) return fail(r);
-      gm_iters += it;
-      worst = std::max(worst, rr);
-      const double t = n * dt;
-      const double phi = -amp * std::sin(omega * t), phidot = -amp * omega * std::cos(omega * t);
-      for (int k = 0; k < nparam; ++k) {
-        double dC = 0.0, dot = 0.0;
-        if ((r = shape_term(c, which, lamn, V + nv * (size_t)k, h_x, 1, phi, phidot, xc, yc, &dC, &dot)))
-          return fail(r);
-        gacc[k] += (w * dC - dot) / (2.0 * h_x);
-      }
-      launch_metrics_fine(F, c->d_x0, c->d_y0, c->st, 1, phi, phidot, xc, yc);
-      ++c->launches;
-      // rotate: lam^(n+2) <- lam^(n+1) <- lam^n
-      double* old2 = lam2;
-      lam2 = lam1;
-      lam1 = lamn;
-      lamn = old2;
-    }
-  }
-  // dJ/du^0 = -(b_1 lam^1 + c_2 lam^2): lam1 holds lam^1, lam2 holds lam^2 (zero when N = 1)
-  double a_1, b_1, c_1, a_2, b_2, c_2;
-  time_coefficients(1, dt, bdf_order, &a_1, &b_1, &c_1);
-  time_coefficients(2, dt, bdf_order, &a_2, &b_2, &c_2);
-  cudaMemsetAsync(rhs, 0, m * sizeof(double), c->st);
-  adj_axpby((int)m, -b_1, lam1, 1.0, rhs, c->st);
-  if (nsteps >= 2) adj_axpby((int)m, -c_2, lam2, 1.0, rhs, c->st);
-  c->launches += 1 + (nsteps >= 2);
-  if (g0 && (r = copy_out(c, g0, rhs, m, on_device))) return fail(r);
-  unsteady_reset(c, u0);
-  if ((r = sync(c))) return r;
-  *objective = J;
-  for (int k = 0; k < nparam; ++k) grad[k] = gacc[k];
-  if (stats) {
-    stats[0] = (double)fsteps;
-    stats[1] = (double)(fsteps - nsteps);
-    stats[2] = (double)gm_iters;
-    stats[3] = (double)cycles;
-    stats[4] = worst;
-  }
-  return soft ? FASW_ERR_NOT_CONVERGED : FASW_OK;
-}
-
-}  // extern "C"
-
-extern "C" {
-
-int fasw_adjoint_vertex_gradient(fasw_ctx* c, int which, const double* lam, double h_x, double* gx, double* gy,
-                                 int on_device) {
-  if (!c || !lam || !gx || !gy || which < 0 || which > 1 || !(h_x > 0.0) || c->ph.moving) return FASW_ERR_ARG;
-  int r = adj_ready(c);
-  if (r) return r;
-  LevelDev& F = c->lev[c->L()];
-  AdjointDev& A = c->adj;
-  if ((r = adj_vertex_setup(A, F.nw, c->allocs, c->st))) return r;
-  adj_vertex_lengths(A, c->d_x0, c->d_y0, c->st);
-  ++c->launches;
-  const size_t m = 4 * (size_t)F.n, nv = (size_t)(F.ni + 1) * (F.nj + 1);
-  if ((r = copy_in(c, c->d_tmp, lam, m, on_device))) return r;
-  double* xo = A.vx;
-  double* yo = A.vx + nv;
-  double* g = c->d_tmp3;  // gx, then gy
-  LevelDev Fz = F;
-  Fz.a_t = 0.0;  // the time term does not depend on X
-  ResArgs a{};
-  a.mode = RES_FULL;
-  const double al = c->ph.alpha_deg * M_PI / 180.0, sa = std::sin(al), ca = std::cos(al);
-  for (int k = 0; k < A.nvcolours; ++k)
-    for (int dir = 0; dir < 2; ++dir) {
-      for (int sgn = 0; sgn < 2; ++sgn) {
-        adj_vertex_perturb(A, k, dir, sgn == 0 ? h_x : -h_x, c->d_x0, c->d_y0, xo, yo, c->st);
-        launch_metrics_fine(Fz, xo, yo, c->st);
-        launch_bc_aux(Fz, c->ph, 1.0, 0, c->st);
-        a.F = sgn == 0 ? A.Fp : A.Fm;
-        launch_residual(Fz, c->ph, a, c->st);
-        launch_wall_force(Fz, c->ph, A.fw + 2 * sgn * A.ni, A.fw + (2 * sgn + 1) * A.ni, c->st);
-        c->launches += 5;
-      }
-      adj_vertex_accumulate(A, k, which, sa, ca, c->d_tmp, A.Fp, A.Fm, A.fw, h_x, g + dir * nv, c->st);
-      ++c->launches;
-    }
-  launch_metrics_fine(F, c->d_x0, c->d_y0, c->st);
-  launch_bc_aux(F, c->ph, 1.0, 0, c->st);
-  c->launches += 2;
-  if ((r = copy_out(c, gx, g, nv, on_device)) || (r = copy_out(c, gy, g + nv, nv, on_device))) return r;
-  return sync(c);
 }
 
 int fasw_set_sweep(fasw_ctx* c, int kind) {
@@ -1265,288 +754,6 @@ int fasw_kernel_time(fasw_ctx* c, int kernel, long long* count, double* total_ms
 }
 
 // ---------------------------------------------------------------- batched cases
-// Many independent cases (own grids, sizes and flow conditions) advanced together: every
-// case is a context on its own stream, and one FAS cycle of all cases is captured into a
-// single CUDA graph as parallel branches (fork on the batch stream, join back), so the GPU
-// runs the cases' kernels concurrently.  The per-case sweep variant is chosen by timing.
-struct fasw_batch {
-  std::vector<fasw_ctx*> cases;
-  std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> joins;
-  cudaEvent_t fork = nullptr;
-  cudaStream_t st = nullptr;
-  int own_stream = 0;
-  struct G { int phase; cudaGraphExec_t exec; long long kernels; };
-  std::vector<G> graphs;
-  long long launches = 0;
-};
-
-static void batch_drop_graphs(fasw_batch* b) {
-  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
-  b->graphs.clear();
-}
-
-int fasw_batch_create(int ncases, const int* ni, const int* nj, const int* n_wake, const double* const* x,
-                      const double* const* y, int coords_on_device, const fasw_params* params, void* stream,
-                      fasw_batch** out) {
-  if (!out || ncases < 1 || !ni || !nj || !n_wake || !x || !y || !params) return FASW_ERR_ARG;
-  *out = nullptr;
-  fasw_batch* b = new (std::nothrow) fasw_batch();
-  if (!b) return FASW_ERR_OOM;
-  b->st = static_cast<cudaStream_t>(stream);
-  if (!b->st) {  // graph capture needs a non-default stream
-    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
-      delete b;
-      return FASW_ERR_CUDA;
-    }
-    b->own_stream = 1;
-  }
-  cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-  for (int k = 0; k < ncases; ++k) {
-    cudaStream_t s = nullptr;
-    cudaEvent_t e = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-      fasw_batch_destroy(b);
-      return FASW_ERR_CUDA;
-    }
-    b->streams.push_back(s);
-    b->joins.push_back(e);
-    fasw_ctx* c = nullptr;
-    const int r = fasw_create(ni[k], nj[k], n_wake[k], x[k], y[k], coords_on_device, &params[k], s, &c);
-    if (r != FASW_OK) {
-      fasw_batch_destroy(b);
-      return r;
-    }
-    b->cases.push_back(c);
-  }
-  *out = b;
-  return FASW_OK;
-}
-
-void fasw_batch_destroy(fasw_batch* b) {
-  if (!b) return;
-  if (b->st) cudaStreamSynchronize(b->st);
-  batch_drop_graphs(b);
-  for (fasw_ctx* c : b->cases) fasw_destroy(c);
-  for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
-  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
-  if (b->fork) cudaEventDestroy(b->fork);
-  if (b->own_stream) cudaStreamDestroy(b->st);
-  delete b;
-}
-
-fasw_ctx* fasw_batch_case(fasw_batch* b, int k) {
-  return (b && k >= 0 && k < (int)b->cases.size()) ? b->cases[k] : nullptr;
-}
-
-static double case_cfl(const fasw_ctx* c, int cycle_index) {
-  return cycle_index < c->prm.ramp_cycles ? std::fmin(c->prm.cfl, c->prm.cfl_ramp) : c->prm.cfl;
-}
-
-int fasw_batch_cycle(fasw_batch* b, int cycle_index, double* norms) {
-  if (!b) return FASW_ERR_ARG;
-  // the cycle's launch sequence depends on each case's c*, i.e. on whether it is still ramped
-  int phase = 0;
-  for (size_t k = 0; k < b->cases.size(); ++k)
-    if (cycle_index < b->cases[k]->prm.ramp_cycles) phase |= 1;
-  cudaGraphExec_t exec = nullptr;
-  for (auto& g : b->graphs)
-    if (g.phase == phase) {
-      exec = g.exec;
-      b->launches += g.kernels;
-    }
-  if (!exec) {
-    long long before = 0;
-    for (fasw_ctx* c : b->cases) before += c->launches;
-    CKR(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
-    cudaEventRecord(b->fork, b->st);
-    for (size_t k = 0; k < b->cases.size(); ++k) {
-      fasw_ctx* c = b->cases[k];
-      cudaStreamWaitEvent(c->st, b->fork, 0);
-      enqueue_cycle(c, case_cfl(c, cycle_index));
-      cudaEventRecord(b->joins[k], c->st);
-      cudaStreamWaitEvent(b->st, b->joins[k], 0);
-    }
-    cudaGraph_t graph = nullptr;
-    CKR(cudaStreamEndCapture(b->st, &graph));
-    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(e);
-    long long after = 0;
-    for (fasw_ctx* c : b->cases) after += c->launches;
-    b->graphs.push_back({phase, exec, after - before});
-    b->launches += after - before;
-  }
-  CKR(cudaGraphLaunch(exec, b->st));
-  CKR(cudaStreamSynchronize(b->st));
-  CKR(cudaGetLastError());
-  for (size_t k = 0; k < b->cases.size(); ++k) {
-    if (*b->cases[k]->h_err) return FASW_ERR_DEVICE_TIMEOUT;
-    if (norms) norms[k] = *b->cases[k]->h_norm;
-  }
-  return FASW_OK;
-}
-
-int fasw_batch_solve(fasw_batch* b, double drop, int max_cycles, int* cycles, double* final_drop, int* ncycles) {
-  if (!b || max_cycles < 1) return FASW_ERR_ARG;
-  const size_t nc = b->cases.size();
-  std::vector<double> n0(nc, 0.0), nk(nc, 0.0);
-  std::vector<int> done(nc, 0);  // 1 converged, 2 diverged (its cycles[] is -2)
-  int diverged = 0;
-  for (int k = 0; k < max_cycles; ++k) {
-    int r = fasw_batch_cycle(b, k, nk.data());
-    if (r) return r;
-    if (ncycles) *ncycles = k + 1;
-    size_t ndone = 0;
-    for (size_t q = 0; q < nc; ++q) {
-      if (k == 0) n0[q] = nk[q];
-      if (!done[q]) {
-        if (final_drop) final_drop[q] = nk[q] / n0[q];
-        if (!std::isfinite(nk[q]) || (k > 0 && nk[q] > 1e8 * n0[q])) {
-          done[q] = 2;
-          diverged = 1;
-          if (cycles) cycles[q] = -2;
-        } else if (k > 0 && nk[q] <= drop * n0[q]) {
-          done[q] = 1;
-          if (cycles) cycles[q] = k + 1;
-        }
-      }
-      ndone += done[q] != 0;
-    }
-    if (ndone == nc) return diverged ? FASW_ERR_DIVERGED : FASW_OK;
-  }
-  for (size_t q = 0; q < nc; ++q)
-    if (!done[q] && cycles) cycles[q] = -1;
-  return diverged ? FASW_ERR_DIVERGED : FASW_ERR_NOT_CONVERGED;
-}
-
-// Autotuner.  Candidates are the sweep variants whose CTAs never wait on one another (strip
-// sweeps are not candidates: their CTAs wait on each other, which is safe only while all CTAs
-// of one sweep are resident, and concurrent branches of a batch graph do not guarantee that):
-// the hyperplane-staged FP32 sweep with a ring of 8 or 4 steps and the one-CTA sweep.  Which
-// wins depends on the grid shape and on how full the GPU is, so the tuner times whole batch
-// cycles (all cases concurrently, CUDA events, states saved and restored) and improves the
-// choice one grid shape (ni, nj) at a time, keeping a change only when the batch gets faster.
-// Results are cached per (ni, nj, precision) for the process: a later batch whose shapes are
-// all cached takes them without timing.
-namespace {
-struct TuneKey {
-  int ni, nj, mixed;
-  bool operator<(const TuneKey& o) const {
-    return ni != o.ni ? ni < o.ni : nj != o.nj ? nj < o.nj : mixed < o.mixed;
-  }
-};
-std::map<TuneKey, int> g_tune_cache;
-std::mutex g_tune_mutex;
-
-TuneKey key_of(fasw_ctx* c) {
-  const LevelDev& F = c->lev[c->L()];
-  return TuneKey{F.ni, F.nj, c->mixed};
-}
-}  // namespace
-
-// Times `reps` batch cycles with kinds[k] on case k (after one capturing cycle); states restored.
-static int batch_time(fasw_batch* b, const std::vector<int>& kinds, const std::vector<double*>& saved, int reps,
-                      cudaEvent_t e0, cudaEvent_t e1, float* ms) {
-  for (size_t k = 0; k < b->cases.size(); ++k) {
-    b->cases[k]->sweep_kind = kinds[k];
-    drop_graphs(b->cases[k]);
-  }
-  batch_drop_graphs(b);
-  int r = fasw_batch_cycle(b, 0, nullptr);  // capture + warm-up
-  if (r) return r;
-  CKR(cudaEventRecord(e0, b->st));
-  for (int rep = 0; rep < reps; ++rep)
-    if ((r = fasw_batch_cycle(b, 0, nullptr))) return r;
-  CKR(cudaEventRecord(e1, b->st));
-  CKR(cudaEventSynchronize(e1));
-  CKR(cudaEventElapsedTime(ms, e0, e1));
-  for (size_t k = 0; k < b->cases.size(); ++k) {  // restore the states
-    fasw_ctx* c = b->cases[k];
-    launch_pack(c->lev[c->L()], saved[k], 1, nullptr, c->st);
-    launch_bc(c->lev[c->L()], c->ph, c->st);
-    CKR(cudaStreamSynchronize(c->st));
-  }
-  return FASW_OK;
-}
-
-// choice (nullable, ncases): the kind used for case k.
-int fasw_batch_autotune(fasw_batch* b, int* choice) {
-  if (!b) return FASW_ERR_ARG;
-  const size_t nc = b->cases.size();
-  std::vector<int> kinds(nc, SWEEP_HP);
-  std::map<TuneKey, std::vector<size_t>> groups;
-  for (size_t k = 0; k < nc; ++k) groups[key_of(b->cases[k])].push_back(k);
-  bool all_cached = true;
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mutex);
-    for (auto& gk : groups) {
-      auto it = g_tune_cache.find(gk.first);
-      if (it == g_tune_cache.end()) {
-        all_cached = false;
-        continue;
-      }
-      for (size_t k : gk.second) kinds[k] = it->second;
-    }
-  }
-  if (!all_cached) {
-    std::vector<double*> saved(nc, nullptr);
-    for (size_t k = 0; k < nc; ++k) {
-      fasw_ctx* c = b->cases[k];
-      saved[k] = c->d_tmp2;  // 4 x n of the finest level
-      launch_pack(c->lev[c->L()], nullptr, 0, saved[k], c->st);
-      CKR(cudaStreamSynchronize(c->st));
-    }
-    cudaEvent_t e0, e1;
-    CKR(cudaEventCreate(&e0));
-    CKR(cudaEventCreate(&e1));
-    const int reps = 3;
-    int r = FASW_OK;
-    // the faster of two timings of the same kinds, so that one noisy timing decides nothing
-    auto timed = [&](float* out) {
-      float a = 0.f, c2 = 0.f;
-      if ((r = batch_time(b, kinds, saved, reps, e0, e1, &a))) return;
-      if ((r = batch_time(b, kinds, saved, reps, e0, e1, &c2))) return;
-      *out = std::min(a, c2);
-    };
-    const int cand[3] = {SWEEP_HP8, SWEEP_HP4, SWEEP_CTA};
-    // larger shapes first: they dominate the batch time
-    std::vector<std::pair<TuneKey, std::vector<size_t>>> order(groups.begin(), groups.end());
-    std::sort(order.begin(), order.end(), [](const auto& x, const auto& y) {
-      return (long long)x.first.ni * x.first.nj * x.second.size() > (long long)y.first.ni * y.first.nj * y.second.size();
-    });
-    // each candidate against the incumbent timed right beside it; a switch must gain 2 %
-    for (size_t gi = 0; gi < order.size() && r == FASW_OK; ++gi) {
-      const std::vector<size_t>& members = order[gi].second;
-      int keep = kinds[members[0]];
-      for (int k : cand) {
-        if (k == keep || r) continue;
-        float t_keep = 0.f, t_k = 0.f;
-        timed(&t_keep);
-        for (size_t m : members) kinds[m] = k;
-        if (r == FASW_OK) timed(&t_k);
-        if (r == FASW_OK && t_k < 0.98f * t_keep) keep = k;
-        for (size_t m : members) kinds[m] = keep;
-      }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (r) return r;
-    std::lock_guard<std::mutex> lk(g_tune_mutex);
-    for (auto& gk : groups) g_tune_cache[gk.first] = kinds[gk.second[0]];
-  }
-  for (size_t k = 0; k < nc; ++k) {
-    b->cases[k]->sweep_kind = kinds[k];
-    drop_graphs(b->cases[k]);
-    if (choice) choice[k] = kinds[k];
-  }
-  batch_drop_graphs(b);
-  return FASW_OK;
-}
-
-long long fasw_batch_launch_count(fasw_batch* b) { return b ? b->launches : -1; }
-
 const char* fasw_strerror(int code) {
   switch (code) {
     case FASW_OK: return "ok";
