@@ -137,3 +137,38 @@ def test_cycle_preconditioned_adjoint_solves_the_rans_workload():
     grad = s.adjoint_shape_gradient(1, out["cycle"][0], bump_fields(g, 16))
     assert np.abs(grad[:8] + grad[8:]).max() <= 5e-3 * np.abs(grad).max(), grad
     s.close()
+
+
+def _asymptotic_rate(norms, floor):
+    """Mean per-iteration reduction over the last 10 iterations above `floor`."""
+    n = [x for x in norms if x > floor]
+    assert len(n) >= 12, len(n)
+    return (n[-1] / n[-11]) ** 0.1
+
+
+def test_adjoint_iteration_converges_at_the_primal_rate():
+    """The adjoint iteration lam <- lam + C^T (g - J^T lam) has the iteration matrix (I - J C)^T,
+    whose spectrum is that of the primal's linearised iteration I - C J: both reduce their
+    residuals at the same asymptotic rate (and so does the nonlinear FAS iteration near its
+    fixed point)."""
+    g = make_cgrid(64, 16)
+    s = _converged_solver(g, nlevels=2, gamma_cycle=1, mach=0.6, alpha_deg=ALPHA, cfl=1e4)
+    s.adjoint_jacobian(1e-7)
+    cfl = 1e4
+    e = _direction(16, 64, 7)
+    primal = []
+    for _ in range(60):
+        e = e - s.adjoint_cycle_apply(s.adjoint_apply(e), cfl, kind="cycle", transpose=False)
+        primal.append(float(np.linalg.norm(e)))
+    gD = s.adjoint_objective_gradient(1)
+    lam = np.zeros_like(gD)
+    adjoint = []
+    for _ in range(60):
+        r = gD - s.adjoint_apply(lam, transpose=True)
+        adjoint.append(float(np.linalg.norm(r)))
+        lam = lam + s.adjoint_cycle_apply(r, cfl, kind="cycle", transpose=True)
+    rp = _asymptotic_rate(primal, 1e-9 * primal[0])
+    ra = _asymptotic_rate(adjoint, 1e-9 * adjoint[0])
+    print(f"asymptotic rates: linearised primal {rp:.4f}, adjoint {ra:.4f}")
+    assert rp < 0.95 and abs(ra - rp) <= 0.05 * rp, (rp, ra)
+    s.close()
