@@ -331,7 +331,6 @@ int adj_setup(AdjointDev& A, int ni, int nj, int nw, std::vector<void*>& allocs,
   rev_ptr[n] = (int)rev.size();
   A.ni = ni;
   A.nj = nj;
-  A.n = n;
   int r;
   if ((r = adj_alloc(allocs, &A.nbr, nbr.size())) || (r = adj_alloc(allocs, &A.col, (size_t)n)) ||
       (r = adj_alloc(allocs, &A.rev_ptr, (size_t)n + 1)) || (r = adj_alloc(allocs, &A.rev, rev.size())) ||
@@ -362,7 +361,9 @@ int adj_setup(AdjointDev& A, int ni, int nj, int nw, std::vector<void*>& allocs,
   cudaMemsetAsync(A.J, 0, (size_t)n * ADJ_SLOTS * 16 * sizeof(double), st);
   cudaMemsetAsync(A.Jv, 0, (size_t)n * ADJ_SLOTS * 16 * sizeof(double), st);
   // the host vectors above are freed on return: wait for the copies
-  return cudaStreamSynchronize(st) == cudaSuccess ? FASW_OK : FASW_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FASW_ERR_CUDA;
+  A.n = n;  // published last: a failed set-up is redone by the next call
+  return FASW_OK;
 }
 
 int adj_assemble(AdjointDev& A, const LevelDev& L, const PhysParams& ph, double h_rel, cudaStream_t st,
@@ -929,7 +930,7 @@ __global__ void k_vertex_accum(int nv, int n, int ni, const int* col, int k, con
 }  // namespace
 
 int adj_vertex_setup(AdjointDev& A, int nw, std::vector<void*>& allocs, cudaStream_t st) {
-  if (A.vcol) return FASW_OK;
+  if (A.nvcolours > 0) return FASW_OK;  // set last, on success
   const int ni = A.ni, nj = A.nj, n = A.n, V = ni + 1, nv = (ni + 1) * (nj + 1);
   auto on_cut = [&](int i) { return nw > 0 && (i < nw || i >= ni - nw); };
   std::vector<std::vector<int>> infl(nv);
@@ -980,8 +981,9 @@ int adj_vertex_setup(AdjointDev& A, int nw, std::vector<void*>& allocs, cudaStre
   cudaMemcpyAsync(A.vcol, col.data(), nv * sizeof(int), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(A.vinfl_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(A.vinfl, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FASW_ERR_CUDA;  // host vectors die here
   A.nvcolours = ncol;
-  return cudaStreamSynchronize(st) == cudaSuccess ? FASW_OK : FASW_ERR_CUDA;  // host vectors die here
+  return FASW_OK;
 }
 
 void adj_vertex_lengths(const AdjointDev& A, const double* x0, const double* y0, cudaStream_t st) {
@@ -1021,7 +1023,12 @@ int adj_mg_setup(AdjointDev& A, const std::vector<LevelDev>& lev, int gamma, int
   G->lv.resize(L);
   G->pm.resize(L + 1);
   G->wk.resize(L + 1);
-  A.mg = G;
+  // published in A only when complete (device memory of a failed attempt stays in allocs)
+  auto fail = [&](int r) {
+    for (auto& C : G->lv) adj_release(C);
+    delete G;
+    return r;
+  };
   int r;
   for (int l = 0; l < L; ++l) {
     AdjointDev& C = G->lv[l];
@@ -1030,15 +1037,16 @@ int adj_mg_setup(AdjointDev& A, const std::vector<LevelDev>& lev, int gamma, int
     C.prog = A.prog;
     C.err = A.err;
     C.spin_limit = A.spin_limit;
-    if ((r = adj_setup(C, lev[l].ni, lev[l].nj, lev[l].nw, allocs, st))) return r;
+    if ((r = adj_setup(C, lev[l].ni, lev[l].nj, lev[l].nw, allocs, st))) return fail(r);
   }
   for (int l = 1; l <= L; ++l)
-    if ((r = build_prolong_map(lev[l], lev[l - 1], G->pm[l], allocs, st))) return r;
+    if ((r = build_prolong_map(lev[l], lev[l - 1], G->pm[l], allocs, st))) return fail(r);
   for (int l = 0; l <= L; ++l) {
     G->wk[l].assign(8, nullptr);
     for (int k = 0; k < 8; ++k)
-      if ((r = adj_alloc(allocs, &G->wk[l][k], 4 * (size_t)lev[l].n))) return r;
+      if ((r = adj_alloc(allocs, &G->wk[l][k], 4 * (size_t)lev[l].n))) return fail(r);
   }
+  A.mg = G;
   return FASW_OK;
 }
 
