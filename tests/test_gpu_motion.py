@@ -3,6 +3,7 @@ and for dual time stepping (implicit Euler first step, then BDF2)."""
 import numpy as np
 import pytest
 
+import oracle as O
 from synth.cgrid import make_cgrid
 from tests.helpers import make_pair, perturbed_state, rel_err
 
@@ -48,3 +49,29 @@ def test_pitching_dual_time_steps_match_the_oracle():
         m = ho > 1e-12 * ho[0]
         assert np.all(np.abs(hg - ho)[m] <= 1e-7 * ho[m] + 1e-13 * ho[0])
         assert rel_err(s.get_state(), o.get_state()) < 1e-9
+
+
+def test_pitching_dual_step_parity_full_size():
+    """The first pitching step on the 512x128 RANS grid (M 0.8, Re 1e6, 4-level W-cycles, moving
+    walls and grid fluxes at full size): three pseudo-time cycles from the same state."""
+    from synth.cases import config_c3
+    import paper_1710_04875_gb300 as P
+    from tests.helpers import pair_params
+    c = config_c3()
+    g = c.grid()
+    po, pg = pair_params(nlevels=4, gamma_cycle=2, viscous=1, turb=1, mach=c.mach, alpha_deg=0.0, re=c.reynolds,
+                         cfl=100.0)
+    o, s = O.Oracle(g, po), P.Solver(g, pg)
+    for k in range(10):
+        o.fas_cycle(k)
+    u = o.get_state()
+    s.set_state(u)
+    dt = 2 * np.pi / 0.4 / 64
+    for solver in (o, s):
+        solver.set_motion(*_pitch(dt))
+    nco, ho = o.dual_time_step(dt, 1e-12, 3)
+    code, ncg, hg = s.dual_time_step(dt, 1e-12, 3)
+    assert nco == ncg == 3
+    assert np.all(np.abs(hg - ho) <= 1e-9 * ho)
+    assert rel_err(s.get_state(), o.get_state()) < 1e-9
+

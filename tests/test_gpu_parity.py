@@ -157,6 +157,25 @@ def test_pitching_grid_cycle_parity_full_size(precision, tol_norm, tol_f):
     assert rel_err(Fg, Fo) < tol_f
 
 
+@pytest.mark.parametrize("precision,tol_norm,tol_f", [("fp64", 1e-10, 1e-9), ("mixed", 1e-3, 1e-2)])
+def test_largest_grid_cycle_parity(precision, tol_norm, tol_f):
+    """The 1024x256 C-grid of the sensitivity case (thin-layer RANS, Baldwin-Lomax, M 0.75,
+    Re 6.5e6, 5-level W-cycles): two cycles from the free stream against the FP64 oracle."""
+    g = make_cgrid(1024, 256, n_wake=128, wall_spacing=1e-5)
+    kw = dict(nlevels=5, gamma_cycle=2, viscous=1, turb=1, mach=0.75, alpha_deg=0.0, re=6.5e6, cfl=100.0)
+    po, _ = pair_params(**kw)
+    _, pg = pair_params(precision=precision, **kw)
+    import paper_1710_04875_gb300 as P
+    o, s = O.Oracle(g, po), P.Solver(g, pg)
+    for k in range(2):
+        no = o.fas_cycle(k)
+        ng = s.fas_cycle(k)
+        assert abs(ng - no) <= tol_norm * abs(no), k
+    Fo, _, _ = o.residual()
+    Fg, _, _ = s.residual()
+    assert rel_err(Fg, Fo) < tol_f
+
+
 @pytest.mark.parametrize("sweep", ["auto", "staged", "cta"])
 def test_mixed_precision_reaches_the_fp64_fixed_point(sweep):
     """FP32 preconditioner only changes the iteration, not the converged answer (every FP32
