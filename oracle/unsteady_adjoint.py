@@ -17,7 +17,9 @@ both X-derivatives by central differences over deformed grids rotated to phi(t_n
 terms do not depend on X), and the sensitivity to the initial state is
     dJ/du^0 = -(b_1 lam^1 + c_2 lam^2).
 Every state u^n is stored (no checkpointing) and every adjoint system is solved by a sparse LU.
-The eddy viscosity is not part of this oracle (Euler and laminar only).
+With a turbulence model the eddy viscosity is frozen at its Baldwin-Lomax value at each level's
+state u^n (in the Jacobian and in the X-derivatives alike), the linearisation the library's
+adjoint takes.
 
 Only tests/ import this module; it shares nothing with the CUDA library.
 """
@@ -87,6 +89,7 @@ def gradient(grid, params, u0: np.ndarray, fields: np.ndarray, amp: float, omega
         o = Oracle(grid, params)
         o.set_motion(phi, phidot, xc, yc)
         o.set_state(states[n])
+        mut = o.compute_mut() if params.turb else None  # frozen at its value for u^n
         o.set_time_source(a_n, None)
         Jn, gL, gD = jacobian(o, alpha, h_rel)
         rhs = w * (gL if which == 0 else gD)
@@ -103,6 +106,8 @@ def gradient(grid, params, u0: np.ndarray, fields: np.ndarray, amp: float, omega
                 ok = Oracle(deformed(grid, sgn * e, fields), params)
                 ok.set_motion(phi, phidot, xc, yc)
                 ok.set_state(states[n])
+                if mut is not None:
+                    ok.set_mut(mut)
                 F.append(ok.residual()[0].ravel())
                 C.append(_objective(ok, which, alpha))
             grad[k] += w * (C[0] - C[1]) / (2.0 * h_x) - lam[n] @ (F[0] - F[1]) / (2.0 * h_x)

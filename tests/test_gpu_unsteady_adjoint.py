@@ -75,6 +75,32 @@ def test_laminar_unsteady_adjoint_matches_the_oracle():
     s.close()
 
 
+def test_rans_unsteady_adjoint_matches_the_oracle():
+    """Thin-layer RANS with Baldwin-Lomax on the pitching grid: the eddy viscosity frozen at each
+    level's value on both sides; three levels against the oracle."""
+    import paper_1710_04875_gb300 as P
+    g = make_cgrid(64, 16, wall_spacing=1e-3)
+    kw = dict(nlevels=2, viscous=1, turb=1, mach=0.5, alpha_deg=0.0, re=1e5, cfl=100.0)
+    po, pg = pair_params(**kw)
+    o = O.Oracle(g, po)
+    for k in range(400):
+        o.fas_cycle(k)
+    u0 = o.get_state()
+    V = bump_fields(g, 2)
+    N = 3
+    drop = 1e-10
+    Jo, go, g0o, _ = U.gradient(g, po, u0, V, AMP, OMEGA, XC, YC, DT, N, drop, CYCLES, 1)
+    s = P.Solver(g, pg)
+    s.set_state(u0)
+    Jg, gg, g0g, code, st = s.unsteady_adjoint(AMP, OMEGA, DT, N, V, which=1, xc=XC, yc=YC, drop=drop,
+                                               max_cycles=CYCLES, tol=1e-11, max_iters=600, restart=250)
+    assert code == 0, st
+    assert abs(Jg - Jo) <= 1e-8 * abs(Jo)
+    assert rel_err(gg, go) < 1e-5, (gg, go)
+    assert rel_err(g0g, g0o) < 1e-5
+    s.close()
+
+
 def test_implicit_euler_unsteady_adjoint_matches_the_oracle(euler_case):
     """bdf_order 1: implicit Euler on every level (no second history term in the adjoint)."""
     import paper_1710_04875_gb300 as P
