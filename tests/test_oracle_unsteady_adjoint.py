@@ -113,10 +113,13 @@ def test_adjoint_matches_finite_differences_of_unsteady_solves(case):
     assert abs((Jp - Jm) / (2 * hp) - np.sum(g0 * d)) <= 1e-3 * abs(np.sum(g0 * d))
 
 
-def test_laminar_adjoint_equals_tangent():
-    """The same identity with the thin-layer viscous flux on the moving no-slip wall."""
+@pytest.mark.parametrize("turb", [0, 1])
+def test_viscous_adjoint_equals_tangent(turb):
+    """The same identity with the thin-layer viscous flux on the moving no-slip wall, laminar and
+    with Baldwin-Lomax (frozen at each level's value on both sides of the identity)."""
     g = make_cgrid(32, 8, n_wake=4, wall_spacing=5e-3)
-    p = O.make_params("AW3", nlevels=2, viscous=1, turb=0, sensor=1, mach=0.5, alpha_deg=0.0, re=5e3, cfl=1e3)
+    p = O.make_params("AW3", nlevels=2, viscous=1, turb=turb, sensor=1, mach=0.5, alpha_deg=0.0,
+                      re=5e3 if turb == 0 else 1e5, cfl=1e3 if turb == 0 else 100.0)
     o = O.Oracle(g, p)
     for k in range(300):
         o.fas_cycle(k)
@@ -135,6 +138,7 @@ def test_laminar_adjoint_equals_tangent():
         on = O.Oracle(g, p)
         on.set_motion(phi, phidot, XC, YC)
         on.set_state(states[m])
+        mut = on.compute_mut() if turb else None
         on.set_time_source(a, None)
         Jn, _, gD = jacobian(on, 0.0)
         F, C = [], []
@@ -142,6 +146,8 @@ def test_laminar_adjoint_equals_tangent():
             ok = O.Oracle(deformed(g, sgn * e, V), p)
             ok.set_motion(phi, phidot, XC, YC)
             ok.set_state(states[m])
+            if mut is not None:
+                ok.set_mut(mut)
             F.append(ok.residual()[0].ravel())
             C.append(force_coefficients(*ok.wall_force(), 0.0)[1])
         rhs = -(F[0] - F[1]) / 2e-6 - b * du[m - 1] - (c * du[m - 2] if m >= 2 else 0.0)
