@@ -87,9 +87,9 @@ int adj_setup(AdjointDev& A, int ni, int nj, int nw, std::vector<void*>& allocs,
 int adj_assemble(AdjointDev& A, const LevelDev& L, const PhysParams& ph, double h_rel, cudaStream_t st,
                  long long& launches);
 void adj_apply(const AdjointDev& A, const double* v, double* out, int transpose, cudaStream_t st);
-// Flexible GMRES(restart) on J^T lam = g, right-preconditioned by steps of the transposed
-// primal stage loop with the transposed AW preconditioner built on L at pseudo CFL cfl
-// (overwrites L's blocks and dt*); the preconditioned basis vectors are kept, so an FP32
+// Flexible GMRES(restart) on J^T lam = g, right-preconditioned by A.precond_kind (the transposed
+// linearised FAS cycle by default, built on every level at pseudo CFL cfl; overwrites the
+// levels' blocks and dt*); the preconditioned basis vectors are kept, so an FP32
 // preconditioner does not limit the attainable residual.  Returns FASW_OK or
 // FASW_ERR_NOT_CONVERGED; *iters, *relres.
 // lev: the context's levels (the coarse ones are used by ADJ_FAS_CYCLE_T).

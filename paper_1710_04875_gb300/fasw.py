@@ -325,7 +325,8 @@ class Solver:
 
     def adjoint_precond_apply(self, r, cfl, steps=0):
         """z = P^-T r, the transposed primal AW preconditioner scaled by eta dt* (steps 0), or that
-        many steps of the transposed primal stage loop from zero (the GMRES preconditioner)."""
+        many steps of the primal stage loop run on J^T from zero (preconditioner kind
+        "stage_loop")."""
         r = np.ascontiguousarray(r, dtype=np.float64)
         z = np.zeros(self._shape(self.finest))
         _check(self.lib.fasw_adjoint_precond_apply(self.h, cfl, int(steps), r.ctypes.data, z.ctypes.data,
