@@ -1,7 +1,7 @@
-// Discrete adjoint of the steady finest-level residual (kernels_adjoint.cu): the Jacobian
-// dF/du by coloured central differences with the eddy viscosity frozen, its products with
-// vectors and its transpose, and a GMRES solve of the adjoint system preconditioned by the
-// transposed primal AW preconditioner.
+// Discrete adjoint of the residual (kernels_adjoint.cu): the Jacobian dF/du by coloured central
+// differences with the eddy viscosity frozen, its products with vectors and its transpose, the
+// transposed smoothing step and FAS cycle, a flexible GMRES solve of the adjoint system, and
+// the vertex colouring of the transposed grid product.
 #pragma once
 #include <vector>
 

@@ -6,11 +6,14 @@
 // groups of cells of one colour (no residual stencil holds two cells of a colour), so the
 // Jacobian is that of exactly the discrete operator the smoother drives to zero, with the
 // eddy viscosity frozen.  The transposed product is then an exact gather over the stored
-// blocks.  The adjoint system is solved by restarted GMRES, right-preconditioned by the
-// transpose of the primal AW preconditioner (flux-vector-split blocks with the eigenvalue
-// cutoff, symmetric Gauss-Seidel factors) scaled to approximate J: Gauss-Seidel on the
-// central-difference Jacobian itself is not usable, its diagonal blocks hold only the
-// artificial dissipation.
+// blocks (the dissipative part's Jacobian is kept apart as well, for the smoother's beta
+// blending).  The adjoint system is solved by flexible GMRES, right-preconditioned by the
+// exact transpose of the primal's linearised FAS cycle: the transposed AW smoothing step (the
+// primal's flux-vector-split SGS preconditioner with the eigenvalue cutoff, run transposed)
+// on every level, with transposed restriction and prolongation and coarse Jacobians at the
+// restricted state.  Gauss-Seidel on the central-difference Jacobian itself is not usable, its
+// diagonal blocks hold only the artificial dissipation.  Also here: the vertex colouring of the
+// transposed grid product (dF/dX)^T lambda.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
