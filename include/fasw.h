@@ -147,7 +147,7 @@ int fasw_use_graphs(fasw_ctx* ctx, int enable);
  * hyperplane-staged sweep where the level fits, else one-CTA sweep), 1 = one thread per cell
  * applying the LU blocks (reference kernel), 2 = one CTA with precomputed transfer blocks
  * (strips where a hyperplane exceeds 128 cells), 3 = strip-pipelined with 8 rows per strip,
- * 4 = with 16 rows per strip, 5 = hyperplane-staged (mixed precision only, nj <= 128: blocks
+ * 4 = with 16 rows per strip, 5 = hyperplane-staged (mixed precision only, nj <= 256: blocks
  * stored hyperplane-major and staged through shared memory by cp.async; elsewhere as 0), 6 / 7 =
  * hyperplane-staged with a staging ring of 4 / 8 steps, 8 = strip-pipelined with 4 rows per
  * strip.  All give the same Gauss-Seidel result up to rounding.  Synchronizes the stream; drops

@@ -534,7 +534,7 @@ inline size_t hp_smem_bytes(int stages, int nt, int njp, int ni, int nw) {
 // The step loop is unrolled by the ring depth, so ring slots and exchange buffers are fixed
 // shared-memory offsets, and the global sources advance by one hyperplane per issue.
 template <int STAGES>
-__global__ void __launch_bounds__(512) k_sweep_hp(LevelDev L) {
+__global__ void __launch_bounds__(1024) k_sweep_hp(LevelDev L) {
   pdl_entry();
   static_assert((STAGES & (STAGES - 1)) == 0 && STAGES >= 4, "ring depth: power of two, at least 4");
   extern __shared__ float4 sm4[];
@@ -714,14 +714,14 @@ void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st) {
 
 namespace {
 int hp_threads(int nj) { return 4 * ((nj + 7) / 8 * 8); }
-int hp_stages(int nt) { return nt <= 256 ? 8 : 4; }  // 512 threads: ring of 4 keeps shared memory < 227 KB
+int hp_stages(int nt) { return nt <= 256 ? 8 : 4; }  // 512 and 1024 threads: ring of 4 keeps shared memory < 227 KB
 constexpr size_t kHpSmemMax = 227 * 1024;
 }  // namespace
 
 size_t hp_floats(int ni, int nj) { return (size_t)(ni + nj - 1) * nj; }
 
 bool hp_fits(int ni, int nj, int nw) {
-  if (nj > 128) return false;
+  if (nj > 256) return false;  // one CTA of 4 nj threads
   const int nt = hp_threads(nj);
   return hp_smem_bytes(hp_stages(nt), nt, nt / 4, ni, nw) <= kHpSmemMax;
 }

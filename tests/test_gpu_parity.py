@@ -258,10 +258,12 @@ def test_sweep_kinds_match_the_oracle(kind, scheme, ni, nj, nw):
 
 
 @pytest.mark.parametrize("kind", ["staged", "staged4", "staged8", "cta", "strips"])
-@pytest.mark.parametrize("ni,nj,nw", [(128, 32, 16), (72, 20, 8), (16, 6, 2), (256, 64, 32), (128, 128, 16)])
+@pytest.mark.parametrize("ni,nj,nw", [(128, 32, 16), (72, 20, 8), (16, 6, 2), (256, 64, 32), (128, 128, 16),
+                                      (256, 256, 32), (192, 200, 24)])
 def test_mixed_sweep_is_the_fp32_preconditioner(kind, ni, nj, nw):
     """Mixed precision: every FP32 sweep kernel applies the oracle's operator to FP32 accuracy,
-    including partial 8-row groups (nj = 20, 6) and the 128-row staged variant."""
+    including partial 8-row groups (nj = 20, 6, 200) and the 128- and 256-row staged variants
+    (one CTA of up to 1024 threads)."""
     g = make_cgrid(ni, nj, n_wake=nw, jitter=0.03, seed=ni + nj, wall_spacing=2e-3 if nj < 64 else 1e-4)
     o, s = make_pair(g, nlevels=1, d_cut=0.5, precision="mixed")
     s.set_sweep(kind)
