@@ -29,9 +29,9 @@
 //   * an independent dense path assembles (D+L) D^{-1} (D+U) and solves it
 //     with partially pivoted LU (used by tests on tiny grids).
 //
-// Parity unpinned: the Baldwin-Lomax closure (beyond mu_t = 0 for
-// irrotational flow and a hand-checked inner-layer value) follows only this
-// file's own restatement of the 1978 model.
+// The Baldwin-Lomax closure is pinned by closed forms (linear shear over a
+// plate and across the wake cut, where every discrete step is exact) and by
+// the model's exact similarity laws (velocity, density and length scalings).
 
 #include <algorithm>
 #include <array>
