@@ -373,6 +373,15 @@ int fasw_batch_solve(fasw_batch* batch, double drop, int max_cycles, int* cycles
 int fasw_batch_autotune(fasw_batch* batch, int* choice);
 long long fasw_batch_launch_count(fasw_batch* batch);
 
+/* Verification hook for two FP64 powers the per-cell auxiliaries form by Newton's method (the
+ * sensor quantity p rho^-gamma of section 2's pressure switch, and the cube root in Martinelli's
+ * radius scaling), computed beside the CUDA math library on the current device: for t < n,
+ * out[4t..4t+3] = (rho^-gamma of a[t] by Newton, pow(a[t], -gamma), (a[t]/b[t])^(1/3) by Newton,
+ * cbrt(a[t]/b[t])).  a, b: n doubles (positive, finite); out: 4n doubles; all host pointers, or
+ * device pointers with on_device = 1.  Synchronous.  FASW_ERR_ARG for n < 0 or null pointers,
+ * FASW_ERR_OOM / FASW_ERR_CUDA on device failures. */
+int fasw_check_math(int n, const double* a, const double* b, double* out, int on_device);
+
 /* Message for an error code; and the last CUDA error string seen by the library. */
 const char* fasw_strerror(int code);
 const char* fasw_last_cuda_error(void);

@@ -753,6 +753,29 @@ int fasw_kernel_time(fasw_ctx* c, int kernel, long long* count, double* total_ms
   return FASW_OK;
 }
 
+int fasw_check_math(int n, const double* a, const double* b, double* out, int on_device) {
+  if (n < 0 || (n > 0 && (!a || !b || !out))) return FASW_ERR_ARG;
+  if (n == 0) return FASW_OK;
+  const size_t m = (size_t)n;
+  if (on_device) {
+    launch_check_math(n, a, b, out, 0);
+    CKR(cudaGetLastError());
+    CKR(cudaDeviceSynchronize());
+    return FASW_OK;
+  }
+  double* d = nullptr;
+  if (cudaMalloc(&d, 6 * m * sizeof(double)) != cudaSuccess) return FASW_ERR_OOM;
+  cudaError_t e = cudaMemcpy(d, a, m * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d + m, b, m * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    launch_check_math(n, d, d + m, d + 2 * m, 0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + 2 * m, 4 * m * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? FASW_OK : cuda_fail(e);
+}
+
 // ---------------------------------------------------------------- batched cases
 const char* fasw_strerror(int code) {
   switch (code) {

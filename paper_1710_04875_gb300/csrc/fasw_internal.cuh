@@ -131,6 +131,8 @@ void launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, 
 int residual_blocks(const LevelDev& L);
 void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* out, cudaStream_t st);
 void launch_bl(const LevelDev& L, const PhysParams& ph, cudaStream_t st);
+// the auxiliaries' FP64 powers beside pow()/cbrt(), n values (device pointers)
+void launch_check_math(int n, const double* a, const double* b, double* out, cudaStream_t st);
 // per-wall-face force on the body from the j = 0 face fluxes (ghosts and auxiliaries current)
 void launch_wall_force(const LevelDev& L, const PhysParams& ph, double* fx, double* fy, cudaStream_t st);
 

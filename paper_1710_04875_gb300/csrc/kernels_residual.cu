@@ -181,7 +181,46 @@ __global__ void k_bc(LevelDev L, PhysParams ph) {
   store4(L, gidx(L, gi, gj), g);
 }
 
-// Pressure, 1/rho and sensor quantity of one (ghosted) cell.
+// FP64 on this part issues one warp instruction per ~64 clocks per scheduler, and the library
+// pow() costs about 3.3 us of dependent chain per call (cbrt 0.54 us, a division 0.29 us, an
+// FMA 32 ns): the per-cell auxiliaries are bound by that chain, not by memory.  The two powers
+// they need are computed as roots of polynomial equations by Newton's method in FP64 from an
+// FP32 estimate; both are checked against pow() and cbrt() by fasw_check_math.
+
+// rho^(-gamma) for gamma = 7/5: the root z of f(z) = rho^7 z^5 - 1.  The FP32 estimate
+// (log2/exp2) has relative error d ~ 5e-7; the step z <- z (1 - f/5) is Newton's step to
+// first order in f and leaves a relative error of about 3 d^2, so two steps reach FP64
+// rounding (about one ulp of the exact 7/5 power; pow(rho, 1.4) raises to the double nearest
+// 1.4, 8.9e-17 below 7/5, and differs from it by |ln rho| 8.9e-17 relative).
+static_assert(GAM == 1.4, "rho^-gamma is formed as the root of rho^7 z^5 = 1");
+__device__ __forceinline__ double pow_neg_gamma(double rho) {
+  const float rf = (float)rho;
+  double z = (double)exp2f(-1.4f * __log2f(rf));
+  const double r2 = rho * rho, r7 = (r2 * r2) * (r2 * rho);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double z2 = z * z, z5 = (z2 * z2) * z;
+    const double f = fma(r7, z5, -1.0);
+    z = fma(-0.2 * f, z, z);
+  }
+  return z;
+}
+
+// (num/den)^(1/3) for positive num, den: the root c of den c^3 - num = 0, by Newton's method
+// from the FP32 cube root with the derivative's reciprocal 1/(3 den c^2) taken in FP32 (the
+// error contracts by ~1e-7 per step: two steps reach FP64 rounding).  No FP64 division.
+__device__ __forceinline__ double cbrt_ratio(double num, double den) {
+  const float nf = (float)num, df = (float)den;
+  const float c0 = cbrtf(nf / df);
+  const double d = (double)(1.0f / (3.0f * df * c0 * c0));
+  double c = (double)c0;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) c = fma(-fma(den, (c * c) * c, -num), d, c);
+  return c;
+}
+
+// Pressure, 1/rho and (finest level only: the coarse levels' dissipation has no sensor) the
+// sensor quantity of one (ghosted) cell.
 __device__ __forceinline__ void cell_thermo(const LevelDev& L, const PhysParams& ph, int g, const double w[4],
                                             double& rr, double& u, double& v, double& p) {
   rr = 1.0 / w[0];
@@ -190,7 +229,7 @@ __device__ __forceinline__ void cell_thermo(const LevelDev& L, const PhysParams&
   p = (GAM - 1.0) * (w[3] - 0.5 * (w[1] * u + w[2] * v));
   L.p[g] = p;
   L.rinv[g] = rr;
-  L.q[g] = ph.sensor ? p / pow(w[0], GAM) : p;
+  if (L.finest) L.q[g] = ph.sensor ? p * pow_neg_gamma(w[0]) : p;
 }
 
 // Auxiliaries: blocks [0, nbi) take the interior cells (pressure, 1/rho, sensor quantity,
@@ -232,11 +271,11 @@ __global__ void k_cell_aux(LevelDev L, PhysParams ph, double cfl, int want_dts, 
   const double ve = 0.5 * (L.vfe[fs] + L.vfe[fs + ni]);
   const double rxi = fabs(u * sx + v * sy - vx) + a * sqrt(sx * sx + sy * sy);
   const double reta = fabs(u * ex + v * ey - ve) + a * sqrt(ex * ex + ey * ey);
-  // Martinelli scaling: (r_eta/r_xi)^(2/3) = cr^2 with cr the cube root of the ratio, and the
-  // other direction's factor is 1/cr^2 (one cbrt instead of two pow).
-  const double cr = cbrt(reta / rxi), t2 = cr * cr;
-  L.rt[c] = rxi + rxi * t2;
-  L.rt[L.n + c] = reta + reta / t2;
+  // Martinelli scaling: with cr = (r_eta/r_xi)^(1/3), r_xi (r_eta/r_xi)^(2/3) = r_xi cr^2 and
+  // r_eta (r_xi/r_eta)^(2/3) = r_xi cr (one cube root, no division).
+  const double cr = cbrt_ratio(reta, rxi);
+  L.rt[c] = rxi + rxi * (cr * cr);
+  L.rt[L.n + c] = reta + rxi * cr;
   if (want_dts) L.dts[c] = cfl * L.vol[c] / (rxi + reta);
 }
 
@@ -609,7 +648,22 @@ __global__ void k_bl_lines(LevelDev L, PhysParams ph) {
   }
 }
 
+// The two powers of the auxiliaries beside the CUDA math library's: out[4 t ..] =
+// (pow_neg_gamma(a), pow(a, -gamma), cbrt_ratio(a, b), cbrt(a / b)).
+__global__ void k_check_math(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  out[4 * t + 0] = pow_neg_gamma(a[t]);
+  out[4 * t + 1] = pow(a[t], -GAM);
+  out[4 * t + 2] = cbrt_ratio(a[t], b[t]);
+  out[4 * t + 3] = cbrt(a[t] / b[t]);
+}
+
 }  // namespace
+
+void launch_check_math(int n, const double* a, const double* b, double* out, cudaStream_t st) {
+  if (n > 0) k_check_math<<<(n + 127) / 128, 128, 0, st>>>(n, a, b, out);
+}
 
 void launch_bc(const LevelDev& L, const PhysParams& ph, cudaStream_t st) {
   const int nt = 4 * L.ni + 4 * L.nj;

@@ -97,6 +97,7 @@ def library():
             "fasw_adjoint_cycle_apply": (i, [p, d, i, i, dp, dp, i]),
             "fasw_adjoint_shape_gradient": (i, [p, i, dp, i, dp, d, dp, i]),
             "fasw_checkpoint_schedule": (i, [i, i, dp, dp, i, C.POINTER(i), C.POINTER(ll)]),
+            "fasw_check_math": (i, [i, p, p, p, i]),
             "fasw_unsteady_adjoint": (i, [p, d, d, d, d, d, i, i, d, i, i, i, i, dp, d, d, d, i, i, d, C.POINTER(d),
                                           dp, dp, i, dp]),
             "fasw_residual_noalloc": (i, [i, i, i, dp, dp, dp, dp, C.POINTER(Params), p]),
@@ -438,6 +439,18 @@ def checkpoint_schedule(nsteps, snapshots):
     _check(lib.fasw_checkpoint_schedule(nsteps, snapshots, ops.ctypes.data, args.ctypes.data, n.value, C.byref(n),
                                         C.byref(fs)), "fasw_checkpoint_schedule")
     return list(zip(ops.tolist(), args.tolist())), fs.value
+
+
+def check_math(a, b):
+    """(rho^-gamma by Newton, pow(a, -gamma), (a/b)^(1/3) by Newton, cbrt(a/b)) per element, each an
+    array like a: the library's FP64 powers beside the CUDA math library's, on the current GPU."""
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    b = np.ascontiguousarray(b, dtype=np.float64).ravel()
+    if a.shape != b.shape:
+        raise ValueError("a and b differ in size")
+    out = np.zeros((a.size, 4))
+    _check(library().fasw_check_math(a.size, a.ctypes.data, b.ctypes.data, out.ctypes.data, 0), "fasw_check_math")
+    return out[:, 0], out[:, 1], out[:, 2], out[:, 3]
 
 
 class Batch:

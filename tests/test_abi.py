@@ -37,6 +37,14 @@ def test_default_params_and_strerror_are_host_only():
     assert lib.fasw_strerror(-4) == b"residual diverged"
 
 
+def test_check_math_rejects_bad_arguments_before_touching_the_device():
+    import paper_1710_04875_gb300 as P
+    lib = P.library()
+    assert lib.fasw_check_math(-1, None, None, None, 0) == -1
+    assert lib.fasw_check_math(4, None, None, None, 0) == -1
+    assert lib.fasw_check_math(0, None, None, None, 0) == 0
+
+
 def test_create_rejects_bad_arguments_before_touching_the_device():
     import paper_1710_04875_gb300 as P
     from synth.cgrid import make_cgrid

@@ -53,6 +53,28 @@ def test_residual_parity_thin_layer_with_eddy_viscosity(sensor):
     assert rel_err(Fg, Fo) < 1e-11
 
 
+@pytest.mark.parametrize("h", [1.3e-3, 6e-5])
+def test_baldwin_lomax_on_closed_form_states(h):
+    """The library's Baldwin-Lomax on the linear-shear plate states whose eddy viscosity has a
+    closed form (both branches of F_wake, density varying through the layer): element by
+    element against the oracle, and on the plate lines against the closed form itself."""
+    from tests.test_oracle_baldwin_lomax import _plate_grid, _state, _wall_line_closed_form
+    ni, nj, nw = 64, 32, 8
+    g = _plate_grid(ni, nj, nw, h)
+    a, re = 100.0, 1e6
+    yc = np.abs(0.25 * (g.y[:-1, :-1] + g.y[:-1, 1:] + g.y[1:, 1:] + g.y[1:, :-1]))
+    rho_of = lambda y: 0.7 + 0.3 * y / (y + 4.0 * h)
+    u = _state(rho_of(yc), a * yc, np.zeros((nj, ni)), np.full((nj, ni), 100.0))
+    o, s = make_pair(g, nlevels=1, viscous=1, turb=1, mach=0.5, re=re)
+    o.set_state(u); s.set_state(u)
+    mg = s.get_mut()
+    assert rel_err(mg, o.compute_mut()) < 1e-12
+    expect, _, _ = _wall_line_closed_form(a, h, rho_of((np.arange(nj) + 0.5) * h), 1.0 / re, nj)
+    for i in [i for i in range(nw, ni - nw) if i not in (ni // 2 - 1, ni // 2)]:
+        assert np.allclose(mg[:, i], expect, rtol=1e-11, atol=0.0), i
+    s.close()
+
+
 @pytest.mark.parametrize("cfl", [3.0, 1e4])
 def test_pseudo_dt_and_face_blocks(cfl):
     ni, nj, nw = 72, 20, 8
