@@ -378,6 +378,7 @@ int fasw_create(int ni, int nj, int n_wake, const double* x, const double* y, in
   c->ph.turb = p->turb;
   c->ph.sensor = p->sensor;
   free_stream(p->mach, p->alpha_deg, c->ph.uinf);
+  set_free_stream_prims(c->ph);
   const Coef& cf = kCoef[p->scheme % 4];
   c->sc.aw = p->scheme < 4 ? 1 : 0;
   c->sc.nstages = cf.s;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of the fasw library.
 #pragma once
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cstdint>
 
 namespace fasw {
@@ -90,10 +91,21 @@ struct PhysParams {
   double mach, alpha_deg, re, pr, prt;
   double inv_re, inv_pr, inv_prt;  // reciprocals of re, pr, prt (set with them by the host)
   double uinf[4];
+  double finf[4];  // free-stream u, v, p, a (set by the host with uinf: set_free_stream_prims)
   double s_coarse;
   int viscous, turb, sensor;
   int moving;  // grid in rigid motion: moving-wall ghosts
 };
+
+// Primitive variables of the free stream for the far-field boundary, formed once on the host.
+inline void set_free_stream_prims(PhysParams& ph) {
+  const double rr = 1.0 / ph.uinf[0], u = ph.uinf[1] * rr, v = ph.uinf[2] * rr;
+  const double p = (GAM - 1.0) * (ph.uinf[3] - 0.5 * (ph.uinf[1] * u + ph.uinf[2] * v));
+  ph.finf[0] = u;
+  ph.finf[1] = v;
+  ph.finf[2] = p;
+  ph.finf[3] = std::sqrt(GAM * p * rr);
+}
 
 struct SchemeParams {
   int aw;        // 1 = additive W, 0 = preconditioned ARK

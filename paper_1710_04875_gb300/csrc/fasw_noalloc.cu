@@ -115,6 +115,7 @@ extern "C" int fasw_residual_noalloc(int ni, int nj, int n_wake, const double* x
     ph.uinf[2] = vv;
     ph.uinf[3] = pinf / (GAM - 1.0) + 0.5 * (uu * uu + vv * vv);
   }
+  set_free_stream_prims(ph);
 
   // The scratch keeps the previous call's contents: clear what the residual reads as zero
   // (eddy viscosity, forcing, dual-time source) before use.

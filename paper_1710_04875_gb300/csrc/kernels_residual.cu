@@ -41,12 +41,13 @@ __device__ __forceinline__ double pressure(const double w[4]) {
 // gamma = 1.4 the exponent is the integer 5 (FP64 pow costs about a hundred FP64 instructions
 // on a part whose FP64 issue rate is the bound of this kernel).
 static_assert(GAM == 1.4, "far-field density uses 2/(gamma-1) = 5");
-__device__ void farfield(const double wi[4], const double wf[4], double nx, double ny, double vb, double out[4]) {
+// The free stream's primitives (u, v, p, a) come from the host (PhysParams::finf).
+__device__ void farfield(const double wi[4], const PhysParams& ph, double nx, double ny, double vb, double out[4]) {
+  const double* wf = ph.uinf;
   const double ri = wi[0], rri = 1.0 / ri, ui = wi[1] * rri, vi = wi[2] * rri;
   const double pi = (GAM - 1.0) * (wi[3] - 0.5 * (wi[1] * ui + wi[2] * vi));
-  const double rf = wf[0], rrf = 1.0 / rf, uf = wf[1] * rrf, vf = wf[2] * rrf;
-  const double pf = (GAM - 1.0) * (wf[3] - 0.5 * (wf[1] * uf + wf[2] * vf));
-  const double ai = sqrt(GAM * pi * rri), af = sqrt(GAM * pf * rrf);
+  const double rf = wf[0], uf = ph.finf[0], vf = ph.finf[1], af = ph.finf[3];
+  const double ai = sqrt(GAM * pi * rri);
   const double vni = ui * nx + vi * ny, vnf = uf * nx + vf * ny;
   if (fabs(vni - vb) >= ai) {
     const double* src = vni - vb > 0.0 ? wi : wf;
@@ -131,21 +132,21 @@ __device__ void ghost_state(const LevelDev& L, const PhysParams& ph, int gi, int
   if (gj >= nj) {  // outward +S_eta
     const int i = gi, f = nj * ni + i;
     const double sx = L.seta[f], sy = L.seta[L.nfe + f];
-    const double len = sqrt(sx * sx + sy * sy);
+    const double il = 1.0 / sqrt(sx * sx + sy * sy);
     load4(L, gidx(L, i, nj - 1), w);
-    farfield(w, ph.uinf, sx / len, sy / len, L.vfe[f] / len, g);
+    farfield(w, ph, sx * il, sy * il, L.vfe[f] * il, g);
   } else if (gi < 0) {  // outward -S_xi
     const int j = gj, f = j * (ni + 1);
     const double sx = L.sxi[f], sy = L.sxi[L.nfx + f];
-    const double len = sqrt(sx * sx + sy * sy);
+    const double il = 1.0 / sqrt(sx * sx + sy * sy);
     load4(L, gidx(L, 0, j), w);
-    farfield(w, ph.uinf, -sx / len, -sy / len, -L.vfx[f] / len, g);
+    farfield(w, ph, -sx * il, -sy * il, -L.vfx[f] * il, g);
   } else {  // gi >= ni, outward +S_xi
     const int j = gj, f = j * (ni + 1) + ni;
     const double sx = L.sxi[f], sy = L.sxi[L.nfx + f];
-    const double len = sqrt(sx * sx + sy * sy);
+    const double il = 1.0 / sqrt(sx * sx + sy * sy);
     load4(L, gidx(L, ni - 1, j), w);
-    farfield(w, ph.uinf, sx / len, sy / len, L.vfx[f] / len, g);
+    farfield(w, ph, sx * il, sy * il, L.vfx[f] * il, g);
   }
 }
 
