@@ -76,3 +76,33 @@ def test_fourth_difference_dissipation_with_martinelli_radii(direction):
     assert np.allclose(got, want, rtol=1e-9, atol=1e-15), np.abs(got - want).max()
     assert np.abs(F[1:][(slice(None),) + inner]).max() < 1e-13
     assert np.abs(Fc[(slice(None),) + inner]).max() < 1e-13
+
+
+def test_pressure_switch_dissipation_on_an_odd_even_pressure():
+    """Euler, fluid at rest, constant density, p = p0 + c (-1)^i.  The pressure switch
+    |p+ - 2p + p-| / (p+ + 2p + p- + 0.001) is 4|c| / (4 p0 + 0.001) in every cell, above 1/64
+    here, so eps4 = max(0, r/32 - 2 eps2) = 0 and eps2 = s r with r the larger Martinelli
+    radius of the two cells (the high-pressure cell's).  Only rho H = gamma p / (gamma - 1)
+    varies in w, so the energy residual is 4 eps2 gamma/(gamma-1) c (-1)^i / (dx dy) and the
+    other components vanish; with rho E in w the factor gamma would be missing."""
+    ni, nj, lx, ly = 16, 8, 1.0, 0.3
+    g = make_rect_grid(ni, nj, lx=lx, ly=ly)
+    dx, dy = lx / ni, ly / nj
+    rho, p0 = 1.1, 0.7
+    c = 0.05 * p0
+    sgn = (-1.0) ** np.arange(ni)
+    p = np.tile(p0 + c * sgn, (nj, 1))
+    zero = np.zeros((nj, ni))
+    o = O.Oracle(g, O.make_params(nlevels=1, mach=0.5, alpha_deg=0.0))
+    o.set_state(np.stack([rho + zero, zero, zero, p / (GAM - 1.0)]))
+    _, _, Fv = o.residual()
+    s = 4.0 * c / (4.0 * p0 + 0.001)
+    assert 1.0 / 64.0 < s < 0.25
+    a_hi = np.sqrt(GAM * (p0 + c) / rho)
+    r = _martinelli(a_hi * dy, a_hi * dx)
+    eps2 = s * r
+    want = 4.0 * eps2 * GAM / (GAM - 1.0) * c * sgn / (dx * dy)
+    inner = (slice(2, nj - 2), slice(2, ni - 2))
+    got = Fv[3][inner]
+    assert np.allclose(got, np.tile(want, (nj, 1))[inner], rtol=1e-11, atol=0.0), got[0] / want[2:ni - 2]
+    assert np.abs(Fv[:3][(slice(None),) + inner]).max() < 1e-12 * np.abs(want).max()
