@@ -78,13 +78,16 @@ def test_fourth_difference_dissipation_with_martinelli_radii(direction):
     assert np.abs(Fc[(slice(None),) + inner]).max() < 1e-13
 
 
-def test_pressure_switch_dissipation_on_an_odd_even_pressure():
-    """Euler, fluid at rest, constant density, p = p0 + c (-1)^i.  The pressure switch
-    |p+ - 2p + p-| / (p+ + 2p + p- + 0.001) is 4|c| / (4 p0 + 0.001) in every cell, above 1/64
-    here, so eps4 = max(0, r/32 - 2 eps2) = 0 and eps2 = s r with r the larger Martinelli
-    radius of the two cells (the high-pressure cell's).  Only rho H = gamma p / (gamma - 1)
-    varies in w, so the energy residual is 4 eps2 gamma/(gamma-1) c (-1)^i / (dx dy) and the
-    other components vanish; with rho E in w the factor gamma would be missing."""
+@pytest.mark.parametrize("switch", ["pressure", "entropy"])
+def test_switch_dissipation_on_an_odd_even_pressure(switch):
+    """Fluid at rest, constant density, p = p0 + c (-1)^i.  The switch quantity q is p (Euler) or
+    p / rho^gamma (viscous flows; the thin-layer flux has no jump across a j-face here), and
+    |q+ - 2q + q-| / (q+ + 2q + q- + 0.001) is 4|c'| / (4 q0 + 0.001) in every cell (c', q0 the
+    scaled amplitude and mean), above 1/64 here, so eps4 = max(0, r/32 - 2 eps2) = 0 and
+    eps2 = s r with r the larger Martinelli radius of the two cells (the high-pressure cell's).
+    Only rho H = gamma p / (gamma - 1) varies in w, so the energy residual is
+    4 eps2 gamma/(gamma-1) c (-1)^i / (dx dy) and the other components vanish; with rho E in w
+    the factor gamma would be missing."""
     ni, nj, lx, ly = 16, 8, 1.0, 0.3
     g = make_rect_grid(ni, nj, lx=lx, ly=ly)
     dx, dy = lx / ni, ly / nj
@@ -93,10 +96,12 @@ def test_pressure_switch_dissipation_on_an_odd_even_pressure():
     sgn = (-1.0) ** np.arange(ni)
     p = np.tile(p0 + c * sgn, (nj, 1))
     zero = np.zeros((nj, ni))
-    o = O.Oracle(g, O.make_params(nlevels=1, mach=0.5, alpha_deg=0.0))
+    viscous = 1 if switch == "entropy" else 0
+    o = O.Oracle(g, O.make_params(nlevels=1, viscous=viscous, sensor=viscous, mach=0.5, alpha_deg=0.0, re=1e3))
     o.set_state(np.stack([rho + zero, zero, zero, p / (GAM - 1.0)]))
     _, _, Fv = o.residual()
-    s = 4.0 * c / (4.0 * p0 + 0.001)
+    scale = rho ** -GAM if switch == "entropy" else 1.0
+    s = 4.0 * c * scale / (4.0 * p0 * scale + 0.001)
     assert 1.0 / 64.0 < s < 0.25
     a_hi = np.sqrt(GAM * (p0 + c) / rho)
     r = _martinelli(a_hi * dy, a_hi * dx)
