@@ -111,3 +111,33 @@ def test_switch_dissipation_on_an_odd_even_pressure(switch):
     got = Fv[3][inner]
     assert np.allclose(got, np.tile(want, (nj, 1))[inner], rtol=1e-11, atol=0.0), got[0] / want[2:ni - 2]
     assert np.abs(Fv[:3][(slice(None),) + inner]).max() < 1e-12 * np.abs(want).max()
+
+
+def test_coarse_level_first_order_dissipation():
+    """A coarse level (2x2 agglomeration of a Cartesian grid: cells 2dx x 2dy) uses first-order
+    dissipation eps2 = s_c r with s_c = 0.25 and no fourth difference (the reading of the
+    paper's coarse-grid scheme).  At rest, uniform pressure, density linear in the coarse cell
+    index with slope c1: F_rho = -s_c c1 (r~_e - r~_w) / (4 dx dy), r~ the larger Martinelli
+    radius of each face's two cells."""
+    ni, nj, lx, ly = 32, 16, 1.0, 0.45
+    g = make_rect_grid(ni, nj, lx=lx, ly=ly)
+    o = O.Oracle(g, O.make_params(nlevels=2, mach=0.5, alpha_deg=0.0, s_coarse=0.25))
+    nic, njc, _ = o.dims(0)
+    assert (nic, njc) == (ni // 2, nj // 2)
+    dx, dy = 2 * lx / ni, 2 * ly / nj
+    p, c1 = 0.7, 0.03
+    prof = 1.0 + c1 * (np.arange(nic) - 7.5)
+    rho = np.tile(prof, (njc, 1))
+    zero = np.zeros((njc, nic))
+    o.set_state(np.stack([rho, zero, zero, p / (GAM - 1.0) + zero]), 0)
+    o.set_forcing(np.zeros((4, njc, nic)), 0)
+    F, Fc, Fv = o.residual(0)
+    a = np.sqrt(GAM * p / prof)
+    rt = _martinelli(a * dy, a * dx)
+    rf = np.maximum(rt[:-1], rt[1:])             # face between coarse cells m and m+1
+    Frho = np.zeros(nic)
+    Frho[1:-1] = -0.25 * c1 * (rf[1:] - rf[:-1]) / (dx * dy)
+    inner = (slice(1, njc - 1), slice(1, nic - 1))
+    want = np.tile(Frho, (njc, 1))[inner]
+    assert np.allclose(F[0][inner], want, rtol=1e-11, atol=0.0), F[0][inner][0] / want[0]
+    assert np.abs(F[1:][(slice(None),) + inner]).max() < 1e-12 * np.abs(want).max()
