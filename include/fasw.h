@@ -33,6 +33,11 @@
  *     allocates (cudaMalloc at create, cudaFree at destroy).
  *   - There is no CPU fallback: without a usable CUDA device every call that
  *     touches the device returns FASW_ERR_CUDA.
+ *   - Bounded device-side waits (the strip-pipelined sweeps, where one CTA waits for the
+ *     rows of another) give up after spin_limit polls and set the context's device error
+ *     word; the call that ran the sweep returns FASW_ERR_DEVICE_TIMEOUT (its results are
+ *     then incomplete).  Every call that runs sweeps clears the word first, so a timeout is
+ *     reported by the call in which it happened and does not poison later calls.
  */
 #ifndef FASW_H
 #define FASW_H
@@ -381,6 +386,23 @@ long long fasw_batch_launch_count(fasw_batch* batch);
  * device pointers with on_device = 1.  Synchronous.  FASW_ERR_ARG for n < 0 or null pointers,
  * FASW_ERR_OOM / FASW_ERR_CUDA on device failures. */
 int fasw_check_math(int n, const double* a, const double* b, double* out, int on_device);
+
+/* Coefficients of the stage loop of a scheme, Table "RK smoothers" (section 4.1): *nstages
+ * (3 or 5) and alpha[k], beta[k] for k < *nstages (alpha, beta nullable, 5 doubles each).  The
+ * W methods use the ARK coefficients of the same name; AW51/AW52 and ARK51/ARK52 take the
+ * ARK5J betas (section 4.1), and the ARK5J beta row is read as (1, 0, 0.56, 0, 0.44).  Host
+ * only (no device needed).  FASW_ERR_ARG for an unknown scheme or nstages NULL. */
+int fasw_scheme_coefficients(int scheme, int* nstages, double* alpha, double* beta);
+
+/* Failure detection without a GPU fault (no counterpart in the paper).  After
+ * fasw_fault_inject_alloc(n), the library's (n+1)-th following device allocation fails on the
+ * host, before cudaMalloc is called, as if the device were out of memory (FASW_ERR_OOM); n < 0
+ * switches the injection off (the default).  It fires once.  fasw_live_allocations() is the
+ * number of device buffers the library currently holds (every context, batch and adjoint
+ * workspace), so a caller can check that a failed call released what it had allocated.  Both
+ * are process-wide and host only. */
+void fasw_fault_inject_alloc(long long n);
+long long fasw_live_allocations(void);
 
 /* Message for an error code; and the last CUDA error string seen by the library. */
 const char* fasw_strerror(int code);

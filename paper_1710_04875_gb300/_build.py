@@ -1,7 +1,13 @@
-"""Build the CUDA library libfasw.so in-tree for sm_103a (nvcc, no cmake).
+"""Build the CUDA library in-tree for sm_103a (nvcc, no cmake).
 
-Translation units compile in parallel; the shared object lands in
-``paper_1710_04875_gb300/_build/``.  Rebuilds only when a source is newer.
+Two variants of the same sources:
+
+* ``perf`` (``_build/libfasw.so``): the production build, FMA contraction on;
+* ``parity`` (``_build_parity/libfasw_parity.so``): ``-fmad=false``, no FMA contraction, so
+  that every multiply and add rounds on its own as in a CPU reference compiled without
+  contraction.  Only the contraction differs; the kernels and launch shapes are the same.
+
+Translation units compile in parallel; rebuilds only when a source is newer.
 """
 from __future__ import annotations
 
@@ -12,11 +18,20 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-OUT = os.path.join(HERE, "_build")
-LIB = os.path.join(OUT, "libfasw.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-std=c++17", ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+VARIANTS = {
+    "perf": (os.path.join(HERE, "_build"), "libfasw.so", []),
+    "parity": (os.path.join(HERE, "_build_parity"), "libfasw_parity.so", ["-fmad=false"]),
+}
+OUT, _name, _ = VARIANTS["perf"]
+LIB = os.path.join(OUT, _name)
+
+
+def lib_path(variant: str = "perf") -> str:
+    out, name, _ = VARIANTS[variant]
+    return os.path.join(out, name)
 
 
 def _sources():
@@ -28,42 +43,65 @@ def _deps():
         os.path.join(HERE, "..", "include", "fasw.h"), __file__]
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(variant: str = "perf") -> bool:
+    lib = lib_path(variant)
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and not needs_build():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
-    procs = []
-    objs = []
+def _start(variant: str, extra: list[str] | None, verbose: bool):
+    out, name, vflags = VARIANTS[variant]
+    os.makedirs(out, exist_ok=True)
+    jobs = []
     for src in _sources():
-        obj = os.path.join(OUT, os.path.basename(src).replace(".cu", ".o"))
-        objs.append(obj)
-        cmd = [NVCC, *FLAGS, *(extra or []), "-c", src, "-o", obj]
+        obj = os.path.join(out, os.path.basename(src).replace(".cu", ".o"))
+        cmd = [NVCC, *FLAGS, *vflags, *(extra or []), "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
-        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        jobs.append((obj, cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    return jobs
+
+
+def _finish(variant: str, jobs, verbose: bool) -> str:
+    out, name, _ = VARIANTS[variant]
     failed = []
-    for cmd, p in procs:
-        out, _ = p.communicate()
-        if verbose and out:
-            sys.stdout.write(out.decode())
+    for obj, cmd, p in jobs:
+        text, _ = p.communicate()
+        if verbose and text:
+            sys.stdout.write(text.decode())
         if p.returncode != 0:
-            failed.append((cmd, out.decode()))
+            failed.append((cmd, text.decode()))
     if failed:
         msg = "\n".join(f"{' '.join(c)}\n{o}" for c, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([NVCC, "-shared", ARCH, "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    lib = os.path.join(out, name)
+    tmp = lib + f".tmp{os.getpid()}"
+    subprocess.check_call([NVCC, "-shared", ARCH, "-o", tmp, *[o for o, _, _ in jobs]])
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          variant: str = "perf") -> str:
+    """Build one variant (when a source is newer than it, or force); returns its path."""
+    if not force and not needs_build(variant):
+        return lib_path(variant)
+    return _finish(variant, _start(variant, extra, verbose), verbose)
+
+
+def build_all(force: bool = False, verbose: bool = False) -> list[str]:
+    """Both variants, their translation units compiled side by side."""
+    todo = [v for v in VARIANTS if force or needs_build(v)]
+    started = [(v, _start(v, None, verbose)) for v in todo]
+    for v, jobs in started:
+        _finish(v, jobs, verbose)
+    return [lib_path(v) for v in VARIANTS]
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+    if "--ptxas" in sys.argv:
+        print(build(force=True, verbose=True, extra=["-Xptxas", "-v"]))
+    else:
+        print(build_all(force="--force" in sys.argv, verbose=True))

@@ -38,12 +38,8 @@ static int adj_assemble_all(fasw_ctx* c, double h_rel) {
   return FASW_OK;
 }
 
-// FASW_ERR_DEVICE_TIMEOUT when a bounded wait of the sweeps ran out (device error word set).
-static int adj_err_check(fasw_ctx* c) {
-  CKR(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-  CKR(cudaStreamSynchronize(c->st));
-  return *c->h_err ? FASW_ERR_DEVICE_TIMEOUT : FASW_OK;
-}
+// FASW_ERR_DEVICE_TIMEOUT when a bounded wait of the sweeps ran out since the last err_clear.
+static int adj_err_check(fasw_ctx* c) { return err_read(c); }
 
 int fasw_force_coefficients(fasw_ctx* c, double* cl, double* cd) {
   if (!c || !cl || !cd) return FASW_ERR_ARG;
@@ -88,6 +84,7 @@ int fasw_adjoint_precond_apply(fasw_ctx* c, double cfl, int steps, const double*
   if (e) return e;
   const size_t m = 4 * (size_t)c->adj.n;
   if ((e = copy_in(c, c->d_tmp, r, m, on_device))) return e;
+  err_clear(c);
   adj_build_precond(c->adj, c->lev[c->L()], c->ph, c->sc, cfl, c->st, c->launches);
   adj_steps_apply(c->adj, steps, c->d_tmp, c->d_tmp2, c->st);
   c->launches += 2;
@@ -116,6 +113,7 @@ int fasw_adjoint_cycle_apply(fasw_ctx* c, double cfl, int kind, int transpose, c
   const size_t m = 4 * (size_t)c->adj.n;
   int e = copy_in(c, c->d_tmp, r, m, on_device);
   if (e) return e;
+  err_clear(c);
   adj_build_precond(c->adj, c->lev[c->L()], c->ph, c->sc, cfl, c->st, c->launches);
   if (kind == 2) {
     adj_mg_build_precond(c->adj, c->lev, c->ph, c->sc, cfl, c->st, c->launches);
@@ -141,6 +139,7 @@ int fasw_adjoint_solve(fasw_ctx* c, int which, const double* g, double* lam, dou
     rhs = c->d_tmp;
   }
   const double pcfl = cfl > 0.0 ? cfl : c->prm.cfl;
+  err_clear(c);
   const int code = adj_solve(c->adj, c->lev, c->ph, c->sc, pcfl, rhs, c->d_tmp2, tol, max_iters, restart,
                              c->allocs, c->st, iters, rel_res, c->launches);
   if (code != FASW_OK && code != FASW_ERR_NOT_CONVERGED) return code;
@@ -228,15 +227,12 @@ void time_coefficients(int n, double dt, int bdf_order, double* a, double* b, do
 struct RunBuffers {
   std::vector<void*> mem;
   ~RunBuffers() {
-    for (void* p : mem) cudaFree(p);
+    for (void* p : mem) device_free(p);
   }
   int get(double** p, size_t count) {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, (count ? count : 1) * sizeof(double));
-    if (e != cudaSuccess) {
-      g_last_cuda_error = cudaGetErrorString(e);
-      return FASW_ERR_OOM;
-    }
+    const int r = device_alloc(&q, (count ? count : 1) * sizeof(double));
+    if (r != FASW_OK) return r;
     mem.push_back(q);
     *p = static_cast<double*>(q);
     return FASW_OK;
@@ -386,6 +382,7 @@ int fasw_unsteady_adjoint(fasw_ctx* c, double amp, double omega, double xc, doub
       c->launches += 1 + (n + 1 <= nsteps) + (n + 2 <= nsteps);
       int it = 0;
       double rr = 0.0;
+      err_clear(c);
       r = adj_solve(c->adj, c->lev, c->ph, c->sc, pcfl, rhs, lamn, tol, max_iters, restart, c->allocs, c->st, &it, &rr,
                     c->launches);
       if (r == FASW_ERR_NOT_CONVERGED) soft = true;

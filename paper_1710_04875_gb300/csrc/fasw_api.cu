@@ -8,6 +8,7 @@
 #include <new>
 #include <string>
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "fasw_ctx.cuh"
@@ -41,18 +42,55 @@ const Coef kCoef[4] = {
 
 namespace fasw {
 
-template <typename T>
-int dalloc(fasw_ctx* c, T** p, size_t count) {
-  void* q = nullptr;
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+// Host-side allocation-failure injection and a count of the library's live device
+// allocations (fasw_fault_inject_alloc, fasw_live_allocations): a failure is made on the host,
+// before cudaMalloc would be called, so no GPU fault is involved.
+std::atomic<long long> g_fail_alloc_in{-1};
+std::atomic<long long> g_live_allocs{0};
+
+int device_alloc(void** q, size_t bytes) {
+  long long k = g_fail_alloc_in.load();
+  while (k >= 0 && !g_fail_alloc_in.compare_exchange_weak(k, k - 1)) {
+  }
+  if (k == 0) {
+    g_last_cuda_error = "allocation failure injected on the host";
+    return FASW_ERR_OOM;
+  }
+  cudaError_t e = cudaMalloc(q, bytes);
   if (e != cudaSuccess) {
     g_last_cuda_error = cudaGetErrorString(e);
     return FASW_ERR_OOM;
   }
+  g_live_allocs.fetch_add(1);
+  return FASW_OK;
+}
+
+void device_free(void* q) {
+  if (!q) return;
+  cudaFree(q);
+  g_live_allocs.fetch_sub(1);
+}
+
+template <typename T>
+int dalloc(fasw_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  if (count == 0) count = 1;
+  const int r = device_alloc(&q, count * sizeof(T));
+  if (r != FASW_OK) return r;
   c->allocs.push_back(q);
   *p = static_cast<T*>(q);
   return FASW_OK;
+}
+
+// The device error word records a bounded wait that ran out.  Each call that runs sweeps clears
+// it first (on the stream, so a captured cycle clears it too) and reads it at its end, so a
+// timeout is reported by the call in which it happened and later calls start clean.
+void err_clear(fasw_ctx* c) { cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st); }
+
+int err_read(fasw_ctx* c) {
+  CKR(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CKR(cudaStreamSynchronize(c->st));
+  return *c->h_err ? FASW_ERR_DEVICE_TIMEOUT : FASW_OK;
 }
 
 cudaEvent_t pool_get(fasw_ctx* c) {
@@ -278,6 +316,7 @@ int sync(fasw_ctx* c) {
 
 void enqueue_cycle(fasw_ctx* c, double cfl) {
   const int Lf = c->L();
+  err_clear(c);
   if (c->prm.turb) {
     bc_aux(c, Lf, cfl, 0);
     { Prof p(c, FASW_K_BL); launch_bl(c->lev[Lf], c->ph, c->st); }
@@ -469,7 +508,7 @@ void fasw_destroy(fasw_ctx* c) {
     c->event_pool.push_back(q.b);
   }
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
-  for (void* q : c->allocs) cudaFree(q);
+  for (void* q : c->allocs) device_free(q);
   if (c->h_norm) cudaFreeHost(c->h_norm);
   if (c->h_err) cudaFreeHost(c->h_err);
   adj_release(c->adj);
@@ -571,6 +610,7 @@ int fasw_precond_apply(fasw_ctx* c, int l, double cfl, const double* rin, double
     launch_sgs_prep(L, c->mixed, level_sweep_kind(c, L), c->st);
     ++c->launches;
   }
+  err_clear(c);
   run_sweep(c, L, 0, 0.0, c->d_tmp2);
   const double* zsrc = L.yz64;
   if (c->mixed) {
@@ -580,7 +620,8 @@ int fasw_precond_apply(fasw_ctx* c, int l, double cfl, const double* rin, double
   }
   r = copy_out(c, z, zsrc, m, on_device);
   if (r) return r;
-  return sync(c);
+  r = sync(c);
+  return r ? r : err_read(c);
 }
 
 int fasw_face_blocks(fasw_ctx* c, int l, double* axp, double* axm, double* aep, double* aem, int on_device) {
@@ -605,8 +646,10 @@ int fasw_face_blocks(fasw_ctx* c, int l, double* axp, double* axm, double* aep, 
 
 int fasw_smooth(fasw_ctx* c, int l, int nsteps, double cfl) {
   if (check_level(c, l) || nsteps < 0) return FASW_ERR_ARG;
+  err_clear(c);
   for (int k = 0; k < nsteps; ++k) smooth_step(c, l, cfl, false);
-  return sync(c);
+  int r = sync(c);
+  return r ? r : err_read(c);
 }
 
 int fasw_fas_cycle(fasw_ctx* c, int cycle_index, double* res_norm) {
@@ -775,6 +818,21 @@ int fasw_check_math(int n, const double* a, const double* b, double* out, int on
   if (e == cudaSuccess) e = cudaMemcpy(out, d + 2 * m, 4 * m * sizeof(double), cudaMemcpyDeviceToHost);
   cudaFree(d);
   return e == cudaSuccess ? FASW_OK : cuda_fail(e);
+}
+
+void fasw_fault_inject_alloc(long long n) { g_fail_alloc_in.store(n < 0 ? -1 : n); }
+
+long long fasw_live_allocations(void) { return g_live_allocs.load(); }
+
+int fasw_scheme_coefficients(int scheme, int* nstages, double* alpha, double* beta) {
+  if (scheme < 0 || scheme > 7 || !nstages) return FASW_ERR_ARG;
+  const Coef& cf = kCoef[scheme % 4];
+  *nstages = cf.s;
+  for (int k = 0; k < cf.s; ++k) {
+    if (alpha) alpha[k] = cf.a[k];
+    if (beta) beta[k] = cf.b[k];
+  }
+  return FASW_OK;
 }
 
 // ---------------------------------------------------------------- batched cases

@@ -74,4 +74,8 @@ int check_level(fasw_ctx* c, int l);
 int copy_in(fasw_ctx* c, double* dst, const double* src, size_t count, int on_device);
 int copy_out(fasw_ctx* c, double* dst, const double* src, size_t count, int on_device);
 int sync(fasw_ctx* c);
+// device error word of the bounded waits: cleared on the stream at the start of a call that runs
+// sweeps, read (with a stream synchronize) at its end
+void err_clear(fasw_ctx* c);
+int err_read(fasw_ctx* c);
 }  // namespace fasw

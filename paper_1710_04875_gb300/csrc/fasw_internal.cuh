@@ -38,6 +38,11 @@ inline cudaError_t launch_pdl(void (*kernel)(KP...), dim3 grid, dim3 block, size
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KP>(args)...);
 }
 
+// Every device allocation of the library goes through these (fasw_api.cu): they honour the
+// host-side failure injection and keep the count of live allocations.
+int device_alloc(void** q, size_t bytes);
+void device_free(void* q);
+
 struct LevelDev {
   int ni, nj, nw;
   int P;        // ghost pitch ni + 4
@@ -135,11 +140,11 @@ struct ResArgs {
 };
 
 // ---- launchers (kernels_residual.cu)
-void launch_bc(const LevelDev& L, const PhysParams& ph, cudaStream_t st);
-void launch_cell_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st);
+cudaError_t launch_bc(const LevelDev& L, const PhysParams& ph, cudaStream_t st);
+cudaError_t launch_cell_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st);
 // ghost fill and cell auxiliaries in one launch
 void launch_bc_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st);
-void launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, cudaStream_t st);
+cudaError_t launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, cudaStream_t st);
 int residual_blocks(const LevelDev& L);
 void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* out, cudaStream_t st);
 void launch_bl(const LevelDev& L, const PhysParams& ph, cudaStream_t st);
@@ -159,6 +164,6 @@ void launch_sgs(const LevelDev& L, const SchemeParams& sc, int mixed, int do_upd
 void launch_copy_u0(const LevelDev& L, cudaStream_t st);
 void launch_restrict(const LevelDev& F, const LevelDev& C, int restrict_mut, cudaStream_t st);
 void launch_prolong(const LevelDev& F, const LevelDev& C, cudaStream_t st);
-void launch_pack(const LevelDev& L, const double* interior_in, int to_ghosted, double* out, cudaStream_t st);
+cudaError_t launch_pack(const LevelDev& L, const double* interior_in, int to_ghosted, double* out, cudaStream_t st);
 
 }  // namespace fasw

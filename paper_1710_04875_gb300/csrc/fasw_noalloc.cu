@@ -62,9 +62,17 @@ size_t carve(LevelDev& L, double* base) {
 extern "C" int fasw_residual_noalloc(int ni, int nj, int n_wake, const double* x, const double* y,
                                      const double* u, double* F, const fasw_params* p, void* stream) {
   if (!x || !y || !u || !F || !p) return FASW_ERR_ARG;
-  if (ni < 4 || nj < 2 || n_wake < 0 || 2 * n_wake >= ni || p->turb != 0 || !(p->mach > 0.0) ||
+  if (ni < 4 || nj < 2 || n_wake < 0 || n_wake >= ni / 2 + (ni % 2) || p->turb != 0 || !(p->mach > 0.0) ||
       (p->viscous && !(p->re > 0.0)))
     return FASW_ERR_ARG;
+  // The scratch need in 64-bit arithmetic from the raw sizes, before any int product of them
+  // is formed: a grid that cannot fit is rejected here, whatever its size.
+  {
+    const unsigned long long I = (unsigned long long)ni, J = (unsigned long long)nj;
+    const unsigned long long G = (I + 4) * (J + 4), n = I * J;
+    const unsigned long long need = 7 * G + 20 * n + 64 * 32;  // every sub-array padded to 32 doubles
+    if (need > (unsigned long long)kScratchDoubles) return FASW_ERR_TOO_LARGE;
+  }
   LevelDev L;
   std::memset(&L, 0, sizeof(L));
   L.ni = ni;
@@ -123,15 +131,15 @@ extern "C" int fasw_residual_noalloc(int ni, int nj, int n_wake, const double* x
       cudaMemsetAsync(L.s, 0, 4 * (size_t)L.n * sizeof(double), st) != cudaSuccess ||
       cudaMemsetAsync(L.src, 0, 4 * (size_t)L.n * sizeof(double), st) != cudaSuccess)
     return FASW_ERR_CUDA;
-  launch_metrics_fine(L, x, y, st);
-  launch_fill_state(L, ph.uinf, st);
-  launch_pack(L, u, 1, nullptr, st);
-  launch_bc(L, ph, st);
-  launch_cell_aux(L, ph, 1.0, 0, st);
   ResArgs a;
   std::memset(&a, 0, sizeof(a));
   a.mode = RES_FULL;
   a.F = F;
-  launch_residual(L, ph, a, st);
-  return cudaGetLastError() == cudaSuccess ? FASW_OK : FASW_ERR_CUDA;
+  // each launch's own status: an error left by unrelated earlier work is neither reported
+  // nor cleared here
+  if (launch_metrics_fine(L, x, y, st) != cudaSuccess || launch_fill_state(L, ph.uinf, st) != cudaSuccess ||
+      launch_pack(L, u, 1, nullptr, st) != cudaSuccess || launch_bc(L, ph, st) != cudaSuccess ||
+      launch_cell_aux(L, ph, 1.0, 0, st) != cudaSuccess || launch_residual(L, ph, a, st) != cudaSuccess)
+    return FASW_ERR_CUDA;
+  return FASW_OK;
 }

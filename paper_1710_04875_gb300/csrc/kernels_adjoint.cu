@@ -34,7 +34,8 @@ constexpr size_t PARTS = (size_t)RED_BLOCKS * MAXV + 2 * MAXV;  // partials, row
 template <typename T>
 int adj_alloc(std::vector<void*>& allocs, T** p, size_t count) {
   void* q = nullptr;
-  if (cudaMalloc(&q, (count ? count : 1) * sizeof(T)) != cudaSuccess) return FASW_ERR_OOM;
+  const int r = device_alloc(&q, (count ? count : 1) * sizeof(T));
+  if (r != FASW_OK) return r;
   allocs.push_back(q);
   *p = static_cast<T*>(q);
   return FASW_OK;

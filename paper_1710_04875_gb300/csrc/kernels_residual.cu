@@ -666,14 +666,14 @@ void launch_check_math(int n, const double* a, const double* b, double* out, cud
   if (n > 0) k_check_math<<<(n + 127) / 128, 128, 0, st>>>(n, a, b, out);
 }
 
-void launch_bc(const LevelDev& L, const PhysParams& ph, cudaStream_t st) {
+cudaError_t launch_bc(const LevelDev& L, const PhysParams& ph, cudaStream_t st) {
   const int nt = 4 * L.ni + 4 * L.nj;
-  launch_pdl(k_bc, (nt + 63) / 64, 64, 0, st, L, ph);
+  return launch_pdl(k_bc, (nt + 63) / 64, 64, 0, st, L, ph);
 }
 
-void launch_cell_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st) {
+cudaError_t launch_cell_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st) {
   const int nbi = (L.n + 63) / 64, nbg = (4 * (L.ni + L.nj) + 63) / 64;
-  launch_pdl(k_cell_aux, nbi + nbg, 64, 0, st, L, ph, cfl, want_dts, 0, nbi);
+  return launch_pdl(k_cell_aux, nbi + nbg, 64, 0, st, L, ph, cfl, want_dts, 0, nbi);
 }
 
 void launch_bc_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st) {
@@ -690,14 +690,13 @@ int residual_blocks(const LevelDev& L) {
   return ((L.ni + TX - 1) / TX) * ((L.nj + ty - 1) / ty);
 }
 
-void launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, cudaStream_t st) {
+cudaError_t launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, cudaStream_t st) {
   if (res_ty(L) == 4) {
     dim3 grid((L.ni + TX - 1) / TX, (L.nj + 3) / 4);
-    launch_pdl(k_residual<4>, grid, res_threads(4), 0, st, L, ph, a);
-  } else {
-    dim3 grid((L.ni + TX - 1) / TX, L.nj);
-    launch_pdl(k_residual<1>, grid, res_threads(1), 0, st, L, ph, a);
+    return launch_pdl(k_residual<4>, grid, res_threads(4), 0, st, L, ph, a);
   }
+  dim3 grid((L.ni + TX - 1) / TX, L.nj);
+  return launch_pdl(k_residual<1>, grid, res_threads(1), 0, st, L, ph, a);
 }
 
 void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* out, cudaStream_t st) {

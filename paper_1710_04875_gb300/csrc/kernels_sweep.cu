@@ -23,6 +23,7 @@
 //    every CHUNK steps (fence + flag); the consumer copies the boundary row of a whole
 //    chunk at once.  Every wait is bounded; on timeout the kernel raises an error flag and
 //    all strips return.
+#include <atomic>
 #include "fasw_internal.cuh"
 #include "fasw_sweep.cuh"
 
@@ -713,6 +714,22 @@ void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st) {
 }
 
 namespace {
+// The dynamic shared-memory limit is a per-device attribute of a kernel: set it once on each
+// device that launches the kernel (slot: which kernel).  Two host threads may both set it the
+// first time; the call is idempotent.
+constexpr int kAttrDevices = 64;
+std::atomic<unsigned long long> g_attr_done[4];
+
+template <typename Kernel>
+void smem_attr_once(Kernel k, int bytes, int slot) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return;
+  const unsigned long long bit = dev < kAttrDevices ? 1ull << dev : 0ull;
+  if (bit && (g_attr_done[slot].load(std::memory_order_acquire) & bit)) return;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess && bit)
+    g_attr_done[slot].fetch_or(bit, std::memory_order_acq_rel);
+}
+
 int hp_threads(int nj) { return 4 * ((nj + 7) / 8 * 8); }
 int hp_stages(int nt) { return nt <= 256 ? 8 : 4; }  // 512 and 1024 threads: ring of 4 keeps shared memory < 227 KB
 constexpr size_t kHpSmemMax = 227 * 1024;
@@ -735,18 +752,10 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
     if (hp_smem_bytes(stages, nt, nt / 4, L.ni, L.nw) > kHpSmemMax) stages = 4;  // hp_fits checked 4 or 8
     const size_t sm = hp_smem_bytes(stages, nt, nt / 4, L.ni, L.nw);
     if (stages == 8) {
-      static bool attr8 = false;
-      if (!attr8) {
-        cudaFuncSetAttribute(k_sweep_hp<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHpSmemMax);
-        attr8 = true;
-      }
+      smem_attr_once(k_sweep_hp<8>, (int)kHpSmemMax, 0);
       launch_pdl(k_sweep_hp<8>, 1, nt, sm, st, L);
     } else {
-      static bool attr4 = false;
-      if (!attr4) {
-        cudaFuncSetAttribute(k_sweep_hp<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHpSmemMax);
-        attr4 = true;
-      }
+      smem_attr_once(k_sweep_hp<4>, (int)kHpSmemMax, 1);
       launch_pdl(k_sweep_hp<4>, 1, nt, sm, st, L);
     }
     launch_pdl(k_hp_finish, (L.n + 63) / 64, 64, 0, st, L, do_update, aw, alpha);
@@ -762,20 +771,12 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
     threads = (threads + 31) / 32 * 32;
     if (mixed) {
       const size_t sm = 2 * (size_t)L.ni * 4 * sizeof(float);
-      static bool attr_f = false;
-      if (!attr_f) {
-        cudaFuncSetAttribute(k_sweep_cta<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_f = true;
-      }
+      smem_attr_once(k_sweep_cta<float>, 200 * 1024, 2);
       launch_pdl(k_sweep_cta<float>, 1, threads, sm, st, L, reinterpret_cast<const float*>(L.tb), L.yz32, rhs, do_update, aw,
                                                  alpha);
     } else {
       const size_t sm = 2 * (size_t)L.ni * 4 * sizeof(double);
-      static bool attr_d = false;
-      if (!attr_d) {
-        cudaFuncSetAttribute(k_sweep_cta<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_d = true;
-      }
+      smem_attr_once(k_sweep_cta<double>, 200 * 1024, 3);
       launch_pdl(k_sweep_cta<double>, 1, threads, sm, st, L, L.tb, L.yz64, rhs, do_update, aw, alpha);
     }
     return 1;

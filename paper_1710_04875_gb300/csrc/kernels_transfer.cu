@@ -226,11 +226,11 @@ __global__ void k_blocks_transpose(const double* a, double* b, int nf) {
 
 }  // namespace
 
-void launch_metrics_fine(const LevelDev& L, const double* x, const double* y, cudaStream_t st, int rotate, double phi,
-                         double phidot, double xc, double yc) {
+cudaError_t launch_metrics_fine(const LevelDev& L, const double* x, const double* y, cudaStream_t st, int rotate,
+                                double phi, double phidot, double xc, double yc) {
   const int m = L.nfx > L.nfe ? L.nfx : L.nfe;
   Motion mo{cos(phi), sin(phi), phidot, xc, yc, rotate};
-  launch_pdl(k_metrics_fine, (m + 127) / 128, 128, 0, st, L, x, y, mo);
+  return launch_pdl(k_metrics_fine, (m + 127) / 128, 128, 0, st, L, x, y, mo);
 }
 
 // Dual-time source of the finest level: src = c1 u^n + c2 u^(n-1)
@@ -249,8 +249,8 @@ void launch_agglomerate(const LevelDev& F, const LevelDev& C, cudaStream_t st) {
   launch_pdl(k_agglomerate, (m + 127) / 128, 128, 0, st, F, C);
 }
 
-void launch_fill_state(const LevelDev& L, const double w[4], cudaStream_t st) {
-  launch_pdl(k_fill_state, (L.Gn + 255) / 256, 256, 0, st, L, w[0], w[1], w[2], w[3]);
+cudaError_t launch_fill_state(const LevelDev& L, const double w[4], cudaStream_t st) {
+  return launch_pdl(k_fill_state, (L.Gn + 255) / 256, 256, 0, st, L, w[0], w[1], w[2], w[3]);
 }
 
 void launch_copy_u0(const LevelDev& L, cudaStream_t st) { launch_pdl(k_copy_u0, (L.n + 255) / 256, 256, 0, st, L); }
@@ -263,8 +263,8 @@ void launch_prolong(const LevelDev& F, const LevelDev& C, cudaStream_t st) {
   launch_pdl(k_prolong, (F.n + 63) / 64, 64, 0, st, F, C);
 }
 
-void launch_pack(const LevelDev& L, const double* in, int to_ghosted, double* out, cudaStream_t st) {
-  launch_pdl(k_pack, (L.n + 255) / 256, 256, 0, st, L, in, to_ghosted, out);
+cudaError_t launch_pack(const LevelDev& L, const double* in, int to_ghosted, double* out, cudaStream_t st) {
+  return launch_pdl(k_pack, (L.n + 255) / 256, 256, 0, st, L, in, to_ghosted, out);
 }
 
 void launch_f2d(const float* a, double* b, int m, cudaStream_t st) { launch_pdl(k_f2d, (m + 255) / 256, 256, 0, st, a, b, m); }

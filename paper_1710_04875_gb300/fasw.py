@@ -44,17 +44,20 @@ class Params(C.Structure):
 
 
 _lib = None
+_libs: dict = {}
 
 
-def library_path() -> str:
-    return _build.LIB
+def library_path(variant: str = "perf") -> str:
+    return _build.lib_path(variant)
 
 
-def library():
-    """Load libfasw.so (building it first when sources are newer)."""
+def library(variant: str = "perf"):
+    """Load the CUDA library (building it first when sources are newer).  variant "perf" is
+    libfasw.so (FMA contraction on); "parity" is libfasw_parity.so, the same sources built
+    with -fmad=false, for comparisons with a CPU reference compiled without contraction."""
     global _lib
-    if _lib is None:
-        path = _build.build()
+    if variant not in _libs:
+        path = _build.build(variant=variant)
         if not os.path.exists(path):
             raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
         lib = C.CDLL(path)
@@ -109,6 +112,9 @@ def library():
             "fasw_batch_solve": (i, [p, d, i, dp, dp, C.POINTER(i)]),
             "fasw_batch_autotune": (i, [p, dp]),
             "fasw_batch_launch_count": (ll, [p]),
+            "fasw_scheme_coefficients": (i, [i, C.POINTER(i), dp, dp]),
+            "fasw_fault_inject_alloc": (None, [ll]),
+            "fasw_live_allocations": (ll, []),
             "fasw_strerror": (C.c_char_p, [i]),
             "fasw_last_cuda_error": (C.c_char_p, []),
         }
@@ -116,8 +122,10 @@ def library():
             fn = getattr(lib, name)
             fn.restype = res
             fn.argtypes = args
-        _lib = lib
-    return _lib
+        _libs[variant] = lib
+        if variant == "perf":
+            _lib = lib
+    return _libs[variant]
 
 
 def default_params(**kw) -> Params:
@@ -152,8 +160,8 @@ def _ptr(a):
 class Solver:
     """One solver context on one grid; methods mirror the C entry points."""
 
-    def __init__(self, grid, params: Params, stream=None, coords_on_device=False):
-        self.lib = library()
+    def __init__(self, grid, params: Params, stream=None, coords_on_device=False, variant="perf"):
+        self.lib = library(variant)
         self.grid = grid
         self.params = params
         x, y = grid.coords() if not coords_on_device else grid

@@ -69,3 +69,30 @@ def test_product_package_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text and "fasw_oracle" not in text, f
+
+
+def test_noalloc_rejects_oversized_dimensions_before_touching_the_device():
+    """Sizes whose int products would overflow are rejected from 64-bit arithmetic on the raw
+    sizes, before any pointer is used (host arrays stand in for the device pointers here)."""
+    import numpy as np
+    import paper_1710_04875_gb300 as P
+    lib = P.library()
+    p = P.default_params(nlevels=1)
+    buf = np.zeros(16)
+    ptr = buf.ctypes.data
+    for ni, nj in [(1 << 20, 1 << 20), (2**31 - 1, 4), (4, 2**31 - 1), (70000, 70000), (512, 128)]:
+        nw = ni // 8
+        rc = lib.fasw_residual_noalloc(ni, nj, nw, ptr, ptr, ptr, ptr, ctypes.byref(p), None)
+        assert rc == -7, (ni, nj, rc)
+    assert lib.fasw_residual_noalloc(64, 16, 2**31 - 1, ptr, ptr, ptr, ptr, ctypes.byref(p), None) == -1
+
+
+def test_scheme_coefficients_and_fault_injection_are_host_only():
+    import paper_1710_04875_gb300 as P
+    lib = P.library()
+    lib.fasw_live_allocations.restype = ctypes.c_longlong
+    lib.fasw_fault_inject_alloc.argtypes = [ctypes.c_longlong]
+    assert lib.fasw_live_allocations() >= 0
+    lib.fasw_fault_inject_alloc(-1)
+    ns = ctypes.c_int()
+    assert lib.fasw_scheme_coefficients(0, ctypes.byref(ns), None, None) == 0 and ns.value == 3

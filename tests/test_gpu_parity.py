@@ -102,7 +102,7 @@ def test_preconditioner_apply_parity(scheme, ni, nj, nw):
     assert rel_err(zg, zo) < 1e-11
 
 
-@pytest.mark.parametrize("scheme", ["AW3", "ARK3J", "AW5J"])
+@pytest.mark.parametrize("scheme", ["AW3", "ARK3J", "AW5J", "AW51", "AW52", "ARK5J", "ARK51", "ARK52"])
 def test_smoothing_step_parity(scheme):
     ni, nj, nw = 64, 16, 8
     g = make_cgrid(ni, nj, n_wake=nw)
@@ -231,18 +231,6 @@ def test_mixed_ark_stage_update_tracks_fp64(sweep):
     ha = np.array([a.fas_cycle(k) for k in range(15)])
     hb = np.array([b.fas_cycle(k) for k in range(15)])
     assert np.all(np.abs(hb - ha) <= 1e-4 * ha)
-
-
-def test_solver_reports_divergence_not_garbage():
-    g = make_cgrid(32, 8)
-    import paper_1710_04875_gb300 as P
-    from tests.helpers import pair_params
-    _, p = pair_params(scheme="ARK3J", nlevels=2, cfl=50.0, cfl_ramp=50.0)
-    s = P.Solver(g, p)
-    code, nc, hist = s.solve(1e-6, 60)
-    assert code in (0, -4, -6)
-    if code == -4:
-        assert not np.isfinite(hist[-1]) or hist[-1] > 1e8 * hist[0]
 
 
 def test_graph_replayed_cycles_equal_eager_cycles():
