@@ -1,11 +1,15 @@
-"""Benchmark: FAS cycles of the preconditioned AW3 smoother on the 256x64 thin-layer RANS
-C-grid workload (M = 0.5, Re = 1e7, wall spacing 1e-5, 4-level W-cycle, Baldwin-Lomax).
+"""Benchmark: FAS W-cycles of the preconditioned AW3 smoother on the 1024x256 thin-layer RANS
+C-grid (M = 0.75, Re = 6.5e6, wall spacing 1e-5, 5 levels, Baldwin-Lomax), the largest
+configuration that runs on one GPU.
 
-One step = one FAS cycle over the whole grid (all steps of the method's hot path).  Prints
-one JSON line.  Metric: Mcell-iterations/s (fine cells x cycles / s), plus the wall time to a
-6-order residual drop for the FP64 and the mixed-precision preconditioner.
+One step = one FAS cycle over the whole grid (every step of the method's hot path).  Prints
+one JSON line.  Metric: Mcell-iterations/s (fine cells x cycles / s), beside the wall time to a
+6-order residual drop for the FP64 and the mixed-precision preconditioner and the HBM roofline
+of the dominant kernel.  Extras (rank 0, one GPU): the 256x64 and 512x128 workloads, pitching
+steps to 11 orders, the batched cases, the adjoints and the CPU oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision fp64|mixed]
+                  [--quick]
 
 Multi-GPU: the exact method does not shard (the SGS sweep is one global wavefront), so N GPUs
 run N independent replicas of the same case; value = all ranks' cell-iterations / max time.
@@ -15,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -27,20 +32,33 @@ sys.path.insert(0, ROOT)
 
 from synth.cgrid import make_cgrid  # noqa: E402
 
-WORKLOAD = dict(name="rans_256x64_thin_layer_bl", ni=256, nj=64, n_wake=32, wall_spacing=1e-5,
-                mach=0.5, alpha_deg=0.0, re=1e7, nlevels=4, gamma_cycle=2, scheme="AW3", eta=0.8,
-                d_cut=0.5, cfl=100.0, cfl_ramp=20.0, ramp_cycles=2, viscous=1, turb=1)
+_RANS = dict(scheme="AW3", eta=0.8, d_cut=0.5, cfl=100.0, cfl_ramp=20.0, ramp_cycles=2, viscous=1, turb=1,
+             gamma_cycle=2, alpha_deg=0.0)
+HEADLINE = dict(name="rans_1024x256_thin_layer_bl", ni=1024, nj=256, n_wake=128, wall_spacing=1e-5, mach=0.75,
+                re=6.5e6, nlevels=5, **_RANS)
+C2 = dict(name="rans_256x64_thin_layer_bl", ni=256, nj=64, n_wake=32, wall_spacing=1e-5, mach=0.5, re=1e7,
+          nlevels=4, **_RANS)
+C3 = dict(name="rans_512x128_thin_layer_bl", ni=512, nj=128, n_wake=64, wall_spacing=1e-5, mach=0.8, re=1e6,
+          nlevels=4, **_RANS)
+WORKLOAD = HEADLINE
 METRIC = "Mcell-iter/s"
 L2_FLUSH_BYTES = 256 << 20
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 peak from unit counts and clock: 152 SMs x 4 FP64 flop/clk (2 DFMA) x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-# algorithmic FP64 flops per cell and launch, counted from the kernels (FMA = 2)
-FLOPS_PER_CELL = {"sgs": 230.0, "residual": 310.0, "face_blocks": 380.0, "diag_blocks": 100.0}
-# DRAM bytes per cell of one FP64 strip-sweep launch (dram__bytes_read.sum + write, cold caches):
-# 11.6 MB for the 16,384 cells of the finest 256x64 level (profiles/sweep_strips_fp64_dram_rans_256x64.md);
-# the traffic is the transfer blocks and vectors of each cell, so it scales with the cells
-SWEEP_DRAM_BYTES_PER_CELL = 11.6e6 / 16384
+HBM_FALLBACK_GBS = 6800.0
+# Algorithmic DRAM bytes per cell of one launch of each kernel class (the compulsory traffic:
+# every input read once, every output written once), by preconditioner precision.
+#   sgs, FP64 strip sweep (forward + backward + stage update): transfer blocks D^-1, G_W, G_S,
+#     H_E, H_N (80 doubles) + right-hand side (4) + u^(0) (4) read, u written (4): 736 B;
+#   sgs, FP32 hyperplane-staged sweep: D^-1 (16 floats) and r (4 doubles) read, D^-1 r written
+#     and read (4 + 4 floats), G_W G_S and H_E H_N (64 floats) read, y written and read (8
+#     floats), z (4 floats) + u^(0) (4 doubles) read, u written (4 doubles): 528 B;
+#   residual: ghosted u (4), p, q, 1/rho, radii (2), dt*, volume, mu_t, face vectors (4) read,
+#     the stage right-hand side and the F^v carry written and the carry read (12): 232 B.
+BYTES_PER_CELL = {"fp64": {"sgs": 736.0, "residual": 232.0}, "mixed": {"sgs": 528.0, "residual": 232.0}}
+# DRAM traffic per cell of one launch of the dominant kernel, from an ncu capture of a finest-level
+# launch (dram__bytes_read.sum + dram__bytes_write.sum over the cells of that launch); None where
+# no capture of the current kernel exists.
+DRAM_BYTES_PER_CELL = {"fp64": {"sgs": None}, "mixed": {"sgs": None}}
 
 
 def level_visits(nlevels, gamma):
@@ -134,32 +152,56 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload_grid():
-    w = WORKLOAD
+def grid_of(w):
     return make_cgrid(w["ni"], w["nj"], n_wake=w["n_wake"], wall_spacing=w["wall_spacing"])
 
 
+def workload_grid():
+    return grid_of(WORKLOAD)
+
+
+def params_of(P, w, precision, **over):
+    kw = dict(scheme=w["scheme"], nlevels=w["nlevels"], gamma_cycle=w["gamma_cycle"], viscous=w["viscous"],
+              turb=w["turb"], sensor=1, mach=w["mach"], alpha_deg=w["alpha_deg"], re=w["re"], eta=w["eta"],
+              d_cut=w["d_cut"], cfl=w["cfl"], cfl_ramp=w["cfl_ramp"], ramp_cycles=w["ramp_cycles"],
+              precision=precision)
+    kw.update(over)
+    return P.default_params(**kw)
+
+
 def gpu_params(P, precision):
-    w = WORKLOAD
-    return P.default_params(scheme=w["scheme"], nlevels=w["nlevels"], gamma_cycle=w["gamma_cycle"],
-                            viscous=w["viscous"], turb=w["turb"],
-                            sensor=1, mach=w["mach"], alpha_deg=w["alpha_deg"], re=w["re"], eta=w["eta"],
-                            d_cut=w["d_cut"], cfl=w["cfl"], cfl_ramp=w["cfl_ramp"], ramp_cycles=w["ramp_cycles"],
-                            precision=precision)
+    return params_of(P, WORKLOAD, precision)
+
+
+def oracle_of(w, variant="timing", grid=None):
+    import oracle as O
+    p = O.make_params(w["scheme"], nlevels=w["nlevels"], gamma_cycle=w["gamma_cycle"], viscous=w["viscous"],
+                      turb=w["turb"], sensor=1, mach=w["mach"], alpha_deg=w["alpha_deg"], re=w["re"], eta=w["eta"],
+                      d_cut=w["d_cut"], cfl=w["cfl"], cfl_ramp=w["cfl_ramp"], ramp_cycles=w["ramp_cycles"])
+    return O.Oracle(grid if grid is not None else grid_of(w), p, variant=variant)
 
 
 def oracle_solver():
-    import oracle as O
-    w = WORKLOAD
-    p = O.make_params(w["scheme"], nlevels=w["nlevels"], gamma_cycle=w["gamma_cycle"], viscous=w["viscous"],
-                      turb=w["turb"], sensor=1,
-                      mach=w["mach"], alpha_deg=w["alpha_deg"], re=w["re"], eta=w["eta"], d_cut=w["d_cut"],
-                      cfl=w["cfl"], cfl_ramp=w["cfl_ramp"], ramp_cycles=w["ramp_cycles"])
-    return O.Oracle(workload_grid(), p)
+    return oracle_of(WORKLOAD)
 
 
-def cpu_oracle_sample(budget_s=12.0, max_cycles=400, min_cycles=3):
-    """Time the oracle (as it stands, one host thread) on consecutive cycles of the workload."""
+def host_cpu():
+    """CPU model and logical core count of this host."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"model": model, "machine": platform.machine(), "nproc": os.cpu_count()}
+
+
+def cpu_oracle_sample(budget_s=15.0, max_cycles=200, min_cycles=3):
+    """Time the oracle (its -O3 timing build, as it stands, one host thread) on consecutive
+    cycles of the headline workload from the free stream."""
     o = oracle_solver()
     ncell = WORKLOAD["ni"] * WORKLOAD["nj"]
     t0 = time.perf_counter()
@@ -169,8 +211,8 @@ def cpu_oracle_sample(budget_s=12.0, max_cycles=400, min_cycles=3):
         k += 1
     dt = time.perf_counter() - t0
     return {"value": ncell * k / dt / 1e6, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{k} FAS cycles of the 256x64 RANS workload from the free stream, single thread, "
-                      f"{dt:.1f} s"}
+            "sample": f"{k} FAS W-cycles of the {WORKLOAD['name']} workload from the free stream, one host "
+                      f"thread, oracle timing build (-O3), {dt:.1f} s", "host": host_cpu()}
 
 
 def run_reference(args, rank, world):
@@ -191,10 +233,10 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD["name"], "cells": ncell, "levels": WORKLOAD["nlevels"],
-                                             "l2": "host run"},
+                                             "cycle": "W", "l2": "host run"},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} timed FAS cycles after {args.warmup} warm-up cycles, "
-                                       "single host thread"},
+                             "sample": f"{args.steps} timed FAS W-cycles after {args.warmup} warm-up cycles, one "
+                                       "host thread, oracle timing build (-O3)", "host": host_cpu()},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -216,24 +258,83 @@ def time_cycles(s, stream, flush, steps, k0):
     return ms
 
 
-def measure_c3(P, stream, flush, steps, warmup):
-    """W-cycle device time on the 512 x 128 C-grid of the pitching case (thin-layer RANS with
-    Baldwin-Lomax, M 0.8, Re 1e6, 4 levels), FP64 and mixed precision, from the free stream."""
-    from synth.cases import config_c3
-    c = config_c3()
-    g = c.grid()
-    out = {"cells": g.ni * g.nj}
+def measure_wcycles(P, w, stream, flush, steps, warmup):
+    """W-cycle device time of a workload in both precisions, from the free stream."""
+    g = grid_of(w)
+    out = {"workload": w["name"], "cells": g.ni * g.nj}
     for prec in ("fp64", "mixed"):
-        p = P.default_params(scheme="AW3", nlevels=4, gamma_cycle=2, viscous=1, turb=1, sensor=1, mach=c.mach,
-                             alpha_deg=0.0, re=c.reynolds, eta=0.8, d_cut=0.5, cfl=100.0, cfl_ramp=20.0,
-                             ramp_cycles=2, precision=prec)
-        s = P.Solver(g, p, stream=stream.cuda_stream)
+        s = P.Solver(g, params_of(P, w, prec), stream=stream.cuda_stream)
         for k in range(warmup):
             s.fas_cycle(k)
         ms = time_cycles(s, stream, flush, steps, warmup)
         out[prec] = {"ms_per_cycle": sum(ms) / len(ms), "value": g.ni * g.nj * len(ms) / (sum(ms) / 1e3) / 1e6,
                      "unit": METRIC}
         s.close()
+    return out
+
+
+def solve_timed(s, drop, max_cycles):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    code, nc, hist = s.solve(drop, max_cycles)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "cycles": nc, "status": int(code),
+            "final_drop": float(hist[-1] / hist[0]) if len(hist) else None,
+            "rate": float((hist[-1] / hist[0]) ** (1.0 / max(nc - 1, 1))) if len(hist) > 1 else None}
+
+
+def measure_smoothers_c2(P, stream, max_cycles=1000):
+    """The 256x64 RANS workload from the free stream to a 6-order drop with AW3 (robust W
+    method, c* = 100) and with preconditioned ARK3J at c* = 1 (the value at which section 6.2
+    finds it at its stability limit), both FP64; a run that stops early records its status."""
+    g = grid_of(C2)
+    out = {"workload": C2["name"]}
+    for name, over in (("AW3", {}), ("ARK3J", dict(scheme="ARK3J", cfl=1.0, cfl_ramp=1.0))):
+        s = P.Solver(g, params_of(P, C2, "fp64", **over), stream=stream.cuda_stream)
+        out[name] = solve_timed(s, 1e-6, max_cycles)
+        out[name]["cfl"] = over.get("cfl", C2["cfl"])
+        s.close()
+    return out
+
+
+def measure_pitching_c3(P, stream, nsteps=4, max_cycles=1500):
+    """The pitching 512x128 RANS case (alpha = 2 deg sin(2kt), k = 0.2, 64 steps per period):
+    a steady start converged 6 orders (mixed precision), then the first nsteps physical steps
+    (implicit Euler, then BDF2), each converged 11 orders in pseudo time, once with the FP64 and
+    once with the mixed preconditioner from the same start; cycles and seconds per step and the
+    state gap between the two precisions after the last step."""
+    import torch
+    g = grid_of(C3)
+    s0 = P.Solver(g, params_of(P, C3, "mixed"), stream=stream.cuda_stream)
+    start = solve_timed(s0, 1e-6, 2000)
+    u0 = s0.get_state()
+    s0.close()
+    omega = 0.4
+    dt = 2.0 * np.pi / omega / 64
+    amp = np.radians(2.0)
+    out = {"workload": C3["name"], "steady_start": start, "dt": dt, "steps": {}}
+    final = {}
+    for prec in ("fp64", "mixed"):
+        s = P.Solver(g, params_of(P, C3, prec), stream=stream.cuda_stream)
+        s.set_state(u0)
+        rows = []
+        for step in range(1, nsteps + 1):
+            t = step * dt
+            s.set_motion(-amp * np.sin(omega * t), -amp * omega * np.cos(omega * t))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            code, nc, h = s.dual_time_step(dt, 1e-11, max_cycles)
+            torch.cuda.synchronize()
+            rows.append({"kind": "implicit Euler" if step == 1 else "BDF2", "seconds": time.perf_counter() - t0,
+                         "cycles": nc, "status": int(code), "final_drop": float(h[-1] / h[0]) if len(h) else None,
+                         "final_residual": float(h[-1]) if len(h) else None})
+        out["steps"][prec] = rows
+        final[prec] = s.get_state()
+        s.close()
+    out["state_gap_after_last_step"] = float(np.linalg.norm(final["mixed"] - final["fp64"])
+                                             / np.linalg.norm(final["fp64"]))
     return out
 
 
@@ -347,8 +448,8 @@ def adjoint_profile(P, iters=30):
     """One adjoint GMRES(250) solve of C_D with a fixed count of iterations on the workload grid
     (FP64, thin-layer RANS, frozen eddy viscosity) at a smoothly perturbed free stream, so that
     a kernel-filtered ncu launch list of this process shows the adjoint's kernels only."""
-    g = workload_grid()
-    s = P.Solver(g, gpu_params(P, "fp64"))
+    g = grid_of(C2)
+    s = P.Solver(g, params_of(P, C2, "fp64"))
     u = s.get_state()
     jj, ii = np.meshgrid(np.arange(g.nj), np.arange(g.ni), indexing="ij")
     u = u * (1.0 + 0.02 * np.sin(2 * np.pi * ii / g.ni) * np.cos(np.pi * jj / g.nj))[None]
@@ -358,7 +459,7 @@ def adjoint_profile(P, iters=30):
     lam, code, it, rr = s.adjoint_solve(1, tol=1e-14, max_iters=iters, restart=250)
     t = time.perf_counter() - t0
     s.close()
-    return {"adjoint_profile": WORKLOAD["name"], "gmres_iterations": it, "seconds": t,
+    return {"adjoint_profile": C2["name"], "gmres_iterations": it, "seconds": t,
             "ms_per_iteration": 1e3 * t / max(it, 1), "relative_residual": rr}
 
 
@@ -394,68 +495,176 @@ def measure_unsteady_adjoint(P, stream, nsteps=128, snapshots=8, n_bumps=16):
                     "steady adjoint of the initial state"}
 
 
-def measure_batched(P, stream, flush, steps, warmup, precision="mixed"):
-    """64 uneven Euler cases (128x32 .. 512x128 cells, seeded M, alpha, thickness) advanced
-    together, one captured CUDA graph per cycle; sweep variants chosen by the autotuner."""
-    import torch
+def _c4_inputs(P, precision):
     from synth.cases import config_c4_cases
     cases = config_c4_cases()
-    grids, params = [], []
-    for c in cases:
-        grids.append(c.grid())
-        params.append(P.default_params(scheme="AW3", nlevels=c.levels, mach=c.mach, alpha_deg=c.alpha_deg,
-                                       cfl=100.0, precision=precision))
-    cells = sum(g.ni * g.nj for g in grids)
-    b = P.fasw.Batch(grids, params, stream=stream.cuda_stream)
-    choice = b.autotune()
-    for k in range(warmup):
-        b.cycle(k)
-    ms = []
-    for k in range(steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b.cycle(warmup + k)
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    value = cells * steps / (sum(ms) / 1e3) / 1e6
-    b.close()
-    b = P.fasw.Batch(grids, params, stream=stream.cuda_stream)
-    b.autotune()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    code, cyc, drops, ncy = b.solve(1e-6, 300)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    b.close()
-    return {"cases": len(grids), "cells": cells, "precision": precision, "value": value, "unit": METRIC,
+    grids = [c.grid() for c in cases]
+    params = [P.default_params(scheme="AW3", nlevels=c.levels, mach=c.mach, alpha_deg=c.alpha_deg, cfl=100.0,
+                               precision=precision) for c in cases]
+    return cases, grids, params
+
+
+def measure_batched(P, stream, flush, steps, warmup, sequential=True):
+    """The 64 uneven Euler cases (128x32 .. 512x128 cells, seeded M, alpha, thickness):
+    (i) mixed precision batched (one captured CUDA graph per cycle, sweep variants from the
+    autotuner): cycle throughput and time until every case has dropped 6 orders; (ii) the same
+    batched in FP64; (iii) the plain FP64 path, one case after another, each to 6 orders."""
+    import torch
+    out = {}
+    for prec in ("mixed", "fp64"):
+        cases, grids, params = _c4_inputs(P, prec)
+        cells = sum(g.ni * g.nj for g in grids)
+        b = P.fasw.Batch(grids, params, stream=stream.cuda_stream)
+        choice = b.autotune()
+        for k in range(warmup):
+            b.cycle(k)
+        ms = []
+        for k in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.cycle(warmup + k)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        b.close()
+        b = P.fasw.Batch(grids, params, stream=stream.cuda_stream)
+        b.autotune()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        code, cyc, drops, ncy = b.solve(1e-6, 400)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        b.close()
+        out["batched_" + prec] = {
+            "cases": len(grids), "cells": cells, "value": cells * steps / (sum(ms) / 1e3) / 1e6, "unit": METRIC,
             "ms_per_cycle": sum(ms) / steps,
             "sweep_choice": {"staged8": choice.count(7), "staged4": choice.count(6), "staged": choice.count(5),
                              "cta": choice.count(2)},
             "time_to_6_orders": {"seconds": dt, "cycles_run": ncy, "status": int(code),
                                  "cases_converged": int((cyc > 0).sum()), "cases_diverged": int((cyc == -2).sum()),
                                  "median_cycles": float(np.median(cyc[cyc > 0])) if (cyc > 0).any() else None}}
+    if sequential:
+        cases, grids, params = _c4_inputs(P, "fp64")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        conv, cyc_total = 0, 0
+        for g, p in zip(grids, params):
+            s = P.Solver(g, p, stream=stream.cuda_stream)
+            code, nc, hist = s.solve(1e-6, 400)
+            conv += int(code == 0)
+            cyc_total += nc
+            s.close()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out["sequential_fp64"] = {"cases": len(grids), "seconds": dt, "cases_converged": conv,
+                                  "cycles_total": cyc_total,
+                                  "note": "one context per case, created, solved to 6 orders and destroyed in turn"}
+    return out
+
+
+def oracle_all_cores_c4(budget_cycles=2):
+    """The oracle (timing build, as it stands) over all host cores: one case per thread (ctypes
+    releases the interpreter lock during each call), each case running `budget_cycles` cycles
+    from the free stream; the throughput over the whole host."""
+    import oracle as O
+    from synth.cases import config_c4_cases
+    cases = config_c4_cases()
+    ncores = os.cpu_count() or 1
+    solvers = []
+    for c in cases:
+        p = O.make_params("AW3", nlevels=c.levels, mach=c.mach, alpha_deg=c.alpha_deg, cfl=100.0)
+        solvers.append((c.ni * c.nj, O.Oracle(c.grid(), p, variant="timing")))
+    todo = list(range(len(solvers)))
+    lock = threading.Lock()
+
+    def worker():
+        while True:
+            with lock:
+                if not todo:
+                    return
+                k = todo.pop()
+            for cyc in range(budget_cycles):
+                solvers[k][1].fas_cycle(cyc)
+
+    t0 = time.perf_counter()
+    threads = [threading.Thread(target=worker) for _ in range(ncores)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    dt = time.perf_counter() - t0
+    cells = sum(n for n, _ in solvers)
+    return {"value": cells * budget_cycles / dt / 1e6, "unit": METRIC, "cores": ncores, "kind": "oracle",
+            "sample": f"{budget_cycles} cycles of each of the 64 batched cases from the free stream, one case per "
+                      f"thread on {ncores} threads, oracle timing build, {dt:.1f} s", "host": host_cpu()}
+
+
+def hbm_peak():
+    try:
+        pk = json.load(open(MEASURED_PEAKS))
+        return float(pk["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs: STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def roofline(kt, steps, precision, w):
+    """HBM roofline of the dominant kernel class: its algorithmic bytes per launch (bytes per cell
+    x the cells one launch processes on average over the cycle) / its average launch time."""
+    dom = max(kt, key=lambda k: kt[k][1])
+    n_l, ms_l = kt[dom]
+    avg_ms = ms_l / max(n_l, 1)
+    nl, gam = w["nlevels"], w["gamma_cycle"]
+    visits = level_visits(nl, gam)
+    ncell = w["ni"] * w["nj"]
+    cells = [ncell // (4 ** (nl - 1 - l)) for l in range(nl)]
+    stages = 3
+    per_cycle = {
+        "sgs": sum(stages * visits[l] * cells[l] for l in range(nl)),
+        "residual": sum(stages * visits[l] * cells[l] for l in range(nl))
+        + sum(visits[l] * cells[l] for l in range(1, nl)) + sum(visits[l] * cells[l] for l in range(0, nl - 1)),
+    }
+    peak, src = hbm_peak()
+    bpc = BYTES_PER_CELL[precision].get(dom)
+    if bpc is None or dom not in per_cycle:
+        return {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+                "traffic": None, "avg_launch_ms": avg_ms, "peak_source": src}
+    cells_per_launch = per_cycle[dom] / (n_l / steps)
+    achieved = bpc * cells_per_launch / (avg_ms / 1e3) / 1e9
+    dram = DRAM_BYTES_PER_CELL[precision].get(dom)
+    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": dram * cells_per_launch if dram else None,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per cell of a captured launch, "
+                              "times the cells of the average launch" if dram else None,
+            "avg_launch_ms": avg_ms, "launches_per_cycle": n_l / steps, "cells_per_launch": cells_per_launch,
+            "bytes_per_cell": bpc, "peak_source": src,
+            "note": "the SGS sweep is a recurrence along i+j: its time is set by the per-step latency of the "
+                    "wavefront, not by HBM bandwidth; the fraction states how far from the memory bound it runs"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--quick", action="store_true", help="the headline line only (no extras)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-sequential", action="store_true", help="skip the one-case-at-a-time FP64 batch leg")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-unsteady-adjoint", action="store_true")
+    ap.add_argument("--pitch-steps", type=int, default=4, help="physical steps of the 512x128 pitching case")
     ap.add_argument("--c5", action="store_true",
                     help="only the 1024x256 RANS shape-sensitivity case (steady solve, adjoint, 16 bump gradients)")
     ap.add_argument("--c5-unsteady", action="store_true",
                     help="only the two-period unsteady adjoint of the pitching 512x128 RANS case (minutes)")
+    ap.add_argument("--c3-period", action="store_true",
+                    help="only the full 64-step period of the 512x128 pitching case, FP64 and mixed (minutes)")
     ap.add_argument("--adjoint-profile", action="store_true",
-                    help="only one 30-iteration adjoint GMRES solve on the workload grid (for ncu launch lists)")
+                    help="only one 30-iteration adjoint GMRES solve on the 256x64 grid (for ncu launch lists)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.warmup < 3:
@@ -484,6 +693,9 @@ def main():
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()          # non-default stream: cycles are replayed as CUDA graphs
     torch.cuda.set_stream(stream)
+    if args.c3_period:
+        print(json.dumps(measure_pitching_c3(P, stream, nsteps=64)), flush=True)
+        return
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     g = workload_grid()
     ncell = g.ni * g.nj
@@ -506,18 +718,7 @@ def main():
         dist.barrier()
     value = whole_job_value(ncell, args.steps, world, tot_ms)
 
-    # same measurement with the mixed-precision preconditioner (FP32 blocks / sweeps)
-    sm = P.Solver(g, gpu_params(P, "mixed" if args.precision == "fp64" else "fp64"), stream=stream.cuda_stream)
-    for k in range(args.warmup):
-        sm.fas_cycle(k)
-    ms_other = time_cycles(sm, stream, flush, args.steps, args.warmup)
-    other_value = world * ncell * args.steps / (sum(ms_other) / 1e3) / 1e6
-    sm.close()
-
-    # the 512x128 pitching-airfoil grid (M 0.8, Re 1e6): W-cycle throughput of both precisions
-    c3 = measure_c3(P, stream, flush, min(args.steps, 10), args.warmup)
-
-    # per-kernel device time over a second pass of the same number of cycles
+    # per-kernel-class device time over a second pass of the same number of cycles
     s.profile(True)
     for k in range(args.steps):
         flush.zero_()
@@ -529,117 +730,80 @@ def main():
     # memory, one cycle, D2H of the new state and the residual norm
     u_host = torch.from_numpy(s.get_state()).pin_memory()
     u_out = torch.empty_like(u_host).pin_memory()
-    e2e_steps = args.steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for k in range(e2e_steps):
+    for k in range(args.steps):
         s.set_state(u_host.numpy())
         s.fas_cycle(10**6)
         s.get_state(out=u_out.numpy())
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * ncell * e2e_steps / e2e_s / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = world * ncell * args.steps / e2e_s / 1e6
     state_bytes = 4 * ncell * 8
+    s.close()
 
-    # time to a 6-order drop from the free stream, FP64 and mixed preconditioner; then the
-    # pitching motion (alpha = 2 deg sin(2kt), k = 0.2, 64 steps per period): an implicit-Euler
-    # start step and one BDF2 step, each to an 11-order drop in pseudo time
-    drops, unsteady = {}, {}
-    states6, states11, final6, final11 = {}, {}, {}, {}
-    adjoint = None
-    omega = 0.4
-    dt_phys = 2.0 * np.pi / omega / 64
-    amp = np.radians(2.0)
-    for prec in ("fp64", "mixed"):
-        sd = P.Solver(g, gpu_params(P, prec), stream=stream.cuda_stream)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        code, nc, hist = sd.solve(1e-6, 600)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        drops[prec] = {"seconds": dt if code == 0 else None, "cycles": nc, "status": int(code),
-                       "final_drop": float(hist[-1] / hist[0]) if len(hist) else None}
-        states6[prec] = sd.get_state()
-        final6[prec] = float(hist[-1]) if len(hist) else None
+    extras = {}
+    if not args.quick and rank == 0 and world == 1:
+        # the other precision on the same workload
+        so = P.Solver(g, gpu_params(P, "mixed" if args.precision == "fp64" else "fp64"), stream=stream.cuda_stream)
+        for k in range(args.warmup):
+            so.fas_cycle(k)
+        ms_other = time_cycles(so, stream, flush, args.steps, args.warmup)
+        so.close()
+        extras["other_precision"] = {"precision": "mixed" if args.precision == "fp64" else "fp64",
+                                     "value": ncell * args.steps / (sum(ms_other) / 1e3) / 1e6,
+                                     "ms_per_step": sum(ms_other) / args.steps}
+        # time to a 6-order drop from the free stream, FP64 and mixed preconditioner
+        drops, states = {}, {}
+        for prec in ("fp64", "mixed"):
+            sd = P.Solver(g, gpu_params(P, prec), stream=stream.cuda_stream)
+            drops[prec] = solve_timed(sd, 1e-6, 1500)
+            states[prec] = sd.get_state()
+            sd.close()
+        extras["time_to_6_orders"] = drops
+        extras["precision_gap_6_orders"] = float(np.linalg.norm(states["mixed"] - states["fp64"])
+                                                 / np.linalg.norm(states["fp64"]))
+        extras["c2_256x64"] = measure_wcycles(P, C2, stream, flush, args.steps, args.warmup)
+        extras["c2_256x64"]["smoothers_to_6_orders"] = measure_smoothers_c2(P, stream)
+        extras["c3_512x128"] = measure_wcycles(P, C3, stream, flush, min(args.steps, 10), args.warmup)
+        if args.pitch_steps > 0:
+            extras["c3_512x128"]["pitching"] = measure_pitching_c3(P, stream, nsteps=args.pitch_steps)
+        if not args.no_batched:
+            extras["batched_64_cases"] = measure_batched(P, stream, flush, args.steps, args.warmup,
+                                                         sequential=not args.no_sequential)
+            if not args.no_cpu_baseline:
+                extras["batched_64_cases"]["oracle_all_cores"] = oracle_all_cores_c4()
         if not args.no_adjoint:
-            adjoint = adjoint or {}
-            adjoint[prec] = measure_adjoint(sd, g)
-        steps = []
-        for step in (1, 2):
-            tt = step * dt_phys
-            sd.set_motion(-amp * np.sin(omega * tt), -amp * omega * np.cos(omega * tt))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            c2, n2, h2 = sd.dual_time_step(dt_phys, 1e-11, 1000)
-            torch.cuda.synchronize()
-            steps.append({"kind": "implicit Euler" if step == 1 else "BDF2", "seconds": time.perf_counter() - t0,
-                          "cycles": n2, "status": int(c2),
-                          "final_drop": float(h2[-1] / h2[0]) if len(h2) else None})
-        unsteady[prec] = steps
-        states11[prec] = sd.get_state()
-        final11[prec] = float(h2[-1]) if len(h2) else None
-        sd.close()
-
-    def gap(st):
-        return float(np.linalg.norm(st["mixed"] - st["fp64"]) / np.linalg.norm(st["fp64"]))
-    precision_gap = {"state_6_orders": gap(states6), "state_11_orders_second_pitching_step": gap(states11),
-                     "final_residual_6_orders": final6, "final_residual_11_orders": final11,
-                     "note": "||u_mixed - u_fp64|| / ||u_fp64|| after the same number of cycles, and the RMS "
-                             "density residual at the stop of each precision"}
-    batched = None if args.no_batched else measure_batched(P, stream, flush, args.steps, args.warmup)
-    unsteady_adjoint = None if (args.no_adjoint or args.no_unsteady_adjoint) else measure_unsteady_adjoint(P, stream)
-    c5 = None if args.no_adjoint else measure_c5(P, stream)
+            adj = {}
+            for prec in ("fp64", "mixed"):
+                sa = P.Solver(grid_of(C2), params_of(P, C2, prec), stream=stream.cuda_stream)
+                sa.solve(1e-6, 1000)
+                adj[prec] = measure_adjoint(sa, grid_of(C2))
+                sa.close()
+            extras["adjoint_256x64"] = adj
+            if not args.no_unsteady_adjoint:
+                extras["unsteady_adjoint"] = measure_unsteady_adjoint(P, stream)
+            extras["c5_1024x256_sensitivity"] = measure_c5(P, stream)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel class: algorithmic FP64 flops per cell of each class
-    # (counted from the kernels) x cells processed per launch / average launch time
-    dom = max(kt, key=lambda k: kt[k][1])
-    n_l, ms_l = kt[dom]
-    avg_ms = ms_l / max(n_l, 1)
-    visits = level_visits(WORKLOAD["nlevels"], WORKLOAD["gamma_cycle"])
-    cells = [ncell // (4 ** (WORKLOAD["nlevels"] - 1 - l)) for l in range(WORKLOAD["nlevels"])]
-    per_cycle_cells = {
-        "sgs": sum(3 * visits[l] * cells[l] for l in range(len(cells))),
-        "residual": sum(3 * visits[l] * cells[l] for l in range(len(cells)))
-        + sum(visits[l] * cells[l] for l in range(1, len(cells)))
-        + sum(visits[l] * cells[l] for l in range(0, len(cells) - 1)),
-        "face_blocks": sum(visits[l] * cells[l] for l in range(len(cells))),
-        "diag_blocks": sum(visits[l] * cells[l] for l in range(len(cells))),
-    }
-    if dom in FLOPS_PER_CELL:
-        cells_per_launch = per_cycle_cells[dom] / (n_l / (2 * args.steps) * 2)
-        achieved = FLOPS_PER_CELL[dom] * cells_per_launch / (avg_ms / 1e3) / 1e12
-        traffic = SWEEP_DRAM_BYTES_PER_CELL * cells_per_launch if dom == "sgs" else None
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "traffic_source": "ncu dram bytes of a finest-level launch (708 B/cell), scaled by cells" if traffic else None,
-                "avg_launch_ms": avg_ms,
-                "launches_per_cycle": n_l / args.steps, "cells_per_launch": cells_per_launch,
-                "flops_per_cell": FLOPS_PER_CELL[dom],
-                "peak_source": "FP64 from unit counts and clock (152 SMs x 4 flop/clk x 2.07 GHz)"}
-    else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "avg_launch_ms": avg_ms}
     share = {k: round(v[1] / max(sum(x[1] for x in kt.values()), 1e-12), 4) for k, v in kt.items()}
-    cpu = None if args.no_cpu_baseline else cpu_oracle_sample()
+    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_oracle_sample()
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "cells": ncell, "levels": WORKLOAD["nlevels"],
                        "cycle": "W", "scheme": "AW3", "precision": args.precision, "cfl": WORKLOAD["cfl"],
-                       "l2": "flushed (256 MiB write) between timed cycles", "parallelism": "replicas"},
-            "other_precision": {"precision": "mixed" if args.precision == "fp64" else "fp64",
-                                "value": other_value, "ms_per_step": sum(ms_other) / args.steps},
-            "time_to_6_orders": drops, "time_to_11_orders_per_time_step": unsteady, "precision_gap": precision_gap,
-            "batched_64_cases": batched, "c3_512x128": c3, "adjoint": adjoint,
-            "unsteady_adjoint": unsteady_adjoint, "c5_1024x256": c5, "kernel_share": share,
+                       "l2": "inputs larger than L2 (about 0.5 GB resident); L2 also flushed (256 MiB write) "
+                             "between timed cycles", "parallelism": "replicas"},
+            **extras, "kernel_share": share,
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes + 8},
-            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "cpu_baseline": cpu}
+            "gpu_launches": int(launches), "clocks": clk.summary(),
+            "roofline": roofline(kt, args.steps, args.precision, WORKLOAD), "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

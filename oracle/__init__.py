@@ -51,24 +51,35 @@ class OrParams(C.Structure):
     ]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (no FMA contraction, plain -O2)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC])
-        os.replace(tmp, _LIB)
-    return _LIB
+# Two builds of the same source: "parity" (the reference the tests compare with: no FMA
+# contraction, -O2) and "timing" (the CPU baseline the benchmark times: -O3 with contraction
+# allowed; the same arithmetic up to rounding, no machine-specific flags so that it builds the
+# same on x86 and Arm hosts).
+_FLAGS = {"parity": ["-O2", "-ffp-contract=off"], "timing": ["-O3", "-ffp-contract=fast"]}
+_LIBS = {"parity": _LIB, "timing": os.path.join(_HERE, "_build", "libfasw_oracle_timing.so")}
 
 
-_lib = None
+def build(force: bool = False, variant: str = "parity") -> str:
+    """Compile one build of the oracle with g++ (see _FLAGS)."""
+    out = _LIBS[variant]
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", *_FLAGS[variant], "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC])
+        os.replace(tmp, out)
+    return out
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = C.CDLL(build())
+def build_all(force: bool = False):
+    return [build(force, v) for v in _FLAGS]
+
+
+_libs: dict = {}
+
+
+def lib(variant: str = "parity"):
+    if variant not in _libs:
+        _lib = C.CDLL(build(variant=variant))
         d, i, p = C.c_double, C.c_int, C.c_void_p
         dp = C.POINTER(C.c_double)
         sig = {
@@ -113,7 +124,8 @@ def lib():
             fn = getattr(_lib, name)
             fn.restype = res
             fn.argtypes = args
-    return _lib
+        _libs[variant] = _lib
+    return _libs[variant]
 
 
 def _dp(a: np.ndarray):
@@ -146,8 +158,8 @@ def make_params(scheme: str = "AW3", nlevels: int = 3, gamma_cycle: int = 1, nu1
 class Oracle:
     """One oracle solver instance on a C-grid (all levels)."""
 
-    def __init__(self, grid, params: OrParams):
-        self.L = lib()
+    def __init__(self, grid, params: OrParams, variant: str = "parity"):
+        self.L = lib(variant)
         self.grid = grid
         self.params = params
         x, y = grid.coords()
