@@ -179,6 +179,25 @@ int alloc_level(fasw_ctx* c, LevelDev& L) {
     A(L.hpC, 4 * h);
     A(L.hpY, 4 * h);
   }
+  if (ws_fits(L.ni, L.nj, L.nw)) {
+    const size_t wf = ws_floats(L.ni, L.nj), wv = ws_vec_floats(L.ni, L.nj);
+    A(L.wsF, wf);
+    A(L.wsB, wf);
+    A(L.wsC, wv);
+    A(L.wsY, wv);
+    A(L.wsCut, 16 * (size_t)(L.nw > 0 ? L.nw : 1));
+    A(L.wsEdge, ws_edge_floats(L.ni, L.nj));
+    A(L.wsZ, 2 * wv);
+    A(L.wsT, 4 * n);
+    // padding positions of the skewed arrays are never written: they must read as zero
+    CKR(cudaMemsetAsync(L.wsF, 0, wf * sizeof(float), c->st));
+    CKR(cudaMemsetAsync(L.wsB, 0, wf * sizeof(float), c->st));
+    CKR(cudaMemsetAsync(L.wsC, 0, wv * sizeof(float), c->st));
+    CKR(cudaMemsetAsync(L.wsY, 0, wv * sizeof(float), c->st));
+    CKR(cudaMemsetAsync(L.wsZ, 0, 2 * wv * sizeof(float), c->st));
+    CKR(cudaMemsetAsync(L.wsEdge, 0, ws_edge_floats(L.ni, L.nj) * sizeof(float), c->st));
+    CKR(cudaMemsetAsync(L.wsCut, 0, 16 * (size_t)(L.nw > 0 ? L.nw : 1) * sizeof(float), c->st));
+  }
 #undef A
   CKR(cudaMemsetAsync(L.vfx, 0, nfx * sizeof(double), c->st));
   CKR(cudaMemsetAsync(L.vfe, 0, nfe * sizeof(double), c->st));
@@ -210,8 +229,16 @@ void free_stream(double mach, double alpha_deg, double w[4]) {
 // level or precision falls back the same way.
 int level_sweep_kind(const fasw_ctx* c, const LevelDev& L) {
   int k = c->sweep_kind;
-  if (k == SWEEP_AUTO || (is_hp(k) && !(c->mixed && L.hpF)))
-    k = c->mixed ? (L.hpF ? SWEEP_HP : SWEEP_CTA) : SWEEP_STRIPS;
+  if (k == SWEEP_AUTO) {
+    // measured per level on GB300: the warp strips win for FP64 on every level and for FP32 from
+    // 64 rows up; below that the one-CTA hyperplane-staged FP32 sweep is faster
+    if (L.wsF && (!c->mixed || L.nj >= 64)) return SWEEP_WS;
+    return c->mixed ? (L.hpF ? SWEEP_HP : SWEEP_CTA) : SWEEP_STRIPS;
+  }
+  if (k == SWEEP_WS && !L.wsF) k = c->mixed ? SWEEP_CTA : SWEEP_STRIPS;
+  if (is_hp(k) && !(c->mixed && L.hpF)) k = c->mixed ? SWEEP_CTA : SWEEP_STRIPS;
+  if (c->in_batch && (k == SWEEP_STRIPS || k == SWEEP_STRIPS16 || k == SWEEP_STRIPS4))
+    k = L.wsF ? SWEEP_WS : SWEEP_CTA;  // concurrent cases: only sweeps whose CTAs are co-scheduled
   return k;
 }
 
@@ -665,7 +692,7 @@ int fasw_fas_cycle(fasw_ctx* c, int cycle_index, double* res_norm) {
 }
 
 int fasw_set_sweep(fasw_ctx* c, int kind) {
-  if (!c || kind < SWEEP_AUTO || kind > SWEEP_STRIPS4) return FASW_ERR_ARG;
+  if (!c || kind < SWEEP_AUTO || kind > SWEEP_WS) return FASW_ERR_ARG;
   int r = sync(c);
   if (r) return r;
   c->sweep_kind = kind;

@@ -65,6 +65,8 @@ int fasw_batch_create(int ncases, const int* ni, const int* nj, const int* n_wak
       fasw_batch_destroy(b);
       return r;
     }
+    c->in_batch = 1;
+    c->sweep_kind = c->mixed ? SWEEP_HP : SWEEP_WS;
     b->cases.push_back(c);
   }
   *out = b;

@@ -48,6 +48,7 @@ struct fasw_ctx {
   std::vector<CycleGraph> graphs;
   int use_graphs = 1;
   int sweep_kind = fasw::SWEEP_AUTO;
+  int in_batch = 0;             // a case of a batch: its kernels run beside other cases' kernels
   long long spin_limit = 1LL << 22;
   long long* d_prog = nullptr;  // strip progress flags
   int* d_err = nullptr;         // device error word (bounded waits)

@@ -7,9 +7,12 @@ namespace fasw {
 // SWEEP_HP: hyperplane-staged FP32 sweep with the default ring depth; SWEEP_HP4 / SWEEP_HP8: with a
 // ring of 4 / 8 steps (where 8 does not fit in shared memory, 4).  SWEEP_STRIPS / STRIPS16 /
 // STRIPS4: pipelined strips of 8 / 16 / 4 rows.
+// SWEEP_WS: warp strips of 32 rows, operands staged by bulk copies, FP32 recurrence; in FP64
+// contexts followed by one FP64 defect correction (a second FP32 sweep on the FP64 residual of
+// the first), which brings the result to FP64 accuracy.
 enum SweepKind {
   SWEEP_AUTO = 0, SWEEP_LEGACY = 1, SWEEP_CTA = 2, SWEEP_STRIPS = 3, SWEEP_STRIPS16 = 4,
-  SWEEP_HP = 5, SWEEP_HP4 = 6, SWEEP_HP8 = 7, SWEEP_STRIPS4 = 8
+  SWEEP_HP = 5, SWEEP_HP4 = 6, SWEEP_HP8 = 7, SWEEP_STRIPS4 = 8, SWEEP_WS = 9
 };
 inline bool is_hp(int kind) { return kind == SWEEP_HP || kind == SWEEP_HP4 || kind == SWEEP_HP8; }
 
@@ -22,6 +25,18 @@ void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st);
 int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, double alpha, const double* rhs,
                  long long* prog, int* err, long long limit, cudaStream_t st);
 int sweep_strips(const LevelDev& L);
+// Warp-strip sweep (kernels_sweep_ws.cu): whether a level can use it, the sizes of its arrays
+// (floats of wsF / wsB; of wsC / wsY), its strips, the skewed blocks from the transfer blocks
+// (after launch_sgs_prep), and one application (refine: FP64 defect correction in FP64
+// contexts).  Returns the kernels launched.
+bool ws_fits(int ni, int nj, int nw);
+size_t ws_floats(int ni, int nj);
+size_t ws_vec_floats(int ni, int nj);
+size_t ws_edge_floats(int ni, int nj);
+int ws_strips(int nj);
+void launch_ws_prep(const LevelDev& L, int mixed, cudaStream_t st);
+int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int aw, double alpha, const double* rhs,
+                    long long* prog, int* err, long long limit, cudaStream_t st);
 // Hyperplane-staged FP32 sweep: whether a level fits (rows, shared memory), and the entries
 // (ni + nj - 1) * nj of its hyperplane-major arrays (hpF, hpB: 32 floats each; hpC, hpY: 4).
 bool hp_fits(int ni, int nj, int nw);

@@ -1,0 +1,606 @@
+// Warp-strip SGS sweep with bulk-copy staging (FP32 recurrence), and the FP64 defect correction
+// that turns two such sweeps into an FP64-accurate application of the preconditioner.
+//
+// The sweeps apply P^-1 = ((D+L) D^-1 (D+U))^-1 of eq. (sgs-precon) (section 4.4) in the
+// transfer-block form of kernels_sweep.cu:
+//   forward  y_c = D_c^-1 r_c + G_W y_W + G_S y_S            (y_S: the wake-cut mirror on row 0
+//                                                             of the upper wake),
+//   backward z_c = y_c + H_E z_E + H_N z_N (+ G_S z_mirror on row 0 of the lower wake).
+// Rows are cut into strips of 32, one warp each (lane = row); a lane holds all four components
+// of its cell, so a step of the recurrence is its own previous vector (the west / east
+// neighbour), the neighbour row's previous vector by one shuffle (south / north), and 32 FMAs.
+// There is no barrier inside a step: a strip is one warp.  A strip's operands are laid out in
+// the order the warp consumes them (strip-major, step by step; "skewed" so that lane jl at
+// step s holds cell i = s - jl, with zero padding where that cell does not exist), so that the
+// operands of CHUNK steps are one contiguous block: one elected lane moves it into shared
+// memory with one cp.async.bulk per chunk and array, completion tracked by an mbarrier, STAGES
+// chunks ahead of use.  Strip b follows strip b-1 (forward; b+1 backward) through the
+// neighbour's boundary row, published in global memory every chunk (release / acquire flags).
+// Every wait is bounded; on timeout the kernel sets the error word, waits (bounded) for its own
+// copies in flight and returns.
+#include <atomic>
+#include <cstdint>
+#include <type_traits>
+
+#include "fasw_internal.cuh"
+#include "fasw_sweep.cuh"
+
+namespace fasw {
+
+namespace {
+
+constexpr int WS_K = 8;        // steps per chunk
+constexpr int WS_STAGES = 4;   // chunks in flight
+constexpr int WS_ROWS = 32;    // rows per strip (lanes)
+constexpr int WS_F4_STEP = 8 * WS_ROWS;  // float4 of blocks per step: 8 block rows x 32 lanes
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ long long ld_acquire_ws(const long long* p) {
+  long long v;
+  asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_ws(long long* p, long long v) {
+  asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ float4 shfl_up4(float4 v) {
+  v.x = __shfl_up_sync(0xffffffffu, v.x, 1);
+  v.y = __shfl_up_sync(0xffffffffu, v.y, 1);
+  v.z = __shfl_up_sync(0xffffffffu, v.z, 1);
+  v.w = __shfl_up_sync(0xffffffffu, v.w, 1);
+  return v;
+}
+
+__device__ __forceinline__ float4 shfl_down4(float4 v) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, 1);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, 1);
+  v.z = __shfl_down_sync(0xffffffffu, v.z, 1);
+  v.w = __shfl_down_sync(0xffffffffu, v.w, 1);
+  return v;
+}
+
+// out = c + A x + B w for row-major 4x4 blocks given as block rows A[0..3], B[0..3]
+__device__ __forceinline__ float4 two_blocks(float4 c, const float4* A, float4 x, const float4* B, float4 w) {
+  float o[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    // x (this lane's previous vector) is ready a shuffle earlier than w: fold the A-part into
+    // one chain and keep the w-part two FMAs deep, joined by one add
+    const float4 a = A[q], b = B[q];
+    float s = (q == 0 ? c.x : q == 1 ? c.y : q == 2 ? c.z : c.w);
+    s = fmaf(a.x, x.x, s);
+    s = fmaf(a.y, x.y, s);
+    s = fmaf(a.z, x.z, s);
+    s = fmaf(a.w, x.w, s);
+    const float t1 = fmaf(b.y, w.y, fmaf(b.x, w.x, s));
+    const float t2 = fmaf(b.w, w.w, b.z * w.z);
+    o[q] = t1 + t2;
+  }
+  return make_float4(o[0], o[1], o[2], o[3]);
+}
+
+__device__ __forceinline__ float4 add_block(float4 v, const float* G, float4 x) {
+  v.x += G[0] * x.x + G[1] * x.y + G[2] * x.z + G[3] * x.w;
+  v.y += G[4] * x.x + G[5] * x.y + G[6] * x.z + G[7] * x.w;
+  v.z += G[8] * x.x + G[9] * x.y + G[10] * x.z + G[11] * x.w;
+  v.w += G[12] * x.x + G[13] * x.y + G[14] * x.z + G[15] * x.w;
+  return v;
+}
+
+// Shared memory of the sweep: [mbarriers][ring of blocks][ring of vectors][edge][cut vectors][cut blocks]
+struct WsSmem {
+  uint64_t* bar;
+  float4* ringF;  // WS_STAGES x WS_K x WS_F4_STEP
+  float4* ringC;  // WS_STAGES x WS_K x 32
+  float4* edge;   // WS_PUB (one publication block of the neighbour's boundary row)
+  float4* cutv;   // nw
+  float* cutG;    // nw x 16
+};
+
+__device__ __forceinline__ WsSmem ws_carve(unsigned char* base, int nw) {
+  WsSmem S;
+  S.bar = reinterpret_cast<uint64_t*>(base);
+  S.ringF = reinterpret_cast<float4*>(base + 128);
+  S.ringC = S.ringF + WS_STAGES * WS_K * WS_F4_STEP;
+  S.edge = S.ringC + WS_STAGES * WS_K * WS_ROWS;
+  S.cutv = S.edge + 32;
+  S.cutG = reinterpret_cast<float*>(S.cutv + (nw > 0 ? nw : 1));
+  return S;
+}
+
+}  // namespace
+
+size_t ws_smem_bytes(int nw) {
+  const int m = nw > 0 ? nw : 1;
+  return 128 + 16 * ((size_t)WS_STAGES * WS_K * (WS_F4_STEP + WS_ROWS) + 32 + m) + 64 * (size_t)m;
+}
+
+int ws_strips(int nj) { return (nj + WS_ROWS - 1) / WS_ROWS; }
+// steps stored per strip: the ni + 31 steps that hold a cell, padded to whole chunks
+__host__ __device__ __forceinline__ int ws_steps(int ni) { return (ni + WS_ROWS - 1 + WS_K - 1) / WS_K * WS_K; }
+
+namespace {
+
+constexpr int WS_PUB = 32;   // steps between publications of a strip's boundary row (one column per lane)
+constexpr int WS_EPAD = 64;  // padding columns on each side of a boundary row (steps with no cell)
+
+// Skewed index of cell (i, j) in the backward order (the layout of y as the backward pass reads
+// it and of its result z): strip j / 32, step Mp - 1 - i - jl, lane jl.
+__device__ __forceinline__ size_t ws_bpos(int i, int j, int Mp) {
+  const int jl = j & (WS_ROWS - 1);
+  return ((size_t)(j / WS_ROWS) * Mp + (Mp - 1 - i - jl)) * WS_ROWS + jl;
+}
+
+// One pass (forward: FWD, else backward) of one strip.  Returns false on a timeout.
+// F: blocks of the pass, C: its right-hand side vectors (forward: D^-1 r; backward: y), both
+// skewed; Out: the pass's result, skewed in the backward order (forward: y; backward: z);
+// edge_in / edge_out: boundary rows (float4 per column); flag_in / flag_out: progress.
+template <bool FWD>
+__device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, int nb, const float4* F, const float4* C,
+                        float4* Out, const float4* edge_in, float4* edge_out, const long long* flag_in,
+                        long long* flag_out, int* err, long long limit, unsigned& phase_bits) {
+  const int lane = threadIdx.x;
+  const int ni = L.ni, nw = L.nw;
+  const int Mp = ws_steps(ni);              // steps (ni + 31 that hold a cell, padded to whole chunks)
+  const int nch = Mp / WS_K;
+  // the neighbour strip whose boundary row this one reads: below (forward) / above (backward)
+  const bool has_in = FWD ? b > 0 : b < nb - 1;
+  const bool has_out = FWD ? b < nb - 1 : b > 0;
+  const int edge_lane = FWD ? 0 : WS_ROWS - 1;      // lane that reads the neighbour's row
+  const int out_lane = FWD ? WS_ROWS - 1 : 0;       // lane whose row the other neighbour reads
+  const float4* Fs = F + (size_t)b * Mp * WS_F4_STEP;
+  const float4* Cs = C + (size_t)b * Mp * WS_ROWS;
+  float4* Os = Out + (size_t)b * Mp * WS_ROWS + lane;
+  const bool out_ok = has_out && lane == out_lane;
+  const unsigned bytesF = WS_K * WS_F4_STEP * 16, bytesC = WS_K * WS_ROWS * 16;
+
+  auto issue = [&](int ch) {  // lane 0 only
+    const int slot = ch % WS_STAGES;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&S.bar[slot], bytesF + bytesC);
+    bulk_copy(S.ringF + (size_t)slot * WS_K * WS_F4_STEP, Fs + (size_t)ch * WS_K * WS_F4_STEP, bytesF, &S.bar[slot]);
+    bulk_copy(S.ringC + (size_t)slot * WS_K * WS_ROWS, Cs + (size_t)ch * WS_K * WS_ROWS, bytesC, &S.bar[slot]);
+  };
+  // bounded wait for the chunk in a slot; false on timeout
+  auto wait_slot = [&](int slot) -> bool {
+    const unsigned par = (phase_bits >> slot) & 1u;
+    long long spins = 0;
+    bool ok = true;
+    while (!mbar_test(&S.bar[slot], par)) {
+      if (++spins > limit) {
+        ok = false;
+        break;
+      }
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (ok) phase_bits ^= 1u << slot;
+    return ok;
+  };
+  // after a timeout: wait for every copy still in flight into this CTA's shared memory before
+  // returning.  These copies depend on no other CTA and finish within microseconds, so their
+  // bound is fixed and generous, independent of the caller's (possibly tiny) spin limit.
+  auto drain = [&](int first, int last) {
+    for (int ch = first; ch < last; ++ch) {
+      const int slot = ch % WS_STAGES;
+      const unsigned par = (phase_bits >> slot) & 1u;
+      long long spins = 0;
+      while (!mbar_test(&S.bar[slot], par) && ++spins <= (1LL << 26)) {
+      }
+      phase_bits ^= 1u << slot;
+    }
+  };
+
+  if (lane == 0)
+    for (int ch = 0; ch < WS_STAGES && ch < nch; ++ch) issue(ch);
+  __syncwarp();
+  int issued = nch < WS_STAGES ? nch : WS_STAGES;
+
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);  // this lane's vector at the previous step
+  // Operands of one step: this lane's rows of the two blocks, its right-hand side vector and
+  // the neighbour strip's boundary value.  They are loaded one step ahead of their use (the
+  // loads do not depend on the recurrence), so that shared-memory latency stays off the chain.
+  struct Ops {
+    float4 A[4], B[4], c, e;
+  };
+  auto load = [&](Ops& o, const float4* rF, const float4* rC, const float4* ek, int k) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      o.A[q] = rF[k * WS_F4_STEP + q * WS_ROWS + lane];
+      o.B[q] = rF[k * WS_F4_STEP + (4 + q) * WS_ROWS + lane];
+    }
+    o.c = rC[k * WS_ROWS + lane];
+    o.e = ek[k];
+  };
+  // One step.  Padded positions (no cell) carry zero blocks and vectors, so they compute zero
+  // and need no test: every step writes its result, and the boundary-row arrays are padded by
+  // WS_EPAD columns on both sides.  Only the wake-cut coupling of row 0 (strip 0, lane 0) is
+  // special, and chunks that hold no cut cell run the step without it (CUT false).
+  auto step = [&](const Ops& o, int s, auto cut_tag) {
+    constexpr bool CUT = decltype(cut_tag)::value;
+    float4 w = FWD ? shfl_up4(v) : shfl_down4(v);  // the row below (forward) / above (backward)
+    if (lane == edge_lane) w = o.e;                 // neighbour strip's row, or zero
+    const int i = FWD ? s - lane : Mp - 1 - s - lane;  // this lane's cell (i, j)
+    if constexpr (CUT && FWD)
+      if (lane == 0 && i >= ni - nw && i < ni) w = S.cutv[ni - 1 - i];  // upper wake: its mirror
+    float4 y = two_blocks(o.c, o.A, v, o.B, w);
+    if constexpr (CUT && !FWD)
+      if (lane == 0 && i >= 0 && i < nw) y = add_block(y, S.cutG + 16 * i, S.cutv[i]);  // lower wake
+    if constexpr (CUT) {
+      if (lane == 0 && FWD && i >= 0 && i < nw) S.cutv[i] = y;                   // read by its mirror
+      if (lane == 0 && !FWD && i >= ni - nw && i < ni) S.cutv[ni - 1 - i] = y;   // read by its mirror
+    }
+    Os[(size_t)(FWD ? Mp - 1 - s : s) * WS_ROWS] = y;
+    if (out_ok) edge_out[i] = y;
+    v = y;
+  };
+  auto run_chunk = [&](const float4* rF, const float4* rC, const float4* ek, int s0, auto cut_tag) {
+    Ops o[2];
+    load(o[0], rF, rC, ek, 0);
+#pragma unroll
+    for (int k = 0; k < WS_K; ++k) {
+      if (k + 1 < WS_K) load(o[(k + 1) & 1], rF, rC, ek, k + 1);
+      step(o[k & 1], s0 + k, cut_tag);
+    }
+  };
+
+  for (int ch = 0; ch < nch; ++ch) {
+    const int s0 = ch * WS_K;
+    const int p0 = s0 - s0 % WS_PUB;  // first step of this publication block
+    // boundary row of the neighbour strip for the steps of this publication block: one column
+    // per lane
+    if (has_in && s0 == p0) {
+      bool ok = true;
+      if (lane == 0) {
+        const long long need = min((long long)s0 + WS_PUB + WS_ROWS - 1, (long long)Mp);
+        long long spins = 0;
+        while (ld_acquire_ws(flag_in) < need) {
+          if (*((volatile int*)err) != 0 || ++spins > limit) {
+            atomicExch(err, 1);
+            ok = false;
+            break;
+          }
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        drain(ch, issued);
+        return false;
+      }
+      const int s = s0 + lane;
+      const int col = FWD ? s : Mp - 1 - s - (WS_ROWS - 1);   // within the padded columns
+      const float4 e = __ldcg(edge_in + col);
+      __syncwarp();
+      S.edge[lane] = e;
+      __syncwarp();
+    }
+    const int slot = ch % WS_STAGES;
+    if (!wait_slot(slot)) {
+      if (lane == 0) atomicExch(err, 1);
+      drain(ch, issued);
+      return false;
+    }
+    const float4* rF = S.ringF + (size_t)slot * WS_K * WS_F4_STEP;
+    const float4* rC = S.ringC + (size_t)slot * WS_K * WS_ROWS;
+    const float4* ek = S.edge + (s0 - p0);
+    // does lane 0 of strip 0 meet a wake-cut cell in this chunk?
+    const int ilo = FWD ? s0 : Mp - s0 - WS_K, ihi = FWD ? s0 + WS_K - 1 : Mp - 1 - s0;
+    const bool cut = b == 0 && nw > 0 && (ilo < nw || ihi >= ni - nw);
+    if (cut)
+      run_chunk(rF, rC, ek, s0, std::true_type{});
+    else
+      run_chunk(rF, rC, ek, s0, std::false_type{});
+    __syncwarp();
+    if (lane == 0 && issued < nch) {
+      issue(issued);
+      ++issued;
+    }
+    const int done = s0 + WS_K;
+    if (has_out && lane == out_lane && (done % WS_PUB == 0 || done == Mp)) st_release_ws(flag_out, (long long)done);
+  }
+  return true;
+}
+
+// One launch: forward then backward pass of strip b (one warp per CTA).  flags: 2 nb progress
+// words (forward, backward), cleared by the host before the launch.
+__global__ void __launch_bounds__(32) k_sweep_ws(LevelDev L, const float4* Fb, const float4* Bb, const float4* C,
+                                                 float4* Y, const float* cutG, float4* edges, float4* Z,
+                                                 long long* flags, int* err, long long limit) {
+  pdl_entry();
+  extern __shared__ __align__(128) unsigned char ws_raw[];
+  const int nw = L.nw;
+  WsSmem S = ws_carve(ws_raw, nw);
+  const int b = blockIdx.x, nb = gridDim.x, lane = threadIdx.x;
+  if (lane == 0) {
+    for (int k = 0; k < WS_STAGES; ++k) mbar_init(&S.bar[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  S.edge[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (b == 0)
+    for (int x = lane; x < 16 * nw; x += 32) S.cutG[x] = cutG[x];
+  __syncwarp();
+  unsigned phase_bits = 0;
+  const size_t ew = (size_t)L.ni + 2 * WS_EPAD;  // padded boundary row of one strip
+  float4* edgeF = edges + WS_EPAD;               // column i of strip b's top row (forward) at b * ew + i
+  float4* edgeB = edges + (size_t)nb * ew + WS_EPAD;  // bottom rows (backward)
+  long long* fF = flags;
+  long long* fB = flags + nb;
+  if (!ws_pass<true>(L, S, b, nb, Fb, C, Y, b > 0 ? edgeF + (size_t)(b - 1) * ew : nullptr,
+                     edgeF + (size_t)b * ew, b > 0 ? fF + b - 1 : nullptr, fF + b, err, limit, phase_bits))
+    return;
+  // the backward pass reads, through the async proxy, the y this warp has just written
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  __syncwarp();
+  S.edge[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncwarp();
+  ws_pass<false>(L, S, b, nb, Bb, Y, Z, b < nb - 1 ? edgeB + (size_t)(b + 1) * ew : nullptr,
+                 edgeB + (size_t)b * ew, b < nb - 1 ? fB + b + 1 : nullptr, fB + b, err, limit, phase_bits);
+}
+
+// ---------------------------------------------------------------- operand layout
+// Skewed position of cell (i, j): strip b = j / 32, lane jl = j % 32, forward step s = i + jl,
+// backward step Mp - 1 - i - jl (Mp: the ni + 31 steps that hold a cell, padded to whole chunks).
+
+// Blocks of the warp-strip sweep from the transfer blocks (entry-major planes, T = double or
+// float): forward G_W, G_S (zero on row 0 except the upper wake, whose mirror precedes it),
+// backward H_E, H_N; the lower wake's G_S (backward coupling to its mirror) to cutG.
+template <typename T>
+__global__ void k_ws_blocks(LevelDev L, const T* tb, float4* Fb, float4* Bb, float* cutG) {
+  pdl_entry();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  const int ni = L.ni, n = L.n, i = c % ni, j = c / ni;
+  const int b = j / WS_ROWS, jl = j % WS_ROWS;
+  const int Mp = ws_steps(ni);
+  const bool cut = L.nw > 0 && (i < L.nw || i >= ni - L.nw);
+  const bool gs_fwd = j > 0 || (cut && ni - 1 - i < i);
+  float4* f = Fb + ((size_t)b * Mp + (i + jl)) * WS_F4_STEP + jl;
+  float4* g = Bb + ((size_t)b * Mp + (Mp - 1 - i - jl)) * WS_F4_STEP + jl;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const T* w = tb + (size_t)(16 + 4 * q) * n + c;
+    const T* s = tb + (size_t)(32 + 4 * q) * n + c;
+    const T* e = tb + (size_t)(48 + 4 * q) * n + c;
+    const T* nn = tb + (size_t)(64 + 4 * q) * n + c;
+    f[q * WS_ROWS] = make_float4(float(w[0]), float(w[n]), float(w[2 * n]), float(w[3 * n]));
+    f[(4 + q) * WS_ROWS] = gs_fwd ? make_float4(float(s[0]), float(s[n]), float(s[2 * n]), float(s[3 * n]))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    g[q * WS_ROWS] = make_float4(float(e[0]), float(e[n]), float(e[2 * n]), float(e[3 * n]));
+    g[(4 + q) * WS_ROWS] = make_float4(float(nn[0]), float(nn[n]), float(nn[2 * n]), float(nn[3 * n]));
+    if (j == 0 && cut && ni - 1 - i > i)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) cutG[16 * i + 4 * q + t] = float(s[(size_t)t * n]);
+  }
+}
+
+// Forward right-hand side D^-1 r (FP32), skewed.
+template <typename T>
+__global__ void k_ws_rhs(LevelDev L, const T* tb, const double* rhs, float4* C) {
+  pdl_entry();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  const int ni = L.ni, n = L.n, i = c % ni, j = c / ni;
+  const int b = j / WS_ROWS, jl = j % WS_ROWS, Mp = ws_steps(ni);
+  double r[4], y[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) r[t] = rhs[(size_t)t * n + c];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double a = 0.0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) a += double(tb[(size_t)(4 * q + t) * n + c]) * r[t];
+    y[q] = a;
+  }
+  C[((size_t)b * Mp + (i + jl)) * WS_ROWS + jl] = make_float4(float(y[0]), float(y[1]), float(y[2]), float(y[3]));
+}
+
+// ---------------------------------------------------------------- FP64 defect correction
+// t = (I + U~) z0: the vector the backward sweep would have started from to reach z0,
+//   t_c = z0_c - H_E z0_E - H_N z0_N (- G_S z0_mirror on row 0 of the lower wake).
+__global__ void k_ws_defect_t(LevelDev L, const double* tb, const float4* z0, double* t) {
+  pdl_entry();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  const int ni = L.ni, nj = L.nj, n = L.n, i = c % ni, j = c / ni;
+  const int Mp = ws_steps(ni);
+  const float4 zc = z0[ws_bpos(i, j, Mp)];
+  double acc[4] = {zc.x, zc.y, zc.z, zc.w};
+  auto sub = [&](int blk, int cn) {
+    const float4 zn = z0[ws_bpos(cn % ni, cn / ni, Mp)];
+    const double x[4] = {zn.x, zn.y, zn.z, zn.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[q] -= tb[(size_t)(blk * 16 + 4 * q + k) * n + c] * x[k];
+  };
+  if (i < ni - 1) sub(3, c + 1);
+  if (j < nj - 1) sub(4, c + ni);
+  if (j == 0 && L.nw > 0 && i < L.nw && ni - 1 - i > i) sub(2, ni - 1 - i);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) t[(size_t)q * n + c] = acc[q];
+}
+
+// d = D^-1 r - (I + L~) t = D^-1 r - t_c + G_W t_W + G_S t_S (t_S: the mirror on row 0 of the
+// upper wake, none elsewhere on row 0), written as the next forward right-hand side (FP32).
+__global__ void k_ws_defect_d(LevelDev L, const double* tb, const double* rhs, const double* t, float4* C) {
+  pdl_entry();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  const int ni = L.ni, n = L.n, i = c % ni, j = c / ni;
+  double r[4], acc[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = rhs[(size_t)k * n + c];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double a = -t[(size_t)q * n + c];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a += tb[(size_t)(4 * q + k) * n + c] * r[k];
+    acc[q] = a;
+  }
+  auto add = [&](int blk, int cn) {
+    double x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = t[(size_t)k * n + cn];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[q] += tb[(size_t)(blk * 16 + 4 * q + k) * n + c] * x[k];
+  };
+  if (i > 0) add(1, c - 1);
+  if (j > 0) add(2, c - ni);
+  else if (L.nw > 0 && i >= ni - L.nw && ni - 1 - i < i) add(2, ni - 1 - i);
+  const int b = j / WS_ROWS, jl = j % WS_ROWS, Mp = ws_steps(ni);
+  C[((size_t)b * Mp + (i + jl)) * WS_ROWS + jl] =
+      make_float4(float(acc[0]), float(acc[1]), float(acc[2]), float(acc[3]));
+}
+
+// z = z0 (+ dz): the stage update u = u0 - alpha z (scaled by dt* for ARK), or z to the level's
+// sweep vector (FP64 contexts: yz64; mixed: yz32).
+__global__ void k_ws_finish(LevelDev L, const float4* z0, const float4* dz, int do_update, int aw, double alpha,
+                            int mixed) {
+  pdl_entry();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  const int n = L.n, i = c % L.ni, j = c / L.ni;
+  const size_t zp = ws_bpos(i, j, ws_steps(L.ni));
+  const float4 a = z0[zp];
+  double z[4] = {a.x, a.y, a.z, a.w};
+  if (dz) {
+    const float4 d = dz[zp];
+    z[0] += d.x;
+    z[1] += d.y;
+    z[2] += d.z;
+    z[3] += d.w;
+  }
+  if (do_update) {
+    const double sc = aw ? alpha : alpha * L.dts[c];
+    const size_t g = (size_t)(j + 2) * L.P + (i + 2);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) L.u[q * (size_t)L.Gn + g] = L.u0[q * (size_t)n + c] - sc * z[q];
+  } else if (mixed) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) L.yz32[q * (size_t)n + c] = float(z[q]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) L.yz64[q * (size_t)n + c] = z[q];
+  }
+}
+
+constexpr size_t kWsSmemMax = 227 * 1024;
+
+}  // namespace
+
+bool ws_fits(int ni, int nj, int nw) {
+  (void)ni;
+  return ws_strips(nj) <= 8 && ws_smem_bytes(nw) <= kWsSmemMax;  // one portable cluster per sweep
+}
+
+void launch_ws_prep(const LevelDev& L, int mixed, cudaStream_t st) {
+  if (mixed)
+    launch_pdl(k_ws_blocks<float>, (L.n + 127) / 128, 128, 0, st, L, reinterpret_cast<const float*>(L.tb),
+               reinterpret_cast<float4*>(L.wsF), reinterpret_cast<float4*>(L.wsB), L.wsCut);
+  else
+    launch_pdl(k_ws_blocks<double>, (L.n + 127) / 128, 128, 0, st, L, static_cast<const double*>(L.tb),
+               reinterpret_cast<float4*>(L.wsF), reinterpret_cast<float4*>(L.wsB), L.wsCut);
+}
+
+namespace {
+cudaError_t ws_sweep_launch(const LevelDev& L, float4* zout, long long* prog, int* err, long long limit,
+                            cudaStream_t st) {
+  const int nb = ws_strips(L.nj);
+  const size_t sm = ws_smem_bytes(L.nw);
+  // the shared-memory limit is a per-device attribute: set once on each device (idempotent if
+  // two host threads race on the first launch)
+  static std::atomic<unsigned long long> attr_done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !(attr_done.load() & (1ull << dev))) {
+    if (cudaFuncSetAttribute(k_sweep_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemMax) ==
+        cudaSuccess)
+      attr_done.fetch_or(1ull << dev);
+  }
+  cudaMemsetAsync(prog, 0, 2 * (size_t)nb * sizeof(long long), st);
+  // The strips of one sweep wait on one another, so they are launched as one thread-block
+  // cluster (nb <= 8 CTAs): the hardware schedules a cluster's CTAs together, so every strip is
+  // resident whatever else runs beside it (concurrent cases of a batch included).
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  at[1].id = cudaLaunchAttributeClusterDimension;
+  at[1].val.clusterDim.x = nb;
+  at[1].val.clusterDim.y = 1;
+  at[1].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nb);
+  cfg.blockDim = dim3(32);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, k_sweep_ws, L, reinterpret_cast<const float4*>(L.wsF),
+                            reinterpret_cast<const float4*>(L.wsB), reinterpret_cast<const float4*>(L.wsC),
+                            reinterpret_cast<float4*>(L.wsY), static_cast<const float*>(L.wsCut),
+                            reinterpret_cast<float4*>(L.wsEdge), zout, prog, err, limit);
+}
+}  // namespace
+
+int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int aw, double alpha, const double* rhs,
+                    long long* prog, int* err, long long limit, cudaStream_t st) {
+  const int g = (L.n + 127) / 128;
+  float4* z0 = reinterpret_cast<float4*>(L.wsZ);
+  float4* dz = z0 + ws_vec_floats(L.ni, L.nj) / 4;
+  int launches = 0;
+  if (mixed)
+    launch_pdl(k_ws_rhs<float>, g, 128, 0, st, L, reinterpret_cast<const float*>(L.tb), rhs,
+               reinterpret_cast<float4*>(L.wsC));
+  else
+    launch_pdl(k_ws_rhs<double>, g, 128, 0, st, L, static_cast<const double*>(L.tb), rhs,
+               reinterpret_cast<float4*>(L.wsC));
+  ws_sweep_launch(L, z0, prog, err, limit, st);
+  launches += 2;
+  const bool corr = refine && !mixed;
+  if (corr) {
+    launch_pdl(k_ws_defect_t, g, 128, 0, st, L, static_cast<const double*>(L.tb), static_cast<const float4*>(z0),
+               L.wsT);
+    launch_pdl(k_ws_defect_d, g, 128, 0, st, L, static_cast<const double*>(L.tb), rhs,
+               static_cast<const double*>(L.wsT), reinterpret_cast<float4*>(L.wsC));
+    ws_sweep_launch(L, dz, prog, err, limit, st);
+    launches += 3;
+  }
+  launch_pdl(k_ws_finish, g, 128, 0, st, L, static_cast<const float4*>(z0), corr ? static_cast<const float4*>(dz) : nullptr,
+             do_update, aw, alpha, mixed);
+  return launches + 1;
+}
+
+size_t ws_edge_floats(int ni, int nj) { return 2 * 4 * (size_t)ws_strips(nj) * ((size_t)ni + 2 * WS_EPAD); }
+size_t ws_floats(int ni, int nj) { return (size_t)ws_strips(nj) * ws_steps(ni) * WS_F4_STEP * 4; }
+size_t ws_vec_floats(int ni, int nj) { return (size_t)ws_strips(nj) * ws_steps(ni) * WS_ROWS * 4; }
+
+}  // namespace fasw

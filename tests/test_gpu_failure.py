@@ -113,3 +113,24 @@ def test_solver_reports_divergence_not_garbage():
     assert code == -4
     assert not np.isfinite(hist[-1]) or hist[-1] > 1e8 * hist[0]
     assert nc < 60
+
+
+def test_warp_strip_sweep_wait_that_runs_out_reports_a_timeout():
+    """The warp-strip sweep on a 128 x 96 grid (three strips of 32 rows, each waiting for its
+    neighbour's boundary row): with a limit of one poll a wait gives up and the call reports
+    FASW_ERR_DEVICE_TIMEOUT; the error word does not outlive the call."""
+    import paper_1710_04875_gb300 as P
+    g = make_cgrid(128, 96, n_wake=16)
+    _, pg = pair_params(nlevels=1, mach=0.8, alpha_deg=1.25, precision="mixed")
+    pg.spin_limit = 1
+    s = P.Solver(g, pg)
+    s.set_sweep("warp")
+    r = np.random.default_rng(3).standard_normal((4, 96, 128))
+    with pytest.raises(P.FaswError) as e:
+        for _ in range(3):
+            s.precond_apply(r, 50.0)
+    assert e.value.code == -5
+    s.set_sweep("staged")          # one CTA, no cross-CTA wait
+    z = s.precond_apply(r, 50.0)
+    assert np.all(np.isfinite(z))
+    s.close()
