@@ -515,7 +515,8 @@ def measure_batched(P, stream, flush, steps, warmup, sequential=True):
         cases, grids, params = _c4_inputs(P, prec)
         cells = sum(g.ni * g.nj for g in grids)
         b = P.fasw.Batch(grids, params, stream=stream.cuda_stream)
-        choice = b.autotune()
+        tuned = b.autotune(with_tiles=True)
+        choice = [k for k, _ in tuned]
         for k in range(warmup):
             b.cycle(k)
         ms = []
@@ -541,7 +542,8 @@ def measure_batched(P, stream, flush, steps, warmup, sequential=True):
             "cases": len(grids), "cells": cells, "value": cells * steps / (sum(ms) / 1e3) / 1e6, "unit": METRIC,
             "ms_per_cycle": sum(ms) / steps,
             "sweep_choice": {"staged8": choice.count(7), "staged4": choice.count(6), "staged": choice.count(5),
-                             "cta": choice.count(2)},
+                             "cta": choice.count(2), "warp": choice.count(9)},
+            "residual_tile_choice": {str(t): sum(1 for _, x in tuned if x == t) for t in (0, 1, 2, 4, 8)},
             "time_to_6_orders": {"seconds": dt, "cycles_run": ncy, "status": int(code),
                                  "cases_converged": int((cyc > 0).sum()), "cases_diverged": int((cyc == -2).sum()),
                                  "median_cycles": float(np.median(cyc[cyc > 0])) if (cyc > 0).any() else None}}

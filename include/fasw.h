@@ -148,16 +148,28 @@ int fasw_solve_steady(fasw_ctx* ctx, double drop, int max_cycles, double* histor
  * stream; with the legacy default stream (NULL) cycles are always launched individually. */
 int fasw_use_graphs(fasw_ctx* ctx, int enable);
 
-/* How the SGS sweeps run: 0 = automatic (FP64: strip-pipelined multi-CTA sweep; mixed:
- * hyperplane-staged sweep where the level fits, else one-CTA sweep), 1 = one thread per cell
+/* How the SGS sweeps run: 0 = automatic (FP64: warp strips, 9; mixed: warp strips from 64 rows
+ * up, below that the hyperplane-staged sweep where the level fits, else one CTA; a level the warp
+ * strips do not fit -- more than 256 rows -- takes the strip-pipelined sweep in FP64), 1 = one
+ * thread per cell
  * applying the LU blocks (reference kernel), 2 = one CTA with precomputed transfer blocks
  * (strips where a hyperplane exceeds 128 cells), 3 = strip-pipelined with 8 rows per strip,
  * 4 = with 16 rows per strip, 5 = hyperplane-staged (mixed precision only, nj <= 256: blocks
  * stored hyperplane-major and staged through shared memory by cp.async; elsewhere as 0), 6 / 7 =
  * hyperplane-staged with a staging ring of 4 / 8 steps, 8 = strip-pipelined with 4 rows per
- * strip.  All give the same Gauss-Seidel result up to rounding.  Synchronizes the stream; drops
- * captured cycles. */
+ * strip, 9 = warp strips: one warp per strip of 32 rows, each lane a row holding all four
+ * components of its cell, operands staged into shared memory by bulk asynchronous copies, the
+ * strips of one sweep launched as one thread-block cluster; its recurrence runs in FP32, and in
+ * FP64 contexts it is followed by one FP64 defect correction (the FP64 residual of the SGS system
+ * at the FP32 result, solved by a second FP32 sweep and added), which brings the result to FP64
+ * accuracy.  All give the same Gauss-Seidel result up to rounding.  Synchronizes the stream; drops captured
+ * cycles. */
 int fasw_set_sweep(fasw_ctx* ctx, int kind);
+
+/* Tile height of the residual kernel (tiles of 31 x rows cells, one thread per face), on every
+ * level: rows = 1, 2, 4 or 8, or 0 (the default) for a choice from each level's size.  The
+ * result does not depend on it.  Synchronizes the stream; drops captured cycles. */
+int fasw_set_residual_tile(fasw_ctx* ctx, int rows);
 
 /* Eddy viscosity of the finest level (Baldwin-Lomax from the current state); n doubles.  A
  * laminar context (turb = 0) keeps a zero eddy viscosity in its own residual. */
@@ -367,14 +379,16 @@ int fasw_batch_cycle(fasw_batch* batch, int cycle_index, double* norms);
  * final_drop[k] = its last finite norm ratio, *ncycles = cycles run.  Returns FASW_OK,
  * FASW_ERR_NOT_CONVERGED or FASW_ERR_DIVERGED (some case diverged). */
 int fasw_batch_solve(fasw_batch* batch, double drop, int max_cycles, int* cycles, double* final_drop, int* ncycles);
-/* Picks the sweep variant (see fasw_set_sweep) of every case among those that never wait on
- * another CTA (kinds 7, 6 and 2; strips are excluded because concurrent cases do not guarantee
- * that all CTAs of a sweep are resident), one grid shape (ni, nj) at a time, by timing whole
- * batch cycles (states are saved and restored; each candidate against the incumbent timed beside
- * it, the faster of two timings each, a switch must gain 2 %); results are cached per shape and
- * precision for
- * the process, so a batch whose shapes are all cached is not timed again.  choice[k] (nullable)
- * receives the kind used for case k. */
+/* Picks, for every grid shape (ni, nj) and precision of the batch, the sweep variant (see
+ * fasw_set_sweep) and then the residual tile height (see fasw_set_residual_tile) by timing whole
+ * batch cycles: states are saved and restored; each candidate is timed beside the incumbent, the
+ * faster of two timings each, and a switch must gain 2 %.  Candidates are the variants whose CTAs
+ * never wait on a CTA that might not be resident beside the other cases' kernels: mixed precision
+ * 7, 6, 2 and 9 (the warp strips run as one thread-block cluster, which the hardware schedules
+ * together); FP64 9 and 2.  Tile heights 0 (size rule), 1, 2, 4, 8.  Results are cached per shape
+ * and precision for the process, so a batch whose shapes are all cached is not timed again.
+ * choice[k] (nullable) receives kind | (tile height << 8) for case k.  Batch cases start with
+ * kind 5 (mixed) or 9 (FP64); strip-pipelined kinds are never used inside a batch. */
 int fasw_batch_autotune(fasw_batch* batch, int* choice);
 long long fasw_batch_launch_count(fasw_batch* batch);
 

@@ -166,7 +166,7 @@ int alloc_level(fasw_ctx* c, LevelDev& L) {
   A(L.blk32, 32 * (nfx + nfe));
   A(L.dlu32, 16 * n);
   A(L.yz32, 4 * n);
-  A(L.norm_part, (size_t)residual_blocks(L));
+  A(L.norm_part, (size_t)residual_blocks_max(L));
   A(L.tb, 80 * n);
   A(L.vfx, nfx);
   A(L.vfe, nfe);
@@ -696,6 +696,15 @@ int fasw_set_sweep(fasw_ctx* c, int kind) {
   int r = sync(c);
   if (r) return r;
   c->sweep_kind = kind;
+  drop_graphs(c);
+  return FASW_OK;
+}
+
+int fasw_set_residual_tile(fasw_ctx* c, int rows) {
+  if (!c || !(rows == 0 || rows == 1 || rows == 2 || rows == 4 || rows == 8)) return FASW_ERR_ARG;
+  int r = sync(c);
+  if (r) return r;
+  for (auto& L : c->lev) L.res_ty = rows;
   drop_graphs(c);
   return FASW_OK;
 }

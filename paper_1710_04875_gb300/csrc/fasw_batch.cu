@@ -186,7 +186,7 @@ struct TuneKey {
     return ni != o.ni ? ni < o.ni : nj != o.nj ? nj < o.nj : mixed < o.mixed;
   }
 };
-std::map<TuneKey, int> g_tune_cache;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // (sweep kind, residual tile height)
 std::mutex g_tune_mutex;
 
 TuneKey key_of(fasw_ctx* c) {
@@ -195,11 +195,17 @@ TuneKey key_of(fasw_ctx* c) {
 }
 }  // namespace
 
-// Times `reps` batch cycles with kinds[k] on case k (after one capturing cycle); states restored.
-static int batch_time(fasw_batch* b, const std::vector<int>& kinds, const std::vector<double*>& saved, int reps,
-                      cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+static void set_tile(fasw_ctx* c, int rows) {
+  for (auto& L : c->lev) L.res_ty = rows;
+}
+
+// Times `reps` batch cycles with sweep kinds[k] and residual tile height tys[k] on case k (after
+// one capturing cycle); states restored.
+static int batch_time(fasw_batch* b, const std::vector<int>& kinds, const std::vector<int>& tys,
+                      const std::vector<double*>& saved, int reps, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
   for (size_t k = 0; k < b->cases.size(); ++k) {
     b->cases[k]->sweep_kind = kinds[k];
+    set_tile(b->cases[k], tys[k]);
     drop_graphs(b->cases[k]);
   }
   batch_drop_graphs(b);
@@ -224,7 +230,8 @@ static int batch_time(fasw_batch* b, const std::vector<int>& kinds, const std::v
 int fasw_batch_autotune(fasw_batch* b, int* choice) {
   if (!b) return FASW_ERR_ARG;
   const size_t nc = b->cases.size();
-  std::vector<int> kinds(nc, SWEEP_HP);
+  std::vector<int> kinds(nc), tys(nc, 0);
+  for (size_t k = 0; k < nc; ++k) kinds[k] = b->cases[k]->mixed ? SWEEP_HP : SWEEP_WS;
   std::map<TuneKey, std::vector<size_t>> groups;
   for (size_t k = 0; k < nc; ++k) groups[key_of(b->cases[k])].push_back(k);
   bool all_cached = true;
@@ -236,7 +243,10 @@ int fasw_batch_autotune(fasw_batch* b, int* choice) {
         all_cached = false;
         continue;
       }
-      for (size_t k : gk.second) kinds[k] = it->second;
+      for (size_t k : gk.second) {
+        kinds[k] = it->second.first;
+        tys[k] = it->second.second;
+      }
     }
   }
   if (!all_cached) {
@@ -255,11 +265,15 @@ int fasw_batch_autotune(fasw_batch* b, int* choice) {
     // the faster of two timings of the same kinds, so that one noisy timing decides nothing
     auto timed = [&](float* out) {
       float a = 0.f, c2 = 0.f;
-      if ((r = batch_time(b, kinds, saved, reps, e0, e1, &a))) return;
-      if ((r = batch_time(b, kinds, saved, reps, e0, e1, &c2))) return;
+      if ((r = batch_time(b, kinds, tys, saved, reps, e0, e1, &a))) return;
+      if ((r = batch_time(b, kinds, tys, saved, reps, e0, e1, &c2))) return;
       *out = std::min(a, c2);
     };
-    const int cand[3] = {SWEEP_HP8, SWEEP_HP4, SWEEP_CTA};
+    // sweep variants whose CTAs never wait on a CTA that may not be resident (one CTA, or the
+    // warp strips launched as one cluster); the FP32 staged kinds only in mixed precision
+    const int cand_mixed[4] = {SWEEP_HP8, SWEEP_HP4, SWEEP_CTA, SWEEP_WS};
+    const int cand_fp64[2] = {SWEEP_WS, SWEEP_CTA};
+    const int tile_cand[5] = {0, 1, 2, 4, 8};
     // larger shapes first: they dominate the batch time
     std::vector<std::pair<TuneKey, std::vector<size_t>>> order(groups.begin(), groups.end());
     std::sort(order.begin(), order.end(), [](const auto& x, const auto& y) {
@@ -268,8 +282,13 @@ int fasw_batch_autotune(fasw_batch* b, int* choice) {
     // each candidate against the incumbent timed right beside it; a switch must gain 2 %
     for (size_t gi = 0; gi < order.size() && r == FASW_OK; ++gi) {
       const std::vector<size_t>& members = order[gi].second;
+      const bool mixed = order[gi].first.mixed != 0;
+      const int* cand = mixed ? cand_mixed : cand_fp64;
+      const int ncand = mixed ? 4 : 2;
+      // sweep variant first (it dominates), then the residual tile height with it
       int keep = kinds[members[0]];
-      for (int k : cand) {
+      for (int ci = 0; ci < ncand; ++ci) {
+        const int k = cand[ci];
         if (k == keep || r) continue;
         float t_keep = 0.f, t_k = 0.f;
         timed(&t_keep);
@@ -278,17 +297,28 @@ int fasw_batch_autotune(fasw_batch* b, int* choice) {
         if (r == FASW_OK && t_k < 0.98f * t_keep) keep = k;
         for (size_t m : members) kinds[m] = keep;
       }
+      int keep_ty = tys[members[0]];
+      for (int ty : tile_cand) {
+        if (ty == keep_ty || r) continue;
+        float t_keep = 0.f, t_k = 0.f;
+        timed(&t_keep);
+        for (size_t m : members) tys[m] = ty;
+        if (r == FASW_OK) timed(&t_k);
+        if (r == FASW_OK && t_k < 0.98f * t_keep) keep_ty = ty;
+        for (size_t m : members) tys[m] = keep_ty;
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (r) return r;
     std::lock_guard<std::mutex> lk(g_tune_mutex);
-    for (auto& gk : groups) g_tune_cache[gk.first] = kinds[gk.second[0]];
+    for (auto& gk : groups) g_tune_cache[gk.first] = {kinds[gk.second[0]], tys[gk.second[0]]};
   }
   for (size_t k = 0; k < nc; ++k) {
     b->cases[k]->sweep_kind = kinds[k];
+    set_tile(b->cases[k], tys[k]);
     drop_graphs(b->cases[k]);
-    if (choice) choice[k] = kinds[k];
+    if (choice) choice[k] = kinds[k] | (tys[k] << 8);
   }
   batch_drop_graphs(b);
   return FASW_OK;

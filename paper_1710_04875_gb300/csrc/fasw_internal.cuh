@@ -51,6 +51,7 @@ struct LevelDev {
   int nfx;      // i-faces (ni+1)*nj
   int nfe;      // j-faces ni*(nj+1)
   int finest;   // full JST (sensor + fourth differences) on the finest level only
+  int res_ty;   // residual tile height (0: chosen from the level size)
   double a_t;   // time-derivative coefficient (0 = steady)
   double* u;    // 4*Gn ghosted conservative state
   double* u0;   // 4*n  state at the start of the smoothing step
@@ -158,6 +159,7 @@ cudaError_t launch_cell_aux(const LevelDev& L, const PhysParams& ph, double cfl,
 void launch_bc_aux(const LevelDev& L, const PhysParams& ph, double cfl, int want_dts, cudaStream_t st);
 cudaError_t launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, cudaStream_t st);
 int residual_blocks(const LevelDev& L);
+int residual_blocks_max(const LevelDev& L);  // the most tiles any tile height gives (height 1)
 void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* out, cudaStream_t st);
 void launch_bl(const LevelDev& L, const PhysParams& ph, cudaStream_t st);
 // the auxiliaries' FP64 powers beside pow()/cbrt(), n values (device pointers)

@@ -16,7 +16,12 @@ namespace {
 // computed by both neighbouring tiles).
 constexpr int TX = 31;
 constexpr int res_threads(int ty) { return 32 * (2 * ty + 1); }
-inline int res_ty(const LevelDev& L) { return ((L.ni + TX - 1) / TX) * ((L.nj + 3) / 4) >= 76 ? 4 : 1; }
+// Tile height: the level's setting (1, 2, 4 or 8, chosen by the batch autotuner or the caller),
+// else 4 rows where that still gives a grid of at least 76 tiles (half the SMs), else 1.
+inline int res_ty(const LevelDev& L) {
+  if (L.res_ty > 0) return L.res_ty;
+  return ((L.ni + TX - 1) / TX) * ((L.nj + 3) / 4) >= 76 ? 4 : 1;
+}
 
 __device__ __forceinline__ int gidx(const LevelDev& L, int i, int j) { return (j + 2) * L.P + (i + 2); }
 __device__ __forceinline__ bool on_cut(const LevelDev& L, int i) { return L.nw > 0 && (i < L.nw || i >= L.ni - L.nw); }
@@ -691,13 +696,17 @@ int residual_blocks(const LevelDev& L) {
 }
 
 cudaError_t launch_residual(const LevelDev& L, const PhysParams& ph, const ResArgs& a, cudaStream_t st) {
-  if (res_ty(L) == 4) {
-    dim3 grid((L.ni + TX - 1) / TX, (L.nj + 3) / 4);
-    return launch_pdl(k_residual<4>, grid, res_threads(4), 0, st, L, ph, a);
+  const int ty = res_ty(L);
+  const dim3 grid((L.ni + TX - 1) / TX, (L.nj + ty - 1) / ty);
+  switch (ty) {
+    case 8: return launch_pdl(k_residual<8>, grid, res_threads(8), 0, st, L, ph, a);
+    case 4: return launch_pdl(k_residual<4>, grid, res_threads(4), 0, st, L, ph, a);
+    case 2: return launch_pdl(k_residual<2>, grid, res_threads(2), 0, st, L, ph, a);
+    default: return launch_pdl(k_residual<1>, grid, res_threads(1), 0, st, L, ph, a);
   }
-  dim3 grid((L.ni + TX - 1) / TX, L.nj);
-  return launch_pdl(k_residual<1>, grid, res_threads(1), 0, st, L, ph, a);
 }
+
+int residual_blocks_max(const LevelDev& L) { return ((L.ni + TX - 1) / TX) * L.nj; }
 
 void launch_norm_final(const LevelDev& L, int nparts, int ncomp_cells, double* out, cudaStream_t st) {
   launch_pdl(k_norm_final, 1, 256, 0, st, L.norm_part, nparts, (double)ncomp_cells, out);

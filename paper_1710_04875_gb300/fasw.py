@@ -84,6 +84,7 @@ def library(variant: str = "perf"):
             "fasw_launch_count": (ll, [p]),
             "fasw_profile": (i, [p, i]),
             "fasw_use_graphs": (i, [p, i]),
+            "fasw_set_residual_tile": (i, [p, i]),
             "fasw_set_sweep": (i, [p, i]),
             "fasw_set_motion": (i, [p, d, d, d, d]),
             "fasw_dual_time_step": (i, [p, d, i, d, i, dp, C.POINTER(i)]),
@@ -294,6 +295,10 @@ class Solver:
         kinds = {"auto": 0, "reference": 1, "cta": 2, "strips": 3, "strips16": 4, "staged": 5, "staged4": 6,
                  "staged8": 7, "strips4": 8, "warp": 9}
         _check(self.lib.fasw_set_sweep(self.h, kinds.get(kind, kind)), "fasw_set_sweep")
+
+    def set_residual_tile(self, rows: int):
+        """Residual tile height on every level: 1, 2, 4, 8, or 0 for the size rule."""
+        _check(self.lib.fasw_set_residual_tile(self.h, int(rows)), "fasw_set_residual_tile")
 
     def use_graphs(self, enable: bool):
         _check(self.lib.fasw_use_graphs(self.h, 1 if enable else 0), "fasw_use_graphs")
@@ -507,10 +512,13 @@ class Batch:
             _check(code, "fasw_batch_solve")
         return code, np.array(list(ci)), fd, ncy.value
 
-    def autotune(self):
+    def autotune(self, with_tiles=False):
+        """Sweep kind per case (with_tiles: (kind, residual tile height) per case)."""
         ch = (C.c_int * self.n)()
         _check(self.lib.fasw_batch_autotune(self.h, C.cast(ch, C.c_void_p)), "fasw_batch_autotune")
-        return list(ch)
+        if with_tiles:
+            return [(x & 0xFF, x >> 8) for x in ch]
+        return [x & 0xFF for x in ch]
 
     def get_state(self, k):
         g = self.grids[k]

@@ -35,8 +35,9 @@ def test_batch_equals_single_case_runs(precision):
 def test_batch_solve_and_autotune():
     gs, ps = zip(*[_case(*c) for c in CASES])
     b = P.fasw.Batch(list(gs), list(ps))
-    choice = b.autotune()
-    assert all(c in (2, 5, 6, 7) for c in choice)
+    tuned = b.autotune(with_tiles=True)
+    assert all(c in (2, 9) for c, _ in tuned)            # FP64 cases: one CTA or the warp strips
+    assert all(t in (0, 1, 2, 4, 8) for _, t in tuned)
     code, cycles, drops, ncy = b.solve(1e-3, 120)
     assert code == 0 and np.all(cycles > 0) and np.all(drops <= 1e-3)
     ref = P.Solver(gs[0], ps[0])
@@ -60,3 +61,14 @@ def test_autotune_choices_are_cached_per_shape():
     for g, c in zip(gs, c1):
         shapes.setdefault((g.ni, g.nj), set()).add(c)
     assert all(len(v) == 1 for v in shapes.values())
+
+
+def test_mixed_batch_autotune_candidates_and_results():
+    """Mixed-precision batch: the tuner picks among the co-scheduled sweep kinds and a residual
+    tile height, and the tuned batch still converges like the single-case run."""
+    gs, ps = zip(*[_case(*c, precision="mixed") for c in CASES])
+    b = P.fasw.Batch(list(gs), list(ps))
+    tuned = b.autotune(with_tiles=True)
+    assert all(c in (2, 5, 6, 7, 9) for c, _ in tuned)
+    code, cycles, drops, ncy = b.solve(1e-3, 120)
+    assert code == 0 and np.all(cycles > 0)

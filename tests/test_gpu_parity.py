@@ -35,6 +35,22 @@ def test_residual_parity_euler(ni, nj, nw, finest):
     assert abs(ng - np.sqrt(np.mean(Fo[0] ** 2))) < 1e-11 * abs(ng)
 
 
+@pytest.mark.parametrize("rows", [1, 2, 4, 8])
+@pytest.mark.parametrize("ni,nj,nw", [(128, 32, 16), (72, 20, 8)])
+def test_residual_parity_every_tile_height(rows, ni, nj, nw):
+    """The residual kernel with each tile height the autotuner may pick (tiles of 31 x rows
+    cells, ragged in both directions here): the same F as the oracle."""
+    g = make_cgrid(ni, nj, n_wake=nw, jitter=0.05, seed=ni, wall_spacing=1e-3)
+    o, s = make_pair(g, nlevels=1, viscous=1, mach=0.7, alpha_deg=1.0, re=1e5)
+    s.set_residual_tile(rows)
+    u = perturbed_state(0.7, 1.0, nj, ni, amp=0.05, seed=4)
+    o.set_state(u); s.set_state(u)
+    Fo, _, _ = o.residual()
+    Fg, _, _, ng = s.residual(want_norm=True)
+    assert rel_err(Fg, Fo) < 1e-11
+    assert abs(ng - np.sqrt(np.mean(Fo[0] ** 2))) < 1e-11 * abs(ng)
+
+
 @pytest.mark.parametrize("sensor", [0, 1])
 def test_residual_parity_thin_layer_with_eddy_viscosity(sensor):
     ni, nj, nw = 64, 16, 8
