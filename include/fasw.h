@@ -261,9 +261,20 @@ int fasw_adjoint_solve(fasw_ctx* ctx, int which, const double* g, double* lam, d
 /* Shape gradient of objective `which` for nparam vertex fields: vy is nparam x (nj+1) x (ni+1)
  * y-displacements per unit parameter (index k*(nj+1)*(ni+1) + j*(ni+1) + i);
  * grad[k] = dJ/dX V_k - lam^T dF/dX V_k, both X-derivatives by central differences of step
- * h_x along V_k at the current state.  The grid is restored.  grad is host memory. */
+ * h_x along V_k at the current state; which = -1 leaves out the objective's explicit part
+ * (grad[k] = -lam^T dF/dX V_k, the term through which a state adjoint lam reaches the shape).
+ * The grid is restored.  grad is host memory. */
 int fasw_adjoint_shape_gradient(fasw_ctx* ctx, int which, const double* lam, int nparam, const double* vy, double h_x,
                                 double* grad, int on_device);
+
+/* The objective of the pitching case (section 6's motion, applied as in fasw_set_motion):
+ * nsteps dual-time steps (fasw_dual_time_step with bdf_order, drop, max_cycles) from the current
+ * state, the grid placed at phi(t_n) = -amp sin(omega t_n) about (xc, yc) with rate
+ * -amp omega cos(omega t_n) before step n, t_n = n dt; *objective = the average over the steps of
+ * C_L (which 0) or C_D (1) at the end of each step; *cycles (nullable) the pseudo-time cycles run.
+ * FASW_ERR_NOT_CONVERGED (soft, objective set) if a step stopped at max_cycles. */
+int fasw_pitching_objective(fasw_ctx* ctx, double amp, double omega, double xc, double yc, double dt, int nsteps,
+                            int bdf_order, double drop, int max_cycles, int which, double* objective, int* cycles);
 
 /* The transposed product (dF/dX)^T lam with the objective's explicit part: for every vertex
  * coordinate, gx/gy = dJ/dX - lam^T dF/dX ((nj+1) x (ni+1) each, index j*(ni+1) + i), by central

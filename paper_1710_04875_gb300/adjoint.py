@@ -75,9 +75,9 @@ def pitching_gradient(solver: Solver, fields, amp, omega, dt, nsteps, which=1, x
         snapshots=snapshots, h_rel=h_rel, h_x=h_x, tol=tol, max_iters=max_iters, restart=restart, cfl=cfl)
     solver.adjoint_jacobian(h_rel)
     nu, code0, it0, rr0 = solver.adjoint_solve(which, g=g0, tol=tol, max_iters=max_iters, restart=restart, cfl=cfl)
-    # -nu . dR/dX V: the shape gradient with lam = nu minus its explicit objective part (lam = 0)
+    # -nu . dR/dX V: the shape gradient of the steady adjoint nu without an explicit objective part
     V = np.ascontiguousarray(fields, dtype=np.float64)
-    steady = solver.adjoint_shape_gradient(which, nu, V, h_x) - solver.adjoint_shape_gradient(which, 0.0 * nu, V, h_x)
+    steady = solver.adjoint_shape_gradient(-1, nu, V, h_x)
     info = dict(stats, unsteady_status=int(code), steady_status=int(code0), steady_iterations=it0,
                 steady_relative_residual=rr0)
     return J, grad + steady, info
@@ -117,13 +117,9 @@ class PitchingForces(torch.autograd.Function):
     @staticmethod
     def forward(ctx, p: torch.Tensor, actx: PitchingContext):
         s = _steady_solver(actx, p)
-        J = 0.0
-        for n in range(1, actx.nsteps + 1):
-            t = n * actx.dt
-            s.set_motion(-actx.amp * np.sin(actx.omega * t), -actx.amp * actx.omega * np.cos(actx.omega * t),
-                         actx.xc, actx.yc)
-            s.dual_time_step(actx.dt, actx.drop, actx.max_cycles)
-            J += s.force_coefficients()[actx.which] / actx.nsteps
+        J, code, cycles = s.pitching_objective(actx.amp, actx.omega, actx.dt, actx.nsteps, which=actx.which,
+                                               xc=actx.xc, yc=actx.yc, drop=actx.drop, max_cycles=actx.max_cycles)
+        actx.info["forward"] = (int(code), int(cycles))
         s.close()
         ctx.actx = actx
         ctx.save_for_backward(p)

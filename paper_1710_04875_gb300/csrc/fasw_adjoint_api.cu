@@ -179,7 +179,7 @@ int shape_term(fasw_ctx* c, int which, const double* d_lam, const double* vk, do
     if (r) return r;
   }
   adj_lincomb((int)m, c->adj.Fp, -1.0, c->adj.Fm, c->d_tmp2, c->st);  // F+ - F-
-  *dC = which == 0 ? cl[0] - cl[1] : cd[0] - cd[1];
+  *dC = which < 0 ? 0.0 : which == 0 ? cl[0] - cl[1] : cd[0] - cd[1];  // which -1: no explicit part
   return adj_dot(c->adj, d_lam, c->d_tmp2, (int)m, c->st, dot);
 }
 
@@ -189,7 +189,7 @@ extern "C" {
 
 int fasw_adjoint_shape_gradient(fasw_ctx* c, int which, const double* lam, int nparam, const double* vy, double h_x,
                                 double* grad, int on_device) {
-  if (!c || !lam || !vy || !grad || nparam < 1 || which < 0 || which > 1 || !(h_x > 0.0) || c->ph.moving)
+  if (!c || !lam || !vy || !grad || nparam < 1 || which < -1 || which > 1 || !(h_x > 0.0) || c->ph.moving)
     return FASW_ERR_ARG;
   int r = adj_ready(c);
   if (r) return r;
@@ -207,6 +207,31 @@ int fasw_adjoint_shape_gradient(fasw_ctx* c, int which, const double* lam, int n
   launch_bc_aux(F, c->ph, 1.0, 0, c->st);
   c->launches += 2;
   return sync(c);
+}
+
+int fasw_pitching_objective(fasw_ctx* c, double amp, double omega, double xc, double yc, double dt, int nsteps,
+                            int bdf_order, double drop, int max_cycles, int which, double* objective, int* cycles) {
+  if (!c || !objective || nsteps < 1 || which < 0 || which > 1 || !(dt > 0.0)) return FASW_ERR_ARG;
+  double J = 0.0;
+  int total = 0, soft = 0;
+  for (int n = 1; n <= nsteps; ++n) {
+    const double t = n * dt;
+    int r = fasw_set_motion(c, -amp * std::sin(omega * t), -amp * omega * std::cos(omega * t), xc, yc);
+    if (r) return r;
+    int nc = 0;
+    r = fasw_dual_time_step(c, dt, bdf_order, drop, max_cycles, nullptr, &nc);
+    total += nc;
+    if (r == FASW_ERR_NOT_CONVERGED)
+      soft = 1;
+    else if (r)
+      return r;
+    double cl = 0.0, cd = 0.0;
+    if ((r = fasw_force_coefficients(c, &cl, &cd))) return r;
+    J += (which == 0 ? cl : cd) / nsteps;
+  }
+  *objective = J;
+  if (cycles) *cycles = total;
+  return soft ? FASW_ERR_NOT_CONVERGED : FASW_OK;
 }
 
 }  // extern "C"

@@ -100,6 +100,7 @@ def library(variant: str = "perf"):
             "fasw_adjoint_vertex_gradient": (i, [p, i, dp, d, dp, dp, i]),
             "fasw_adjoint_cycle_apply": (i, [p, d, i, i, dp, dp, i]),
             "fasw_adjoint_shape_gradient": (i, [p, i, dp, i, dp, d, dp, i]),
+            "fasw_pitching_objective": (i, [p, d, d, d, d, d, i, i, d, i, i, C.POINTER(d), C.POINTER(i)]),
             "fasw_checkpoint_schedule": (i, [i, i, dp, dp, i, C.POINTER(i), C.POINTER(ll)]),
             "fasw_check_math": (i, [i, p, p, p, i]),
             "fasw_unsteady_adjoint": (i, [p, d, d, d, d, d, i, i, d, i, i, i, i, dp, d, d, d, i, i, d, C.POINTER(d),
@@ -402,8 +403,21 @@ class Solver:
                                                      gy.ctypes.data, 0), "fasw_adjoint_vertex_gradient")
         return gx, gy
 
+    def pitching_objective(self, amp, omega, dt, nsteps, which=1, xc=0.25, yc=0.0, bdf_order=2, drop=1e-10,
+                           max_cycles=500):
+        """(J, code, cycles): the average of C_L (which 0) or C_D (1) over nsteps dual-time steps of the
+        pitching motion alpha + amp sin(omega t), from the current state."""
+        J = C.c_double()
+        nc = C.c_int()
+        code = self.lib.fasw_pitching_objective(self.h, amp, omega, xc, yc, dt, nsteps, bdf_order, drop, max_cycles,
+                                                which, C.byref(J), C.byref(nc))
+        if code not in (0, -6):
+            _check(code, "fasw_pitching_objective")
+        return J.value, code, nc.value
+
     def adjoint_shape_gradient(self, which, lam, fields, h_x=1e-6):
-        """grad[k] = dJ/dX V_k - lam^T dF/dX V_k for y-displacement fields (nparam, nj+1, ni+1)."""
+        """grad[k] = dJ/dX V_k - lam^T dF/dX V_k for y-displacement fields (nparam, nj+1, ni+1);
+        which -1: without the objective's explicit part."""
         lam = np.ascontiguousarray(lam, dtype=np.float64)
         V = np.ascontiguousarray(fields, dtype=np.float64)
         grad = np.zeros(V.shape[0])

@@ -201,3 +201,27 @@ def test_pitching_forces_autograd():
     assert abs(float(J.detach()) - Jr) <= 1e-12 * abs(Jr)
     assert rel_err(p.grad.numpy(), gr) < 1e-12
 
+
+
+def test_library_pitching_objective_and_state_term(euler_case):
+    """The library's time average of C_D over the pitching steps equals the step-by-step loop
+    through the single-step calls, and the shape gradient without the explicit objective part
+    (which -1) equals the full one minus the one at lam = 0."""
+    import paper_1710_04875_gb300 as P
+    g, po, pg, u0, V = euler_case
+    N = 3
+    s = P.Solver(g, pg)
+    assert s.solve(1e-12, 2000)[0] == 0
+    J, code, cycles = s.pitching_objective(AMP, OMEGA, DT, N, which=1, xc=XC, yc=YC, drop=DROP,
+                                           max_cycles=CYCLES)
+    s.close()
+    assert code == 0 and cycles > 0
+    assert abs(J - _unsteady_objective(P, g, pg, N, 1)) <= 1e-13 * abs(J)
+    s = P.Solver(g, pg)
+    assert s.solve(1e-12, 2000)[0] == 0
+    lam = np.random.default_rng(5).standard_normal((4, g.nj, g.ni))
+    full = s.adjoint_shape_gradient(1, lam, V)
+    expl = s.adjoint_shape_gradient(1, 0.0 * lam, V)
+    state = s.adjoint_shape_gradient(-1, lam, V)
+    s.close()
+    assert rel_err(state, full - expl) < 1e-12
