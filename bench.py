@@ -46,15 +46,22 @@ L2_FLUSH_BYTES = 256 << 20
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK_GBS = 6800.0
 # Algorithmic DRAM bytes per cell of one launch of each kernel class (the compulsory traffic:
-# every input read once, every output written once), by preconditioner precision.
-#   sgs, FP64 strip sweep (forward + backward + stage update): transfer blocks D^-1, G_W, G_S,
-#     H_E, H_N (80 doubles) + right-hand side (4) + u^(0) (4) read, u written (4): 736 B;
-#   sgs, FP32 hyperplane-staged sweep: D^-1 (16 floats) and r (4 doubles) read, D^-1 r written
-#     and read (4 + 4 floats), G_W G_S and H_E H_N (64 floats) read, y written and read (8
-#     floats), z (4 floats) + u^(0) (4 doubles) read, u written (4 doubles): 528 B;
+# every input read once, every output written once), by preconditioner precision.  The "sgs"
+# class is one preconditioner application of a stage with its update; on the headline workload
+# every level runs the warp-strip sweep in FP64, and the levels of 64 rows and more in mixed
+# precision (the smaller ones the one-CTA staged sweep, 528 B).
+#   FP64 (two FP32 warp-strip sweeps and one FP64 defect correction):
+#     D^-1 r: D^-1 (16 doubles) and r (4 doubles) read, the FP32 right-hand side written (4 floats)  176 B
+#     each sweep: forward blocks G_W G_S and backward blocks H_E H_N (64 floats), its right-hand
+#       side read, y written and read back, z written (4 x 4 floats)                            2 x 320 B
+#     defect: z read (4 floats), H_E H_N (32 doubles) read, t written (4 doubles); D^-1 G_W G_S
+#       (48 doubles), r and t (8 doubles) read, the defect written (4 floats)                  304 + 464 B
+#     update: z and dz read (8 floats), u^(0) read and u written (8 doubles)                      96 B
+#   mixed (one warp-strip sweep): D^-1 (16 floats) and r read, right-hand side written, the
+#     sweep, z and u^(0) read, u written: 112 + 320 + 80                                            512 B
 #   residual: ghosted u (4), p, q, 1/rho, radii (2), dt*, volume, mu_t, face vectors (4) read,
-#     the stage right-hand side and the F^v carry written and the carry read (12): 232 B.
-BYTES_PER_CELL = {"fp64": {"sgs": 736.0, "residual": 232.0}, "mixed": {"sgs": 528.0, "residual": 232.0}}
+#     the stage right-hand side and the F^v carry written and the carry read (12)                 232 B
+BYTES_PER_CELL = {"fp64": {"sgs": 1680.0, "residual": 232.0}, "mixed": {"sgs": 512.0, "residual": 232.0}}
 # DRAM traffic per cell of one launch of the dominant kernel, from an ncu capture of a finest-level
 # launch (dram__bytes_read.sum + dram__bytes_write.sum over the cells of that launch); None where
 # no capture of the current kernel exists.
@@ -299,7 +306,7 @@ def measure_smoothers_c2(P, stream, max_cycles=1000):
     return out
 
 
-def measure_pitching_c3(P, stream, nsteps=4, max_cycles=1500):
+def measure_pitching_c3(P, stream, nsteps=4, max_cycles=600):
     """The pitching 512x128 RANS case (alpha = 2 deg sin(2kt), k = 0.2, 64 steps per period):
     a steady start converged 6 orders (mixed precision), then the first nsteps physical steps
     (implicit Euler, then BDF2), each converged 11 orders in pseudo time, once with the FP64 and
@@ -495,6 +502,36 @@ def measure_unsteady_adjoint(P, stream, nsteps=128, snapshots=8, n_bumps=16):
                     "steady adjoint of the initial state"}
 
 
+def measure_mesh_independence(P, stream, max_cycles=1500):
+    """Convergence rates of AW3 on three synthetic C-grids of one family (cells 256x32, 384x48,
+    512x64: the sizes of the paper's mesh-independence table), thin-layer RANS at M 0.796,
+    Re 1e6, 3-level W-cycles (coarsest grids 64x8, 96x12, 128x16), mixed precision: the steady
+    solve from the free stream to a 6-order drop, then the first pitching step (implicit Euler,
+    k = 0.202, amplitude 1.01 deg, 36 steps per period) to an 11-order drop.  Rates are the
+    average per-cycle reduction (final / first) ^ (1 / cycles)."""
+    import torch
+    omega = 2 * 0.202
+    dt = 2.0 * np.pi / omega / 36
+    amp = np.radians(1.01)
+    out = {"flow": "M 0.796, Re 1e6, thin layer + Baldwin-Lomax, AW3, d 0.5, eta 0.8, c* 100, 3-level W"}
+    for ni, nj in ((256, 32), (384, 48), (512, 64)):
+        w = dict(C2, name=f"rans_{ni}x{nj}", ni=ni, nj=nj, n_wake=ni // 8, mach=0.796, re=1e6, nlevels=3)
+        g = grid_of(w)
+        s = P.Solver(g, params_of(P, w, "mixed"), stream=stream.cuda_stream)
+        steady = solve_timed(s, 1e-6, max_cycles)
+        s.set_motion(-amp * np.sin(omega * dt), -amp * omega * np.cos(omega * dt))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        code, nc, h = s.dual_time_step(dt, 1e-11, max_cycles)
+        torch.cuda.synchronize()
+        first = {"seconds": time.perf_counter() - t0, "cycles": nc, "status": int(code),
+                 "final_drop": float(h[-1] / h[0]) if len(h) else None,
+                 "rate": float((h[-1] / h[0]) ** (1.0 / max(nc - 1, 1))) if len(h) > 1 else None}
+        out[f"{ni}x{nj}"] = {"steady": steady, "first_pitching_step": first}
+        s.close()
+    return out
+
+
 def _c4_inputs(P, precision):
     from synth.cases import config_c4_cases
     cases = config_c4_cases()
@@ -665,6 +702,8 @@ def main():
                     help="only the two-period unsteady adjoint of the pitching 512x128 RANS case (minutes)")
     ap.add_argument("--c3-period", action="store_true",
                     help="only the full 64-step period of the 512x128 pitching case, FP64 and mixed (minutes)")
+    ap.add_argument("--mesh-independence", action="store_true",
+                    help="only the convergence rates on the 256x32 / 384x48 / 512x64 grid family")
     ap.add_argument("--adjoint-profile", action="store_true",
                     help="only one 30-iteration adjoint GMRES solve on the 256x64 grid (for ncu launch lists)")
     args = ap.parse_args()
@@ -697,6 +736,9 @@ def main():
     torch.cuda.set_stream(stream)
     if args.c3_period:
         print(json.dumps(measure_pitching_c3(P, stream, nsteps=64)), flush=True)
+        return
+    if args.mesh_independence:
+        print(json.dumps(measure_mesh_independence(P, stream)), flush=True)
         return
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     g = workload_grid()
