@@ -47,7 +47,7 @@ class OrParams(C.Structure):
         ("eta", C.c_double), ("d_cut", C.c_double), ("cfl", C.c_double),
         ("cfl_ramp", C.c_double), ("ramp_cycles", C.c_int),
         ("s_coarse", C.c_double), ("dt_phys", C.c_double), ("bdf_order", C.c_int),
-        ("norm_all", C.c_int),
+        ("norm_all", C.c_int), ("flux", C.c_int), ("precond", C.c_int),
     ]
 
 
@@ -119,6 +119,7 @@ def lib(variant: str = "parity"):
             "or_set_motion": (None, [p, d, d, d, d]),
             "or_dual_time_step": (i, [p, d, d, i, dp]),
             "or_grid_fluxes": (None, [p, i, dp, dp]),
+            "or_block_apply": (None, [p, i, d, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -138,7 +139,7 @@ def make_params(scheme: str = "AW3", nlevels: int = 3, gamma_cycle: int = 1, nu1
                 alpha_deg: float = 0.0, re: float = 1e6, pr: float = 0.75, prt: float = 0.9,
                 eta: float = 0.8, d_cut: float = 0.5, cfl: float = 1e4, cfl_ramp: float = 20.0,
                 ramp_cycles: int = 2, s_coarse: float = 0.25, dt_phys: float = 0.0,
-                bdf_order: int = 2, norm_all: int = 0) -> OrParams:
+                bdf_order: int = 2, norm_all: int = 0, flux: str = "jst", precond: str = "sgs") -> OrParams:
     al, be = SCHEMES[scheme]
     p = OrParams()
     p.scheme = 1 if (scheme.startswith("ARK") or scheme.startswith("ERK")) else 0
@@ -152,6 +153,8 @@ def make_params(scheme: str = "AW3", nlevels: int = 3, gamma_cycle: int = 1, nu1
     p.mach, p.alpha_deg, p.re, p.pr, p.prt = mach, alpha_deg, re, pr, prt
     p.eta, p.d_cut, p.cfl, p.cfl_ramp, p.ramp_cycles = eta, d_cut, cfl, cfl_ramp, ramp_cycles
     p.s_coarse, p.dt_phys, p.bdf_order, p.norm_all = s_coarse, dt_phys, bdf_order, norm_all
+    p.flux = {"jst": 0, "fvs": 1}[flux]
+    p.precond = {"sgs": 0, "exact": 1}[precond]
     return p
 
 
@@ -261,13 +264,22 @@ class Oracle:
         self.L.or_pseudo_dt(self.h, l, cfl, _dp(d))
         return d
 
+    def block_apply(self, x, cfl, l=None):
+        """(D + L + U) x with the blocks at the level's current state."""
+        l = self.finest if l is None else l
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros_like(x)
+        self.L.or_block_apply(self.h, l, cfl, _dp(x), _dp(y))
+        return y
+
     def precond_apply(self, r, cfl, l=None, dense=False):
         l = self.finest if l is None else l
         ni, nj, _ = self.dims(l)
         r = np.ascontiguousarray(r, dtype=np.float64)
         z = np.zeros((4, nj, ni))
         D = np.zeros((nj * ni, 4, 4))
-        self.L.or_precond_apply(self.h, l, cfl, _dp(r), _dp(z), 1 if dense else 0, _dp(D))
+        mode = 2 if dense == "exact" else (1 if dense else 0)   # "exact": (D + L + U)^-1
+        self.L.or_precond_apply(self.h, l, cfl, _dp(r), _dp(z), mode, _dp(D))
         return z, D
 
     def face_blocks(self, l=None):

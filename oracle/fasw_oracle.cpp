@@ -69,6 +69,8 @@ struct OrParams {
   double dt_phys;      // physical time step (0 = steady)
   int bdf_order;       // 1 = implicit Euler, 2 = BDF2
   int norm_all;        // 0 = density RMS, 1 = RMS over 4 components
+  int flux;            // residual face flux: 0 = JST (section 2), 1 = first-order flux-vector splitting
+  int precond;         // smoother preconditioner: 0 = SGS (D+L) D^-1 (D+U), 1 = exact D+L+U (dense)
 };
 
 // ---------------------------------------------------------------- gas model
@@ -543,6 +545,30 @@ static FaceFlux jst_face(const Solver& S, const V4& uLL, const V4& uL, const V4&
   return out;
 }
 
+// First-order flux-vector-split face flux (the discretization the preconditioner linearizes,
+// section 4.4): h = A+(u_bar) u_L + A-(u_bar) u_R with u_bar the mean of the two states (G22)
+// and the cutoff eigenvalues of eq. (cutoff).  Split as the JST flux is (h = hc - hd): the
+// central part hc = A(u_bar) (u_L + u_R) / 2 and the upwind dissipation
+// hd = (A+ - A-)(u_R - u_L) / 2, since A+ + A- = A.  A(u) u = F(u) . S for the Euler flux
+// (homogeneous of degree one), so the flux is consistent: uniform flow gives F . S.
+static FaceFlux fvs_face(const Solver& S, const V4& uL, const V4& uR, double sx, double sy, double vf) {
+  V4 ub;
+  for (int k = 0; k < 4; ++k) ub[k] = 0.5 * (uL[k] + uR[k]);
+  M4 Ap, Am;
+  split_jacobians(ub, sx, sy, vf, S.P.d_cut, Ap, Am);
+  FaceFlux out;
+  for (int r = 0; r < 4; ++r) {
+    double c = 0.0, d = 0.0;
+    for (int k = 0; k < 4; ++k) {
+      c += (Ap[r][k] + Am[r][k]) * (uL[k] + uR[k]);
+      d += (Ap[r][k] - Am[r][k]) * (uR[k] - uL[k]);
+    }
+    out.hc[r] = 0.5 * c;
+    out.hd[r] = 0.5 * d;
+  }
+  return out;
+}
+
 // Martinelli-corrected radius of a (possibly ghost) cell in direction dir (0 = xi, 1 = eta).
 // Ghost cells take the adjacent interior cell's value; across the wake cut the mirror cell's.
 static double rtilde(const Level& g, int i, int j, int dir) {
@@ -615,16 +641,21 @@ static void residual(const Solver& S, Level& g, bool finest, std::vector<V4>& Fc
   const int ni = g.ni, nj = g.nj;
   std::vector<FaceFlux> fx((ni + 1) * nj), fe(ni * (nj + 1));
   std::vector<V4> fvis(ni * (nj + 1), V4{});
+  const bool fvs = S.P.flux == 1;
   for (int j = 0; j < nj; ++j)
     for (int i = 0; i <= ni; ++i)
-      fx[g.FX(i, j)] = jst_face(S, g.u[g.G(i - 2, j)], g.u[g.G(i - 1, j)], g.u[g.G(i, j)],
-                                g.u[g.G(i + 1, j)], g.sxi_x[g.FX(i, j)], g.sxi_y[g.FX(i, j)], g.vfx[g.FX(i, j)],
-                                rtilde(g, i - 1, j, 0), rtilde(g, i, j, 0), finest);
+      fx[g.FX(i, j)] = fvs ? fvs_face(S, g.u[g.G(i - 1, j)], g.u[g.G(i, j)], g.sxi_x[g.FX(i, j)],
+                                      g.sxi_y[g.FX(i, j)], g.vfx[g.FX(i, j)])
+                           : jst_face(S, g.u[g.G(i - 2, j)], g.u[g.G(i - 1, j)], g.u[g.G(i, j)],
+                                      g.u[g.G(i + 1, j)], g.sxi_x[g.FX(i, j)], g.sxi_y[g.FX(i, j)],
+                                      g.vfx[g.FX(i, j)], rtilde(g, i - 1, j, 0), rtilde(g, i, j, 0), finest);
   for (int j = 0; j <= nj; ++j)
     for (int i = 0; i < ni; ++i) {
-      fe[g.FE(i, j)] = jst_face(S, g.u[g.G(i, j - 2)], g.u[g.G(i, j - 1)], g.u[g.G(i, j)],
-                                g.u[g.G(i, j + 1)], g.seta_x[g.FE(i, j)], g.seta_y[g.FE(i, j)], g.vfe[g.FE(i, j)],
-                                rtilde(g, i, j - 1, 1), rtilde(g, i, j, 1), finest);
+      fe[g.FE(i, j)] = fvs ? fvs_face(S, g.u[g.G(i, j - 1)], g.u[g.G(i, j)], g.seta_x[g.FE(i, j)],
+                                      g.seta_y[g.FE(i, j)], g.vfe[g.FE(i, j)])
+                           : jst_face(S, g.u[g.G(i, j - 2)], g.u[g.G(i, j - 1)], g.u[g.G(i, j)],
+                                      g.u[g.G(i, j + 1)], g.seta_x[g.FE(i, j)], g.seta_y[g.FE(i, j)],
+                                      g.vfe[g.FE(i, j)], rtilde(g, i, j - 1, 1), rtilde(g, i, j, 1), finest);
       if (S.P.viscous) fvis[g.FE(i, j)] = visc_face(S, g, i, j);
     }
   Fc.assign(ni * nj, V4{});
@@ -954,6 +985,86 @@ static void dense_apply(const Level& g, const std::vector<V4>& r, std::vector<V4
     for (int a = 0; a < 4; ++a) z[c][a] = sol[4 * c + a];
 }
 
+// y = (D + L + U) x: the block operator of eq. (steadylinearized) / (form1) with the blocks of
+// the current build (the same neighbour sets the sweeps use).  With the ARK scaling (1/Omega)
+// and a_t = 0 it is the first-order flux-vector-split residual linearized at frozen face states.
+static void block_apply(const Level& g, const std::vector<V4>& x, std::vector<V4>& y) {
+  const int n = g.ni * g.nj;
+  y.assign(n, V4{});
+  std::vector<Nb> lo, up;
+  for (int j = 0; j < g.nj; ++j)
+    for (int i = 0; i < g.ni; ++i) {
+      const int c = g.C(i, j);
+      V4 t = matvec(g.D[c], x[c]);
+      neighbours(g, i, j, lo, up);
+      for (const Nb& nb : lo) {
+        const V4 m = matvec(nb.B, x[nb.c]);
+        for (int k = 0; k < 4; ++k) t[k] += m[k];
+      }
+      for (const Nb& nb : up) {
+        const V4 m = matvec(nb.B, x[nb.c]);
+        for (int k = 0; k < 4; ++k) t[k] += m[k];
+      }
+      y[c] = t;
+    }
+}
+
+// The "exact" preconditioner (the column of the same name in Table Prec-ARK-stability,
+// section 5.4): z = (D + L + U)^-1 r instead of the SGS factorization, by Gaussian
+// elimination with partial pivoting on the band of the lexicographic ordering (couplings reach
+// one grid row, ni cells, away; the wake cut stays within row 0).  For tiny grids.
+static void exact_apply(const Level& g, const std::vector<V4>& r, std::vector<V4>& z) {
+  const int n = g.ni * g.nj, N = 4 * n;
+  const int b = 4 * g.ni + 3;     // lower and upper bandwidth of D + L + U
+  const int w = 3 * b + 1;        // stored columns: the band plus fill from row exchanges
+  std::vector<double> A((size_t)N * w, 0.0);  // A(row, col) at row * w + (col - row + b)
+  auto at = [&](int row, int col) -> double& { return A[(size_t)row * w + (col - row + b)]; };
+  std::vector<Nb> lo, up;
+  for (int j = 0; j < g.nj; ++j)
+    for (int i = 0; i < g.ni; ++i) {
+      const int c = g.C(i, j);
+      for (int a = 0; a < 4; ++a)
+        for (int q = 0; q < 4; ++q) at(4 * c + a, 4 * c + q) += g.D[c][a][q];
+      neighbours(g, i, j, lo, up);
+      for (const Nb& nb : lo)
+        for (int a = 0; a < 4; ++a)
+          for (int q = 0; q < 4; ++q) at(4 * c + a, 4 * nb.c + q) += nb.B[a][q];
+      for (const Nb& nb : up)
+        for (int a = 0; a < 4; ++a)
+          for (int q = 0; q < 4; ++q) at(4 * c + a, 4 * nb.c + q) += nb.B[a][q];
+    }
+  std::vector<double> rhs(N);
+  for (int c = 0; c < n; ++c)
+    for (int a = 0; a < 4; ++a) rhs[4 * c + a] = r[c][a];
+  for (int k = 0; k < N; ++k) {
+    const int last = std::min(N - 1, k + b);
+    int p = k;
+    for (int a = k + 1; a <= last; ++a)
+      if (std::fabs(at(a, k)) > std::fabs(at(p, k))) p = a;
+    const int cmax = std::min(N - 1, k + 2 * b);  // upper band after row exchanges: b_l + b_u = 2b
+    if (p != k) {
+      for (int col = k; col <= cmax; ++col) std::swap(at(k, col), at(p, col));
+      std::swap(rhs[k], rhs[p]);
+    }
+    for (int a = k + 1; a <= last; ++a) {
+      const double m = at(a, k) / at(k, k);
+      if (m == 0.0) continue;
+      for (int col = k; col <= cmax; ++col) at(a, col) -= m * at(k, col);
+      rhs[a] -= m * rhs[k];
+    }
+  }
+  std::vector<double> sol(N);
+  for (int a = N - 1; a >= 0; --a) {
+    double s = rhs[a];
+    const int cmax = std::min(N - 1, a + 2 * b);
+    for (int col = a + 1; col <= cmax; ++col) s -= at(a, col) * sol[col];
+    sol[a] = s / at(a, a);
+  }
+  z.assign(n, V4{});
+  for (int c = 0; c < n; ++c)
+    for (int a = 0; a < 4; ++a) z[c][a] = sol[4 * c + a];
+}
+
 // ---------------------------------------------------------------- stage loop
 // Generic low-storage preconditioned additive RK / additive W step (sections 4.1, 4.2):
 //   u^(0) = u;  u^(i) = u - alpha_i [dt* W^{-1}] (f^{c,(i-1)} + f^{v,(i-1)}),  i = 1..s
@@ -1029,9 +1140,9 @@ struct LevelOps : StageOps {
       std::vector<V4> tr(n);
       for (size_t c = 0; c < n; ++c)
         for (int k = 0; k < 4; ++k) tr[c][k] = g.dts[c] * r[c][k];
-      if (dense) dense_apply(g, tr, z); else sgs_apply(g, tr, z);
+      if (S.P.precond == 1) exact_apply(g, tr, z); else if (dense) dense_apply(g, tr, z); else sgs_apply(g, tr, z);
     } else {
-      if (dense) dense_apply(g, r, z); else sgs_apply(g, r, z);
+      if (S.P.precond == 1) exact_apply(g, r, z); else if (dense) dense_apply(g, r, z); else sgs_apply(g, r, z);
       for (size_t c = 0; c < n; ++c)
         for (int k = 0; k < 4; ++k) z[c][k] = g.dts[c] * z[c][k];
     }
@@ -1507,7 +1618,7 @@ void or_precond_apply(void* h, int l, double cfl, const double* r, double* z, in
   std::vector<V4> rv(n), zv;
   for (int q = 0; q < n; ++q)
     for (int k = 0; k < 4; ++k) rv[q][k] = r[k * n + q];
-  if (dense) dense_apply(g, rv, zv); else sgs_apply(g, rv, zv);
+  if (dense == 2 || S->P.precond == 1) exact_apply(g, rv, zv); else if (dense) dense_apply(g, rv, zv); else sgs_apply(g, rv, zv);
   for (int q = 0; q < n; ++q)
     for (int k = 0; k < 4; ++k) z[k * n + q] = zv[q][k];
   if (D_out)
@@ -1518,6 +1629,22 @@ void or_precond_apply(void* h, int l, double cfl, const double* r, double* z, in
 
 // Face blocks (A+, A- times |S|) built from the current state: i-faces then j-faces,
 // 16 per block row-major.
+// y = (D + L + U) x with the blocks built at level l's current state and pseudo CFL cfl.
+void or_block_apply(void* h, int l, double cfl, const double* x, double* y) {
+  Solver* S = static_cast<Solver*>(h);
+  Level& g = S->lev[l];
+  bc_fill(*S, g);
+  pseudo_dt(*S, g, cfl);
+  build_blocks(*S, g);
+  const int n = g.ni * g.nj;
+  std::vector<V4> xv(n), yv;
+  for (int q = 0; q < n; ++q)
+    for (int k = 0; k < 4; ++k) xv[q][k] = x[k * n + q];
+  block_apply(g, xv, yv);
+  for (int q = 0; q < n; ++q)
+    for (int k = 0; k < 4; ++k) y[k * n + q] = yv[q][k];
+}
+
 void or_face_blocks(void* h, int l, double* axp, double* axm, double* aep, double* aem) {
   Solver* S = static_cast<Solver*>(h);
   Level& g = S->lev[l];
