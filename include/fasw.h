@@ -82,6 +82,10 @@ typedef struct fasw_params {
   int precision;       /* enum fasw_precision */
   int norm_all;        /* 0: RMS of the density residual; 1: RMS over all 4 components */
   long long spin_limit;/* bound on device-side waits (iterations); <= 0 picks the default */
+  int flux;            /* residual face flux: 0 = JST (section 2), 1 = first-order flux-vector splitting
+                          A+(u_bar) u_L + A-(u_bar) u_R with the cutoff d_cut (the discretization of
+                          eqs. steadylinearized / form1, section 4.4, whose linearization at frozen
+                          face states the preconditioner's blocks are) */
 } fasw_params;
 
 typedef struct fasw_ctx fasw_ctx;

@@ -1589,9 +1589,12 @@ void or_wall_force(void* h, double* fx, double* fy) {
       fx[i] = fy[i] = 0.0;
       continue;
     }
-    const FaceFlux f = jst_face(*S, g.u[g.G(i, -2)], g.u[g.G(i, -1)], g.u[g.G(i, 0)], g.u[g.G(i, 1)],
-                                g.seta_x[g.FE(i, 0)], g.seta_y[g.FE(i, 0)], g.vfe[g.FE(i, 0)],
-                                rtilde(g, i, -1, 1), rtilde(g, i, 0, 1), true);
+    const FaceFlux f = S->P.flux == 1
+                           ? fvs_face(*S, g.u[g.G(i, -1)], g.u[g.G(i, 0)], g.seta_x[g.FE(i, 0)],
+                                      g.seta_y[g.FE(i, 0)], g.vfe[g.FE(i, 0)])
+                           : jst_face(*S, g.u[g.G(i, -2)], g.u[g.G(i, -1)], g.u[g.G(i, 0)], g.u[g.G(i, 1)],
+                                      g.seta_x[g.FE(i, 0)], g.seta_y[g.FE(i, 0)], g.vfe[g.FE(i, 0)],
+                                      rtilde(g, i, -1, 1), rtilde(g, i, 0, 1), true);
     const V4 v = S->P.viscous ? visc_face(*S, g, i, 0) : V4{};
     fx[i] = -(f.hc[1] - f.hd[1] - v[1]);
     fy[i] = -(f.hc[2] - f.hd[2] - v[2]);

@@ -420,6 +420,7 @@ int fasw_create(int ni, int nj, int n_wake, const double* x, const double* y, in
   *out = nullptr;
   if (ni < 4 || nj < 2 || n_wake < 0 || 2 * n_wake >= ni || p->nlevels < 1 || p->nlevels > 12) return FASW_ERR_ARG;
   if (p->scheme < 0 || p->scheme > 7 || p->gamma_cycle < 1 || p->gamma_cycle > 2 || p->nu1 < 1) return FASW_ERR_ARG;
+  if (p->flux < 0 || p->flux > 1) return FASW_ERR_ARG;
   const int f = 1 << (p->nlevels - 1);
   if (ni % f || nj % f || n_wake % f || ni / f < 4 || nj / f < 2) return FASW_ERR_ARG;
   if (!(p->mach > 0.0) || (p->viscous && !(p->re > 0.0))) return FASW_ERR_ARG;
@@ -443,6 +444,8 @@ int fasw_create(int ni, int nj, int n_wake, const double* x, const double* y, in
   c->ph.viscous = p->viscous;
   c->ph.turb = p->turb;
   c->ph.sensor = p->sensor;
+  c->ph.flux = p->flux;
+  c->ph.d_cut = p->d_cut;
   free_stream(p->mach, p->alpha_deg, c->ph.uinf);
   set_free_stream_prims(c->ph);
   const Coef& cf = kCoef[p->scheme % 4];

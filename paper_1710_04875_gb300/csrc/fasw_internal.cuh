@@ -113,6 +113,8 @@ struct PhysParams {
   double s_coarse;
   int viscous, turb, sensor;
   int moving;  // grid in rigid motion: moving-wall ghosts
+  int flux;    // residual face flux: 0 = JST, 1 = first-order flux-vector splitting
+  double d_cut;  // eigenvalue cutoff of the flux-vector splitting (also the preconditioner's)
 };
 
 // Primitive variables of the free stream for the far-field boundary, formed once on the host.

@@ -114,6 +114,8 @@ extern "C" int fasw_residual_noalloc(int ni, int nj, int n_wake, const double* x
   ph.viscous = p->viscous;
   ph.turb = 0;
   ph.sensor = p->sensor;
+  ph.flux = p->flux == 1 ? 1 : 0;
+  ph.d_cut = p->d_cut;
   {
     const double al = p->alpha_deg * M_PI / 180.0;
     const double pinf = 1.0 / (GAM * p->mach * p->mach);

@@ -305,6 +305,62 @@ __device__ __forceinline__ double sensor_val(double qm, double q0, double qp) {
 // JST flux through a face with area vector (sx, sy) from L to R; stencil LL, L, R, RR
 // given as ghosted indices.  hc: central part; hd: dissipation d (section 2).
 // On a moving face (grid volume flux vf) the convective flux is F . S - u vf.
+// First-order flux-vector-split face flux (the discretization section 4.4 linearizes for the
+// preconditioner): h = A+(u_bar) u_L + A-(u_bar) u_R at the mean state u_bar, with the cutoff
+// eigenvalues of eq. (cutoff), split as the JST flux is (h = hc - hd): hc = A(u_bar)(u_L + u_R)/2,
+// hd = (A+ - A-)(u_R - u_L)/2.  Each product uses the closed rank-2 form of R diag(l) R^-1 for
+// the wave pattern (l1, l1, l3, l4): M(l) x = l1 x + r0 (g0 . x) + r1 (g1 . x) with
+// r0 = (1, u, v, H), r1 = (0, nx, ny, vn), g0 = c1/a^2 dp + c2/a dvn, g1 = c2/a dp + c1 dvn,
+// dp = (gamma-1)(q^2/2, -u, -v, 1), dvn = (-vn, nx, ny, 0), c1 = (l3+l4)/2 - l1, c2 = (l3-l4)/2.
+__device__ __forceinline__ double fvs_cutabs(double lam, double a, double d) {
+  const double al = fabs(lam), ad = a * d;
+  return (d > 0.0 && al <= ad) ? 0.5 * (ad + lam * lam / ad) : al;
+}
+
+__device__ void fvs_face(const LevelDev& L, int gL, int gR, double sx, double sy, double vf, double dcut,
+                         double hc[4], double hd[4]) {
+  double uL[4], uR[4], ub[4], xs[4], xd[4];
+  load4(L, gL, uL);
+  load4(L, gR, uR);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    ub[k] = 0.5 * (uL[k] + uR[k]);
+    xs[k] = uL[k] + uR[k];
+    xd[k] = uR[k] - uL[k];
+  }
+  const double g1 = GAM - 1.0;
+  const double len = sqrt(sx * sx + sy * sy), rl = 1.0 / len;
+  const double nx = sx * rl, ny = sy * rl;
+  const double rr = 1.0 / ub[0], u = ub[1] * rr, v = ub[2] * rr;
+  const double q2 = u * u + v * v;
+  const double p = g1 * (ub[3] - 0.5 * ub[0] * q2);
+  const double a = sqrt(GAM * p * rr), ia = 1.0 / a;
+  const double H = (ub[3] + p) * rr;
+  const double vn = u * nx + v * ny, vr = vn - vf * rl;
+  const double r0[4] = {1.0, u, v, H}, r1[4] = {0.0, nx, ny, vn};
+  const double dp[4] = {0.5 * g1 * q2, -g1 * u, -g1 * v, g1}, dv[4] = {-vn, nx, ny, 0.0};
+  // M(l) x for the eigenvalue triple (l1, l3, l4), times the face length
+  auto apply = [&](double l1, double l3, double l4, const double x[4], double out[4]) {
+    double dpx = 0.0, dvx = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      dpx += dp[k] * x[k];
+      dvx += dv[k] * x[k];
+    }
+    const double c1 = 0.5 * (l3 + l4) - l1, c2 = 0.5 * (l3 - l4);
+    const double s0 = c1 * ia * ia * dpx + c2 * ia * dvx, s1 = c2 * ia * dpx + c1 * dvx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = len * (l1 * x[k] + r0[k] * s0 + r1[k] * s1);
+  };
+  apply(vr, vr + a, vr - a, xs, hc);
+  apply(fvs_cutabs(vr, a, dcut), fvs_cutabs(vr + a, a, dcut), fvs_cutabs(vr - a, a, dcut), xd, hd);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    hc[k] *= 0.5;
+    hd[k] *= 0.5;
+  }
+}
+
 __device__ void jst_face(const LevelDev& L, int gLL, int gL, int gR, int gRR, double sx, double sy, double vf,
                          double rtL, double rtR, double s_coarse, double hc[4], double hd[4]) {
   double uL[4], uR[4];
@@ -434,8 +490,11 @@ __global__ void __launch_bounds__(res_threads(TY)) k_residual(LevelDev L, PhysPa
     if (i <= ni && j < nj) {
       const int f = j * (ni + 1) + i;
       double hc[4], hd[4];
-      jst_face(L, gidx(L, i - 2, j), gidx(L, i - 1, j), gidx(L, i, j), gidx(L, i + 1, j), L.sxi[f],
-               L.sxi[L.nfx + f], L.vfx[f], rt_cell(L, i - 1, j, 0), rt_cell(L, i, j, 0), ph.s_coarse, hc, hd);
+      if (ph.flux)
+        fvs_face(L, gidx(L, i - 1, j), gidx(L, i, j), L.sxi[f], L.sxi[L.nfx + f], L.vfx[f], ph.d_cut, hc, hd);
+      else
+        jst_face(L, gidx(L, i - 2, j), gidx(L, i - 1, j), gidx(L, i, j), gidx(L, i + 1, j), L.sxi[f],
+                 L.sxi[L.nfx + f], L.vfx[f], rt_cell(L, i - 1, j, 0), rt_cell(L, i, j, 0), ph.s_coarse, hc, hd);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         xc[k][ty][tx] = hc[k];
@@ -449,8 +508,11 @@ __global__ void __launch_bounds__(res_threads(TY)) k_residual(LevelDev L, PhysPa
       const int f = j * ni + i;
       const double sx = L.seta[f], sy = L.seta[L.nfe + f];
       double hc[4], hd[4];
-      jst_face(L, gidx(L, i, j - 2), gidx(L, i, j - 1), gidx(L, i, j), gidx(L, i, j + 1), sx, sy, L.vfe[f],
-               rt_cell(L, i, j - 1, 1), rt_cell(L, i, j, 1), ph.s_coarse, hc, hd);
+      if (ph.flux)
+        fvs_face(L, gidx(L, i, j - 1), gidx(L, i, j), sx, sy, L.vfe[f], ph.d_cut, hc, hd);
+      else
+        jst_face(L, gidx(L, i, j - 2), gidx(L, i, j - 1), gidx(L, i, j), gidx(L, i, j + 1), sx, sy, L.vfe[f],
+                 rt_cell(L, i, j - 1, 1), rt_cell(L, i, j, 1), ph.s_coarse, hc, hd);
       if (ph.viscous) {
         double hv[4];
         visc_face(L, ph, i, j, sx, sy, hv);
@@ -540,8 +602,11 @@ __global__ void k_wall_force(LevelDev L, PhysParams ph, double* fx, double* fy) 
   }
   const double sx = L.seta[i], sy = L.seta[L.nfe + i];
   double hc[4], hd[4];
-  jst_face(L, gidx(L, i, -2), gidx(L, i, -1), gidx(L, i, 0), gidx(L, i, 1), sx, sy, L.vfe[i], rt_cell(L, i, -1, 1),
-           rt_cell(L, i, 0, 1), ph.s_coarse, hc, hd);
+  if (ph.flux)
+    fvs_face(L, gidx(L, i, -1), gidx(L, i, 0), sx, sy, L.vfe[i], ph.d_cut, hc, hd);
+  else
+    jst_face(L, gidx(L, i, -2), gidx(L, i, -1), gidx(L, i, 0), gidx(L, i, 1), sx, sy, L.vfe[i],
+             rt_cell(L, i, -1, 1), rt_cell(L, i, 0, 1), ph.s_coarse, hc, hd);
   if (ph.viscous) {
     double hv[4];
     visc_face(L, ph, i, 0, sx, sy, hv);

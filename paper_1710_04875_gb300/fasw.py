@@ -39,7 +39,7 @@ class Params(C.Structure):
         ("mach", C.c_double), ("alpha_deg", C.c_double), ("re", C.c_double), ("pr", C.c_double),
         ("prt", C.c_double), ("eta", C.c_double), ("d_cut", C.c_double), ("cfl", C.c_double),
         ("cfl_ramp", C.c_double), ("ramp_cycles", C.c_int), ("s_coarse", C.c_double),
-        ("precision", C.c_int), ("norm_all", C.c_int), ("spin_limit", C.c_longlong),
+        ("precision", C.c_int), ("norm_all", C.c_int), ("spin_limit", C.c_longlong), ("flux", C.c_int),
     ]
 
 
@@ -138,6 +138,8 @@ def default_params(**kw) -> Params:
             v = SCHEME_IDS[v]
         if k == "precision" and isinstance(v, str):
             v = {"fp64": FASW_FP64, "mixed": FASW_MIXED}[v]
+        if k == "flux" and isinstance(v, str):
+            v = {"jst": 0, "fvs": 1}[v]
         setattr(p, k, v)
     return p
 

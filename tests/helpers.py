@@ -8,17 +8,17 @@ import oracle as O
 
 def pair_params(scheme="AW3", nlevels=3, gamma_cycle=1, nu1=1, viscous=0, turb=0, sensor=None,
                 mach=0.8, alpha_deg=1.25, re=1e6, pr=0.75, prt=0.9, eta=0.8, d_cut=0.5, cfl=1e4,
-                cfl_ramp=20.0, ramp_cycles=2, s_coarse=0.25, norm_all=0, precision="fp64"):
+                cfl_ramp=20.0, ramp_cycles=2, s_coarse=0.25, norm_all=0, precision="fp64", flux="jst"):
     sensor = (1 if viscous else 0) if sensor is None else sensor
     po = O.make_params(scheme, nlevels=nlevels, gamma_cycle=gamma_cycle, nu1=nu1, viscous=viscous, turb=turb,
                        sensor=sensor, mach=mach, alpha_deg=alpha_deg, re=re, pr=pr, prt=prt, eta=eta,
                        d_cut=d_cut, cfl=cfl, cfl_ramp=cfl_ramp, ramp_cycles=ramp_cycles, s_coarse=s_coarse,
-                       norm_all=norm_all)
+                       norm_all=norm_all, flux=flux)
     import paper_1710_04875_gb300 as P
     pg = P.default_params(scheme=scheme, nlevels=nlevels, gamma_cycle=gamma_cycle, nu1=nu1, viscous=viscous,
                           turb=turb, sensor=sensor, mach=mach, alpha_deg=alpha_deg, re=re, pr=pr, prt=prt,
                           eta=eta, d_cut=d_cut, cfl=cfl, cfl_ramp=cfl_ramp, ramp_cycles=ramp_cycles,
-                          s_coarse=s_coarse, norm_all=norm_all, precision=precision)
+                          s_coarse=s_coarse, norm_all=norm_all, precision=precision, flux=flux)
     return po, pg
 
 
