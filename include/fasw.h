@@ -170,6 +170,15 @@ int fasw_use_graphs(fasw_ctx* ctx, int enable);
  * cycles. */
 int fasw_set_sweep(fasw_ctx* ctx, int kind);
 
+/* The "exact" preconditioner (the column of that name in section 5.4's tables): iters > 0 makes
+ * every application of the preconditioner, in the smoother and in fasw_precond_apply, continue
+ * the SGS solve by iters block Gauss-Seidel corrections x <- x + P^-1 (r - (D+L+U) x) (P the SGS
+ * factorization, applied by the warp-strip sweep), which converge to (D+L+U)^-1 r, the inverse of
+ * the whole first-order flux-vector-split operator the blocks form; 0 (the default) is the
+ * paper's SGS preconditioner.  FASW_ERR_ARG for iters outside 0..1000 or a level the warp-strip
+ * sweep does not fit.  Synchronizes the stream; drops captured cycles. */
+int fasw_set_exact_preconditioner(fasw_ctx* ctx, int iters);
+
 /* Tile height of the residual kernel (tiles of 31 x rows cells, one thread per face), on every
  * level: rows = 1, 2, 4 or 8, or 0 (the default) for a choice from each level's size.  The
  * result does not depend on it.  Synchronizes the stream; drops captured cycles. */

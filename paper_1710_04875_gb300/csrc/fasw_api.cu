@@ -189,6 +189,7 @@ int alloc_level(fasw_ctx* c, LevelDev& L) {
     A(L.wsEdge, ws_edge_floats(L.ni, L.nj));
     A(L.wsZ, 2 * wv);
     A(L.wsT, 4 * n);
+    A(L.wsX, 4 * n);
     // padding positions of the skewed arrays are never written: they must read as zero
     CKR(cudaMemsetAsync(L.wsF, 0, wf * sizeof(float), c->st));
     CKR(cudaMemsetAsync(L.wsB, 0, wf * sizeof(float), c->st));
@@ -228,6 +229,7 @@ void free_stream(double mach, double alpha_deg, double w[4]) {
 // (mixed), else one CTA (mixed) or strips (FP64); a requested kind that does not apply to the
 // level or precision falls back the same way.
 int level_sweep_kind(const fasw_ctx* c, const LevelDev& L) {
+  if (c->exact_iters > 0 && L.wsF) return SWEEP_WS;  // the exact-preconditioner iterations run on it
   int k = c->sweep_kind;
   if (k == SWEEP_AUTO) {
     // measured per level on GB300: the warp strips win for FP64 on every level and for FP32 from
@@ -249,7 +251,7 @@ void run_sweep(fasw_ctx* c, const LevelDev& L, int do_update, double alpha, cons
     return;
   }
   c->launches += launch_sweep(L, c->mixed, level_sweep_kind(c, L), do_update, c->sc.aw, alpha, rhs, c->d_prog,
-                              c->d_err, c->spin_limit, c->st);
+                              c->d_err, c->spin_limit, c->st, c->exact_iters);
 }
 
 void bc_aux(fasw_ctx* c, int l, double cfl, int want_dts) {
@@ -699,6 +701,17 @@ int fasw_set_sweep(fasw_ctx* c, int kind) {
   int r = sync(c);
   if (r) return r;
   c->sweep_kind = kind;
+  drop_graphs(c);
+  return FASW_OK;
+}
+
+int fasw_set_exact_preconditioner(fasw_ctx* c, int iters) {
+  if (!c || iters < 0 || iters > 1000) return FASW_ERR_ARG;
+  for (auto& L : c->lev)
+    if (iters > 0 && !L.wsF) return FASW_ERR_ARG;
+  int r = sync(c);
+  if (r) return r;
+  c->exact_iters = iters;
   drop_graphs(c);
   return FASW_OK;
 }

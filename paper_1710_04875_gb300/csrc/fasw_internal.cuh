@@ -103,6 +103,7 @@ struct LevelDev {
   float* wsEdge;
   float* wsZ;
   double* wsT;
+  double* wsX;  // accumulated solution of the exact-preconditioner iterations (4 per cell)
 };
 
 struct PhysParams {

@@ -23,7 +23,7 @@ void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st);
 // do_update.  prog: 2 * sweep_strips(L) flags, err: device error word.  Returns the number of
 // kernels launched.
 int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, double alpha, const double* rhs,
-                 long long* prog, int* err, long long limit, cudaStream_t st);
+                 long long* prog, int* err, long long limit, cudaStream_t st, int exact_iters = 0);
 int sweep_strips(const LevelDev& L);
 // Warp-strip sweep (kernels_sweep_ws.cu): whether a level can use it, the sizes of its arrays
 // (floats of wsF / wsB; of wsC / wsY), its strips, the skewed blocks from the transfer blocks
@@ -35,8 +35,9 @@ size_t ws_vec_floats(int ni, int nj);
 size_t ws_edge_floats(int ni, int nj);
 int ws_strips(int nj);
 void launch_ws_prep(const LevelDev& L, int mixed, cudaStream_t st);
+// exact_iters > 0: that many block Gauss-Seidel corrections toward the exact (D + L + U)^-1
 int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int aw, double alpha, const double* rhs,
-                    long long* prog, int* err, long long limit, cudaStream_t st);
+                    long long* prog, int* err, long long limit, cudaStream_t st, int exact_iters = 0);
 // Hyperplane-staged FP32 sweep: whether a level fits (rows, shared memory), and the entries
 // (ni + nj - 1) * nj of its hyperplane-major arrays (hpF, hpB: 32 floats each; hpC, hpY: 4).
 bool hp_fits(int ni, int nj, int nw);

@@ -752,8 +752,9 @@ bool hp_fits(int ni, int nj, int nw) {
 }
 
 int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, double alpha, const double* rhs,
-                 long long* prog, int* err, long long limit, cudaStream_t st) {
-  if (kind == SWEEP_WS && L.wsF) return launch_ws_sweep(L, mixed, 1, do_update, aw, alpha, rhs, prog, err, limit, st);
+                 long long* prog, int* err, long long limit, cudaStream_t st, int exact_iters) {
+  if (kind == SWEEP_WS && L.wsF)
+    return launch_ws_sweep(L, mixed, 1, do_update, aw, alpha, rhs, prog, err, limit, st, exact_iters);
   if (kind == SWEEP_WS) kind = mixed ? SWEEP_AUTO : SWEEP_STRIPS;
   if (is_hp(kind) && mixed && L.hpF) {
     launch_pdl(k_hp_cy, (L.n + 127) / 128, 128, 0, st, L, reinterpret_cast<const float*>(L.tb), rhs);

@@ -514,6 +514,84 @@ __global__ void k_ws_finish(LevelDev L, const float4* z0, const float4* dz, int 
   }
 }
 
+// ---------------------------------------------------------------- the exact preconditioner
+// Block Gauss-Seidel iterations on the full first-order operator A = D + L + U (the "exact"
+// preconditioner of section 5.4's tables is A^-1): x <- x + P^-1 (r - A x), each P^-1 one
+// warp-strip sweep pair, converging to A^-1 r.  x accumulates in FP64 (cell-major, 4 per cell).
+
+// x = (init ? 0 : x) + z0 (+ dz), z0 / dz skewed in the backward order
+__global__ void k_ws_accum(LevelDev L, const float4* z0, const float4* dz, double* x, int init) {
+  pdl_entry();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  const int i = c % L.ni, j = c / L.ni;
+  const size_t zp = ws_bpos(i, j, ws_steps(L.ni));
+  const float4 a = z0[zp];
+  double v[4] = {a.x, a.y, a.z, a.w};
+  if (dz) {
+    const float4 d = dz[zp];
+    v[0] += d.x;
+    v[1] += d.y;
+    v[2] += d.z;
+    v[3] += d.w;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) x[4 * (size_t)c + q] = (init ? 0.0 : x[4 * (size_t)c + q]) + v[q];
+}
+
+// D^-1 (r - A x) = D^-1 r - x + G_W x_W + G_S x_S + H_E x_E + H_N x_N (+ G_S x_mirror on row 0 of
+// the wake cut, either side), as the next sweep's right-hand side (skewed, FP32)
+template <typename T>
+__global__ void k_ws_exact_defect(LevelDev L, const T* tb, const double* rhs, const double* x, float4* C) {
+  pdl_entry();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  const int ni = L.ni, nj = L.nj, n = L.n, i = c % ni, j = c / ni;
+  double r[4], acc[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = rhs[(size_t)k * n + c];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double a = -x[4 * (size_t)c + q];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a += double(tb[(size_t)(4 * q + k) * n + c]) * r[k];
+    acc[q] = a;
+  }
+  auto add = [&](int blk, int cn) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[q] += double(tb[(size_t)(blk * 16 + 4 * q + k) * n + c]) * x[4 * (size_t)cn + k];
+  };
+  if (i > 0) add(1, c - 1);
+  if (j > 0) add(2, c - ni);
+  else if (L.nw > 0 && (i < L.nw || i >= ni - L.nw)) add(2, ni - 1 - i);
+  if (i < ni - 1) add(3, c + 1);
+  if (j < nj - 1) add(4, c + ni);
+  const int b = j / WS_ROWS, jl = j % WS_ROWS, Mp = ws_steps(ni);
+  C[((size_t)b * Mp + (i + jl)) * WS_ROWS + jl] = make_float4(float(acc[0]), float(acc[1]), float(acc[2]), float(acc[3]));
+}
+
+// the stage update (or the result vector) from the accumulated x
+__global__ void k_ws_finish_x(LevelDev L, const double* x, int do_update, int aw, double alpha, int mixed) {
+  pdl_entry();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  const int n = L.n, i = c % L.ni, j = c / L.ni;
+  if (do_update) {
+    const double sc = aw ? alpha : alpha * L.dts[c];
+    const size_t g = (size_t)(j + 2) * L.P + (i + 2);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) L.u[q * (size_t)L.Gn + g] = L.u0[q * (size_t)n + c] - sc * x[4 * (size_t)c + q];
+  } else if (mixed) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) L.yz32[q * (size_t)n + c] = float(x[4 * (size_t)c + q]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) L.yz64[q * (size_t)n + c] = x[4 * (size_t)c + q];
+  }
+}
+
 constexpr size_t kWsSmemMax = 227 * 1024;
 
 }  // namespace
@@ -572,7 +650,7 @@ cudaError_t ws_sweep_launch(const LevelDev& L, float4* zout, long long* prog, in
 }  // namespace
 
 int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int aw, double alpha, const double* rhs,
-                    long long* prog, int* err, long long limit, cudaStream_t st) {
+                    long long* prog, int* err, long long limit, cudaStream_t st, int exact_iters) {
   const int g = (L.n + 127) / 128;
   float4* z0 = reinterpret_cast<float4*>(L.wsZ);
   float4* dz = z0 + ws_vec_floats(L.ni, L.nj) / 4;
@@ -593,6 +671,24 @@ int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int
                static_cast<const double*>(L.wsT), reinterpret_cast<float4*>(L.wsC));
     ws_sweep_launch(L, dz, prog, err, limit, st);
     launches += 3;
+  }
+  if (exact_iters > 0) {
+    launch_pdl(k_ws_accum, g, 128, 0, st, L, static_cast<const float4*>(z0),
+               corr ? static_cast<const float4*>(dz) : nullptr, L.wsX, 1);
+    ++launches;
+    for (int it = 0; it < exact_iters; ++it) {
+      if (mixed)
+        launch_pdl(k_ws_exact_defect<float>, g, 128, 0, st, L, reinterpret_cast<const float*>(L.tb), rhs,
+                   static_cast<const double*>(L.wsX), reinterpret_cast<float4*>(L.wsC));
+      else
+        launch_pdl(k_ws_exact_defect<double>, g, 128, 0, st, L, static_cast<const double*>(L.tb), rhs,
+                   static_cast<const double*>(L.wsX), reinterpret_cast<float4*>(L.wsC));
+      ws_sweep_launch(L, z0, prog, err, limit, st);
+      launch_pdl(k_ws_accum, g, 128, 0, st, L, static_cast<const float4*>(z0), nullptr, L.wsX, 0);
+      launches += 3;
+    }
+    launch_pdl(k_ws_finish_x, g, 128, 0, st, L, static_cast<const double*>(L.wsX), do_update, aw, alpha, mixed);
+    return launches + 1;
   }
   launch_pdl(k_ws_finish, g, 128, 0, st, L, static_cast<const float4*>(z0), corr ? static_cast<const float4*>(dz) : nullptr,
              do_update, aw, alpha, mixed);

@@ -85,6 +85,7 @@ def library(variant: str = "perf"):
             "fasw_profile": (i, [p, i]),
             "fasw_use_graphs": (i, [p, i]),
             "fasw_set_residual_tile": (i, [p, i]),
+            "fasw_set_exact_preconditioner": (i, [p, i]),
             "fasw_set_sweep": (i, [p, i]),
             "fasw_set_motion": (i, [p, d, d, d, d]),
             "fasw_dual_time_step": (i, [p, d, i, d, i, dp, C.POINTER(i)]),
@@ -298,6 +299,11 @@ class Solver:
         kinds = {"auto": 0, "reference": 1, "cta": 2, "strips": 3, "strips16": 4, "staged": 5, "staged4": 6,
                  "staged8": 7, "strips4": 8, "warp": 9}
         _check(self.lib.fasw_set_sweep(self.h, kinds.get(kind, kind)), "fasw_set_sweep")
+
+    def set_exact_preconditioner(self, iters: int):
+        """iters > 0: every preconditioner application iterates toward (D+L+U)^-1 (the exact
+        preconditioner) by that many block Gauss-Seidel corrections; 0: the SGS preconditioner."""
+        _check(self.lib.fasw_set_exact_preconditioner(self.h, int(iters)), "fasw_set_exact_preconditioner")
 
     def set_residual_tile(self, rows: int):
         """Residual tile height on every level: 1, 2, 4, 8, or 0 for the size rule."""
