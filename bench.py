@@ -502,6 +502,37 @@ def measure_unsteady_adjoint(P, stream, nsteps=128, snapshots=8, n_bumps=16):
                     "steady adjoint of the initial state"}
 
 
+def measure_schemes_c2(P, stream, max_cycles=1500):
+    """The 3- and 5-stage W methods of Table "RK smoothers" (AW3, AW5J, AW51, AW52) on the
+    256x64 RANS workload from the free stream to a 6-order drop (mixed precision)."""
+    g = grid_of(C2)
+    out = {"workload": C2["name"], "precision": "mixed"}
+    for scheme in ("AW3", "AW5J", "AW51", "AW52"):
+        s = P.Solver(g, params_of(P, C2, "mixed", scheme=scheme), stream=stream.cuda_stream)
+        out[scheme] = solve_timed(s, 1e-6, max_cycles)
+        s.close()
+    return out
+
+
+def measure_preconditioners_c1(P, stream, exact_iters=40, max_cycles=400):
+    """The 128x32 Euler case (M 0.8, alpha 1.25 deg, 3-level V, AW3 robust: d 0.5, c* 1e4): the
+    paper's SGS preconditioner against the exact one ((D+L+U)^-1, reached by exact_iters block
+    Gauss-Seidel corrections), with the JST residual and with the first-order flux-vector-split
+    residual whose linearization the blocks are; FP64, to a 6-order drop."""
+    g = make_cgrid(128, 32)
+    out = {"workload": "euler_128x32", "exact_iterations": exact_iters}
+    for flux in ("jst", "fvs"):
+        for prec in ("sgs", "exact"):
+            p = P.default_params(scheme="AW3", nlevels=3, gamma_cycle=1, mach=0.8, alpha_deg=1.25, cfl=1e4,
+                                 flux=flux)
+            s = P.Solver(g, p, stream=stream.cuda_stream)
+            if prec == "exact":
+                s.set_exact_preconditioner(exact_iters)
+            out[f"{flux}_{prec}"] = solve_timed(s, 1e-6, max_cycles)
+            s.close()
+    return out
+
+
 def measure_mesh_independence(P, stream, max_cycles=1500):
     """Convergence rates of AW3 on three synthetic C-grids of one family (cells 256x32, 384x48,
     512x64: the sizes of the paper's mesh-independence table), thin-layer RANS at M 0.796,
@@ -808,6 +839,8 @@ def main():
                                                  / np.linalg.norm(states["fp64"]))
         extras["c2_256x64"] = measure_wcycles(P, C2, stream, flush, args.steps, args.warmup)
         extras["c2_256x64"]["smoothers_to_6_orders"] = measure_smoothers_c2(P, stream)
+        extras["c2_256x64"]["schemes_to_6_orders"] = measure_schemes_c2(P, stream)
+        extras["c1_preconditioners"] = measure_preconditioners_c1(P, stream)
         extras["c3_512x128"] = measure_wcycles(P, C3, stream, flush, min(args.steps, 10), args.warmup)
         if args.pitch_steps > 0:
             extras["c3_512x128"]["pitching"] = measure_pitching_c3(P, stream, nsteps=args.pitch_steps)
