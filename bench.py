@@ -66,8 +66,8 @@ BYTES_PER_CELL = {"fp64": {"sgs": 1680.0, "residual": 232.0}, "mixed": {"sgs": 5
 # launch (dram__bytes_read.sum + dram__bytes_write.sum over the cells of that launch); None where
 # no capture of the current kernel exists.
 # FP64: 395.6 MB read + 1.1 MB written by one finest-level application on the 262,144 cells of
-# the 1024x256 grid (rhs, two sweep pairs, the defect kernels, the update), profiles/ summary
-# sweep_ws_fp64_dram_rans_1024x256.md.
+# the 1024x256 grid (rhs, two sweep pairs, the defect kernels, the update), captured by ncu with
+# dram__bytes_read.sum and dram__bytes_write.sum.
 DRAM_BYTES_PER_CELL = {"fp64": {"sgs": 396.7e6 / 262144}, "mixed": {"sgs": None}}
 
 
