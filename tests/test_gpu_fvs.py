@@ -43,7 +43,10 @@ def test_fvs_cycle_history_and_force():
 @pytest.mark.parametrize("scheme", ["AW3", "ARK3J"])
 def test_exact_preconditioner_converges_to_the_oracles_direct_solve(precision, scheme):
     """The GPU's block Gauss-Seidel corrections toward (D+L+U)^-1 approach the oracle's banded
-    direct solve geometrically; 60 corrections reach it to 1e-9 (FP64) / FP32 accuracy."""
+    direct solve geometrically: with the AW blocks (I + eta dt* J) the SGS factor is close to the
+    whole operator and 60 corrections reach the direct solve to 1e-9 (FP64) / FP32 accuracy; the
+    ARK blocks (J alone) are far less diagonally dominant (measured contraction about 0.93 per
+    correction on this grid), so they take 400."""
     g = make_cgrid(48, 12, n_wake=6, jitter=0.03, seed=5)
     o, s = make_pair(g, scheme=scheme, nlevels=1, d_cut=0.5, precision=precision)
     u = perturbed_state(0.8, 1.25, 12, 48, amp=0.05, seed=6)
@@ -51,7 +54,7 @@ def test_exact_preconditioner_converges_to_the_oracles_direct_solve(precision, s
     r = np.random.default_rng(8).standard_normal((4, 12, 48))
     ze, _ = o.precond_apply(r, 50.0, dense="exact")
     errs = []
-    for k in (2, 8, 60):
+    for k in (2, 8, 60 if scheme == "AW3" else 400):
         s.set_exact_preconditioner(k)
         errs.append(rel_err(s.precond_apply(r, 50.0), ze))
     assert errs[0] > errs[1] > errs[2] or errs[2] < 1e-12
@@ -64,7 +67,7 @@ def test_exact_preconditioner_converges_to_the_oracles_direct_solve(precision, s
 
 def test_exact_preconditioner_in_the_smoother():
     """AW3 with the exact preconditioner inside the stage loop: the GPU's smoothing steps follow
-    the oracle's (precond exact, direct solve) to the accuracy of 60 corrections."""
+    the oracle's (precond exact, direct solve) to the accuracy of 200 corrections."""
     g = make_cgrid(32, 8, n_wake=4)
     from tests.helpers import pair_params
     import oracle as O
@@ -72,7 +75,7 @@ def test_exact_preconditioner_in_the_smoother():
     po, pg = pair_params(nlevels=1, mach=0.8, alpha_deg=1.25, cfl=200.0)
     po.precond = 1
     o, s = O.Oracle(g, po), P.Solver(g, pg)
-    s.set_exact_preconditioner(60)
+    s.set_exact_preconditioner(200)
     u = perturbed_state(0.8, 1.25, 8, 32, amp=0.02, seed=9)
     o.set_state(u); s.set_state(u)
     for _ in range(3):
