@@ -222,12 +222,25 @@ int fasw_dual_time_step(fasw_ctx* ctx, double dt, int bdf_order, double drop, in
 
 /* C_L and C_D at the current state.  Synchronizes. */
 int fasw_force_coefficients(fasw_ctx* ctx, double* cl, double* cd);
-/* Assembles J = dF/du at the current state by central differences with relative step h_rel
- * (step h_rel * max(1, |u|) per unit), perturbing all cells of one colour at a time (a greedy
- * colouring in which no residual stencil holds two cells of one colour), and the state
- * gradients of C_L and C_D the same way.  The state is restored.  Synchronizes.
+/* Assembles J = dF/du at the current state, 11 4x4 blocks per cell, and the state gradients of
+ * C_L and C_D, colour by colour (a greedy colouring in which no residual stencil holds two cells
+ * of one colour).  By default (fasw_adjoint_set_jacobian mode 1) every column comes from the
+ * forward-mode linearization of the residual (fasw_tangent_residual's kernels): exact to rounding;
+ * mode 0 takes central differences of the residual with relative step h_rel (step
+ * h_rel * max(1, |u|) per unit).  The coarse levels' Jacobians of the transposed FAS cycle (a
+ * preconditioner only) are always central differences.  The state is restored.  Synchronizes.
  * Errors: FASW_ERR_ARG (moving grid, dual-time term set, h_rel <= 0), FASW_ERR_OOM. */
 int fasw_adjoint_jacobian(fasw_ctx* ctx, double h_rel);
+/* Jacobian assembly of the finest level: 1 = forward-mode linearization (default), 0 = coloured
+ * central differences.  The next fasw_adjoint_jacobian assembles with it. */
+int fasw_adjoint_set_jacobian(fasw_ctx* ctx, int mode);
+/* The residual's linearization applied to a vector, matrix-free: dF = (dF/du) v at the finest
+ * level's current state (fixed grid, eddy viscosity frozen), by the forward-mode evaluation of
+ * the residual's own formulas -- every quantity of section 2's discretization carried with its
+ * derivative along v, the switches (JST pressure switch, eps4 cutoff, far-field in/outflow) held
+ * on the branch the state takes.  v, dF: 4 x nj x ni; F (nullable) receives the residual itself
+ * (the value part).  Synchronizes.  FASW_ERR_ARG on a moving grid. */
+int fasw_tangent_residual(fasw_ctx* ctx, const double* v, double* dF, double* F, int on_device);
 /* out = J v (transpose = 0) or J^T v (transpose != 0) with the assembled J. */
 int fasw_adjoint_apply(fasw_ctx* ctx, const double* v, double* out, int transpose, int on_device);
 /* State gradient dJ/du of objective `which` (as assembled with J). */

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "fasw_internal.cuh"
+#include "fasw_tangent.cuh"
 
 namespace fasw {
 
@@ -78,6 +79,10 @@ struct AdjointDev {
   double* vlen = nullptr;   // (nj+1)(ni+1) shortest edge at each vertex (scale of its step)
   double* mgw = nullptr;    // work vectors of the linearised smoothing step and its transpose (8 x 4n)
   int smooth_steps = 3;    // smoothing steps per application of the GMRES preconditioner
+  // How the finest level's Jacobian is assembled (fasw_adjoint_set_jacobian): 1 = forward-mode
+  // linearization of the residual (exact), 0 = coloured central differences of the residual.
+  int jac_mode = 1;
+  TanDev tan{};             // tangent arrays of the finest level (kernels_tangent.cu)
 };
 
 // Host-side stencil, colouring and reverse map; allocates the device arrays (cudaMalloc), with

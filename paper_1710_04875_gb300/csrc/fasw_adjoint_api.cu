@@ -17,6 +17,13 @@ extern "C" {
 static int adj_ready(fasw_ctx* c) {
   if (c->adj.n) return FASW_OK;
   const LevelDev& F = c->lev[c->L()];
+  if (!c->adj.tan.u) {  // tangent arrays first: the workspace is published only when complete
+    void* mem = nullptr;
+    const int r = device_alloc(&mem, tangent_doubles(F) * sizeof(double));
+    if (r) return r;
+    c->allocs.push_back(mem);
+    tangent_carve(F, static_cast<double*>(mem), c->adj.tan);
+  }
   c->adj.fp32 = c->mixed != 0;
   c->adj.prog = c->d_prog;
   c->adj.err = c->d_err;
@@ -90,6 +97,29 @@ int fasw_adjoint_precond_apply(fasw_ctx* c, double cfl, int steps, const double*
   c->launches += 2;
   if ((e = adj_err_check(c))) return e;
   if ((e = copy_out(c, z, c->d_tmp2, m, on_device))) return e;
+  return sync(c);
+}
+
+int fasw_adjoint_set_jacobian(fasw_ctx* c, int mode) {
+  if (!c || mode < 0 || mode > 1) return FASW_ERR_ARG;
+  if (mode != c->adj.jac_mode) c->adj.built = false;
+  c->adj.jac_mode = mode;
+  return FASW_OK;
+}
+
+int fasw_tangent_residual(fasw_ctx* c, const double* v, double* dF, double* F, int on_device) {
+  if (!c || !v || !dF || c->ph.moving) return FASW_ERR_ARG;
+  int r = adj_ready(c);
+  if (r) return r;
+  LevelDev& L = c->lev[c->L()];
+  const size_t m = 4 * (size_t)L.n;
+  if ((r = copy_in(c, c->d_tmp, v, m, on_device))) return r;
+  launch_bc_aux(L, c->ph, 1.0, 0, c->st);
+  launch_tangent(L, c->adj.tan, c->ph, c->d_tmp, nullptr, 0, -1, 0.0, c->adj.Fp, nullptr, F ? c->adj.Fm : nullptr,
+                 nullptr, nullptr, c->st);
+  c->launches += 6;
+  if ((r = copy_out(c, dF, c->adj.Fp, m, on_device))) return r;
+  if (F && (r = copy_out(c, F, c->adj.Fm, m, on_device))) return r;
   return sync(c);
 }
 

@@ -377,6 +377,32 @@ int adj_assemble(AdjointDev& A, const LevelDev& L, const PhysParams& ph, double 
   launch_pdl(k_adj_get_state, nb, 128, 0, st, L, A.ub);
   cudaMemsetAsync(A.g, 0, 8 * (size_t)n * sizeof(double), st);
   ++launches;
+  if (A.jac_mode == 1 && A.tan.u) {
+    // Forward mode: one tangent evaluation per colour and component, seeded with
+    // 2 h max(1, |u|) so that the central-difference extraction (F+ - F-) / (2 h max(1, |u|))
+    // with F- = 0 reads the exact Jacobian columns.
+    cudaMemsetAsync(A.Fm, 0, 4 * (size_t)n * sizeof(double), st);
+    cudaMemsetAsync(A.Fvm, 0, 4 * (size_t)n * sizeof(double), st);
+    cudaMemsetAsync(A.fw + 2 * A.ni, 0, 2 * (size_t)A.ni * sizeof(double), st);
+    launch_bc_aux(L, ph, 1.0, 0, st);
+    ++launches;
+    for (int k = 0; k < A.ncolours; ++k)
+      for (int m = 0; m < 4; ++m) {
+        launch_tangent(L, A.tan, ph, nullptr, A.col, k, m, 2.0 * h_rel, A.Fp, A.Fvp, nullptr,
+                       A.finest ? A.fw : nullptr, A.finest ? A.fw + A.ni : nullptr, st);
+        launches += A.finest ? 6 : 5;
+        launch_pdl(k_adj_extract, nb, 128, 0, st, n, A.nbr, A.col, k, m, A.Fp, A.Fm, A.ub, h_rel, A.J);
+        launch_pdl(k_adj_extract, nb, 128, 0, st, n, A.nbr, A.col, k, m, (const double*)A.Fvp, (const double*)A.Fvm,
+                   (const double*)A.ub, h_rel, A.Jv);
+        launches += 2;
+        if (A.finest) {
+          launch_pdl(k_adj_extract_obj, nbf, 128, 0, st, A.ni, n, A.col, k, m, A.fw, A.ub, h_rel, sa, ca, A.g);
+          ++launches;
+        }
+      }
+    A.built = true;
+    return cudaGetLastError() == cudaSuccess ? FASW_OK : FASW_ERR_CUDA;
+  }
   ResArgs a{};
   a.mode = RES_FULL;
   for (int k = 0; k < A.ncolours; ++k)

@@ -92,6 +92,8 @@ def library(variant: str = "perf"):
             "fasw_kernel_time": (i, [p, i, C.POINTER(ll), C.POINTER(d)]),
             "fasw_force_coefficients": (i, [p, C.POINTER(d), C.POINTER(d)]),
             "fasw_adjoint_jacobian": (i, [p, d]),
+            "fasw_adjoint_set_jacobian": (i, [p, i]),
+            "fasw_tangent_residual": (i, [p, dp, dp, dp, i]),
             "fasw_adjoint_apply": (i, [p, dp, dp, i, i]),
             "fasw_adjoint_objective_gradient": (i, [p, i, dp, i]),
             "fasw_adjoint_solve": (i, [p, i, dp, dp, d, i, i, d, C.POINTER(i), C.POINTER(d), i]),
@@ -331,6 +333,21 @@ class Solver:
 
     def adjoint_jacobian(self, h_rel=1e-6):
         _check(self.lib.fasw_adjoint_jacobian(self.h, h_rel), "fasw_adjoint_jacobian")
+
+    def adjoint_set_jacobian(self, mode):
+        """Jacobian assembly: "tangent" (forward-mode linearization, the default) or "differences"
+        (coloured central differences)."""
+        _check(self.lib.fasw_adjoint_set_jacobian(self.h, {"differences": 0, "tangent": 1}[mode]),
+               "fasw_adjoint_set_jacobian")
+
+    def tangent_residual(self, v, with_value=False):
+        """(dF/du) v at the finest level's current state (and F itself with with_value)."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        dF = np.zeros(self._shape(self.finest))
+        F = np.zeros_like(dF) if with_value else None
+        _check(self.lib.fasw_tangent_residual(self.h, v.ctypes.data, dF.ctypes.data,
+                                              F.ctypes.data if with_value else None, 0), "fasw_tangent_residual")
+        return (dF, F) if with_value else dF
 
     def adjoint_apply(self, v, transpose=False, out=None):
         v = np.ascontiguousarray(v, dtype=np.float64) if isinstance(v, np.ndarray) else v
