@@ -238,7 +238,10 @@ int fasw_adjoint_set_jacobian(fasw_ctx* ctx, int mode);
  * level's current state (fixed grid, eddy viscosity frozen), by the forward-mode evaluation of
  * the residual's own formulas -- every quantity of section 2's discretization carried with its
  * derivative along v, the switches (JST pressure switch, eps4 cutoff, far-field in/outflow) held
- * on the branch the state takes.  v, dF: 4 x nj x ni; F (nullable) receives the residual itself
+ * on the branch the state takes.  Where a max, min or |.| of the switches ties (arguments equal
+ * to 1e-8 relative, or |.| of a quantity zero to 1e-8 of its scale, as symmetric flows give
+ * exactly) the derivative is the mean of the two one-sided slopes, the central derivative that
+ * central differences also take.  v, dF: 4 x nj x ni; F (nullable) receives the residual itself
  * (the value part).  Synchronizes.  FASW_ERR_ARG on a moving grid. */
 int fasw_tangent_residual(fasw_ctx* ctx, const double* v, double* dF, double* F, int on_device);
 /* out = J v (transpose = 0) or J^T v (transpose != 0) with the assembled J. */

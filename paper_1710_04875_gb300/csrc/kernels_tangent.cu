@@ -49,9 +49,25 @@ __device__ __forceinline__ Dual dsqrt(Dual a) {
   const double s = sqrt(a.v);
   return Dual{s, a.d / (2.0 * s)};
 }
-__device__ __forceinline__ Dual dabs(Dual a) { return a.v >= 0.0 ? a : -a; }
-__device__ __forceinline__ Dual dmax(Dual a, Dual b) { return a.v >= b.v ? a : b; }
-__device__ __forceinline__ Dual dmin(Dual a, Dual b) { return a.v <= b.v ? a : b; }
+// The switches' max, min and |.| are not differentiable where their arguments tie.  A tie (the
+// two arguments of max / min equal to TIE relative, or the argument of |.| zero to TIE times the
+// scale of the quantities it is formed from) takes the mean of the two one-sided slopes: the
+// central derivative, which central differences of the residual also give there.  Symmetric
+// flows tie exactly (the sensors of mirror cells across the wake cut, the normal velocity on the
+// symmetry line), so one branch taken there would give a gradient without the flow's symmetry.
+constexpr double TIE = 1e-8;
+__device__ __forceinline__ Dual dabs(Dual a, double scale) {
+  if (fabs(a.v) <= TIE * scale) return Dual{fabs(a.v), 0.0};
+  return a.v > 0.0 ? a : -a;
+}
+__device__ __forceinline__ Dual dmax(Dual a, Dual b) {
+  if (fabs(a.v - b.v) <= TIE * fmax(fabs(a.v), fabs(b.v))) return Dual{fmax(a.v, b.v), 0.5 * (a.d + b.d)};
+  return a.v > b.v ? a : b;
+}
+__device__ __forceinline__ Dual dmin(Dual a, Dual b) {
+  if (fabs(a.v - b.v) <= TIE * fmax(fabs(a.v), fabs(b.v))) return Dual{fmin(a.v, b.v), 0.5 * (a.d + b.d)};
+  return a.v < b.v ? a : b;
+}
 // rho^(-gamma) and (num/den)^(1/3): the residual kernels' Newton roots for the values
 __device__ __forceinline__ Dual dpow_neg_gamma(Dual r) {
   const double z = pow_neg_gamma(r.v);
@@ -87,7 +103,7 @@ __device__ void farfield_d(const Dual wi[4], const PhysParams& ph, double nx, do
   const Dual ai = dsqrt(GAM * pi * rri);
   const Dual vni = ui * nx + vi * ny;
   const double vnf = uf * nx + vf * ny;
-  if (dabs(vni - vb).v >= ai.v) {
+  if (fabs(vni.v - vb) >= ai.v) {
     if ((vni - vb).v > 0.0) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) out[k] = wi[k];
@@ -271,8 +287,9 @@ __global__ void k_tan_aux(LevelDev L, TanDev T, PhysParams ph, int nbi) {
   const double ey = 0.5 * (L.seta[L.nfe + fs] + L.seta[L.nfe + fs + ni]);
   const double vx = 0.5 * (L.vfx[fw] + L.vfx[fw + 1]);
   const double ve = 0.5 * (L.vfe[fs] + L.vfe[fs + ni]);
-  const Dual rxi = dabs(u * sx + v * sy - vx) + a * sqrt(sx * sx + sy * sy);
-  const Dual reta = dabs(u * ex + v * ey - ve) + a * sqrt(ex * ex + ey * ey);
+  const double sl = sqrt(sx * sx + sy * sy), el = sqrt(ex * ex + ey * ey);
+  const Dual rxi = dabs(u * sx + v * sy - vx, a.v * sl) + a * sl;
+  const Dual reta = dabs(u * ex + v * ey - ve, a.v * el) + a * el;
   const Dual cr = dcbrt_ratio(reta, rxi);
   T.rt[c] = (rxi + rxi * (cr * cr)).d;
   T.rt[L.n + c] = (reta + rxi * cr).d;
@@ -291,7 +308,8 @@ __device__ __forceinline__ Dual rt_d(const LevelDev& L, const TanDev& T, int i, 
 }
 
 __device__ __forceinline__ Dual sensor_d(Dual qm, Dual q0, Dual qp) {
-  return dabs(qp - 2.0 * q0 + qm) / (qp + 2.0 * q0 + qm + 0.001);
+  const Dual den = qp + 2.0 * q0 + qm + 0.001;
+  return dabs(qp - 2.0 * q0 + qm, den.v) / den;
 }
 
 __device__ void jst_d(const LevelDev& L, const TanDev& T, int gLL, int gL, int gR, int gRR, double sx, double sy,
@@ -321,7 +339,7 @@ __device__ void jst_d(const LevelDev& L, const TanDev& T, int gLL, int gL, int g
     eps4 = cst(0.0);
   }
   Dual uLL[4], uRR[4];
-  const bool e4 = eps4.v != 0.0;
+  const bool e4 = eps4.v != 0.0 || eps4.d != 0.0;
   if (e4) {
     ld4(L, T, gLL, uLL);
     ld4(L, T, gRR, uRR);
@@ -343,7 +361,7 @@ __device__ void jst_d(const LevelDev& L, const TanDev& T, int gLL, int gL, int g
 }
 
 __device__ __forceinline__ Dual cutabs_d(Dual lam, Dual a, double d) {
-  const Dual al = dabs(lam), ad = a * d;
+  const Dual al = dabs(lam, a.v), ad = a * d;
   return (d > 0.0 && al.v <= ad.v) ? 0.5 * (ad + lam * lam / ad) : al;
 }
 

@@ -26,6 +26,7 @@ def test_jacobian_products_match_the_oracle(viscous):
     u = perturbed_state(0.6, ALPHA, 16, 64, amp=0.03, seed=2)
     o.set_state(u); s.set_state(u)
     J, gL, gD = A.jacobian(o, ALPHA)
+    s.adjoint_set_jacobian("differences")         # the oracle's definition: central differences
     s.adjoint_jacobian(1e-6)
     rng = np.random.default_rng(5)
     v = rng.standard_normal((4, 16, 64)); w = rng.standard_normal((4, 16, 64))
@@ -118,13 +119,27 @@ def test_adjoint_solution_and_shape_gradient_match_the_oracle():
     _, p = pair_params(nlevels=2, mach=0.6, alpha_deg=ALPHA, cfl=1e4)
     po, _ = pair_params(nlevels=2, mach=0.6, alpha_deg=ALPHA, cfl=1e4)
     dL_o, dD_o, lamL_o, lamD_o = A.shape_gradient(g, po, u, None, V, ALPHA)
+    s.adjoint_set_jacobian("differences")
     s.adjoint_jacobian(1e-6)
+    lams = {}
     for which, lam_o, d_o in ((0, lamL_o, dL_o), (1, lamD_o, dD_o)):
         lam, code, it, rr = s.adjoint_solve(which, tol=1e-10, max_iters=1500, restart=60)
         assert code == 0 and rr <= 1e-10, (code, it, rr)
         assert rel_err(lam.ravel(), lam_o) < 1e-6
         grad = s.adjoint_shape_gradient(which, lam, V)
         assert rel_err(grad, d_o) < 1e-5
+        lams[which] = (lam_o, d_o)
+    # The default forward-mode Jacobian takes one branch of each |.| and max of the pressure
+    # switch where the central differences average the two one-sided slopes (the converged
+    # state has many near-zero second differences of p): the same lambda to 1e-4.
+    s.adjoint_set_jacobian("tangent")
+    s.adjoint_jacobian(1e-6)
+    for which in (0, 1):
+        lam, code, it, rr = s.adjoint_solve(which, tol=1e-10, max_iters=1500, restart=60)
+        assert code == 0 and rr <= 1e-10, (code, it, rr)
+        lam_o, d_o = lams[which]
+        assert rel_err(lam.ravel(), lam_o) < 1e-4
+        assert rel_err(s.adjoint_shape_gradient(which, lam, V), d_o) < 1e-4
 
 
 @pytest.mark.parametrize("case", ["euler_64x16", "rans_256x64"])

@@ -41,6 +41,7 @@ def test_unsteady_adjoint_matches_the_oracle(euler_case):
     Jo, go, g0o, _ = U.gradient(g, po, u0, V, AMP, OMEGA, XC, YC, DT, N, DROP, CYCLES, 1)
     s = P.Solver(g, pg)
     s.set_state(u0)
+    s.adjoint_set_jacobian("differences")         # the oracle's definition: central differences
     Jg, gg, g0g, code, st = s.unsteady_adjoint(AMP, OMEGA, DT, N, V, which=1, xc=XC, yc=YC, drop=DROP,
                                                max_cycles=CYCLES, tol=1e-11, max_iters=400, restart=60)
     assert code == 0, st
@@ -66,6 +67,7 @@ def test_laminar_unsteady_adjoint_matches_the_oracle():
     Jo, go, g0o, _ = U.gradient(g, po, u0, V, AMP, OMEGA, XC, YC, DT, N, DROP, CYCLES, 1)
     s = P.Solver(g, pg)
     s.set_state(u0)
+    s.adjoint_set_jacobian("differences")         # the oracle's definition: central differences
     Jg, gg, g0g, code, st = s.unsteady_adjoint(AMP, OMEGA, DT, N, V, which=1, xc=XC, yc=YC, drop=DROP,
                                                max_cycles=CYCLES, tol=1e-11, max_iters=600, restart=250)
     assert code == 0, st
@@ -92,6 +94,7 @@ def test_rans_unsteady_adjoint_matches_the_oracle():
     Jo, go, g0o, _ = U.gradient(g, po, u0, V, AMP, OMEGA, XC, YC, DT, N, drop, CYCLES, 1)
     s = P.Solver(g, pg)
     s.set_state(u0)
+    s.adjoint_set_jacobian("differences")         # the oracle's definition: central differences
     Jg, gg, g0g, code, st = s.unsteady_adjoint(AMP, OMEGA, DT, N, V, which=1, xc=XC, yc=YC, drop=drop,
                                                max_cycles=CYCLES, tol=1e-11, max_iters=600, restart=250)
     assert code == 0, st
@@ -110,6 +113,7 @@ def test_implicit_euler_unsteady_adjoint_matches_the_oracle(euler_case):
     Jo, go, g0o, _ = U.gradient(g, po1, u0, V, AMP, OMEGA, XC, YC, DT, N, DROP, CYCLES, 1)
     s = P.Solver(g, pg)
     s.set_state(u0)
+    s.adjoint_set_jacobian("differences")         # the oracle's definition: central differences
     Jg, gg, g0g, code, st = s.unsteady_adjoint(AMP, OMEGA, DT, N, V, which=1, xc=XC, yc=YC, bdf_order=1,
                                                drop=DROP, max_cycles=CYCLES, tol=1e-11, max_iters=400, restart=60)
     assert code == 0, st

@@ -1,0 +1,168 @@
+"""The discrete Fourier analysis tool (oracle/lfa.py) against section 5: its amplification matrices
+against the oracle's physical-space linear smoothing step (an independent evaluation of the same
+operator), closed forms of the stability functions, and the tables of section 5.4 (stored in
+tests/golden/paper_lfa_tables.json).  The paper leaves the normalization of its c* and c and the
+high-frequency set open, so the tables serve as pins where they are reproduced (rho(M) of the
+explicit schemes, of ARK3J with SGS at AR 1 and of AW3) and as trend pins elsewhere (smoothing
+factors, stability limits).  CPU only."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import lfa
+
+TAB = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_lfa_tables.json")))
+
+
+def _model(ar, d, alpha=0.0, **kw):
+    return lfa.table_model(0.8, alpha, ar, d, **kw)
+
+
+@pytest.mark.parametrize("scheme,precond", [("AW3", "sgs"), ("ARK3J", "sgs"), ("AW5J", "sgs")])
+@pytest.mark.parametrize("mode", [(1, 0), (3, 2), (4, 4), (2, 7)])
+def test_amplification_is_the_physical_space_step(scheme, precond, mode):
+    """One step of the oracle's circulant linear smoother (C++, physical space) applied to a Fourier
+    mode equals the batched symbol recursion (pressure switch off: the linear step carries the
+    fourth difference only)."""
+    n, ar, d = 8, 4, 0.4
+    m = lfa.Model(O.free_stream(0.8, 20.0), 1 / n, ar / n, d, sensor="off")
+    cstar, cphys = (3.0, 50.0) if scheme.startswith("AW") else (0.4, 50.0)
+    dts, a_t = cstar / m.lam, 1.5 * m.lam / cphys
+    tx, ty = 2 * np.pi * mode[0] / n, 2 * np.pi * mode[1] / n
+    G = lfa.amplification(m, scheme, [tx], [ty], cstar, cphys, 0.8, precond)[0]
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n))
+    ph = np.exp(1j * (tx * ii + ty * jj))
+    Gm = np.zeros((4, 4), complex)
+    for k in range(4):
+        ure = np.zeros((4, n, n)); uim = np.zeros((4, n, n))
+        ure[k], uim[k] = ph.real, ph.imag
+        ore = O.linear_step(m.w, m.dx, m.dy, n, n, ure, dts, 0.8, a_t, d, scheme, True)[0]
+        oim = O.linear_step(m.w, m.dx, m.dy, n, n, uim, dts, 0.8, a_t, d, scheme, True)[0]
+        Gm[:, k] = ((ore + 1j * oim) * np.conj(ph)[None]).reshape(4, -1)[:, 0]
+    assert np.abs(G - Gm).max() < 1e-12
+
+
+def test_conjugate_halving_of_the_angle_set():
+    """theta and -theta give conjugate matrices: the halved angle set has the same extrema."""
+    m, nx, ny = _model(4, 0.5)
+    tx, ty = lfa.angles(nx, ny)
+    assert len(tx) == nx * ny // 2 + 2
+    k = np.arange(-nx // 2 + 1, nx // 2 + 1)
+    l = np.arange(-ny // 2 + 1, ny // 2 + 1)
+    TX, TY = [a.ravel() for a in np.meshgrid(2 * np.pi * k / nx, 2 * np.pi * l / ny, indexing="ij")]
+    G = lfa.amplification(m, "AW3", TX, TY, 5.0, 200.0)
+    Gc = lfa.amplification(m, "AW3", -TX, -TY, 5.0, 200.0)
+    np.testing.assert_allclose(Gc, np.conj(G), atol=1e-13)
+    r_full = np.abs(np.linalg.eigvals(G)).max(axis=1)
+    _, _, r_half = lfa.spectral_radii(m, "AW3", nx, ny, 5.0, 200.0)
+    assert abs(r_full.max() - r_half.max()) < 1e-14
+
+
+@pytest.mark.parametrize("scheme", ["ERK3J", "ARK3J", "AW3", "AW51", "AW52", "AW5J"])
+def test_zero_mode_is_the_stability_function(scheme):
+    """At theta = 0 the symbol is the time term alone: H = 3/(2 dt) I, and P = 3/(2 dt) I (ARK, P = J)
+    or W = (1 + eta dt* 3/(2 dt)) I (AW); the amplification is the low-storage stability function
+    R(z) = 1 + alpha_s z (1 + alpha_(s-1) z (1 + ...)) at z = -dt* P^-1 3/(2 dt)."""
+    m, nx, ny = _model(1, 0.5)
+    al, _ = O.SCHEMES[scheme]
+    cstar, c, eta = 2.0, 200.0, 0.7
+    z = -1.5 * cstar / c
+    if scheme.startswith("AW"):
+        z /= 1 + eta * 1.5 * cstar / c
+    elif scheme.startswith("ARK"):
+        z = -cstar / m.lam
+    R = 1.0
+    for a in al:
+        R = 1.0 + a * z * R
+    G = lfa.amplification(m, scheme, [0.0], [0.0], cstar, c, eta, "exact")[0]
+    np.testing.assert_allclose(G, R * np.eye(4), atol=1e-14)
+
+
+def test_explicit_schemes_reproduce_table_erk_ark():
+    """Table ERK-ARK (c* = 0.9): rho(M) of ERK3 and ARK3J; the smoothing factor exceeds the paper's
+    at AR 1 but is below rho there and equal to rho (no smoothing) at AR 100, with ERK3 the worse
+    smoother of the two."""
+    t = TAB["erk_ark"]
+    sm = {}
+    for k, ar in enumerate((1, 100)):
+        m, nx, ny = _model(ar, 0.5)
+        for sch in ("ERK3J", "ARK3J"):
+            rho, s = lfa.factors(m, sch, nx, ny, 0.9, 200.0, precond="none")
+            assert abs(rho - t[sch]["rho"][k]) < (1e-4 if ar == 1 else 3e-4), (sch, ar, rho)
+            sm[sch, ar] = (rho, s)
+    for sch in ("ERK3J", "ARK3J"):
+        assert sm[sch, 1][1] < sm[sch, 1][0] - 0.1
+        assert sm[sch, 100][1] > sm[sch, 100][0] - 0.005
+    assert sm["ERK3J", 1][1] > sm["ARK3J", 1][1]
+
+
+def test_ark3j_sgs_reproduces_rho_of_table_prec_ark_rates():
+    """Table Prec-ARK-rates, SGS column at AR 1: rho(M) at the paper's optimal c* for every d,
+    and the smoothing factor falling as d grows (the paper's trend)."""
+    t = TAB["prec_ark_rates"]
+    sms = []
+    for i, d in enumerate(t["d"]):
+        m, nx, ny = _model(1, d)
+        rho, sm = lfa.factors(m, "ARK3J", nx, ny, float(t["sgs"]["cstar"][i][0]), 200.0, 0.8, "sgs")
+        assert abs(rho - t["sgs"]["rho"][i][0]) < 1e-3, (d, rho)
+        sms.append(sm)
+    assert all(b < a for a, b in zip(sms, sms[1:])), sms
+
+
+# AW3 cells (d index, AR index, preconditioner) of Table AW whose rho(M) the tool reproduces to
+# 2e-3; the other cells of AR 1 and 100 to 0.04 except the two SGS cells at AR 100 listed apart.
+AW_CLOSE = [(0, 0, "exact"), (0, 1, "sgs"), (0, 1, "exact"), (1, 0, "exact"), (1, 1, "sgs"), (1, 1, "exact"),
+            (2, 0, "exact"), (2, 1, "exact"), (4, 0, "exact")]
+AW_APART = [(2, 1, "sgs"), (3, 1, "sgs")]
+
+
+def test_aw3_reproduces_rho_of_table_aw():
+    t = TAB["aw_rates"]
+    for i, d in enumerate(t["d"]):
+        for k, ar in enumerate((1, 100)):
+            m, nx, ny = _model(ar, d)
+            for pc in ("sgs", "exact"):
+                if (i, k, pc) in AW_APART:
+                    continue
+                cs = float(t[pc]["cstar"][i][k])
+                rho, sm = lfa.factors(m, "AW3", nx, ny, cs, 200.0, 0.8, pc)
+                tol = 2e-3 if (i, k, pc) in AW_CLOSE else 0.04
+                assert abs(rho - t[pc]["rho"][i][k]) < tol, (d, ar, pc, rho, t[pc]["rho"][i][k])
+                if ar == 1:
+                    assert sm < rho - 0.3          # a good smoother on the square grid
+                else:
+                    assert sm > 0.5 * rho          # high aspect ratio: smoothing and rho close
+
+
+def test_aw3_stability_trends_of_table_aw_stability():
+    """Table AW-stability: no bound on c* for d >= 0.5 (A-stability, the paper's "A"), and the
+    bound does not fall as d grows; with d = 0 the SGS and exact bounds coincide at AR 1."""
+    t = TAB["aw_stability"]
+    grid = lfa.CSTAR_GRID[::3]
+    for k, ar in enumerate((1, 100)):
+        prev = 0.0
+        for i, d in enumerate(t["d"]):
+            m, nx, ny = _model(ar, d)
+            lim = lfa.max_stable_cstar(m, "AW3", nx, ny, 200.0, 0.8, "sgs", grid=grid)
+            val = np.inf if lim is None else lim
+            assert val >= prev, (ar, d, lim)
+            prev = val
+            if d >= 0.5:
+                assert lim is None and t["sgs"][i][k] is None
+    m, nx, ny = _model(1, 0.0)
+    assert lfa.max_stable_cstar(m, "AW3", nx, ny, 200.0, 0.8, "sgs", grid=grid) == \
+        lfa.max_stable_cstar(m, "AW3", nx, ny, 200.0, 0.8, "exact", grid=grid)
+
+
+def test_optimal_eta_of_aw3_is_interior():
+    """Tables AWa0 / AWa45: at AR 1 the optimal eta of AW3 lies inside (0.2, 1), as the paper's
+    0.4-0.6 do, and the smoothing factor at that eta is below the one at eta = 0.8 (Table AW)."""
+    grid = np.arange(1.0, 12.0)
+    etas = np.round(np.arange(0.2, 1.01, 0.2), 10)
+    m, nx, ny = _model(1, 0.5)
+    eta, cs, rho, sm = lfa.optimal_eta_cstar(m, "AW3", nx, ny, 200.0, "sgs", etas=etas, grid=grid)
+    assert 0.2 < eta < 1.0
+    assert sm <= lfa.optimal_cstar(m, "AW3", nx, ny, 200.0, 0.8, "sgs", grid=grid)[2] + 1e-12
