@@ -377,11 +377,14 @@ def measure_adjoint(s, g, n_bumps=16):
                     "preconditioned by the transposed linearised W-cycle"}
 
 
-def measure_c5(P, stream=None, n_bumps=16):
+def measure_c5(P, stream=None, n_bumps=16, check_bumps=()):
     """The 1024x256 RANS sensitivity case (wall spacing 1e-5, M 0.75, Re 6.5e6, alpha 0, 5-level
     W-cycles of AW3, mixed precision): time to a 6-order drop from the free stream, then the
     C_D adjoint (eddy viscosity frozen) to a 6-order drop and the shape gradient for 16
-    Hicks-Henne bumps; host-timed around the synchronous library calls."""
+    Hicks-Henne bumps; host-timed around the synchronous library calls.  check_bumps: bumps whose
+    gradient is checked against central differences (h = 1e-6) of complete solves with the eddy
+    viscosity frozen at the converged state's (the derivative the adjoint computes), after a
+    further solve and adjoint at that frozen eddy viscosity."""
     from synth.shape import bump_fields
     g = make_cgrid(1024, 256, n_wake=128, wall_spacing=1e-5)
     p = P.default_params(scheme="AW3", nlevels=5, gamma_cycle=2, viscous=1, turb=1, sensor=1, mach=0.75,
@@ -418,8 +421,41 @@ def measure_c5(P, stream=None, n_bumps=16):
                vertex_vs_shape_gradient=float(np.abs(via - grad).max() / max(np.abs(grad).max(), 1e-300)),
                upper_lower_antisymmetry=float(np.abs(grad[:half] + grad[half:2 * half]).max()
                                               / max(np.abs(grad).max(), 1e-300)))
+    if check_bumps:
+        out["frozen_mut_check"] = _c5_check(P, s, g, p, V[list(check_bumps)], list(check_bumps))
     s.close()
     return out
+
+
+def _c5_check(P, s, g, p, V, ids, h=1e-6):
+    from synth.shape import deformed
+    t0 = time.perf_counter()
+    mut = s.get_mut()
+    s.freeze_mut(mut)
+    code, nc, hist = s.solve(1e-5, 4000)
+    res = {"bumps": ids, "h": h, "refine_status": int(code), "refine_cycles": nc}
+    u = s.get_state()
+    s.adjoint_jacobian(1e-6)
+    lam, acode, it, rr = s.adjoint_solve(1, tol=1e-10, max_iters=3000, restart=250)
+    grad = s.adjoint_shape_gradient(1, lam, V)
+    res.update(adjoint_status=int(acode), adjoint_relres=rr, grad=[float(x) for x in grad])
+    fd, stat = [], []
+    for k in range(V.shape[0]):
+        cd = []
+        for sgn in (1.0, -1.0):
+            e = np.zeros(V.shape[0])
+            e[k] = sgn * h
+            sd = P.Solver(deformed(g, e, V), p)
+            sd.set_state(u)
+            sd.freeze_mut(mut)
+            c2, n2, h2 = sd.solve(1e-6, 4000)
+            stat.append((int(c2), n2))
+            cd.append(sd.force_coefficients()[1])
+            sd.close()
+        fd.append((cd[0] - cd[1]) / (2 * h))
+    res.update(fd=fd, fd_solves=stat, rel_diff=[abs(a - b) / max(abs(b), 1e-300) for a, b in zip(grad, fd)],
+               seconds=time.perf_counter() - t0)
+    return res
 
 
 def measure_c5_unsteady(P, n_bumps=16):
@@ -731,7 +767,8 @@ def main():
     ap.add_argument("--no-unsteady-adjoint", action="store_true")
     ap.add_argument("--pitch-steps", type=int, default=4, help="physical steps of the 512x128 pitching case")
     ap.add_argument("--c5", action="store_true",
-                    help="only the 1024x256 RANS shape-sensitivity case (steady solve, adjoint, 16 bump gradients)")
+                    help="only the 1024x256 RANS shape-sensitivity case (steady solve, adjoint, 16 bump gradients, "
+                         "two of them against differences of frozen-eddy-viscosity solves)")
     ap.add_argument("--c5-unsteady", action="store_true",
                     help="only the two-period unsteady adjoint of the pitching 512x128 RANS case (minutes)")
     ap.add_argument("--c3-period", action="store_true",
@@ -755,7 +792,7 @@ def main():
         print(json.dumps(adjoint_profile(P)), flush=True)
         return
     if args.c5:
-        print(json.dumps(measure_c5(P)), flush=True)
+        print(json.dumps(measure_c5(P, check_bumps=(2, 11))), flush=True)
         return
     if args.c5_unsteady:
         print(json.dumps(measure_c5_unsteady(P)), flush=True)

@@ -188,6 +188,13 @@ int fasw_set_residual_tile(fasw_ctx* ctx, int rows);
  * laminar context (turb = 0) keeps a zero eddy viscosity in its own residual. */
 int fasw_get_mut(fasw_ctx* ctx, double* mut, int on_device);
 
+/* Holds the finest level's eddy viscosity at mut (n doubles, cell order) in every later cycle,
+ * solve and dual-time step (no Baldwin-Lomax evaluation), or returns to the model (mut = NULL).
+ * A primal solve so frozen is the one the discrete adjoint linearizes (the adjoint holds mu_t
+ * fixed): central differences of such solves check the adjoint gradient.  FASW_ERR_ARG for a
+ * laminar context with mut != NULL.  Synchronizes; drops captured cycles. */
+int fasw_freeze_mut(fasw_ctx* ctx, const double* mut, int on_device);
+
 /* Dual time stepping, eq. (nonlin-eq): set a_t (3/(2 dt) for BDF2, 1/dt for implicit Euler;
  * 0 = steady) on every level and the history source src (finest level, 4 x nj x ni;
  * NULL = zero), so that F gains a_t u + src and D gains eta dt* a_t I (AW) or a_t I (ARK). */

@@ -120,6 +120,7 @@ def lib(variant: str = "parity"):
             "or_dual_time_step": (i, [p, d, d, i, dp]),
             "or_grid_fluxes": (None, [p, i, dp, dp]),
             "or_block_apply": (None, [p, i, d, dp, dp]),
+            "or_residual_complex_step": (None, [p, i, dp, d, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -248,6 +249,17 @@ class Oracle:
         F = np.zeros((4, nj, ni)); Fc = np.zeros_like(F); Fv = np.zeros_like(F)
         self.L.or_residual(self.h, l, _dp(F), _dp(Fc), _dp(Fv))
         return F, Fc, Fv
+
+    def residual_complex_step(self, v, h=1e-30, l=None):
+        """(F, dF): the residual and its directional derivative (dF/du) v by the complex step
+        (the residual's formulas evaluated at u + i h v; Im / h has no differencing error).  The
+        eddy viscosity is held at its current value.  v: (4, nj, ni)."""
+        l = self.finest if l is None else l
+        ni, nj, _ = self.dims(l)
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(4, nj, ni)
+        F = np.zeros((4, nj, ni)); dF = np.zeros_like(F)
+        self.L.or_residual_complex_step(self.h, l, _dp(v), h, _dp(F), _dp(dF))
+        return F, dF
 
     def wall_force(self):
         """Per-wall-face force on the body (fx, fy), ni entries each (zero on the wake cut), from

@@ -36,6 +36,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -44,8 +45,24 @@
 namespace orc {
 
 constexpr double GAM = 1.4;
-using V4 = std::array<double, 4>;
-using M4 = std::array<std::array<double, 4>, 4>;
+template <class T> using V4T = std::array<T, 4>;
+template <class T> using M4T = std::array<std::array<T, 4>, 4>;
+using V4 = V4T<double>;
+using M4 = M4T<double>;
+using CX = std::complex<double>;
+
+// The residual's functions are written once for a scalar type T: double (the oracle itself) or
+// std::complex<double> (the complex-step derivative, Squire & Trapp 1998: F(u + i h v) =
+// F(u) + i h (dF/du) v + O(h^2) with no subtractive cancellation).  Comparisons and branches take
+// the real part; |x| takes the sign of the real part.  For double these are the plain operations.
+inline double re(double x) { return x; }
+inline double re(const CX& x) { return x.real(); }
+inline double absr(double x) { return std::fabs(x); }
+inline CX absr(const CX& x) { return x.real() < 0.0 ? -x : x; }
+inline double maxr(double a, double b) { return std::max(a, b); }
+inline CX maxr(const CX& a, const CX& b) { return a.real() < b.real() ? b : a; }
+inline double minr(double a, double b) { return std::min(a, b); }
+inline CX minr(const CX& a, const CX& b) { return b.real() < a.real() ? b : a; }
 
 // ---------------------------------------------------------------- parameters
 struct OrParams {
@@ -74,10 +91,11 @@ struct OrParams {
 };
 
 // ---------------------------------------------------------------- gas model
-struct Prim { double rho, u, v, p; };
+template <class T> struct PrimT { T rho, u, v, p; };
+using Prim = PrimT<double>;
 
-static Prim prim(const V4& w) {
-  Prim q;
+template <class T> static PrimT<T> prim(const V4T<T>& w) {
+  PrimT<T> q;
   q.rho = w[0];
   q.u = w[1] / w[0];
   q.v = w[2] / w[0];
@@ -94,10 +112,10 @@ static V4 free_stream(double mach, double alpha_deg) {
 }
 
 // Convective flux F^c_1 Sx + F^c_2 Sy (section 2; G1: third row rho v_i v_2 + p delta_i2).
-static V4 conv_flux(const V4& w, double sx, double sy) {
-  const Prim q = prim(w);
-  const double qn = q.u * sx + q.v * sy;
-  V4 f;
+template <class T> static V4T<T> conv_flux(const V4T<T>& w, double sx, double sy) {
+  const PrimT<T> q = prim(w);
+  const T qn = q.u * sx + q.v * sy;
+  V4T<T> f;
   f[0] = q.rho * qn;
   f[1] = w[1] * qn + q.p * sx;
   f[2] = w[2] * qn + q.p * sy;
@@ -116,11 +134,11 @@ static V4 matvec(const M4& A, const V4& x) {
   return y;
 }
 
-static M4 matmul(const M4& A, const M4& B) {
-  M4 C{};
+template <class T> static M4T<T> matmul(const M4T<T>& A, const M4T<T>& B) {
+  M4T<T> C{};
   for (int r = 0; r < 4; ++r)
     for (int c = 0; c < 4; ++c) {
-      double s = 0.0;
+      T s = 0.0;
       for (int k = 0; k < 4; ++k) s += A[r][k] * B[k][c];
       C[r][c] = s;
     }
@@ -150,33 +168,34 @@ static V4 solve4(const M4& Ain, const V4& bin) {
 // ---------------------------------------------------------------- flux-vector splitting
 // Parabolic cutoff of eq. (cutoff): |lambda| -> (ad + lambda^2/(ad))/2 for |lambda| <= ad.
 // d = 0 leaves |lambda| unchanged (G26).
-static double cutoff_abs(double lam, double a, double d) {
-  const double al = std::fabs(lam);
-  const double ad = a * d;
-  if (d > 0.0 && al <= ad) return 0.5 * (ad + lam * lam / ad);
+template <class T> static T cutoff_abs(const T& lam, const T& a, double d) {
+  const T al = absr(lam);
+  const T ad = a * d;
+  if (d > 0.0 && re(al) <= re(ad)) return 0.5 * (ad + lam * lam / ad);
   return al;
 }
 
 // Right eigenvectors R (columns) and R^{-1} of A_n = dF.n/du at state w, unit normal n.
-static void eigvecs(const V4& w, double nx, double ny, M4& R, M4& Ri, double& vn, double& a) {
-  const Prim q = prim(w);
-  const double H = (w[3] + q.p) / q.rho;
+template <class T>
+static void eigvecs(const V4T<T>& w, double nx, double ny, M4T<T>& R, M4T<T>& Ri, T& vn, T& a) {
+  const PrimT<T> q = prim(w);
+  const T H = (w[3] + q.p) / q.rho;
   a = std::sqrt(GAM * q.p / q.rho);
   vn = q.u * nx + q.v * ny;
   const double tx = -ny, ty = nx;
-  const double vt = q.u * tx + q.v * ty;
-  const double q2 = q.u * q.u + q.v * q.v;
+  const T vt = q.u * tx + q.v * ty;
+  const T q2 = q.u * q.u + q.v * q.v;
   const double g1 = GAM - 1.0;
   // columns: entropy, shear, acoustic +, acoustic -
-  const double cols[4][4] = {
+  const T cols[4][4] = {
       {1.0, q.u, q.v, 0.5 * q2},
       {0.0, tx, ty, vt},
       {1.0, q.u + a * nx, q.v + a * ny, H + a * vn},
       {1.0, q.u - a * nx, q.v - a * ny, H - a * vn}};
   for (int r = 0; r < 4; ++r)
     for (int c = 0; c < 4; ++c) R[r][c] = cols[c][r];
-  const double a2 = a * a;
-  const double rows[4][4] = {
+  const T a2 = a * a;
+  const T rows[4][4] = {
       {1.0 - g1 * q2 / (2.0 * a2), g1 * q.u / a2, g1 * q.v / a2, -g1 / a2},
       {-vt, tx, ty, 0.0},
       {(g1 * q2 / 2.0 - a * vn) / (2.0 * a2), (-g1 * q.u + a * nx) / (2.0 * a2),
@@ -191,17 +210,18 @@ static void eigvecs(const V4& w, double nx, double ny, M4& R, M4& Ri, double& vn
 // (section 4.4), each multiplied by the face length |S|.
 // On a moving face with grid volume flux vf (= v_grid . S) the eigenvalues are shifted by
 // -vf/|S| (relative normal velocity); the eigenvectors are those of the fixed face.
-static void split_jacobians(const V4& w, double sx, double sy, double vf, double d, M4& Ap, M4& Am) {
+template <class T>
+static void split_jacobians(const V4T<T>& w, double sx, double sy, double vf, double d, M4T<T>& Ap, M4T<T>& Am) {
   const double len = std::sqrt(sx * sx + sy * sy);
   const double nx = sx / len, ny = sy / len;
-  M4 R, Ri;
-  double vn, a;
+  M4T<T> R, Ri;
+  T vn, a;
   eigvecs(w, nx, ny, R, Ri, vn, a);
-  const double vr = vn - vf / len;
-  const double lam[4] = {vr, vr, vr + a, vr - a};
-  M4 Lp{}, Lm{};
+  const T vr = vn - vf / len;
+  const T lam[4] = {vr, vr, vr + a, vr - a};
+  M4T<T> Lp{}, Lm{};
   for (int k = 0; k < 4; ++k) {
-    const double ab = cutoff_abs(lam[k], a, d);
+    const T ab = cutoff_abs(lam[k], a, d);
     Lp[k][k] = 0.5 * (lam[k] + ab) * len;
     Lm[k][k] = 0.5 * (lam[k] - ab) * len;
   }
@@ -364,17 +384,24 @@ static void alloc_level_state(Level& g) {
 // ---------------------------------------------------------------- boundary conditions
 // Far field by 1-D Riemann invariants normal to the boundary (section 2, G9);
 // n = outward unit normal.  Returns the boundary state given to both ghost layers.
-static V4 farfield_state(const V4& wi, const V4& winf, double nx, double ny, double vb = 0.0) {
-  const Prim qi = prim(wi), qf = prim(winf);
-  const double ai = std::sqrt(GAM * qi.p / qi.rho), af = std::sqrt(GAM * qf.p / qf.rho);
-  const double vni = qi.u * nx + qi.v * ny, vnf = qf.u * nx + qf.v * ny;
-  if (std::fabs(vni - vb) >= ai) return vni - vb > 0.0 ? wi : winf;
-  const double Rp = vni + 2.0 * ai / (GAM - 1.0);
+template <class T>
+static V4T<T> farfield_state(const V4T<T>& wi, const V4& winf, double nx, double ny, double vb = 0.0) {
+  const PrimT<T> qi = prim(wi);
+  const Prim qf = prim(winf);
+  const T ai = std::sqrt(GAM * qi.p / qi.rho);
+  const double af = std::sqrt(GAM * qf.p / qf.rho);
+  const T vni = qi.u * nx + qi.v * ny;
+  const double vnf = qf.u * nx + qf.v * ny;
+  if (re(absr(vni - vb)) >= re(ai)) {
+    if (re(vni - vb) > 0.0) return wi;
+    return V4T<T>{winf[0], winf[1], winf[2], winf[3]};
+  }
+  const T Rp = vni + 2.0 * ai / (GAM - 1.0);
   const double Rm = vnf - 2.0 * af / (GAM - 1.0);
-  const double vnb = 0.5 * (Rp + Rm);
-  const double ab = 0.25 * (GAM - 1.0) * (Rp - Rm);
-  double s, ut, vt;
-  if (vnb - vb > 0.0) {
+  const T vnb = 0.5 * (Rp + Rm);
+  const T ab = 0.25 * (GAM - 1.0) * (Rp - Rm);
+  T s, ut, vt;
+  if (re(vnb - vb) > 0.0) {
     s = qi.p / std::pow(qi.rho, GAM);
     ut = qi.u - vni * nx;
     vt = qi.v - vni * ny;
@@ -383,32 +410,33 @@ static V4 farfield_state(const V4& wi, const V4& winf, double nx, double ny, dou
     ut = qf.u - vnf * nx;
     vt = qf.v - vnf * ny;
   }
-  const double rho = std::pow(ab * ab / (GAM * s), 1.0 / (GAM - 1.0));
-  const double p = rho * ab * ab / GAM;
-  const double u = ut + vnb * nx, v = vt + vnb * ny;
-  return V4{rho, rho * u, rho * v, p / (GAM - 1.0) + 0.5 * rho * (u * u + v * v)};
+  const T rho = std::pow(ab * ab / (GAM * s), 1.0 / (GAM - 1.0));
+  const T p = rho * ab * ab / GAM;
+  const T u = ut + vnb * nx, v = vt + vnb * ny;
+  return V4T<T>{rho, rho * u, rho * v, p / (GAM - 1.0) + 0.5 * rho * (u * u + v * v)};
 }
 
-static void bc_fill(const Solver& S, Level& g) {
+// Ghost states of the state array u (ghosted layout of level g).
+template <class T> static void bc_fill_t(const Solver& S, const Level& g, std::vector<V4T<T>>& u) {
   const int ni = g.ni, nj = g.nj;
   const bool noslip = S.P.viscous != 0;
   // corners (never read by the stencils) get the free stream
   for (int j = -2; j < nj + 2; ++j)
     for (int i = -2; i < ni + 2; ++i)
-      if ((i < 0 || i >= ni) && (j < 0 || j >= nj)) g.u[g.G(i, j)] = S.uinf;
+      if ((i < 0 || i >= ni) && (j < 0 || j >= nj)) u[g.G(i, j)] = V4T<T>{S.uinf[0], S.uinf[1], S.uinf[2], S.uinf[3]};
   // j = 0: wall or wake cut
   for (int i = 0; i < ni; ++i) {
     if (g.cut(i)) {
       const int m = g.mirror(i);
-      g.u[g.G(i, -1)] = g.u[g.G(m, 0)];
-      g.u[g.G(i, -2)] = g.u[g.G(m, 1)];
+      u[g.G(i, -1)] = u[g.G(m, 0)];
+      u[g.G(i, -2)] = u[g.G(m, 1)];
     } else {
       const double sx = g.seta_x[g.FE(i, 0)], sy = g.seta_y[g.FE(i, 0)];
       const double len = std::sqrt(sx * sx + sy * sy);
       const double nx = sx / len, ny = sy / len;
       for (int k = 0; k < 2; ++k) {
-        const V4 w = g.u[g.G(i, k)];
-        V4 gw;
+        const V4T<T> w = u[g.G(i, k)];
+        V4T<T> gw;
         if (!S.moving) {
           gw[0] = w[0];
           gw[3] = w[3];
@@ -416,21 +444,21 @@ static void bc_fill(const Solver& S, Level& g) {
             gw[1] = -w[1];
             gw[2] = -w[2];
           } else {
-            const double mn = w[1] * nx + w[2] * ny;
+            const T mn = w[1] * nx + w[2] * ny;
             gw[1] = w[1] - 2.0 * mn * nx;
             gw[2] = w[2] - 2.0 * mn * ny;
           }
         } else {
           // moving wall with velocity (wx, wy): same density and pressure, velocity mirrored
           // about the wall velocity (no-slip) or its normal component reflected relative to it
-          const Prim q = prim(w);
+          const PrimT<T> q = prim(w);
           const double wx = g.wvx[i], wy = g.wvy[i];
-          double ug, vg;
+          T ug, vg;
           if (noslip) {
             ug = 2.0 * wx - q.u;
             vg = 2.0 * wy - q.v;
           } else {
-            const double rn = (q.u - wx) * nx + (q.v - wy) * ny;
+            const T rn = (q.u - wx) * nx + (q.v - wy) * ny;
             ug = q.u - 2.0 * rn * nx;
             vg = q.v - 2.0 * rn * ny;
           }
@@ -439,7 +467,7 @@ static void bc_fill(const Solver& S, Level& g) {
           gw[2] = q.rho * vg;
           gw[3] = q.p / (GAM - 1.0) + 0.5 * q.rho * (ug * ug + vg * vg);
         }
-        g.u[g.G(i, -1 - k)] = gw;
+        u[g.G(i, -1 - k)] = gw;
       }
     }
   }
@@ -447,65 +475,68 @@ static void bc_fill(const Solver& S, Level& g) {
   for (int i = 0; i < ni; ++i) {
     const double sx = g.seta_x[g.FE(i, nj)], sy = g.seta_y[g.FE(i, nj)];
     const double len = std::sqrt(sx * sx + sy * sy);
-    const V4 b = farfield_state(g.u[g.G(i, nj - 1)], S.uinf, sx / len, sy / len, g.vfe[g.FE(i, nj)] / len);
-    g.u[g.G(i, nj)] = b;
-    g.u[g.G(i, nj + 1)] = b;
+    const V4T<T> b = farfield_state(u[g.G(i, nj - 1)], S.uinf, sx / len, sy / len, g.vfe[g.FE(i, nj)] / len);
+    u[g.G(i, nj)] = b;
+    u[g.G(i, nj + 1)] = b;
   }
   // i = 0 (outward = -S_xi) and i = ni (outward = +S_xi): far field
   for (int j = 0; j < nj; ++j) {
     {
       const double sx = g.sxi_x[g.FX(0, j)], sy = g.sxi_y[g.FX(0, j)];
       const double len = std::sqrt(sx * sx + sy * sy);
-      const V4 b = farfield_state(g.u[g.G(0, j)], S.uinf, -sx / len, -sy / len, -g.vfx[g.FX(0, j)] / len);
-      g.u[g.G(-1, j)] = b;
-      g.u[g.G(-2, j)] = b;
+      const V4T<T> b = farfield_state(u[g.G(0, j)], S.uinf, -sx / len, -sy / len, -g.vfx[g.FX(0, j)] / len);
+      u[g.G(-1, j)] = b;
+      u[g.G(-2, j)] = b;
     }
     {
       const double sx = g.sxi_x[g.FX(ni, j)], sy = g.sxi_y[g.FX(ni, j)];
       const double len = std::sqrt(sx * sx + sy * sy);
-      const V4 b = farfield_state(g.u[g.G(ni - 1, j)], S.uinf, sx / len, sy / len, g.vfx[g.FX(ni, j)] / len);
-      g.u[g.G(ni, j)] = b;
-      g.u[g.G(ni + 1, j)] = b;
+      const V4T<T> b = farfield_state(u[g.G(ni - 1, j)], S.uinf, sx / len, sy / len, g.vfx[g.FX(ni, j)] / len);
+      u[g.G(ni, j)] = b;
+      u[g.G(ni + 1, j)] = b;
     }
   }
 }
+
+static void bc_fill(const Solver& S, Level& g) { bc_fill_t(S, g, g.u); }
 
 // ---------------------------------------------------------------- JST residual
 // Directional spectral radii of a cell: r = |v . S_bar| + a |S_bar|, with S_bar
 // the mean of the cell's two opposite face area vectors (G6).
 // On a moving grid the convective speed is relative: |v . S_bar - V_bar| with V_bar the mean
 // grid volume flux of the same two faces.
-static void cell_radii(const Level& g, const V4& w, int i, int j, double& rxi, double& reta) {
-  const Prim q = prim(w);
-  const double a = std::sqrt(GAM * q.p / q.rho);
+template <class T> static void cell_radii(const Level& g, const V4T<T>& w, int i, int j, T& rxi, T& reta) {
+  const PrimT<T> q = prim(w);
+  const T a = std::sqrt(GAM * q.p / q.rho);
   const double sx = 0.5 * (g.sxi_x[g.FX(i, j)] + g.sxi_x[g.FX(i + 1, j)]);
   const double sy = 0.5 * (g.sxi_y[g.FX(i, j)] + g.sxi_y[g.FX(i + 1, j)]);
   const double ex = 0.5 * (g.seta_x[g.FE(i, j)] + g.seta_x[g.FE(i, j + 1)]);
   const double ey = 0.5 * (g.seta_y[g.FE(i, j)] + g.seta_y[g.FE(i, j + 1)]);
   const double vx = 0.5 * (g.vfx[g.FX(i, j)] + g.vfx[g.FX(i + 1, j)]);
   const double ve = 0.5 * (g.vfe[g.FE(i, j)] + g.vfe[g.FE(i, j + 1)]);
-  rxi = std::fabs(q.u * sx + q.v * sy - vx) + a * std::sqrt(sx * sx + sy * sy);
-  reta = std::fabs(q.u * ex + q.v * ey - ve) + a * std::sqrt(ex * ex + ey * ey);
+  rxi = absr(q.u * sx + q.v * sy - vx) + a * std::sqrt(sx * sx + sy * sy);
+  reta = absr(q.u * ex + q.v * ey - ve) + a * std::sqrt(ex * ex + ey * ey);
 }
 
 // Martinelli correction (eq. spectralcorrection): r~_i = r_i (1 + (r_j/r_i)^(2/3)).
-static void martinelli(double rxi, double reta, double& txi, double& teta) {
+template <class T> static void martinelli(const T& rxi, const T& reta, T& txi, T& teta) {
   txi = rxi * (1.0 + std::pow(reta / rxi, 2.0 / 3.0));
   teta = reta * (1.0 + std::pow(rxi / reta, 2.0 / 3.0));
 }
 
 // Sensor quantity: pressure for Euler, p / rho^gamma (entropy) otherwise.
-static double sensor_q(const Solver& S, const V4& w) {
-  const Prim q = prim(w);
+template <class T> static T sensor_q(const Solver& S, const V4T<T>& w) {
+  const PrimT<T> q = prim(w);
   return S.P.sensor ? q.p / std::pow(q.rho, GAM) : q.p;
 }
 
 // s_k = |S_{k+1} - 2 S_k + S_{k-1}| / (S_{k+1} + 2 S_k + S_{k-1} + 0.001)  (G4)
-static double sensor_val(double qm, double q0, double qp) {
-  return std::fabs(qp - 2.0 * q0 + qm) / (qp + 2.0 * q0 + qm + 0.001);
+template <class T> static T sensor_val(const T& qm, const T& q0, const T& qp) {
+  return absr(qp - 2.0 * q0 + qm) / (qp + 2.0 * q0 + qm + 0.001);
 }
 
-struct FaceFlux { V4 hc, hd; };
+template <class T> struct FaceFluxT { V4T<T> hc, hd; };
+using FaceFlux = FaceFluxT<double>;
 
 // JST flux through one face with area vector S (pointing from L to R), given
 // the stencil LL, L, R, RR along the face-normal grid line (section 2):
@@ -514,32 +545,34 @@ struct FaceFlux { V4 hc, hd; };
 //   eps2 = s r, eps4 = max(0, r/32 - 2 eps2),  s = min(0.25, max(s_L, s_R)),
 //   r = max(r~_L, r~_R).   On coarse levels: s = s_coarse and no eps4 term.
 // On a moving face (grid volume flux vf) the convective flux is F . S - u vf.
-static FaceFlux jst_face(const Solver& S, const V4& uLL, const V4& uL, const V4& uR, const V4& uRR,
-                         double sx, double sy, double vf, double rtL, double rtR, bool finest) {
-  FaceFlux out;
-  const V4 fL = conv_flux(uL, sx, sy), fR = conv_flux(uR, sx, sy);
+template <class T>
+static FaceFluxT<T> jst_face(const Solver& S, const V4T<T>& uLL, const V4T<T>& uL, const V4T<T>& uR,
+                             const V4T<T>& uRR, double sx, double sy, double vf, const T& rtL, const T& rtR,
+                             bool finest) {
+  FaceFluxT<T> out;
+  const V4T<T> fL = conv_flux(uL, sx, sy), fR = conv_flux(uR, sx, sy);
   for (int k = 0; k < 4; ++k) out.hc[k] = 0.5 * ((fL[k] - uL[k] * vf) + (fR[k] - uR[k] * vf));
-  auto wvec = [](const V4& w) {
-    const Prim q = prim(w);
-    return V4{w[0], w[1], w[2], w[3] + q.p};
+  auto wvec = [](const V4T<T>& w) {
+    const PrimT<T> q = prim(w);
+    return V4T<T>{w[0], w[1], w[2], w[3] + q.p};
   };
-  const V4 wLL = wvec(uLL), wL = wvec(uL), wR = wvec(uR), wRR = wvec(uRR);
-  const double r = std::max(rtL, rtR);
-  double eps2, eps4;
+  const V4T<T> wLL = wvec(uLL), wL = wvec(uL), wR = wvec(uR), wRR = wvec(uRR);
+  const T r = maxr(rtL, rtR);
+  T eps2, eps4;
   if (finest) {
-    const double qLL = sensor_q(S, uLL), qL = sensor_q(S, uL), qR = sensor_q(S, uR), qRR = sensor_q(S, uRR);
-    const double sL = sensor_val(qLL, qL, qR), sR = sensor_val(qL, qR, qRR);
-    const double s = std::min(0.25, std::max(sL, sR));
+    const T qLL = sensor_q(S, uLL), qL = sensor_q(S, uL), qR = sensor_q(S, uR), qRR = sensor_q(S, uRR);
+    const T sL = sensor_val(qLL, qL, qR), sR = sensor_val(qL, qR, qRR);
+    const T s = minr(T(0.25), maxr(sL, sR));
     eps2 = s * r;
-    eps4 = std::max(0.0, r / 32.0 - 2.0 * eps2);
+    eps4 = maxr(T(0.0), r / 32.0 - 2.0 * eps2);
   } else {
     eps2 = S.P.s_coarse * r;
-    eps4 = 0.0;
+    eps4 = T(0.0);
   }
   for (int k = 0; k < 4; ++k) {
-    const double dw0 = wR[k] - wL[k];
-    const double dwm = wL[k] - wLL[k];
-    const double dwp = wRR[k] - wR[k];
+    const T dw0 = wR[k] - wL[k];
+    const T dwm = wL[k] - wLL[k];
+    const T dwp = wRR[k] - wR[k];
     out.hd[k] = eps2 * dw0 - eps4 * ((dwp + dwm) - 2.0 * dw0);
   }
   return out;
@@ -551,14 +584,15 @@ static FaceFlux jst_face(const Solver& S, const V4& uLL, const V4& uL, const V4&
 // central part hc = A(u_bar) (u_L + u_R) / 2 and the upwind dissipation
 // hd = (A+ - A-)(u_R - u_L) / 2, since A+ + A- = A.  A(u) u = F(u) . S for the Euler flux
 // (homogeneous of degree one), so the flux is consistent: uniform flow gives F . S.
-static FaceFlux fvs_face(const Solver& S, const V4& uL, const V4& uR, double sx, double sy, double vf) {
-  V4 ub;
+template <class T>
+static FaceFluxT<T> fvs_face(const Solver& S, const V4T<T>& uL, const V4T<T>& uR, double sx, double sy, double vf) {
+  V4T<T> ub;
   for (int k = 0; k < 4; ++k) ub[k] = 0.5 * (uL[k] + uR[k]);
-  M4 Ap, Am;
+  M4T<T> Ap, Am;
   split_jacobians(ub, sx, sy, vf, S.P.d_cut, Ap, Am);
-  FaceFlux out;
+  FaceFluxT<T> out;
   for (int r = 0; r < 4; ++r) {
-    double c = 0.0, d = 0.0;
+    T c = 0.0, d = 0.0;
     for (int k = 0; k < 4; ++k) {
       c += (Ap[r][k] + Am[r][k]) * (uL[k] + uR[k]);
       d += (Ap[r][k] - Am[r][k]) * (uR[k] - uL[k]);
@@ -571,7 +605,7 @@ static FaceFlux fvs_face(const Solver& S, const V4& uL, const V4& uR, double sx,
 
 // Martinelli-corrected radius of a (possibly ghost) cell in direction dir (0 = xi, 1 = eta).
 // Ghost cells take the adjacent interior cell's value; across the wake cut the mirror cell's.
-static double rtilde(const Level& g, int i, int j, int dir) {
+template <class T> static T rtilde_t(const Level& g, const std::vector<V4T<T>>& u, int i, int j, int dir) {
   int ii = i, jj = j;
   if (jj < 0) {
     const int ic = std::min(std::max(ii, 0), g.ni - 1);
@@ -585,17 +619,20 @@ static double rtilde(const Level& g, int i, int j, int dir) {
   }
   ii = std::min(std::max(ii, 0), g.ni - 1);
   jj = std::min(jj, g.nj - 1);
-  double rxi, reta, txi, teta;
-  cell_radii(g, g.u[g.G(ii, jj)], ii, jj, rxi, reta);
+  T rxi, reta, txi, teta;
+  cell_radii(g, u[g.G(ii, jj)], ii, jj, rxi, reta);
   martinelli(rxi, reta, txi, teta);
   return dir == 0 ? txi : teta;
 }
 
+static double rtilde(const Level& g, int i, int j, int dir) { return rtilde_t(g, g.u, i, j, dir); }
+
 // Thin-layer viscous flux through j-face (i, j) between (i, j-1) and (i, j) (G8):
 // gradients from the difference across the face over the mean of the two volumes.
-static V4 visc_face(const Solver& S, const Level& g, int i, int j) {
+template <class T>
+static V4T<T> visc_face_t(const Solver& S, const Level& g, const std::vector<V4T<T>>& u, int i, int j) {
   const int nj = g.nj;
-  const V4 wL = g.u[g.G(i, j - 1)], wR = g.u[g.G(i, j)];
+  const V4T<T> wL = u[g.G(i, j - 1)], wR = u[g.G(i, j)];
   const double sx = g.seta_x[g.FE(i, j)], sy = g.seta_y[g.FE(i, j)];
   double volL, volR, mutf;
   if (j == 0) {
@@ -617,63 +654,71 @@ static V4 visc_face(const Solver& S, const Level& g, int i, int j) {
     mutf = 0.5 * (g.mut[g.C(i, j - 1)] + g.mut[g.C(i, j)]);
   }
   const double volf = 0.5 * (volL + volR);
-  const Prim qL = prim(wL), qR = prim(wR);
+  const PrimT<T> qL = prim(wL), qR = prim(wR);
   const double mu = 1.0 / S.P.re;
   const double mueff = mu + mutf;
   const double keff = mu / S.P.pr + mutf / S.P.prt;
-  const double hL = GAM / (GAM - 1.0) * qL.p / qL.rho, hR = GAM / (GAM - 1.0) * qR.p / qR.rho;
-  const double gux = (qR.u - qL.u) * sx / volf, guy = (qR.u - qL.u) * sy / volf;
-  const double gvx = (qR.v - qL.v) * sx / volf, gvy = (qR.v - qL.v) * sy / volf;
-  const double ghx = (hR - hL) * sx / volf, ghy = (hR - hL) * sy / volf;
-  const double div = gux + gvy;
-  const double txx = mueff * (2.0 * gux - 2.0 / 3.0 * div);
-  const double tyy = mueff * (2.0 * gvy - 2.0 / 3.0 * div);
-  const double txy = mueff * (guy + gvx);
-  const double uf = 0.5 * (qL.u + qR.u), vf = 0.5 * (qL.v + qR.v);
-  const double fx = txx * sx + txy * sy, fy = txy * sx + tyy * sy;
-  return V4{0.0, fx, fy, uf * fx + vf * fy + keff * (ghx * sx + ghy * sy)};
+  const T hL = GAM / (GAM - 1.0) * qL.p / qL.rho, hR = GAM / (GAM - 1.0) * qR.p / qR.rho;
+  const T gux = (qR.u - qL.u) * sx / volf, guy = (qR.u - qL.u) * sy / volf;
+  const T gvx = (qR.v - qL.v) * sx / volf, gvy = (qR.v - qL.v) * sy / volf;
+  const T ghx = (hR - hL) * sx / volf, ghy = (hR - hL) * sy / volf;
+  const T div = gux + gvy;
+  const T txx = mueff * (2.0 * gux - 2.0 / 3.0 * div);
+  const T tyy = mueff * (2.0 * gvy - 2.0 / 3.0 * div);
+  const T txy = mueff * (guy + gvx);
+  const T uf = 0.5 * (qL.u + qR.u), vf = 0.5 * (qL.v + qR.v);
+  const T fx = txx * sx + txy * sy, fy = txy * sx + tyy * sy;
+  return V4T<T>{T(0.0), fx, fy, uf * fx + vf * fy + keff * (ghx * sx + ghy * sy)};
 }
+
+static V4 visc_face(const Solver& S, const Level& g, int i, int j) { return visc_face_t(S, g, g.u, i, j); }
 
 // F^c and F^v of the split (eq. split-rhs), per unit volume, at the level's current
 // (ghost-filled) state:  F^c = Omega^{-1} (central fluxes) + a_t u + src - s,
 //                        F^v = Omega^{-1} (-(dissipation) - (viscous fluxes)).
-static void residual(const Solver& S, Level& g, bool finest, std::vector<V4>& Fc, std::vector<V4>& Fv) {
+template <class T>
+static void residual_t(const Solver& S, const Level& g, const std::vector<V4T<T>>& u, bool finest,
+                       std::vector<V4T<T>>& Fc, std::vector<V4T<T>>& Fv) {
   const int ni = g.ni, nj = g.nj;
-  std::vector<FaceFlux> fx((ni + 1) * nj), fe(ni * (nj + 1));
-  std::vector<V4> fvis(ni * (nj + 1), V4{});
+  std::vector<FaceFluxT<T>> fx((ni + 1) * nj), fe(ni * (nj + 1));
+  std::vector<V4T<T>> fvis(ni * (nj + 1), V4T<T>{});
   const bool fvs = S.P.flux == 1;
   for (int j = 0; j < nj; ++j)
     for (int i = 0; i <= ni; ++i)
-      fx[g.FX(i, j)] = fvs ? fvs_face(S, g.u[g.G(i - 1, j)], g.u[g.G(i, j)], g.sxi_x[g.FX(i, j)],
+      fx[g.FX(i, j)] = fvs ? fvs_face(S, u[g.G(i - 1, j)], u[g.G(i, j)], g.sxi_x[g.FX(i, j)],
                                       g.sxi_y[g.FX(i, j)], g.vfx[g.FX(i, j)])
-                           : jst_face(S, g.u[g.G(i - 2, j)], g.u[g.G(i - 1, j)], g.u[g.G(i, j)],
-                                      g.u[g.G(i + 1, j)], g.sxi_x[g.FX(i, j)], g.sxi_y[g.FX(i, j)],
-                                      g.vfx[g.FX(i, j)], rtilde(g, i - 1, j, 0), rtilde(g, i, j, 0), finest);
+                           : jst_face(S, u[g.G(i - 2, j)], u[g.G(i - 1, j)], u[g.G(i, j)],
+                                      u[g.G(i + 1, j)], g.sxi_x[g.FX(i, j)], g.sxi_y[g.FX(i, j)],
+                                      g.vfx[g.FX(i, j)], rtilde_t(g, u, i - 1, j, 0), rtilde_t(g, u, i, j, 0), finest);
   for (int j = 0; j <= nj; ++j)
     for (int i = 0; i < ni; ++i) {
-      fe[g.FE(i, j)] = fvs ? fvs_face(S, g.u[g.G(i, j - 1)], g.u[g.G(i, j)], g.seta_x[g.FE(i, j)],
+      fe[g.FE(i, j)] = fvs ? fvs_face(S, u[g.G(i, j - 1)], u[g.G(i, j)], g.seta_x[g.FE(i, j)],
                                       g.seta_y[g.FE(i, j)], g.vfe[g.FE(i, j)])
-                           : jst_face(S, g.u[g.G(i, j - 2)], g.u[g.G(i, j - 1)], g.u[g.G(i, j)],
-                                      g.u[g.G(i, j + 1)], g.seta_x[g.FE(i, j)], g.seta_y[g.FE(i, j)],
-                                      g.vfe[g.FE(i, j)], rtilde(g, i, j - 1, 1), rtilde(g, i, j, 1), finest);
-      if (S.P.viscous) fvis[g.FE(i, j)] = visc_face(S, g, i, j);
+                           : jst_face(S, u[g.G(i, j - 2)], u[g.G(i, j - 1)], u[g.G(i, j)],
+                                      u[g.G(i, j + 1)], g.seta_x[g.FE(i, j)], g.seta_y[g.FE(i, j)],
+                                      g.vfe[g.FE(i, j)], rtilde_t(g, u, i, j - 1, 1), rtilde_t(g, u, i, j, 1), finest);
+      if (S.P.viscous) fvis[g.FE(i, j)] = visc_face_t(S, g, u, i, j);
     }
-  Fc.assign(ni * nj, V4{});
-  Fv.assign(ni * nj, V4{});
+  Fc.assign(ni * nj, V4T<T>{});
+  Fv.assign(ni * nj, V4T<T>{});
   for (int j = 0; j < nj; ++j)
     for (int i = 0; i < ni; ++i) {
       const int c = g.C(i, j);
-      const FaceFlux &w = fx[g.FX(i, j)], &e = fx[g.FX(i + 1, j)];
-      const FaceFlux &s = fe[g.FE(i, j)], &n = fe[g.FE(i, j + 1)];
-      const V4 &vs = fvis[g.FE(i, j)], &vn = fvis[g.FE(i, j + 1)];
+      const FaceFluxT<T> &w = fx[g.FX(i, j)], &e = fx[g.FX(i + 1, j)];
+      const FaceFluxT<T> &s = fe[g.FE(i, j)], &n = fe[g.FE(i, j + 1)];
+      const V4T<T> &vs = fvis[g.FE(i, j)], &vn = fvis[g.FE(i, j + 1)];
       for (int k = 0; k < 4; ++k) {
-        const double fc = (e.hc[k] - w.hc[k]) + (n.hc[k] - s.hc[k]);
-        const double fd = -((e.hd[k] - w.hd[k]) + (n.hd[k] - s.hd[k]));
-        const double fv = -(vn[k] - vs[k]);
-        Fc[c][k] = fc / g.vol[c] + g.a_t * g.u[g.G(i, j)][k] + g.src[c][k] - g.s[c][k];
+        const T fc = (e.hc[k] - w.hc[k]) + (n.hc[k] - s.hc[k]);
+        const T fd = -((e.hd[k] - w.hd[k]) + (n.hd[k] - s.hd[k]));
+        const T fv = -(vn[k] - vs[k]);
+        Fc[c][k] = fc / g.vol[c] + g.a_t * u[g.G(i, j)][k] + g.src[c][k] - g.s[c][k];
         Fv[c][k] = (fd + fv) / g.vol[c];
       }
     }
+}
+
+static void residual(const Solver& S, Level& g, bool finest, std::vector<V4>& Fc, std::vector<V4>& Fv) {
+  residual_t(S, g, g.u, finest, Fc, Fv);
 }
 
 // ---------------------------------------------------------------- Baldwin-Lomax
@@ -1572,6 +1617,32 @@ void or_residual(void* h, int l, double* F, double* Fc_out, double* Fv_out) {
       if (F) F[k * n + q] = Fc[q][k] + Fv[q][k];
       if (Fc_out) Fc_out[k * n + q] = Fc[q][k];
       if (Fv_out) Fv_out[k * n + q] = Fv[q][k];
+    }
+}
+
+// Complex-step directional derivative of the residual on level l: the residual functions
+// evaluated at u + i hstep v (v: 4 x nj x ni, interior cells; the ghosts follow from the
+// boundary conditions in complex arithmetic), F = Re F(u + i hstep v) (the residual itself, to
+// rounding) and dF = Im F(u + i hstep v) / hstep = (dF/du) v with no differencing error for a
+// tiny hstep (1e-30).  The eddy viscosity is held at its current value.
+void or_residual_complex_step(void* h, int l, const double* v, double hstep, double* F, double* dF) {
+  Solver* S = static_cast<Solver*>(h);
+  Level& g = S->lev[l];
+  const int ni = g.ni, nj = g.nj, n = ni * nj;
+  std::vector<V4T<CX>> u(g.u.size());
+  for (size_t k = 0; k < g.u.size(); ++k)
+    for (int q = 0; q < 4; ++q) u[k][q] = CX(g.u[k][q], 0.0);
+  for (int j = 0; j < nj; ++j)
+    for (int i = 0; i < ni; ++i)
+      for (int q = 0; q < 4; ++q) u[g.G(i, j)][q] = CX(g.u[g.G(i, j)][q], hstep * v[q * n + g.C(i, j)]);
+  bc_fill_t(*S, g, u);
+  std::vector<V4T<CX>> Fc, Fv;
+  residual_t(*S, g, u, l == S->L(), Fc, Fv);
+  for (int c = 0; c < n; ++c)
+    for (int q = 0; q < 4; ++q) {
+      const CX f = Fc[c][q] + Fv[c][q];
+      if (F) F[q * n + c] = f.real();
+      dF[q * n + c] = f.imag() / hstep;
     }
 }
 

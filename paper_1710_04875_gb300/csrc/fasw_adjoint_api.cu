@@ -424,7 +424,7 @@ int fasw_unsteady_adjoint(fasw_ctx* c, double amp, double omega, double xc, doub
         for (auto& L : c->lev) L.a_t = a_n;
       }
       cudaMemsetAsync(F.src, 0, m * sizeof(double), c->st);
-      if (c->prm.turb) {  // eddy viscosity frozen at its value for u^n
+      if (c->prm.turb && !c->mut_frozen) {  // eddy viscosity frozen at its value for u^n
         launch_bc_aux(F, c->ph, 1.0, 0, c->st);
         launch_bl(F, c->ph, c->st);
         c->launches += 2;

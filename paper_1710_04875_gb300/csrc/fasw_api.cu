@@ -346,7 +346,7 @@ int sync(fasw_ctx* c) {
 void enqueue_cycle(fasw_ctx* c, double cfl) {
   const int Lf = c->L();
   err_clear(c);
-  if (c->prm.turb) {
+  if (c->prm.turb && !c->mut_frozen) {
     bc_aux(c, Lf, cfl, 0);
     { Prof p(c, FASW_K_BL); launch_bl(c->lev[Lf], c->ph, c->st); }
     c->launches += 2;
@@ -753,13 +753,29 @@ int fasw_solve_steady(fasw_ctx* c, double drop, int max_cycles, double* history,
 int fasw_get_mut(fasw_ctx* c, double* mut, int on_device) {
   if (!c || !mut) return FASW_ERR_ARG;
   const int Lf = c->L();
-  bc_aux(c, Lf, 1.0, 0);
-  launch_bl(c->lev[Lf], c->ph, c->st);
-  c->launches += 2;
+  if (!c->mut_frozen) {
+    bc_aux(c, Lf, 1.0, 0);
+    launch_bl(c->lev[Lf], c->ph, c->st);
+    c->launches += 2;
+  }
   int r = copy_out(c, mut, c->lev[Lf].mut, (size_t)c->lev[Lf].n, on_device);
   if (r) return r;
   if (!c->prm.turb)  // a laminar context's residual must not see the eddy viscosity
     CKR(cudaMemsetAsync(c->lev[Lf].mut, 0, (size_t)c->lev[Lf].n * sizeof(double), c->st));
+  return sync(c);
+}
+
+int fasw_freeze_mut(fasw_ctx* c, const double* mut, int on_device) {
+  if (!c) return FASW_ERR_ARG;
+  if (mut && !c->prm.turb) return FASW_ERR_ARG;
+  int r = sync(c);
+  if (r) return r;
+  drop_graphs(c);  // the captured cycles hold the Baldwin-Lomax launches, or not
+  c->mut_frozen = mut != nullptr;
+  if (mut) {
+    LevelDev& F = c->lev[c->L()];
+    if ((r = copy_in(c, F.mut, mut, (size_t)F.n, on_device))) return r;
+  }
   return sync(c);
 }
 

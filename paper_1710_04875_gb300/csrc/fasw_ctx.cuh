@@ -49,6 +49,7 @@ struct fasw_ctx {
   int use_graphs = 1;
   int sweep_kind = fasw::SWEEP_AUTO;
   int in_batch = 0;             // a case of a batch: its kernels run beside other cases' kernels
+  bool mut_frozen = false;       // eddy viscosity held at a value set by fasw_freeze_mut
   int exact_iters = 0;          // > 0: the preconditioner iterates toward the exact (D+L+U)^-1
   long long spin_limit = 1LL << 22;
   long long* d_prog = nullptr;  // strip progress flags

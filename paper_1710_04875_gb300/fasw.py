@@ -80,6 +80,7 @@ def library(variant: str = "perf"):
             "fasw_fas_cycle": (i, [p, i, C.POINTER(d)]),
             "fasw_solve_steady": (i, [p, d, i, dp, C.POINTER(i)]),
             "fasw_get_mut": (i, [p, dp, i]),
+            "fasw_freeze_mut": (i, [p, dp, i]),
             "fasw_set_time_source": (i, [p, d, dp, i]),
             "fasw_launch_count": (ll, [p]),
             "fasw_profile": (i, [p, i]),
@@ -275,6 +276,15 @@ class Solver:
         out = np.zeros((nj, ni))
         _check(self.lib.fasw_get_mut(self.h, out.ctypes.data, 0), "fasw_get_mut")
         return out
+
+    def freeze_mut(self, mut):
+        """Hold the finest level's eddy viscosity at mut (nj x ni) in later cycles and solves, or
+        return to the Baldwin-Lomax model (mut None)."""
+        if mut is None:
+            _check(self.lib.fasw_freeze_mut(self.h, None, 0), "fasw_freeze_mut")
+            return
+        m = np.ascontiguousarray(mut, dtype=np.float64)
+        _check(self.lib.fasw_freeze_mut(self.h, m.ctypes.data, 0), "fasw_freeze_mut")
 
     def set_time_source(self, a_t, src=None):
         p, dev = _ptr(src)

@@ -172,3 +172,44 @@ def test_adjoint_iteration_converges_at_the_primal_rate():
     print(f"asymptotic rates: linearised primal {rp:.4f}, adjoint {ra:.4f}")
     assert rp < 0.95 and abs(ra - rp) <= 0.05 * rp, (rp, ra)
     s.close()
+
+
+def test_rans_gradient_matches_differences_of_frozen_eddy_viscosity_solves():
+    """RANS (Baldwin-Lomax): the discrete adjoint holds mu_t at the converged state's value, so
+    central differences of complete solves with mu_t frozen at that value (fasw_freeze_mut) are
+    the derivative it computes.  Two bumps of the drag gradient against such differences."""
+    import paper_1710_04875_gb300 as P
+    from synth.shape import bump_fields, deformed
+    g = make_cgrid(128, 32, wall_spacing=1e-4)
+    kw = dict(nlevels=3, gamma_cycle=2, viscous=1, turb=1, mach=0.6, alpha_deg=2.0, re=1e6, cfl=100.0)
+    _, p = pair_params(**kw)
+    s = P.Solver(g, p)
+    code, nc, hist = s.solve(1e-6, 3000)
+    assert code == 0
+    mut = s.get_mut()
+    s.freeze_mut(mut)
+    code, nc, hist = s.solve(1e-7, 4000)           # a further 7 orders with mu_t held
+    assert code == 0
+    u = s.get_state()
+    np.testing.assert_array_equal(s.get_mut(), mut)
+    V = bump_fields(g, 16)[[2, 11]]
+    s.adjoint_jacobian(1e-6)
+    lam, code, it, rr = s.adjoint_solve(1, tol=1e-11, max_iters=3000, restart=250)
+    assert code == 0
+    grad = s.adjoint_shape_gradient(1, lam, V)
+    s.close()
+    h = 1e-6
+    for k in range(V.shape[0]):
+        cd = []
+        for sgn in (1.0, -1.0):
+            e = np.zeros(V.shape[0])
+            e[k] = sgn * h
+            sd = P.Solver(deformed(g, e, V), p)
+            sd.set_state(u)
+            sd.freeze_mut(mut)
+            code, nc, hist = sd.solve(1e-6, 4000)
+            assert code == 0
+            cd.append(sd.force_coefficients()[1])
+            sd.close()
+        fd = (cd[0] - cd[1]) / (2 * h)
+        assert abs(fd - grad[k]) <= 1e-4 * abs(grad[k]), (k, fd, grad[k])
