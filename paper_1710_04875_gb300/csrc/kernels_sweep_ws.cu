@@ -145,8 +145,12 @@ size_t ws_smem_bytes(int nw) {
 }
 
 int ws_strips(int nj) { return (nj + WS_ROWS - 1) / WS_ROWS; }
-// steps stored per strip: the ni + 31 steps that hold a cell, padded to whole chunks
-__host__ __device__ __forceinline__ int ws_steps(int ni) { return (ni + WS_ROWS - 1 + WS_K - 1) / WS_K * WS_K; }
+// steps stored per strip: the ni + R - 1 steps that hold a cell (R = min(nj, 32) rows in a
+// strip: a level of fewer than 32 rows skews by its own rows only), padded to whole chunks
+__host__ __device__ __forceinline__ int ws_steps(int ni, int nj) {
+  const int R = nj < WS_ROWS ? nj : WS_ROWS;
+  return (ni + R - 1 + WS_K - 1) / WS_K * WS_K;
+}
 
 namespace {
 
@@ -170,7 +174,7 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, int nb, const
                         long long* flag_out, int* err, long long limit, unsigned& phase_bits) {
   const int lane = threadIdx.x;
   const int ni = L.ni, nw = L.nw;
-  const int Mp = ws_steps(ni);              // steps (ni + 31 that hold a cell, padded to whole chunks)
+  const int Mp = ws_steps(ni, L.nj);        // steps that hold a cell, padded to whole chunks
   const int nch = Mp / WS_K;
   // the neighbour strip whose boundary row this one reads: below (forward) / above (backward)
   const bool has_in = FWD ? b > 0 : b < nb - 1;
@@ -330,7 +334,7 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, int nb, const
 }
 
 // One launch: forward then backward pass of strip b (one warp per CTA).  flags: 2 nb progress
-// words (forward, backward), cleared by the host before the launch.
+// words (forward, backward), cleared by their strips at the start of the launch.
 __global__ void __launch_bounds__(32) k_sweep_ws(LevelDev L, const float4* Fb, const float4* Bb, const float4* C,
                                                  float4* Y, const float* cutG, float4* edges, float4* Z,
                                                  long long* flags, int* err, long long limit) {
@@ -346,6 +350,14 @@ __global__ void __launch_bounds__(32) k_sweep_ws(LevelDev L, const float4* Fb, c
   S.edge[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (b == 0)
     for (int x = lane; x < 16 * nw; x += 32) S.cutG[x] = cutG[x];
+  // Each strip clears its own progress words (the previous sweep on this level has completed:
+  // every launch waits for its predecessor at entry), and no strip reads a neighbour's word
+  // before the whole cluster has passed this barrier (release / acquire at cluster scope).
+  if (lane == 0) {
+    flags[b] = 0;
+    flags[nb + b] = 0;
+  }
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
   __syncwarp();
   unsigned phase_bits = 0;
   const size_t ew = (size_t)L.ni + 2 * WS_EPAD;  // padded boundary row of one strip
@@ -367,7 +379,7 @@ __global__ void __launch_bounds__(32) k_sweep_ws(LevelDev L, const float4* Fb, c
 
 // ---------------------------------------------------------------- operand layout
 // Skewed position of cell (i, j): strip b = j / 32, lane jl = j % 32, forward step s = i + jl,
-// backward step Mp - 1 - i - jl (Mp: the ni + 31 steps that hold a cell, padded to whole chunks).
+// backward step Mp - 1 - i - jl (Mp: the ni + R - 1 steps that hold a cell, R = min(nj, 32), padded to whole chunks).
 
 // Blocks of the warp-strip sweep from the transfer blocks (entry-major planes, T = double or
 // float): forward G_W, G_S (zero on row 0 except the upper wake, whose mirror precedes it),
@@ -379,7 +391,7 @@ __global__ void k_ws_blocks(LevelDev L, const T* tb, float4* Fb, float4* Bb, flo
   if (c >= L.n) return;
   const int ni = L.ni, n = L.n, i = c % ni, j = c / ni;
   const int b = j / WS_ROWS, jl = j % WS_ROWS;
-  const int Mp = ws_steps(ni);
+  const int Mp = ws_steps(ni, L.nj);
   const bool cut = L.nw > 0 && (i < L.nw || i >= ni - L.nw);
   const bool gs_fwd = j > 0 || (cut && ni - 1 - i < i);
   float4* f = Fb + ((size_t)b * Mp + (i + jl)) * WS_F4_STEP + jl;
@@ -408,7 +420,7 @@ __global__ void k_ws_rhs(LevelDev L, const T* tb, const double* rhs, float4* C) 
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int ni = L.ni, n = L.n, i = c % ni, j = c / ni;
-  const int b = j / WS_ROWS, jl = j % WS_ROWS, Mp = ws_steps(ni);
+  const int b = j / WS_ROWS, jl = j % WS_ROWS, Mp = ws_steps(ni, L.nj);
   double r[4], y[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) r[t] = rhs[(size_t)t * n + c];
@@ -430,7 +442,7 @@ __global__ void k_ws_defect_t(LevelDev L, const double* tb, const float4* z0, do
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int ni = L.ni, nj = L.nj, n = L.n, i = c % ni, j = c / ni;
-  const int Mp = ws_steps(ni);
+  const int Mp = ws_steps(ni, L.nj);
   const float4 zc = z0[ws_bpos(i, j, Mp)];
   double acc[4] = {zc.x, zc.y, zc.z, zc.w};
   auto sub = [&](int blk, int cn) {
@@ -477,7 +489,7 @@ __global__ void k_ws_defect_d(LevelDev L, const double* tb, const double* rhs, c
   if (i > 0) add(1, c - 1);
   if (j > 0) add(2, c - ni);
   else if (L.nw > 0 && i >= ni - L.nw && ni - 1 - i < i) add(2, ni - 1 - i);
-  const int b = j / WS_ROWS, jl = j % WS_ROWS, Mp = ws_steps(ni);
+  const int b = j / WS_ROWS, jl = j % WS_ROWS, Mp = ws_steps(ni, L.nj);
   C[((size_t)b * Mp + (i + jl)) * WS_ROWS + jl] =
       make_float4(float(acc[0]), float(acc[1]), float(acc[2]), float(acc[3]));
 }
@@ -490,7 +502,7 @@ __global__ void k_ws_finish(LevelDev L, const float4* z0, const float4* dz, int 
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int n = L.n, i = c % L.ni, j = c / L.ni;
-  const size_t zp = ws_bpos(i, j, ws_steps(L.ni));
+  const size_t zp = ws_bpos(i, j, ws_steps(L.ni, L.nj));
   const float4 a = z0[zp];
   double z[4] = {a.x, a.y, a.z, a.w};
   if (dz) {
@@ -525,7 +537,7 @@ __global__ void k_ws_accum(LevelDev L, const float4* z0, const float4* dz, doubl
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   const int i = c % L.ni, j = c / L.ni;
-  const size_t zp = ws_bpos(i, j, ws_steps(L.ni));
+  const size_t zp = ws_bpos(i, j, ws_steps(L.ni, L.nj));
   const float4 a = z0[zp];
   double v[4] = {a.x, a.y, a.z, a.w};
   if (dz) {
@@ -568,7 +580,7 @@ __global__ void k_ws_exact_defect(LevelDev L, const T* tb, const double* rhs, co
   else if (L.nw > 0 && (i < L.nw || i >= ni - L.nw)) add(2, ni - 1 - i);
   if (i < ni - 1) add(3, c + 1);
   if (j < nj - 1) add(4, c + ni);
-  const int b = j / WS_ROWS, jl = j % WS_ROWS, Mp = ws_steps(ni);
+  const int b = j / WS_ROWS, jl = j % WS_ROWS, Mp = ws_steps(ni, L.nj);
   C[((size_t)b * Mp + (i + jl)) * WS_ROWS + jl] = make_float4(float(acc[0]), float(acc[1]), float(acc[2]), float(acc[3]));
 }
 
@@ -624,7 +636,6 @@ cudaError_t ws_sweep_launch(const LevelDev& L, float4* zout, long long* prog, in
         cudaSuccess)
       attr_done.fetch_or(1ull << dev);
   }
-  cudaMemsetAsync(prog, 0, 2 * (size_t)nb * sizeof(long long), st);
   // The strips of one sweep wait on one another, so they are launched as one thread-block
   // cluster (nb <= 8 CTAs): the hardware schedules a cluster's CTAs together, so every strip is
   // resident whatever else runs beside it (concurrent cases of a batch included).
@@ -696,7 +707,7 @@ int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int
 }
 
 size_t ws_edge_floats(int ni, int nj) { return 2 * 4 * (size_t)ws_strips(nj) * ((size_t)ni + 2 * WS_EPAD); }
-size_t ws_floats(int ni, int nj) { return (size_t)ws_strips(nj) * ws_steps(ni) * WS_F4_STEP * 4; }
-size_t ws_vec_floats(int ni, int nj) { return (size_t)ws_strips(nj) * ws_steps(ni) * WS_ROWS * 4; }
+size_t ws_floats(int ni, int nj) { return (size_t)ws_strips(nj) * ws_steps(ni, nj) * WS_F4_STEP * 4; }
+size_t ws_vec_floats(int ni, int nj) { return (size_t)ws_strips(nj) * ws_steps(ni, nj) * WS_ROWS * 4; }
 
 }  // namespace fasw
