@@ -414,84 +414,104 @@ __global__ void k_ws_blocks(LevelDev L, const T* tb, float4* Fb, float4* Bb, flo
 }
 
 // Forward right-hand side D^-1 r (FP32), skewed.
+// The FP64 kernels of one application, written per row q of their block products: a thread
+// takes one cell and all four rows (SPLIT false: the loads of a warp coalesce along the cells, for
+// levels whose time is their memory traffic), or one cell and one row (SPLIT true: a quarter of
+// the FP64 chain per thread, for the small levels whose time is that chain).  Every row is summed
+// in the same order either way.
+constexpr int WS_SPLIT_CELLS = 16384;  // levels up to this many cells take one thread per row
+
+template <bool SPLIT>
+__device__ __forceinline__ bool ws_thread(const LevelDev& L, int& c, int& q0, int& q1) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (SPLIT) {
+    c = g >> 2;
+    q0 = g & 3;
+    q1 = q0 + 1;
+  } else {
+    c = g;
+    q0 = 0;
+    q1 = 4;
+  }
+  return c < L.n;
+}
+
+// row q of D^-1 r
 template <typename T>
+__device__ __forceinline__ double rhs_row(const LevelDev& L, const T* tb, const double* rhs, int c, int q) {
+  const int n = L.n;
+  double a = 0.0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) a += double(tb[(size_t)(4 * q + t) * n + c]) * rhs[(size_t)t * n + c];
+  return a;
+}
+
+template <typename T, bool SPLIT>
 __global__ void k_ws_rhs(LevelDev L, const T* tb, const double* rhs, float4* C) {
   pdl_entry();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= L.n) return;
-  const int ni = L.ni, n = L.n, i = c % ni, j = c / ni;
+  int c, q0, q1;
+  if (!ws_thread<SPLIT>(L, c, q0, q1)) return;
+  const int ni = L.ni, i = c % ni, j = c / ni;
   const int b = j / WS_ROWS, jl = j % WS_ROWS, Mp = ws_steps(ni, L.nj);
-  double r[4], y[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) r[t] = rhs[(size_t)t * n + c];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    double a = 0.0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) a += double(tb[(size_t)(4 * q + t) * n + c]) * r[t];
-    y[q] = a;
-  }
-  C[((size_t)b * Mp + (i + jl)) * WS_ROWS + jl] = make_float4(float(y[0]), float(y[1]), float(y[2]), float(y[3]));
+  float* out = reinterpret_cast<float*>(C + ((size_t)b * Mp + (i + jl)) * WS_ROWS + jl);
+  for (int q = q0; q < q1; ++q) out[q] = float(rhs_row(L, tb, rhs, c, q));
 }
 
 // ---------------------------------------------------------------- FP64 defect correction
 // t = (I + U~) z0: the vector the backward sweep would have started from to reach z0,
 //   t_c = z0_c - H_E z0_E - H_N z0_N (- G_S z0_mirror on row 0 of the lower wake).
-__global__ void k_ws_defect_t(LevelDev L, const double* tb, const float4* z0, double* t) {
-  pdl_entry();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= L.n) return;
+__device__ __forceinline__ double defect_t_row(const LevelDev& L, const double* tb, const float4* z0, int c, int q) {
   const int ni = L.ni, nj = L.nj, n = L.n, i = c % ni, j = c / ni;
-  const int Mp = ws_steps(ni, L.nj);
+  const int Mp = ws_steps(ni, nj);
   const float4 zc = z0[ws_bpos(i, j, Mp)];
-  double acc[4] = {zc.x, zc.y, zc.z, zc.w};
+  double acc = q == 0 ? zc.x : q == 1 ? zc.y : q == 2 ? zc.z : zc.w;
   auto sub = [&](int blk, int cn) {
     const float4 zn = z0[ws_bpos(cn % ni, cn / ni, Mp)];
     const double x[4] = {zn.x, zn.y, zn.z, zn.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[q] -= tb[(size_t)(blk * 16 + 4 * q + k) * n + c] * x[k];
+    for (int k = 0; k < 4; ++k) acc -= tb[(size_t)(blk * 16 + 4 * q + k) * n + c] * x[k];
   };
   if (i < ni - 1) sub(3, c + 1);
   if (j < nj - 1) sub(4, c + ni);
   if (j == 0 && L.nw > 0 && i < L.nw && ni - 1 - i > i) sub(2, ni - 1 - i);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) t[(size_t)q * n + c] = acc[q];
+  return acc;
+}
+
+template <bool SPLIT>
+__global__ void k_ws_defect_t(LevelDev L, const double* tb, const float4* z0, double* t) {
+  pdl_entry();
+  int c, q0, q1;
+  if (!ws_thread<SPLIT>(L, c, q0, q1)) return;
+  for (int q = q0; q < q1; ++q) t[(size_t)q * L.n + c] = defect_t_row(L, tb, z0, c, q);
 }
 
 // d = D^-1 r - (I + L~) t = D^-1 r - t_c + G_W t_W + G_S t_S (t_S: the mirror on row 0 of the
 // upper wake, none elsewhere on row 0), written as the next forward right-hand side (FP32).
-__global__ void k_ws_defect_d(LevelDev L, const double* tb, const double* rhs, const double* t, float4* C) {
-  pdl_entry();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= L.n) return;
+__device__ __forceinline__ double defect_d_row(const LevelDev& L, const double* tb, const double* rhs,
+                                               const double* t, int c, int q) {
   const int ni = L.ni, n = L.n, i = c % ni, j = c / ni;
-  double r[4], acc[4];
+  double a = -t[(size_t)q * n + c];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) r[k] = rhs[(size_t)k * n + c];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    double a = -t[(size_t)q * n + c];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) a += tb[(size_t)(4 * q + k) * n + c] * r[k];
-    acc[q] = a;
-  }
+  for (int k = 0; k < 4; ++k) a += tb[(size_t)(4 * q + k) * n + c] * rhs[(size_t)k * n + c];
   auto add = [&](int blk, int cn) {
-    double x[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) x[k] = t[(size_t)k * n + cn];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[q] += tb[(size_t)(blk * 16 + 4 * q + k) * n + c] * x[k];
+    for (int k = 0; k < 4; ++k) a += tb[(size_t)(blk * 16 + 4 * q + k) * n + c] * t[(size_t)k * n + cn];
   };
   if (i > 0) add(1, c - 1);
   if (j > 0) add(2, c - ni);
   else if (L.nw > 0 && i >= ni - L.nw && ni - 1 - i < i) add(2, ni - 1 - i);
+  return a;
+}
+
+template <bool SPLIT>
+__global__ void k_ws_defect_d(LevelDev L, const double* tb, const double* rhs, const double* t, float4* C) {
+  pdl_entry();
+  int c, q0, q1;
+  if (!ws_thread<SPLIT>(L, c, q0, q1)) return;
+  const int ni = L.ni, i = c % ni, j = c / ni;
   const int b = j / WS_ROWS, jl = j % WS_ROWS, Mp = ws_steps(ni, L.nj);
-  C[((size_t)b * Mp + (i + jl)) * WS_ROWS + jl] =
-      make_float4(float(acc[0]), float(acc[1]), float(acc[2]), float(acc[3]));
+  float* out = reinterpret_cast<float*>(C + ((size_t)b * Mp + (i + jl)) * WS_ROWS + jl);
+  for (int q = q0; q < q1; ++q) out[q] = float(defect_d_row(L, tb, rhs, t, c, q));
 }
 
 // z = z0 (+ dz): the stage update u = u0 - alpha z (scaled by dt* for ARK), or z to the level's
@@ -666,20 +686,34 @@ int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int
   float4* z0 = reinterpret_cast<float4*>(L.wsZ);
   float4* dz = z0 + ws_vec_floats(L.ni, L.nj) / 4;
   int launches = 0;
-  if (mixed)
-    launch_pdl(k_ws_rhs<float>, g, 128, 0, st, L, reinterpret_cast<const float*>(L.tb), rhs,
-               reinterpret_cast<float4*>(L.wsC));
-  else
-    launch_pdl(k_ws_rhs<double>, g, 128, 0, st, L, static_cast<const double*>(L.tb), rhs,
-               reinterpret_cast<float4*>(L.wsC));
+  const bool split = L.n <= WS_SPLIT_CELLS;
+  const int g4 = (4 * L.n + 127) / 128;  // one thread per cell and row
+  float4* wC = reinterpret_cast<float4*>(L.wsC);
+  const double* tb64 = static_cast<const double*>(L.tb);
+  if (mixed) {
+    const float* tb32 = reinterpret_cast<const float*>(L.tb);
+    if (split)
+      launch_pdl(k_ws_rhs<float, true>, g4, 128, 0, st, L, tb32, rhs, wC);
+    else
+      launch_pdl(k_ws_rhs<float, false>, g, 128, 0, st, L, tb32, rhs, wC);
+  } else if (split) {
+    launch_pdl(k_ws_rhs<double, true>, g4, 128, 0, st, L, tb64, rhs, wC);
+  } else {
+    launch_pdl(k_ws_rhs<double, false>, g, 128, 0, st, L, tb64, rhs, wC);
+  }
   ws_sweep_launch(L, z0, prog, err, limit, st);
   launches += 2;
   const bool corr = refine && !mixed;
   if (corr) {
-    launch_pdl(k_ws_defect_t, g, 128, 0, st, L, static_cast<const double*>(L.tb), static_cast<const float4*>(z0),
-               L.wsT);
-    launch_pdl(k_ws_defect_d, g, 128, 0, st, L, static_cast<const double*>(L.tb), rhs,
-               static_cast<const double*>(L.wsT), reinterpret_cast<float4*>(L.wsC));
+    const float4* z0c = z0;
+    const double* wT = L.wsT;
+    if (split) {
+      launch_pdl(k_ws_defect_t<true>, g4, 128, 0, st, L, tb64, z0c, L.wsT);
+      launch_pdl(k_ws_defect_d<true>, g4, 128, 0, st, L, tb64, rhs, wT, wC);
+    } else {
+      launch_pdl(k_ws_defect_t<false>, g, 128, 0, st, L, tb64, z0c, L.wsT);
+      launch_pdl(k_ws_defect_d<false>, g, 128, 0, st, L, tb64, rhs, wT, wC);
+    }
     ws_sweep_launch(L, dz, prog, err, limit, st);
     launches += 3;
   }
