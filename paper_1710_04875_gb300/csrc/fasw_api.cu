@@ -186,7 +186,6 @@ int alloc_level(fasw_ctx* c, LevelDev& L) {
     A(L.wsC, wv);
     A(L.wsY, wv);
     A(L.wsCut, 16 * (size_t)(L.nw > 0 ? L.nw : 1));
-    A(L.wsEdge, ws_edge_floats(L.ni, L.nj));
     A(L.wsZ, 2 * wv);
     A(L.wsT, 4 * n);
     A(L.wsX, 4 * n);
@@ -196,7 +195,6 @@ int alloc_level(fasw_ctx* c, LevelDev& L) {
     CKR(cudaMemsetAsync(L.wsC, 0, wv * sizeof(float), c->st));
     CKR(cudaMemsetAsync(L.wsY, 0, wv * sizeof(float), c->st));
     CKR(cudaMemsetAsync(L.wsZ, 0, 2 * wv * sizeof(float), c->st));
-    CKR(cudaMemsetAsync(L.wsEdge, 0, ws_edge_floats(L.ni, L.nj) * sizeof(float), c->st));
     CKR(cudaMemsetAsync(L.wsCut, 0, 16 * (size_t)(L.nw > 0 ? L.nw : 1) * sizeof(float), c->st));
   }
 #undef A

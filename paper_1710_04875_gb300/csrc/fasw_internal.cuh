@@ -93,14 +93,13 @@ struct LevelDev {
   float* hpY;
   // warp-strip sweep (kernels_sweep_ws.cu; null where the level does not use it): blocks of the
   // forward (G_W, G_S) and backward (H_E, H_N) passes and their right-hand sides in the order a
-  // strip consumes them, the lower wake's backward coupling blocks, the strips' boundary rows,
-  // the sweep results z0 and dz (skewed in the backward order) and the FP64 defect vector
+  // strip consumes them, the lower wake's backward coupling blocks, the sweep results z0 and dz
+  // (skewed in the backward order) and the FP64 defect vector
   float* wsF;
   float* wsB;
   float* wsC;
   float* wsY;
   float* wsCut;
-  float* wsEdge;
   float* wsZ;
   double* wsT;
   double* wsX;  // accumulated solution of the exact-preconditioner iterations (4 per cell)

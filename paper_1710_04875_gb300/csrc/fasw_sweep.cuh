@@ -32,7 +32,6 @@ int sweep_strips(const LevelDev& L);
 bool ws_fits(int ni, int nj, int nw);
 size_t ws_floats(int ni, int nj);
 size_t ws_vec_floats(int ni, int nj);
-size_t ws_edge_floats(int ni, int nj);
 int ws_strips(int nj);
 void launch_ws_prep(const LevelDev& L, int mixed, cudaStream_t st);
 // exact_iters > 0: that many block Gauss-Seidel corrections toward the exact (D + L + U)^-1

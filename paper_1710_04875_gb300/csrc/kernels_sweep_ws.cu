@@ -15,7 +15,8 @@
 // operands of CHUNK steps are one contiguous block: one elected lane moves it into shared
 // memory with one cp.async.bulk per chunk and array, completion tracked by an mbarrier, STAGES
 // chunks ahead of use.  Strip b follows strip b-1 (forward; b+1 backward) through the
-// neighbour's boundary row, published in global memory every chunk (release / acquire flags).
+// neighbour's boundary row: the neighbour's out lane's results, read from its part of the output
+// once the neighbour has published its progress (release / acquire flags every 32 steps).
 // Every wait is bounded; on timeout the kernel sets the error word, waits (bounded) for its own
 // copies in flight and returns.
 #include <atomic>
@@ -155,7 +156,6 @@ __host__ __device__ __forceinline__ int ws_steps(int ni, int nj) {
 namespace {
 
 constexpr int WS_PUB = 32;   // steps between publications of a strip's boundary row (one column per lane)
-constexpr int WS_EPAD = 64;  // padding columns on each side of a boundary row (steps with no cell)
 
 // Skewed index of cell (i, j) in the backward order (the layout of y as the backward pass reads
 // it and of its result z): strip j / 32, step Mp - 1 - i - jl, lane jl.
@@ -167,10 +167,12 @@ __device__ __forceinline__ size_t ws_bpos(int i, int j, int Mp) {
 // One pass (forward: FWD, else backward) of one strip.  Returns false on a timeout.
 // F: blocks of the pass, C: its right-hand side vectors (forward: D^-1 r; backward: y), both
 // skewed; Out: the pass's result, skewed in the backward order (forward: y; backward: z);
-// edge_in / edge_out: boundary rows (float4 per column); flag_in / flag_out: progress.
+// prod_out: the part of Out of the neighbour strip whose boundary row this strip reads (its out
+// lane's vector of step sp at (FWD ? Mp - 1 - sp : sp) * 32); flag_in / flag_out: progress (the
+// number of steps whose results are in Out).
 template <bool FWD>
 __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, int nb, const float4* F, const float4* C,
-                        float4* Out, const float4* edge_in, float4* edge_out, const long long* flag_in,
+                        float4* Out, const float4* prod_out, const long long* flag_in,
                         long long* flag_out, int* err, long long limit, unsigned& phase_bits) {
   const int lane = threadIdx.x;
   const int ni = L.ni, nw = L.nw;
@@ -184,7 +186,6 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, int nb, const
   const float4* Fs = F + (size_t)b * Mp * WS_F4_STEP;
   const float4* Cs = C + (size_t)b * Mp * WS_ROWS;
   float4* Os = Out + (size_t)b * Mp * WS_ROWS + lane;
-  const bool out_ok = has_out && lane == out_lane;
   const unsigned bytesF = WS_K * WS_F4_STEP * 16, bytesC = WS_K * WS_ROWS * 16;
 
   auto issue = [&](int ch) {  // lane 0 only
@@ -263,7 +264,6 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, int nb, const
       if (lane == 0 && !FWD && i >= ni - nw && i < ni) S.cutv[ni - 1 - i] = y;   // read by its mirror
     }
     Os[(size_t)(FWD ? Mp - 1 - s : s) * WS_ROWS] = y;
-    if (out_ok) edge_out[i] = y;
     v = y;
   };
   auto run_chunk = [&](const float4* rF, const float4* rC, const float4* ek, int s0, auto cut_tag) {
@@ -299,9 +299,10 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, int nb, const
         drain(ch, issued);
         return false;
       }
-      const int s = s0 + lane;
-      const int col = FWD ? s : Mp - 1 - s - (WS_ROWS - 1);   // within the padded columns
-      const float4 e = __ldcg(edge_in + col);
+      // the neighbour's out-lane vector computed WS_ROWS - 1 steps after this strip's step s0 + lane
+      const int sp = s0 + lane + (WS_ROWS - 1);
+      const float4 e = sp < Mp ? __ldcg(prod_out + (size_t)(FWD ? Mp - 1 - sp : sp) * WS_ROWS)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
       __syncwarp();
       S.edge[lane] = e;
       __syncwarp();
@@ -336,8 +337,8 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, int nb, const
 // One launch: forward then backward pass of strip b (one warp per CTA).  flags: 2 nb progress
 // words (forward, backward), cleared by their strips at the start of the launch.
 __global__ void __launch_bounds__(32) k_sweep_ws(LevelDev L, const float4* Fb, const float4* Bb, const float4* C,
-                                                 float4* Y, const float* cutG, float4* edges, float4* Z,
-                                                 long long* flags, int* err, long long limit) {
+                                                 float4* Y, const float* cutG, float4* Z, long long* flags, int* err,
+                                                 long long limit) {
   pdl_entry();
   extern __shared__ __align__(128) unsigned char ws_raw[];
   const int nw = L.nw;
@@ -360,21 +361,20 @@ __global__ void __launch_bounds__(32) k_sweep_ws(LevelDev L, const float4* Fb, c
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
   __syncwarp();
   unsigned phase_bits = 0;
-  const size_t ew = (size_t)L.ni + 2 * WS_EPAD;  // padded boundary row of one strip
-  float4* edgeF = edges + WS_EPAD;               // column i of strip b's top row (forward) at b * ew + i
-  float4* edgeB = edges + (size_t)nb * ew + WS_EPAD;  // bottom rows (backward)
+  const size_t sw = (size_t)ws_steps(L.ni, L.nj) * WS_ROWS;  // one strip's part of Y or Z
   long long* fF = flags;
   long long* fB = flags + nb;
-  if (!ws_pass<true>(L, S, b, nb, Fb, C, Y, b > 0 ? edgeF + (size_t)(b - 1) * ew : nullptr,
-                     edgeF + (size_t)b * ew, b > 0 ? fF + b - 1 : nullptr, fF + b, err, limit, phase_bits))
+  // forward: strip b reads lane 31 of strip b - 1; backward: lane 0 of strip b + 1
+  if (!ws_pass<true>(L, S, b, nb, Fb, C, Y, b > 0 ? Y + (b - 1) * sw + (WS_ROWS - 1) : nullptr,
+                     b > 0 ? fF + b - 1 : nullptr, fF + b, err, limit, phase_bits))
     return;
   // the backward pass reads, through the async proxy, the y this warp has just written
   asm volatile("fence.proxy.async.global;" ::: "memory");
   __syncwarp();
   S.edge[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncwarp();
-  ws_pass<false>(L, S, b, nb, Bb, Y, Z, b < nb - 1 ? edgeB + (size_t)(b + 1) * ew : nullptr,
-                 edgeB + (size_t)b * ew, b < nb - 1 ? fB + b + 1 : nullptr, fB + b, err, limit, phase_bits);
+  ws_pass<false>(L, S, b, nb, Bb, Y, Z, b < nb - 1 ? Z + (b + 1) * sw : nullptr, b < nb - 1 ? fB + b + 1 : nullptr,
+                 fB + b, err, limit, phase_bits);
 }
 
 // ---------------------------------------------------------------- operand layout
@@ -675,8 +675,8 @@ cudaError_t ws_sweep_launch(const LevelDev& L, float4* zout, long long* prog, in
   cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_sweep_ws, L, reinterpret_cast<const float4*>(L.wsF),
                             reinterpret_cast<const float4*>(L.wsB), reinterpret_cast<const float4*>(L.wsC),
-                            reinterpret_cast<float4*>(L.wsY), static_cast<const float*>(L.wsCut),
-                            reinterpret_cast<float4*>(L.wsEdge), zout, prog, err, limit);
+                            reinterpret_cast<float4*>(L.wsY), static_cast<const float*>(L.wsCut), zout, prog,
+                            err, limit);
 }
 }  // namespace
 
@@ -740,7 +740,6 @@ int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int
   return launches + 1;
 }
 
-size_t ws_edge_floats(int ni, int nj) { return 2 * 4 * (size_t)ws_strips(nj) * ((size_t)ni + 2 * WS_EPAD); }
 size_t ws_floats(int ni, int nj) { return (size_t)ws_strips(nj) * ws_steps(ni, nj) * WS_F4_STEP * 4; }
 size_t ws_vec_floats(int ni, int nj) { return (size_t)ws_strips(nj) * ws_steps(ni, nj) * WS_ROWS * 4; }
 
