@@ -611,6 +611,43 @@ def _c4_inputs(P, precision):
     return cases, grids, params
 
 
+def batched_cycle(P, stream, flush, steps=10, warmup=3):
+    """The 64 batched cases in mixed precision, tuned as in the benchmark: the device time of a
+    cycle (steps cycles after warmup, L2 flushed before each), then one more cycle inside the NVTX
+    range "batched_cycle" (the range an ncu capture of the cycle's DRAM traffic filters on)."""
+    import torch
+    cases, grids, params = _c4_inputs(P, "mixed")
+    b = P.fasw.Batch(grids, params, stream=stream.cuda_stream)
+    tuned = b.autotune(with_tiles=True)
+    for k in range(warmup):
+        b.cycle(k)
+    ms = []
+    for k in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.cycle(warmup + k)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    flush.zero_()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("batched_cycle")
+    b.cycle(warmup + steps)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    n0 = b.launch_count()
+    b.cycle(warmup + steps + 1)
+    torch.cuda.synchronize()
+    launches = b.launch_count() - n0
+    b.close()
+    cells = sum(g.ni * g.nj for g in grids)
+    return {"workload": "euler_64_batched_cases", "cells": cells, "precision": "mixed", "ms_per_cycle": sum(ms) / steps,
+            "value": cells * steps / (sum(ms) / 1e3) / 1e6, "unit": METRIC, "launches_per_cycle": launches,
+            "sweep_choice": [int(k) for k, _ in tuned], "tile_choice": [int(t) for _, t in tuned]}
+
+
 def measure_batched(P, stream, flush, steps, warmup, sequential=True):
     """The 64 uneven Euler cases (128x32 .. 512x128 cells, seeded M, alpha, thickness):
     (i) mixed precision batched (one captured CUDA graph per cycle, sweep variants from the
@@ -775,6 +812,9 @@ def main():
                     help="only the full 64-step period of the 512x128 pitching case, FP64 and mixed (minutes)")
     ap.add_argument("--mesh-independence", action="store_true",
                     help="only the convergence rates on the 256x32 / 384x48 / 512x64 grid family")
+    ap.add_argument("--batched-cycle", action="store_true",
+                    help="only the 64 batched cases (mixed): cycle time, then one cycle in the NVTX range "
+                         "'batched_cycle' (for an ncu DRAM capture)")
     ap.add_argument("--adjoint-profile", action="store_true",
                     help="only one 30-iteration adjoint GMRES solve on the 256x64 grid (for ncu launch lists)")
     args = ap.parse_args()
@@ -812,6 +852,9 @@ def main():
         print(json.dumps(measure_mesh_independence(P, stream)), flush=True)
         return
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    if args.batched_cycle:
+        print(json.dumps(batched_cycle(P, stream, flush)), flush=True)
+        return
     g = workload_grid()
     ncell = g.ni * g.nj
     s = P.Solver(g, gpu_params(P, args.precision), stream=stream.cuda_stream)
