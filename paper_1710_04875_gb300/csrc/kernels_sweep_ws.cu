@@ -13,12 +13,16 @@
 // the order the warp consumes them (strip-major, step by step; "skewed" so that lane jl at
 // step s holds cell i = s - jl, with zero padding where that cell does not exist), so that the
 // operands of CHUNK steps are one contiguous block: one elected lane moves it into shared
-// memory with one cp.async.bulk per chunk and array, completion tracked by an mbarrier, STAGES
-// chunks ahead of use.  Strip b follows strip b-1 (forward; b+1 backward) through the
-// neighbour's boundary row: the neighbour's out lane's results, read from its part of the output
-// once the neighbour has published its progress (release / acquire flags every 32 steps).
+// memory with one cp.async.bulk per chunk and array, completion tracked by an mbarrier, double
+// buffered, the first step's operands of the next chunk loaded before the last step of this one.
+// The strips of a sweep form one thread-block cluster.  Strip b follows strip b-1 (forward; b+1
+// backward) through the neighbour's boundary row: the neighbour's out lane stores its vector of
+// every step straight into this strip's shared memory (a remote store inside the cluster), into
+// a buffer that holds a sentinel bit pattern until the value lands; this strip polls its own
+// shared memory once per chunk.  No fence or flag is needed: each 32-bit word arrives whole, and
+// the sentinel (a NaN payload that no arithmetic produces) marks the words not yet written.
 // Every wait is bounded; on timeout the kernel sets the error word, waits (bounded) for its own
-// copies in flight and returns.
+// copies in flight, and still meets the cluster's barriers, so that no strip waits forever.
 #include <atomic>
 #include <cstdint>
 #include <type_traits>
@@ -30,8 +34,10 @@ namespace fasw {
 
 namespace {
 
-constexpr int WS_K = 8;        // steps per chunk
-constexpr int WS_STAGES = 4;   // chunks in flight
+constexpr int WS_K = 16;       // steps per chunk
+constexpr int WS_STAGES = 2;   // chunk buffers (one in use, one in flight)
+constexpr int WS_U = 8;        // steps unrolled together (a chunk is WS_K / WS_U such blocks)
+constexpr unsigned WS_SENT = 0xFFFFFFFFu;  // "not yet written": a NaN payload no FP32 operation returns
 constexpr int WS_ROWS = 32;    // rows per strip (lanes)
 constexpr int WS_F4_STEP = 8 * WS_ROWS;  // float4 of blocks per step: 8 block rows x 32 lanes
 
@@ -63,14 +69,35 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
                : "memory");
 }
 
-__device__ __forceinline__ long long ld_acquire_ws(const long long* p) {
-  long long v;
-  asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+// address of the same shared-memory variable in CTA `rank` of this cluster
+__device__ __forceinline__ unsigned cluster_addr(const void* p, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr(p)), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void st_cluster4(unsigned addr, float4 v) {
+  asm volatile("st.relaxed.cluster.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
+__device__ __forceinline__ uint4 ld_cluster4(const float4* p) {
+  uint4 v;
+  asm volatile("ld.relaxed.cluster.shared::cta.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(smem_addr(p))
+               : "memory");
   return v;
 }
 
-__device__ __forceinline__ void st_release_ws(long long* p, long long v) {
-  asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ bool unwritten(uint4 v) {
+  return v.x == WS_SENT || v.y == WS_SENT || v.z == WS_SENT || v.w == WS_SENT;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  __syncwarp();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ float4 shfl_up4(float4 v) {
@@ -117,33 +144,30 @@ __device__ __forceinline__ float4 add_block(float4 v, const float* G, float4 x) 
   return v;
 }
 
-// Shared memory of the sweep: [mbarriers][ring of blocks][ring of vectors][edge][cut vectors][cut blocks]
+// Shared memory of the sweep: [mbarriers][ring of blocks][ring of vectors][stage][edge][cut vectors][cut blocks]
 struct WsSmem {
   uint64_t* bar;
   float4* ringF;  // WS_STAGES x WS_K x WS_F4_STEP
   float4* ringC;  // WS_STAGES x WS_K x 32
-  float4* edge;   // WS_PUB (one publication block of the neighbour's boundary row)
+  float4* stage;  // WS_K: the neighbour's boundary vectors of the current chunk, checked
+  float4* edge;   // Mp + 32: the neighbour's out-lane vector of its step t (t >= Mp: zero)
   float4* cutv;   // nw
   float* cutG;    // nw x 16
 };
 
-__device__ __forceinline__ WsSmem ws_carve(unsigned char* base, int nw) {
+__device__ __forceinline__ WsSmem ws_carve(unsigned char* base, int Mp, int nw) {
   WsSmem S;
   S.bar = reinterpret_cast<uint64_t*>(base);
   S.ringF = reinterpret_cast<float4*>(base + 128);
   S.ringC = S.ringF + WS_STAGES * WS_K * WS_F4_STEP;
-  S.edge = S.ringC + WS_STAGES * WS_K * WS_ROWS;
-  S.cutv = S.edge + 32;
+  S.stage = S.ringC + WS_STAGES * WS_K * WS_ROWS;
+  S.edge = S.stage + WS_K;
+  S.cutv = S.edge + Mp + 32;
   S.cutG = reinterpret_cast<float*>(S.cutv + (nw > 0 ? nw : 1));
   return S;
 }
 
 }  // namespace
-
-size_t ws_smem_bytes(int nw) {
-  const int m = nw > 0 ? nw : 1;
-  return 128 + 16 * ((size_t)WS_STAGES * WS_K * (WS_F4_STEP + WS_ROWS) + 32 + m) + 64 * (size_t)m;
-}
 
 int ws_strips(int nj) { return (nj + WS_ROWS - 1) / WS_ROWS; }
 // steps stored per strip: the ni + R - 1 steps that hold a cell (R = min(nj, 32) rows in a
@@ -153,9 +177,13 @@ __host__ __device__ __forceinline__ int ws_steps(int ni, int nj) {
   return (ni + R - 1 + WS_K - 1) / WS_K * WS_K;
 }
 
-namespace {
+size_t ws_smem_bytes(int ni, int nj, int nw) {
+  const int m = nw > 0 ? nw : 1;
+  return 128 + 16 * ((size_t)WS_STAGES * WS_K * (WS_F4_STEP + WS_ROWS) + WS_K + ws_steps(ni, nj) + 32 + m) +
+         64 * (size_t)m;
+}
 
-constexpr int WS_PUB = 32;   // steps between publications of a strip's boundary row (one column per lane)
+namespace {
 
 // Skewed index of cell (i, j) in the backward order (the layout of y as the backward pass reads
 // it and of its result z): strip j / 32, step Mp - 1 - i - jl, lane jl.
@@ -166,35 +194,37 @@ __device__ __forceinline__ size_t ws_bpos(int i, int j, int Mp) {
 
 // One pass (forward: FWD, else backward) of one strip.  Returns false on a timeout.
 // F: blocks of the pass, C: its right-hand side vectors (forward: D^-1 r; backward: y), both
-// skewed; Out: the pass's result, skewed in the backward order (forward: y; backward: z);
-// prod_out: the part of Out of the neighbour strip whose boundary row this strip reads (its out
-// lane's vector of step sp at (FWD ? Mp - 1 - sp : sp) * 32); flag_in / flag_out: progress (the
-// number of steps whose results are in Out).
+// skewed; Out: the pass's result, skewed in the backward order (forward: y; backward: z).
+// has_in: a neighbour strip feeds this one's edge lane (below forward, above backward) through
+// S.edge; redge: the cluster address of the edge buffer of the strip this one feeds (0: none).
+// Lane jl at step s holds cell i = s - jl (forward) or Mp - 1 - s - jl (backward); the edge lane
+// needs the neighbour's out-lane vector of the same column, which the neighbour computed at its
+// step s + 31: edge entry s + 31 (entries Mp .. Mp + 31 are zero).
 template <bool FWD>
-__device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, int nb, const float4* F, const float4* C,
-                        float4* Out, const float4* prod_out, const long long* flag_in,
-                        long long* flag_out, int* err, long long limit, unsigned& phase_bits) {
+__device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, const float4* F, const float4* C, float4* Out,
+                        bool has_in, unsigned redge, int* err, long long limit, unsigned& phase_bits) {
   const int lane = threadIdx.x;
   const int ni = L.ni, nw = L.nw;
   const int Mp = ws_steps(ni, L.nj);        // steps that hold a cell, padded to whole chunks
   const int nch = Mp / WS_K;
-  // the neighbour strip whose boundary row this one reads: below (forward) / above (backward)
-  const bool has_in = FWD ? b > 0 : b < nb - 1;
-  const bool has_out = FWD ? b < nb - 1 : b > 0;
   const int edge_lane = FWD ? 0 : WS_ROWS - 1;      // lane that reads the neighbour's row
   const int out_lane = FWD ? WS_ROWS - 1 : 0;       // lane whose row the other neighbour reads
   const float4* Fs = F + (size_t)b * Mp * WS_F4_STEP;
   const float4* Cs = C + (size_t)b * Mp * WS_ROWS;
   float4* Os = Out + (size_t)b * Mp * WS_ROWS + lane;
   const unsigned bytesF = WS_K * WS_F4_STEP * 16, bytesC = WS_K * WS_ROWS * 16;
+  const bool feeds = redge != 0 && lane == out_lane;
 
+  // Refill of a slot by the async proxy: the slot's previous contents were only read (no generic
+  // writes), and every one of those reads has completed, its value used by an earlier step of
+  // this warp, so no proxy fence is needed before the copy overwrites them.
   auto issue = [&](int ch) {  // lane 0 only
     const int slot = ch % WS_STAGES;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&S.bar[slot], bytesF + bytesC);
     bulk_copy(S.ringF + (size_t)slot * WS_K * WS_F4_STEP, Fs + (size_t)ch * WS_K * WS_F4_STEP, bytesF, &S.bar[slot]);
     bulk_copy(S.ringC + (size_t)slot * WS_K * WS_ROWS, Cs + (size_t)ch * WS_K * WS_ROWS, bytesC, &S.bar[slot]);
   };
+  int waited = 0;  // chunks whose copies have landed (and been accounted for)
   // bounded wait for the chunk in a slot; false on timeout
   auto wait_slot = [&](int slot) -> bool {
     const unsigned par = (phase_bits >> slot) & 1u;
@@ -207,14 +237,19 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, int nb, const
       }
     }
     ok = __all_sync(0xffffffffu, ok);
-    if (ok) phase_bits ^= 1u << slot;
+    if (ok) {
+      phase_bits ^= 1u << slot;
+      ++waited;
+    }
     return ok;
   };
+  int issued = 0;
   // after a timeout: wait for every copy still in flight into this CTA's shared memory before
   // returning.  These copies depend on no other CTA and finish within microseconds, so their
   // bound is fixed and generous, independent of the caller's (possibly tiny) spin limit.
-  auto drain = [&](int first, int last) {
-    for (int ch = first; ch < last; ++ch) {
+  auto fail = [&]() {
+    if (lane == 0) atomicExch(err, 1);
+    for (int ch = waited; ch < issued; ++ch) {
       const int slot = ch % WS_STAGES;
       const unsigned par = (phase_bits >> slot) & 1u;
       long long spins = 0;
@@ -222,37 +257,62 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, int nb, const
       }
       phase_bits ^= 1u << slot;
     }
+    __syncwarp();
+    return false;
+  };
+  // the neighbour's boundary vectors of steps s0 .. s0 + WS_K - 1 into S.stage: lane k polls
+  // edge entry s0 + 31 + k until the neighbour's store has landed (bounded; a neighbour that
+  // gave up has set the error word)
+  // The loop is warp-uniform (a vote decides whether any lane still waits), so that the warp
+  // leaves it converged.
+  auto poll_edge = [&](int s0) -> bool {
+    const float4* e = S.edge + s0 + (WS_ROWS - 1) + (lane & (WS_K - 1));
+    uint4 v = ld_cluster4(e);
+    long long spins = 0;
+    while (__any_sync(0xffffffffu, unwritten(v))) {
+      if (++spins > limit || ((spins & 255) == 0 && *((volatile int*)err) != 0)) return false;
+      v = ld_cluster4(e);
+    }
+    if (lane < WS_K)
+      S.stage[lane] = make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
+                                  __uint_as_float(v.w));
+    __syncwarp();
+    return true;
   };
 
   if (lane == 0)
     for (int ch = 0; ch < WS_STAGES && ch < nch; ++ch) issue(ch);
   __syncwarp();
-  int issued = nch < WS_STAGES ? nch : WS_STAGES;
+  issued = nch < WS_STAGES ? nch : WS_STAGES;
+  if (!has_in && lane < WS_K) S.stage[lane] = make_float4(0.f, 0.f, 0.f, 0.f);  // no neighbour: zero
+  __syncwarp();
 
   float4 v = make_float4(0.f, 0.f, 0.f, 0.f);  // this lane's vector at the previous step
-  // Operands of one step: this lane's rows of the two blocks, its right-hand side vector and
-  // the neighbour strip's boundary value.  They are loaded one step ahead of their use (the
-  // loads do not depend on the recurrence), so that shared-memory latency stays off the chain.
+  // Operands of one step: this lane's rows of the two blocks and its right-hand side vector,
+  // loaded one step ahead of their use (across chunk boundaries too: the next chunk's first
+  // step is loaded before this chunk's last), and the edge value, loaded one step ahead inside
+  // a chunk, so that shared-memory latency stays off the chain.
   struct Ops {
-    float4 A[4], B[4], c, e;
+    float4 A[4], B[4], c;
   };
-  auto load = [&](Ops& o, const float4* rF, const float4* rC, const float4* ek, int k) {
+  auto load = [&](Ops& o, int slot, int k) {
+    const float4* rF = S.ringF + (size_t)slot * WS_K * WS_F4_STEP;
+    const float4* rC = S.ringC + (size_t)slot * WS_K * WS_ROWS;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       o.A[q] = rF[k * WS_F4_STEP + q * WS_ROWS + lane];
       o.B[q] = rF[k * WS_F4_STEP + (4 + q) * WS_ROWS + lane];
     }
     o.c = rC[k * WS_ROWS + lane];
-    o.e = ek[k];
   };
   // One step.  Padded positions (no cell) carry zero blocks and vectors, so they compute zero
-  // and need no test: every step writes its result, and the boundary-row arrays are padded by
-  // WS_EPAD columns on both sides.  Only the wake-cut coupling of row 0 (strip 0, lane 0) is
-  // special, and chunks that hold no cut cell run the step without it (CUT false).
-  auto step = [&](const Ops& o, int s, auto cut_tag) {
+  // and need no test: every step writes its result.  Only the wake-cut coupling of row 0
+  // (strip 0, lane 0) is special, and chunks that hold no cut cell run the step without it
+  // (CUT false).
+  auto step = [&](const Ops& o, float4 e, int s, auto cut_tag) {
     constexpr bool CUT = decltype(cut_tag)::value;
     float4 w = FWD ? shfl_up4(v) : shfl_down4(v);  // the row below (forward) / above (backward)
-    if (lane == edge_lane) w = o.e;                 // neighbour strip's row, or zero
+    if (lane == edge_lane) w = e;                   // neighbour strip's row, or zero
     const int i = FWD ? s - lane : Mp - 1 - s - lane;  // this lane's cell (i, j)
     if constexpr (CUT && FWD)
       if (lane == 0 && i >= ni - nw && i < ni) w = S.cutv[ni - 1 - i];  // upper wake: its mirror
@@ -264,117 +324,103 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, int nb, const
       if (lane == 0 && !FWD && i >= ni - nw && i < ni) S.cutv[ni - 1 - i] = y;   // read by its mirror
     }
     Os[(size_t)(FWD ? Mp - 1 - s : s) * WS_ROWS] = y;
+    if (feeds) st_cluster4(redge + 16u * (unsigned)s, y);  // the fed strip's edge entry s
     v = y;
   };
-  auto run_chunk = [&](const float4* rF, const float4* rC, const float4* ek, int s0, auto cut_tag) {
-    Ops o[2];
-    load(o[0], rF, rC, ek, 0);
+  // o[0] holds the next step's operands between chunks: the last step of a chunk loads the next
+  // chunk's first step into it.  A chunk runs as WS_K / WS_U blocks of WS_U unrolled steps, which
+  // keeps the code of a pass small enough for the instruction cache.
+  Ops o[2];
+  float4 e[2];
+  bool late = false;  // the next chunk's wait gave up
+  auto run_chunk = [&](int slot, int ch, int s0, auto cut_tag) {
+    e[0] = S.stage[0];
+#pragma unroll 1
+    for (int kk = 0; kk < WS_K; kk += WS_U) {
 #pragma unroll
-    for (int k = 0; k < WS_K; ++k) {
-      if (k + 1 < WS_K) load(o[(k + 1) & 1], rF, rC, ek, k + 1);
-      step(o[k & 1], s0 + k, cut_tag);
+      for (int u = 0; u < WS_U; ++u) {
+        const int k = kk + u;
+        if (u + 1 < WS_U || kk + WS_U < WS_K) {
+          load(o[(u + 1) & 1], slot, k + 1);
+          e[(u + 1) & 1] = S.stage[k + 1];
+        } else if (ch + 1 < nch) {
+          if (wait_slot((ch + 1) % WS_STAGES))
+            load(o[0], (ch + 1) % WS_STAGES, 0);
+          else
+            late = true;
+        }
+        step(o[u & 1], e[u & 1], s0 + k, cut_tag);
+      }
     }
   };
 
+  if (!wait_slot(0)) return fail();
+  load(o[0], 0, 0);
   for (int ch = 0; ch < nch; ++ch) {
     const int s0 = ch * WS_K;
-    const int p0 = s0 - s0 % WS_PUB;  // first step of this publication block
-    // boundary row of the neighbour strip for the steps of this publication block: one column
-    // per lane
-    if (has_in && s0 == p0) {
-      bool ok = true;
-      if (lane == 0) {
-        const long long need = min((long long)s0 + WS_PUB + WS_ROWS - 1, (long long)Mp);
-        long long spins = 0;
-        while (ld_acquire_ws(flag_in) < need) {
-          if (*((volatile int*)err) != 0 || ++spins > limit) {
-            atomicExch(err, 1);
-            ok = false;
-            break;
-          }
-        }
-      }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) {
-        drain(ch, issued);
-        return false;
-      }
-      // the neighbour's out-lane vector computed WS_ROWS - 1 steps after this strip's step s0 + lane
-      const int sp = s0 + lane + (WS_ROWS - 1);
-      const float4 e = sp < Mp ? __ldcg(prod_out + (size_t)(FWD ? Mp - 1 - sp : sp) * WS_ROWS)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-      __syncwarp();
-      S.edge[lane] = e;
-      __syncwarp();
-    }
+    if (has_in && !poll_edge(s0)) return fail();
     const int slot = ch % WS_STAGES;
-    if (!wait_slot(slot)) {
-      if (lane == 0) atomicExch(err, 1);
-      drain(ch, issued);
-      return false;
-    }
-    const float4* rF = S.ringF + (size_t)slot * WS_K * WS_F4_STEP;
-    const float4* rC = S.ringC + (size_t)slot * WS_K * WS_ROWS;
-    const float4* ek = S.edge + (s0 - p0);
     // does lane 0 of strip 0 meet a wake-cut cell in this chunk?
     const int ilo = FWD ? s0 : Mp - s0 - WS_K, ihi = FWD ? s0 + WS_K - 1 : Mp - 1 - s0;
     const bool cut = b == 0 && nw > 0 && (ilo < nw || ihi >= ni - nw);
     if (cut)
-      run_chunk(rF, rC, ek, s0, std::true_type{});
+      run_chunk(slot, ch, s0, std::true_type{});
     else
-      run_chunk(rF, rC, ek, s0, std::false_type{});
+      run_chunk(slot, ch, s0, std::false_type{});
     __syncwarp();
-    if (lane == 0 && issued < nch) {
-      issue(issued);
-      ++issued;
-    }
-    const int done = s0 + WS_K;
-    if (has_out && lane == out_lane && (done % WS_PUB == 0 || done == Mp)) st_release_ws(flag_out, (long long)done);
+    if (late) return fail();
+    // this chunk's slot is free again (its operands are all in registers or consumed)
+    if (lane == 0 && issued < nch) issue(issued);
+    if (issued < nch) ++issued;
+    __syncwarp();
   }
   return true;
 }
 
-// One launch: forward then backward pass of strip b (one warp per CTA).  flags: 2 nb progress
-// words (forward, backward), cleared by their strips at the start of the launch.
+// the edge buffer before a pass: entries the neighbour will write hold the sentinel, the
+// entries past the last step zero
+__device__ __forceinline__ void ws_clear_edge(const WsSmem& S, int Mp) {
+  const float sent = __uint_as_float(WS_SENT);
+  for (int t = threadIdx.x; t < Mp + 32; t += 32)
+    S.edge[t] = t < Mp ? make_float4(sent, sent, sent, sent) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// One launch: forward then backward pass of strip b (one warp per CTA, the nb strips one
+// cluster).  Every strip meets the cluster barriers (set-up, between the passes, at the end)
+// whatever happened in its passes, so that a strip that gave up leaves no other one waiting on
+// a barrier; the last barrier also keeps every strip's shared memory alive until the
+// neighbours' remote stores into it have completed.
 __global__ void __launch_bounds__(32) k_sweep_ws(LevelDev L, const float4* Fb, const float4* Bb, const float4* C,
-                                                 float4* Y, const float* cutG, float4* Z, long long* flags, int* err,
-                                                 long long limit) {
+                                                 float4* Y, const float* cutG, float4* Z, int* err, long long limit) {
   pdl_entry();
   extern __shared__ __align__(128) unsigned char ws_raw[];
   const int nw = L.nw;
-  WsSmem S = ws_carve(ws_raw, nw);
+  const int Mp = ws_steps(L.ni, L.nj);
+  WsSmem S = ws_carve(ws_raw, Mp, nw);
   const int b = blockIdx.x, nb = gridDim.x, lane = threadIdx.x;
   if (lane == 0) {
     for (int k = 0; k < WS_STAGES; ++k) mbar_init(&S.bar[k], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  S.edge[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (b == 0)
     for (int x = lane; x < 16 * nw; x += 32) S.cutG[x] = cutG[x];
-  // Each strip clears its own progress words (the previous sweep on this level has completed:
-  // every launch waits for its predecessor at entry), and no strip reads a neighbour's word
-  // before the whole cluster has passed this barrier (release / acquire at cluster scope).
-  if (lane == 0) {
-    flags[b] = 0;
-    flags[nb + b] = 0;
-  }
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-  __syncwarp();
+  ws_clear_edge(S, Mp);
+  // every strip's edge buffer holds its sentinels before any neighbour stores into it
+  cluster_sync();
   unsigned phase_bits = 0;
-  const size_t sw = (size_t)ws_steps(L.ni, L.nj) * WS_ROWS;  // one strip's part of Y or Z
-  long long* fF = flags;
-  long long* fB = flags + nb;
-  // forward: strip b reads lane 31 of strip b - 1; backward: lane 0 of strip b + 1
-  if (!ws_pass<true>(L, S, b, nb, Fb, C, Y, b > 0 ? Y + (b - 1) * sw + (WS_ROWS - 1) : nullptr,
-                     b > 0 ? fF + b - 1 : nullptr, fF + b, err, limit, phase_bits))
-    return;
+  // forward: strip b feeds b + 1 (lane 31) and is fed by b - 1; backward the other way round
+  const unsigned up = b < nb - 1 ? cluster_addr(S.edge, (unsigned)(b + 1)) : 0u;
+  const unsigned down = b > 0 ? cluster_addr(S.edge, (unsigned)(b - 1)) : 0u;
+  bool ok = ws_pass<true>(L, S, b, Fb, C, Y, b > 0, up, err, limit, phase_bits);
   // the backward pass reads, through the async proxy, the y this warp has just written
   asm volatile("fence.proxy.async.global;" ::: "memory");
-  __syncwarp();
-  S.edge[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncwarp();
-  ws_pass<false>(L, S, b, nb, Bb, Y, Z, b < nb - 1 ? Z + (b + 1) * sw : nullptr, b < nb - 1 ? fB + b + 1 : nullptr,
-                 fB + b, err, limit, phase_bits);
+  // every strip has read its edge buffer to the end before it is cleared for the backward pass,
+  // and cleared before a neighbour stores into it again
+  cluster_sync();
+  ws_clear_edge(S, Mp);
+  cluster_sync();
+  if (ok) ws_pass<false>(L, S, b, Bb, Y, Z, b < nb - 1, down, err, limit, phase_bits);
+  cluster_sync();
 }
 
 // ---------------------------------------------------------------- operand layout
@@ -629,8 +675,7 @@ constexpr size_t kWsSmemMax = 227 * 1024;
 }  // namespace
 
 bool ws_fits(int ni, int nj, int nw) {
-  (void)ni;
-  return ws_strips(nj) <= 8 && ws_smem_bytes(nw) <= kWsSmemMax;  // one portable cluster per sweep
+  return ws_strips(nj) <= 8 && ws_smem_bytes(ni, nj, nw) <= kWsSmemMax;  // one portable cluster per sweep
 }
 
 void launch_ws_prep(const LevelDev& L, int mixed, cudaStream_t st) {
@@ -643,10 +688,9 @@ void launch_ws_prep(const LevelDev& L, int mixed, cudaStream_t st) {
 }
 
 namespace {
-cudaError_t ws_sweep_launch(const LevelDev& L, float4* zout, long long* prog, int* err, long long limit,
-                            cudaStream_t st) {
+cudaError_t ws_sweep_launch(const LevelDev& L, float4* zout, int* err, long long limit, cudaStream_t st) {
   const int nb = ws_strips(L.nj);
-  const size_t sm = ws_smem_bytes(L.nw);
+  const size_t sm = ws_smem_bytes(L.ni, L.nj, L.nw);
   // the shared-memory limit is a per-device attribute: set once on each device (idempotent if
   // two host threads race on the first launch)
   static std::atomic<unsigned long long> attr_done{0};
@@ -675,13 +719,14 @@ cudaError_t ws_sweep_launch(const LevelDev& L, float4* zout, long long* prog, in
   cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_sweep_ws, L, reinterpret_cast<const float4*>(L.wsF),
                             reinterpret_cast<const float4*>(L.wsB), reinterpret_cast<const float4*>(L.wsC),
-                            reinterpret_cast<float4*>(L.wsY), static_cast<const float*>(L.wsCut), zout, prog,
-                            err, limit);
+                            reinterpret_cast<float4*>(L.wsY), static_cast<const float*>(L.wsCut), zout, err,
+                            limit);
 }
 }  // namespace
 
 int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int aw, double alpha, const double* rhs,
                     long long* prog, int* err, long long limit, cudaStream_t st, int exact_iters) {
+  (void)prog;  // the warp strips exchange their boundary rows in shared memory, not through progress words
   const int g = (L.n + 127) / 128;
   float4* z0 = reinterpret_cast<float4*>(L.wsZ);
   float4* dz = z0 + ws_vec_floats(L.ni, L.nj) / 4;
@@ -701,7 +746,7 @@ int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int
   } else {
     launch_pdl(k_ws_rhs<double, false>, g, 128, 0, st, L, tb64, rhs, wC);
   }
-  ws_sweep_launch(L, z0, prog, err, limit, st);
+  ws_sweep_launch(L, z0, err, limit, st);
   launches += 2;
   const bool corr = refine && !mixed;
   if (corr) {
@@ -714,7 +759,7 @@ int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int
       launch_pdl(k_ws_defect_t<false>, g, 128, 0, st, L, tb64, z0c, L.wsT);
       launch_pdl(k_ws_defect_d<false>, g, 128, 0, st, L, tb64, rhs, wT, wC);
     }
-    ws_sweep_launch(L, dz, prog, err, limit, st);
+    ws_sweep_launch(L, dz, err, limit, st);
     launches += 3;
   }
   if (exact_iters > 0) {
@@ -728,7 +773,7 @@ int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int
       else
         launch_pdl(k_ws_exact_defect<double>, g, 128, 0, st, L, static_cast<const double*>(L.tb), rhs,
                    static_cast<const double*>(L.wsX), reinterpret_cast<float4*>(L.wsC));
-      ws_sweep_launch(L, z0, prog, err, limit, st);
+      ws_sweep_launch(L, z0, err, limit, st);
       launch_pdl(k_ws_accum, g, 128, 0, st, L, static_cast<const float4*>(z0), nullptr, L.wsX, 0);
       launches += 3;
     }
