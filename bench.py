@@ -48,8 +48,7 @@ HBM_FALLBACK_GBS = 6800.0
 # Algorithmic DRAM bytes per cell of one launch of each kernel class (the compulsory traffic:
 # every input read once, every output written once), by preconditioner precision.  The "sgs"
 # class is one preconditioner application of a stage with its update; on the headline workload
-# every level runs the warp-strip sweep in FP64, and the levels of 64 rows and more in mixed
-# precision (the smaller ones the one-CTA staged sweep, 528 B).
+# every level runs the warp-strip sweep in both precisions.
 #   FP64 (two FP32 warp-strip sweeps and one FP64 defect correction):
 #     D^-1 r: D^-1 (16 doubles) and r (4 doubles) read, the FP32 right-hand side written (4 floats)  176 B
 #     each sweep: forward blocks G_W G_S and backward blocks H_E H_N (64 floats), its right-hand

@@ -152,9 +152,9 @@ int fasw_solve_steady(fasw_ctx* ctx, double drop, int max_cycles, double* histor
  * stream; with the legacy default stream (NULL) cycles are always launched individually. */
 int fasw_use_graphs(fasw_ctx* ctx, int enable);
 
-/* How the SGS sweeps run: 0 = automatic (FP64: warp strips, 9; mixed: warp strips from 64 rows
- * up, below that the hyperplane-staged sweep where the level fits, else one CTA; a level the warp
- * strips do not fit -- more than 256 rows -- takes the strip-pipelined sweep in FP64), 1 = one
+/* How the SGS sweeps run: 0 = automatic (warp strips, 9, in both precisions; a level the warp
+ * strips do not fit -- more than 256 rows -- takes the strip-pipelined sweep in FP64 and the
+ * hyperplane-staged sweep, else one CTA, in mixed precision), 1 = one
  * thread per cell
  * applying the LU blocks (reference kernel), 2 = one CTA with precomputed transfer blocks
  * (strips where a hyperplane exceeds 128 cells), 3 = strip-pipelined with 8 rows per strip,
@@ -163,7 +163,8 @@ int fasw_use_graphs(fasw_ctx* ctx, int enable);
  * hyperplane-staged with a staging ring of 4 / 8 steps, 8 = strip-pipelined with 4 rows per
  * strip, 9 = warp strips: one warp per strip of 32 rows, each lane a row holding all four
  * components of its cell, operands staged into shared memory by bulk asynchronous copies, the
- * strips of one sweep launched as one thread-block cluster; its recurrence runs in FP32, and in
+ * strips of one sweep launched as one thread-block cluster, each strip storing its boundary row
+ * straight into the shared memory of the strip that reads it; its recurrence runs in FP32, and in
  * FP64 contexts it is followed by one FP64 defect correction (the FP64 residual of the SGS system
  * at the FP32 result, solved by a second FP32 sweep and added), which brings the result to FP64
  * accuracy.  All give the same Gauss-Seidel result up to rounding.  Synchronizes the stream; drops captured
@@ -435,7 +436,7 @@ int fasw_batch_solve(fasw_batch* batch, double drop, int max_cycles, int* cycles
  * together); FP64 9 and 2.  Tile heights 0 (size rule), 1, 2, 4, 8.  Results are cached per shape
  * and precision for the process, so a batch whose shapes are all cached is not timed again.
  * choice[k] (nullable) receives kind | (tile height << 8) for case k.  Batch cases start with
- * kind 5 (mixed) or 9 (FP64); strip-pipelined kinds are never used inside a batch. */
+ * kind 9 (the warp strips); strip-pipelined kinds are never used inside a batch. */
 int fasw_batch_autotune(fasw_batch* batch, int* choice);
 long long fasw_batch_launch_count(fasw_batch* batch);
 

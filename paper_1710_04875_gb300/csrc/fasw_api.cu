@@ -230,9 +230,10 @@ int level_sweep_kind(const fasw_ctx* c, const LevelDev& L) {
   if (c->exact_iters > 0 && L.wsF) return SWEEP_WS;  // the exact-preconditioner iterations run on it
   int k = c->sweep_kind;
   if (k == SWEEP_AUTO) {
-    // measured per level on GB300: the warp strips win for FP64 on every level and for FP32 from
-    // 64 rows up; below that the one-CTA hyperplane-staged FP32 sweep is faster
-    if (L.wsF && (!c->mixed || L.nj >= 64)) return SWEEP_WS;
+    // measured per level on GB300: the warp strips win on every level in both precisions (mixed,
+    // one application: 64x16 28.6 against 32.3 us for the one-CTA hyperplane-staged sweep,
+    // 128x32 41.9 against 58.3 us)
+    if (L.wsF) return SWEEP_WS;
     return c->mixed ? (L.hpF ? SWEEP_HP : SWEEP_CTA) : SWEEP_STRIPS;
   }
   if (k == SWEEP_WS && !L.wsF) k = c->mixed ? SWEEP_CTA : SWEEP_STRIPS;

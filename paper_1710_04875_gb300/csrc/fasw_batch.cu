@@ -66,7 +66,7 @@ int fasw_batch_create(int ncases, const int* ni, const int* nj, const int* n_wak
       return r;
     }
     c->in_batch = 1;
-    c->sweep_kind = c->mixed ? SWEEP_HP : SWEEP_WS;
+    c->sweep_kind = SWEEP_WS;  // as a single case: the warp strips in both precisions
     b->cases.push_back(c);
   }
   *out = b;
@@ -231,7 +231,7 @@ int fasw_batch_autotune(fasw_batch* b, int* choice) {
   if (!b) return FASW_ERR_ARG;
   const size_t nc = b->cases.size();
   std::vector<int> kinds(nc), tys(nc, 0);
-  for (size_t k = 0; k < nc; ++k) kinds[k] = b->cases[k]->mixed ? SWEEP_HP : SWEEP_WS;
+  for (size_t k = 0; k < nc; ++k) kinds[k] = SWEEP_WS;
   std::map<TuneKey, std::vector<size_t>> groups;
   for (size_t k = 0; k < nc; ++k) groups[key_of(b->cases[k])].push_back(k);
   bool all_cached = true;
