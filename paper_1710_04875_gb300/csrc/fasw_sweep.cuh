@@ -16,7 +16,8 @@ enum SweepKind {
 };
 inline bool is_hp(int kind) { return kind == SWEEP_HP || kind == SWEEP_HP4 || kind == SWEEP_HP8; }
 
-// kind: the resolved sweep kind of this level (SWEEP_HP writes the hyperplane-major blocks).
+// kind: the resolved sweep kind of this level (SWEEP_HP writes the hyperplane-major blocks,
+// SWEEP_WS also the skewed FP32 blocks of the warp strips).
 void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st);
 // Forward and backward sweep of one stage: y = (D+L)^-1 rhs, z = (D+U)^-1 D y into L.yz64 /
 // L.yz32, with the stage update u = u0 - alpha z (AW) or u0 - alpha dt* z (ARK) when
@@ -26,14 +27,24 @@ int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, 
                  long long* prog, int* err, long long limit, cudaStream_t st, int exact_iters = 0);
 int sweep_strips(const LevelDev& L);
 // Warp-strip sweep (kernels_sweep_ws.cu): whether a level can use it, the sizes of its arrays
-// (floats of wsF / wsB; of wsC / wsY), its strips, the skewed blocks from the transfer blocks
-// (after launch_sgs_prep), and one application (refine: FP64 defect correction in FP64
-// contexts).  Returns the kernels launched.
+// (floats of wsF / wsB; of wsC / wsY), its strips, and one application (refine: FP64 defect
+// correction in FP64 contexts; the skewed blocks come from launch_sgs_prep).  Returns the
+// kernels launched.
+// Warp-strip layout: strips of WS_ROWS rows, a strip's operands stored step by step (lane jl at
+// step s holds cell i = s - jl), WS_K steps to a chunk, WS_F4_STEP float4 of blocks per step.
+constexpr int WS_ROWS = 32;
+constexpr int WS_K = 16;
+constexpr int WS_F4_STEP = 8 * WS_ROWS;
+// steps stored per strip: the ni + R - 1 steps that hold a cell (R = min(nj, 32) rows in a
+// strip: a level of fewer than 32 rows skews by its own rows only), padded to whole chunks
+__host__ __device__ __forceinline__ int ws_steps(int ni, int nj) {
+  const int R = nj < WS_ROWS ? nj : WS_ROWS;
+  return (ni + R - 1 + WS_K - 1) / WS_K * WS_K;
+}
 bool ws_fits(int ni, int nj, int nw);
 size_t ws_floats(int ni, int nj);
 size_t ws_vec_floats(int ni, int nj);
 int ws_strips(int nj);
-void launch_ws_prep(const LevelDev& L, int mixed, cudaStream_t st);
 // exact_iters > 0: that many block Gauss-Seidel corrections toward the exact (D + L + U)^-1
 int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int aw, double alpha, const double* rhs,
                     long long* prog, int* err, long long limit, cudaStream_t st, int exact_iters = 0);

@@ -34,11 +34,16 @@ namespace {
 __device__ __forceinline__ bool on_cut(const LevelDev& L, int i) { return L.nw > 0 && (i < L.nw || i >= L.ni - L.nw); }
 
 // Transfer blocks, entry-major: tb[(blk*16 + e) * n + c], blk 0 = D^-1, 1 = G_W, 2 = G_S,
-// 3 = H_E, 4 = H_N.  Blocks of absent neighbours are zero.  With HP (FP32 only) blocks 1-4 go
-// to the hyperplane-major arrays of k_sweep_hp instead: entry h = (i + j) * nj + j holds
+// 3 = H_E, 4 = H_N.  Blocks of absent neighbours are zero.  MODE 1 (HP, FP32 only): blocks 1-4
+// go to the hyperplane-major arrays of k_sweep_hp instead: entry h = (i + j) * nj + j holds
 // hpF[32h..] = G_W, G_S and hpB[32h..] = H_E, H_N (row-major 4x4 each); D^-1 stays in tb.
-template <typename T, bool HP>
+// MODE 2 (WS): tb as MODE 0, and blocks 1-4 also in FP32 in the skewed layout of the warp-strip
+// sweep (kernels_sweep_ws.cu): forward rows G_W, G_S at strip j / 32, step i + j % 32, lane j % 32
+// (G_S zero on row 0 except the upper wake, whose mirror precedes it), backward rows H_E, H_N at
+// step Mp - 1 - i - j % 32; the lower wake's G_S (the backward coupling to its mirror) to wsCut.
+template <typename T, int MODE>
 __global__ void k_sgs_prep(LevelDev L, const T* blk, const T* dlu, T* tb) {
+  constexpr bool HP = MODE == 1;
   pdl_entry();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
@@ -77,6 +82,13 @@ __global__ void k_sgs_prep(LevelDev L, const T* blk, const T* dlu, T* tb) {
 #pragma unroll
   for (int e = 0; e < 16; ++e) tb[e * n + c] = Di[e];
   const size_t h = (size_t)(i + j) * nj + j;
+  // MODE 2: this cell's forward / backward rows in the warp-strip layout
+  const int jl = j % WS_ROWS, Mp = ws_steps(ni, nj);
+  const bool cut = on_cut(L, i);
+  float4* wf = reinterpret_cast<float4*>(L.wsF) + ((size_t)(j / WS_ROWS) * Mp + (i + jl)) * WS_F4_STEP + jl;
+  float4* wb = reinterpret_cast<float4*>(L.wsB) + ((size_t)(j / WS_ROWS) * Mp + (Mp - 1 - i - jl)) * WS_F4_STEP + jl;
+  const bool gs_fwd = j > 0 || (cut && ni - 1 - i < i);
+  const bool cut_lower = j == 0 && cut && ni - 1 - i > i;
   // product helper: out = s * Di * B (B entry-major with stride sb at face f)
   auto prod = [&](int slot, const T* B, int sb, int f, T s, bool present) {
 #pragma unroll
@@ -98,6 +110,16 @@ __global__ void k_sgs_prep(LevelDev L, const T* blk, const T* dlu, T* tb) {
       } else {
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) tb[(slot * 16 + 4 * r + cc) * n + c] = row[cc];
+      }
+      if constexpr (MODE == 2) {
+        const float4 f = make_float4(float(row[0]), float(row[1]), float(row[2]), float(row[3]));
+        if (slot == 1) wf[r * WS_ROWS] = f;
+        if (slot == 2) {
+          wf[(4 + r) * WS_ROWS] = gs_fwd ? f : make_float4(0.f, 0.f, 0.f, 0.f);
+          if (cut_lower) *reinterpret_cast<float4*>(L.wsCut + 16 * i + 4 * r) = f;
+        }
+        if (slot == 3) wb[r * WS_ROWS] = f;
+        if (slot == 4) wb[(4 + r) * WS_ROWS] = f;
       }
     }
   };
@@ -472,7 +494,7 @@ __global__ void __launch_bounds__(16 * SH) k_sweep_strips(LevelDev L, const T* t
 // For the FP32 preconditioner the sweep is bound by how fast one SM can bring in the blocks
 // of the next hyperplane (36 floats per cell and direction) and by the per-step barrier, not
 // by arithmetic.  Cells are therefore stored hyperplane-major (entry h = (i+j)*nj + j, see
-// k_sgs_prep<float, true>), so that the data of one step of all rows are contiguous, and
+// k_sgs_prep<float, 1>), so that the data of one step of all rows are contiguous, and
 // each thread (row j, block row q) copies its own 16-byte pieces with cp.async into a
 // per-thread ring of shared memory STAGES steps ahead of use.  The previous hyperplane's
 // vectors are exchanged through shared memory (one barrier per step); row 0 keeps its values
@@ -707,18 +729,17 @@ __global__ void k_hp_finish(LevelDev L, int do_update, int aw, double alpha) {
 void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st) {
   if (kind == SWEEP_WS && L.wsF) {
     if (mixed)
-      launch_pdl(k_sgs_prep<float, false>, (L.n + 63) / 64, 64, 0, st, L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
+      launch_pdl(k_sgs_prep<float, 2>, (L.n + 63) / 64, 64, 0, st, L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
     else
-      launch_pdl(k_sgs_prep<double, false>, (L.n + 63) / 64, 64, 0, st, L, L.blk64, L.dlu64, L.tb);
-    launch_ws_prep(L, mixed, st);
+      launch_pdl(k_sgs_prep<double, 2>, (L.n + 63) / 64, 64, 0, st, L, L.blk64, L.dlu64, L.tb);
     return;
   }
   if (mixed && is_hp(kind) && L.hpF)
-    launch_pdl(k_sgs_prep<float, true>, (L.n + 63) / 64, 64, 0, st, L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
+    launch_pdl(k_sgs_prep<float, 1>, (L.n + 63) / 64, 64, 0, st, L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
   else if (mixed)
-    launch_pdl(k_sgs_prep<float, false>, (L.n + 63) / 64, 64, 0, st, L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
+    launch_pdl(k_sgs_prep<float, 0>, (L.n + 63) / 64, 64, 0, st, L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
   else
-    launch_pdl(k_sgs_prep<double, false>, (L.n + 63) / 64, 64, 0, st, L, L.blk64, L.dlu64, L.tb);
+    launch_pdl(k_sgs_prep<double, 0>, (L.n + 63) / 64, 64, 0, st, L, L.blk64, L.dlu64, L.tb);
 }
 
 namespace {

@@ -34,12 +34,9 @@ namespace fasw {
 
 namespace {
 
-constexpr int WS_K = 16;       // steps per chunk
 constexpr int WS_STAGES = 2;   // chunk buffers (one in use, one in flight)
 constexpr int WS_U = 8;        // steps unrolled together (a chunk is WS_K / WS_U such blocks)
 constexpr unsigned WS_SENT = 0xFFFFFFFFu;  // "not yet written": a NaN payload no FP32 operation returns
-constexpr int WS_ROWS = 32;    // rows per strip (lanes)
-constexpr int WS_F4_STEP = 8 * WS_ROWS;  // float4 of blocks per step: 8 block rows x 32 lanes
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -76,10 +73,13 @@ __device__ __forceinline__ unsigned cluster_addr(const void* p, unsigned rank) {
   return r;
 }
 
-__device__ __forceinline__ void st_cluster4(unsigned addr, float4 v) {
-  asm volatile("st.relaxed.cluster.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y),
-               "f"(v.z), "f"(v.w)
-               : "memory");
+// predicated in the instruction itself (no branch around it: one lane of the warp stores)
+__device__ __forceinline__ void st_cluster4_if(bool pred, unsigned addr, float4 v) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %5, 0;\n"
+      " @p st.relaxed.cluster.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};\n}\n" ::"r"(addr),
+      "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"((unsigned)pred)
+      : "memory");
 }
 
 __device__ __forceinline__ uint4 ld_cluster4(const float4* p) {
@@ -170,12 +170,6 @@ __device__ __forceinline__ WsSmem ws_carve(unsigned char* base, int Mp, int nw) 
 }  // namespace
 
 int ws_strips(int nj) { return (nj + WS_ROWS - 1) / WS_ROWS; }
-// steps stored per strip: the ni + R - 1 steps that hold a cell (R = min(nj, 32) rows in a
-// strip: a level of fewer than 32 rows skews by its own rows only), padded to whole chunks
-__host__ __device__ __forceinline__ int ws_steps(int ni, int nj) {
-  const int R = nj < WS_ROWS ? nj : WS_ROWS;
-  return (ni + R - 1 + WS_K - 1) / WS_K * WS_K;
-}
 
 size_t ws_smem_bytes(int ni, int nj, int nw) {
   const int m = nw > 0 ? nw : 1;
@@ -324,7 +318,7 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, const float4*
       if (lane == 0 && !FWD && i >= ni - nw && i < ni) S.cutv[ni - 1 - i] = y;   // read by its mirror
     }
     Os[(size_t)(FWD ? Mp - 1 - s : s) * WS_ROWS] = y;
-    if (feeds) st_cluster4(redge + 16u * (unsigned)s, y);  // the fed strip's edge entry s
+    st_cluster4_if(feeds, redge + 16u * (unsigned)s, y);  // the fed strip's edge entry s
     v = y;
   };
   // o[0] holds the next step's operands between chunks: the last step of a chunk loads the next
@@ -426,38 +420,6 @@ __global__ void __launch_bounds__(32) k_sweep_ws(LevelDev L, const float4* Fb, c
 // ---------------------------------------------------------------- operand layout
 // Skewed position of cell (i, j): strip b = j / 32, lane jl = j % 32, forward step s = i + jl,
 // backward step Mp - 1 - i - jl (Mp: the ni + R - 1 steps that hold a cell, R = min(nj, 32), padded to whole chunks).
-
-// Blocks of the warp-strip sweep from the transfer blocks (entry-major planes, T = double or
-// float): forward G_W, G_S (zero on row 0 except the upper wake, whose mirror precedes it),
-// backward H_E, H_N; the lower wake's G_S (backward coupling to its mirror) to cutG.
-template <typename T>
-__global__ void k_ws_blocks(LevelDev L, const T* tb, float4* Fb, float4* Bb, float* cutG) {
-  pdl_entry();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= L.n) return;
-  const int ni = L.ni, n = L.n, i = c % ni, j = c / ni;
-  const int b = j / WS_ROWS, jl = j % WS_ROWS;
-  const int Mp = ws_steps(ni, L.nj);
-  const bool cut = L.nw > 0 && (i < L.nw || i >= ni - L.nw);
-  const bool gs_fwd = j > 0 || (cut && ni - 1 - i < i);
-  float4* f = Fb + ((size_t)b * Mp + (i + jl)) * WS_F4_STEP + jl;
-  float4* g = Bb + ((size_t)b * Mp + (Mp - 1 - i - jl)) * WS_F4_STEP + jl;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const T* w = tb + (size_t)(16 + 4 * q) * n + c;
-    const T* s = tb + (size_t)(32 + 4 * q) * n + c;
-    const T* e = tb + (size_t)(48 + 4 * q) * n + c;
-    const T* nn = tb + (size_t)(64 + 4 * q) * n + c;
-    f[q * WS_ROWS] = make_float4(float(w[0]), float(w[n]), float(w[2 * n]), float(w[3 * n]));
-    f[(4 + q) * WS_ROWS] = gs_fwd ? make_float4(float(s[0]), float(s[n]), float(s[2 * n]), float(s[3 * n]))
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-    g[q * WS_ROWS] = make_float4(float(e[0]), float(e[n]), float(e[2 * n]), float(e[3 * n]));
-    g[(4 + q) * WS_ROWS] = make_float4(float(nn[0]), float(nn[n]), float(nn[2 * n]), float(nn[3 * n]));
-    if (j == 0 && cut && ni - 1 - i > i)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) cutG[16 * i + 4 * q + t] = float(s[(size_t)t * n]);
-  }
-}
 
 // Forward right-hand side D^-1 r (FP32), skewed.
 // The FP64 kernels of one application, written per row q of their block products: a thread
@@ -678,14 +640,6 @@ bool ws_fits(int ni, int nj, int nw) {
   return ws_strips(nj) <= 8 && ws_smem_bytes(ni, nj, nw) <= kWsSmemMax;  // one portable cluster per sweep
 }
 
-void launch_ws_prep(const LevelDev& L, int mixed, cudaStream_t st) {
-  if (mixed)
-    launch_pdl(k_ws_blocks<float>, (L.n + 127) / 128, 128, 0, st, L, reinterpret_cast<const float*>(L.tb),
-               reinterpret_cast<float4*>(L.wsF), reinterpret_cast<float4*>(L.wsB), L.wsCut);
-  else
-    launch_pdl(k_ws_blocks<double>, (L.n + 127) / 128, 128, 0, st, L, static_cast<const double*>(L.tb),
-               reinterpret_cast<float4*>(L.wsF), reinterpret_cast<float4*>(L.wsB), L.wsCut);
-}
 
 namespace {
 cudaError_t ws_sweep_launch(const LevelDev& L, float4* zout, int* err, long long limit, cudaStream_t st) {
