@@ -95,9 +95,14 @@ __device__ __forceinline__ bool unwritten(uint4 v) {
   return v.x == WS_SENT || v.y == WS_SENT || v.z == WS_SENT || v.w == WS_SENT;
 }
 
+// A lone strip (a cluster of one CTA, one warp) shares its shared memory with no one: a warp
+// barrier orders its own accesses, and the cluster barrier is skipped.
 __device__ __forceinline__ void cluster_sync() {
   __syncwarp();
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  if (gridDim.x > 1)
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  else
+    __syncwarp();
 }
 
 __device__ __forceinline__ float4 shfl_up4(float4 v) {
