@@ -685,7 +685,7 @@ def measure_batched(P, stream, flush, steps, warmup, sequential=True):
             "cases": len(grids), "cells": cells, "value": cells * steps / (sum(ms) / 1e3) / 1e6, "unit": METRIC,
             "ms_per_cycle": sum(ms) / steps,
             "sweep_choice": {"staged8": choice.count(7), "staged4": choice.count(6), "staged": choice.count(5),
-                             "cta": choice.count(2), "warp": choice.count(9)},
+                             "cta": choice.count(2), "warp": choice.count(9), "warp8": choice.count(10)},
             "residual_tile_choice": {str(t): sum(1 for _, x in tuned if x == t) for t in (0, 1, 2, 4, 8)},
             "time_to_6_orders": {"seconds": dt, "cycles_run": ncy, "status": int(code),
                                  "cases_converged": int((cyc > 0).sum()), "cases_diverged": int((cyc == -2).sum()),

@@ -167,7 +167,9 @@ int fasw_use_graphs(fasw_ctx* ctx, int enable);
  * straight into the shared memory of the strip that reads it; its recurrence runs in FP32, and in
  * FP64 contexts it is followed by one FP64 defect correction (the FP64 residual of the SGS system
  * at the FP32 result, solved by a second FP32 sweep and added), which brings the result to FP64
- * accuracy.  All give the same Gauss-Seidel result up to rounding.  Synchronizes the stream; drops captured
+ * accuracy; 10 = as 9, with operand chunks of 8 steps instead of 16 staged in shared memory (half
+ * the shared memory per strip, so that strips of different batch cases can share an SM).  All
+ * give the same Gauss-Seidel result up to rounding.  Synchronizes the stream; drops captured
  * cycles. */
 int fasw_set_sweep(fasw_ctx* ctx, int kind);
 
@@ -432,8 +434,8 @@ int fasw_batch_solve(fasw_batch* batch, double drop, int max_cycles, int* cycles
  * batch cycles: states are saved and restored; each candidate is timed beside the incumbent, the
  * faster of two timings each, and a switch must gain 2 %.  Candidates are the variants whose CTAs
  * never wait on a CTA that might not be resident beside the other cases' kernels: mixed precision
- * 7, 6, 2 and 9 (the warp strips run as one thread-block cluster, which the hardware schedules
- * together); FP64 9 and 2.  Tile heights 0 (size rule), 1, 2, 4, 8.  Results are cached per shape
+ * 7, 6, 2, 9 and 10 (the warp strips run as one thread-block cluster, which the hardware
+ * schedules together); FP64 9, 10 and 2.  Tile heights 0 (size rule), 1, 2, 4, 8.  Results are cached per shape
  * and precision for the process, so a batch whose shapes are all cached is not timed again.
  * choice[k] (nullable) receives kind | (tile height << 8) for case k.  Batch cases start with
  * kind 9 (the warp strips); strip-pipelined kinds are never used inside a batch. */

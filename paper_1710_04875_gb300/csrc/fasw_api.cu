@@ -236,7 +236,7 @@ int level_sweep_kind(const fasw_ctx* c, const LevelDev& L) {
     if (L.wsF) return SWEEP_WS;
     return c->mixed ? (L.hpF ? SWEEP_HP : SWEEP_CTA) : SWEEP_STRIPS;
   }
-  if (k == SWEEP_WS && !L.wsF) k = c->mixed ? SWEEP_CTA : SWEEP_STRIPS;
+  if (is_ws(k) && !L.wsF) k = c->mixed ? SWEEP_CTA : SWEEP_STRIPS;
   if (is_hp(k) && !(c->mixed && L.hpF)) k = c->mixed ? SWEEP_CTA : SWEEP_STRIPS;
   if (c->in_batch && (k == SWEEP_STRIPS || k == SWEEP_STRIPS16 || k == SWEEP_STRIPS4))
     k = L.wsF ? SWEEP_WS : SWEEP_CTA;  // concurrent cases: only sweeps whose CTAs are co-scheduled
@@ -696,7 +696,7 @@ int fasw_fas_cycle(fasw_ctx* c, int cycle_index, double* res_norm) {
 }
 
 int fasw_set_sweep(fasw_ctx* c, int kind) {
-  if (!c || kind < SWEEP_AUTO || kind > SWEEP_WS) return FASW_ERR_ARG;
+  if (!c || kind < SWEEP_AUTO || kind > SWEEP_WS8) return FASW_ERR_ARG;
   int r = sync(c);
   if (r) return r;
   c->sweep_kind = kind;

@@ -271,8 +271,8 @@ int fasw_batch_autotune(fasw_batch* b, int* choice) {
     };
     // sweep variants whose CTAs never wait on a CTA that may not be resident (one CTA, or the
     // warp strips launched as one cluster); the FP32 staged kinds only in mixed precision
-    const int cand_mixed[4] = {SWEEP_HP8, SWEEP_HP4, SWEEP_CTA, SWEEP_WS};
-    const int cand_fp64[2] = {SWEEP_WS, SWEEP_CTA};
+    const int cand_mixed[5] = {SWEEP_HP8, SWEEP_HP4, SWEEP_CTA, SWEEP_WS, SWEEP_WS8};
+    const int cand_fp64[3] = {SWEEP_WS, SWEEP_WS8, SWEEP_CTA};
     const int tile_cand[5] = {0, 1, 2, 4, 8};
     // larger shapes first: they dominate the batch time
     std::vector<std::pair<TuneKey, std::vector<size_t>>> order(groups.begin(), groups.end());
@@ -284,7 +284,7 @@ int fasw_batch_autotune(fasw_batch* b, int* choice) {
       const std::vector<size_t>& members = order[gi].second;
       const bool mixed = order[gi].first.mixed != 0;
       const int* cand = mixed ? cand_mixed : cand_fp64;
-      const int ncand = mixed ? 4 : 2;
+      const int ncand = mixed ? 5 : 3;
       // sweep variant first (it dominates), then the residual tile height with it
       int keep = kinds[members[0]];
       for (int ci = 0; ci < ncand; ++ci) {

@@ -12,9 +12,12 @@ namespace fasw {
 // the first), which brings the result to FP64 accuracy.
 enum SweepKind {
   SWEEP_AUTO = 0, SWEEP_LEGACY = 1, SWEEP_CTA = 2, SWEEP_STRIPS = 3, SWEEP_STRIPS16 = 4,
-  SWEEP_HP = 5, SWEEP_HP4 = 6, SWEEP_HP8 = 7, SWEEP_STRIPS4 = 8, SWEEP_WS = 9
+  SWEEP_HP = 5, SWEEP_HP4 = 6, SWEEP_HP8 = 7, SWEEP_STRIPS4 = 8, SWEEP_WS = 9, SWEEP_WS8 = 10
 };
 inline bool is_hp(int kind) { return kind == SWEEP_HP || kind == SWEEP_HP4 || kind == SWEEP_HP8; }
+// SWEEP_WS8: the warp strips staging chunks of 8 steps instead of 16 (half the shared memory, so
+// that two strips, of different cases of a batch, can share an SM)
+inline bool is_ws(int kind) { return kind == SWEEP_WS || kind == SWEEP_WS8; }
 
 // kind: the resolved sweep kind of this level (SWEEP_HP writes the hyperplane-major blocks,
 // SWEEP_WS also the skewed FP32 blocks of the warp strips).
@@ -45,9 +48,11 @@ bool ws_fits(int ni, int nj, int nw);
 size_t ws_floats(int ni, int nj);
 size_t ws_vec_floats(int ni, int nj);
 int ws_strips(int nj);
-// exact_iters > 0: that many block Gauss-Seidel corrections toward the exact (D + L + U)^-1
+// exact_iters > 0: that many block Gauss-Seidel corrections toward the exact (D + L + U)^-1;
+// chunk: steps per staged chunk (16, or 8 for SWEEP_WS8)
 int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int aw, double alpha, const double* rhs,
-                    long long* prog, int* err, long long limit, cudaStream_t st, int exact_iters = 0);
+                    long long* prog, int* err, long long limit, cudaStream_t st, int exact_iters = 0,
+                    int chunk = WS_K);
 // Hyperplane-staged FP32 sweep: whether a level fits (rows, shared memory), and the entries
 // (ni + nj - 1) * nj of its hyperplane-major arrays (hpF, hpB: 32 floats each; hpC, hpY: 4).
 bool hp_fits(int ni, int nj, int nw);

@@ -727,7 +727,7 @@ __global__ void k_hp_finish(LevelDev L, int do_update, int aw, double alpha) {
 }  // namespace
 
 void launch_sgs_prep(const LevelDev& L, int mixed, int kind, cudaStream_t st) {
-  if (kind == SWEEP_WS && L.wsF) {
+  if (is_ws(kind) && L.wsF) {
     if (mixed)
       launch_pdl(k_sgs_prep<float, 2>, (L.n + 63) / 64, 64, 0, st, L, L.blk32, L.dlu32, reinterpret_cast<float*>(L.tb));
     else
@@ -774,9 +774,10 @@ bool hp_fits(int ni, int nj, int nw) {
 
 int launch_sweep(const LevelDev& L, int mixed, int kind, int do_update, int aw, double alpha, const double* rhs,
                  long long* prog, int* err, long long limit, cudaStream_t st, int exact_iters) {
-  if (kind == SWEEP_WS && L.wsF)
-    return launch_ws_sweep(L, mixed, 1, do_update, aw, alpha, rhs, prog, err, limit, st, exact_iters);
-  if (kind == SWEEP_WS) kind = mixed ? SWEEP_AUTO : SWEEP_STRIPS;
+  if (is_ws(kind) && L.wsF)
+    return launch_ws_sweep(L, mixed, 1, do_update, aw, alpha, rhs, prog, err, limit, st, exact_iters,
+                           kind == SWEEP_WS8 ? 8 : WS_K);
+  if (is_ws(kind)) kind = mixed ? SWEEP_AUTO : SWEEP_STRIPS;
   if (is_hp(kind) && mixed && L.hpF) {
     launch_pdl(k_hp_cy, (L.n + 127) / 128, 128, 0, st, L, reinterpret_cast<const float*>(L.tb), rhs);
     const int nt = hp_threads(L.nj);

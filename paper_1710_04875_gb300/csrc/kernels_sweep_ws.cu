@@ -152,21 +152,22 @@ __device__ __forceinline__ float4 add_block(float4 v, const float* G, float4 x) 
 // Shared memory of the sweep: [mbarriers][ring of blocks][ring of vectors][stage][edge][cut vectors][cut blocks]
 struct WsSmem {
   uint64_t* bar;
-  float4* ringF;  // WS_STAGES x WS_K x WS_F4_STEP
-  float4* ringC;  // WS_STAGES x WS_K x 32
-  float4* stage;  // WS_K: the neighbour's boundary vectors of the current chunk, checked
+  float4* ringF;  // WS_STAGES x KC x WS_F4_STEP
+  float4* ringC;  // WS_STAGES x KC x 32
+  float4* stage;  // KC: the neighbour's boundary vectors of the current chunk, checked
   float4* edge;   // Mp + 32: the neighbour's out-lane vector of its step t (t >= Mp: zero)
   float4* cutv;   // nw
   float* cutG;    // nw x 16
 };
 
+template <int KC>
 __device__ __forceinline__ WsSmem ws_carve(unsigned char* base, int Mp, int nw) {
   WsSmem S;
   S.bar = reinterpret_cast<uint64_t*>(base);
   S.ringF = reinterpret_cast<float4*>(base + 128);
-  S.ringC = S.ringF + WS_STAGES * WS_K * WS_F4_STEP;
-  S.stage = S.ringC + WS_STAGES * WS_K * WS_ROWS;
-  S.edge = S.stage + WS_K;
+  S.ringC = S.ringF + WS_STAGES * KC * WS_F4_STEP;
+  S.stage = S.ringC + WS_STAGES * KC * WS_ROWS;
+  S.edge = S.stage + KC;
   S.cutv = S.edge + Mp + 32;
   S.cutG = reinterpret_cast<float*>(S.cutv + (nw > 0 ? nw : 1));
   return S;
@@ -176,9 +177,9 @@ __device__ __forceinline__ WsSmem ws_carve(unsigned char* base, int Mp, int nw) 
 
 int ws_strips(int nj) { return (nj + WS_ROWS - 1) / WS_ROWS; }
 
-size_t ws_smem_bytes(int ni, int nj, int nw) {
+size_t ws_smem_bytes(int ni, int nj, int nw, int KC) {
   const int m = nw > 0 ? nw : 1;
-  return 128 + 16 * ((size_t)WS_STAGES * WS_K * (WS_F4_STEP + WS_ROWS) + WS_K + ws_steps(ni, nj) + 32 + m) +
+  return 128 + 16 * ((size_t)WS_STAGES * KC * (WS_F4_STEP + WS_ROWS) + KC + ws_steps(ni, nj) + 32 + m) +
          64 * (size_t)m;
 }
 
@@ -199,19 +200,19 @@ __device__ __forceinline__ size_t ws_bpos(int i, int j, int Mp) {
 // Lane jl at step s holds cell i = s - jl (forward) or Mp - 1 - s - jl (backward); the edge lane
 // needs the neighbour's out-lane vector of the same column, which the neighbour computed at its
 // step s + 31: edge entry s + 31 (entries Mp .. Mp + 31 are zero).
-template <bool FWD>
+template <bool FWD, int KC>
 __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, const float4* F, const float4* C, float4* Out,
                         bool has_in, unsigned redge, int* err, long long limit, unsigned& phase_bits) {
   const int lane = threadIdx.x;
   const int ni = L.ni, nw = L.nw;
   const int Mp = ws_steps(ni, L.nj);        // steps that hold a cell, padded to whole chunks
-  const int nch = Mp / WS_K;
+  const int nch = Mp / KC;
   const int edge_lane = FWD ? 0 : WS_ROWS - 1;      // lane that reads the neighbour's row
   const int out_lane = FWD ? WS_ROWS - 1 : 0;       // lane whose row the other neighbour reads
   const float4* Fs = F + (size_t)b * Mp * WS_F4_STEP;
   const float4* Cs = C + (size_t)b * Mp * WS_ROWS;
   float4* Os = Out + (size_t)b * Mp * WS_ROWS + lane;
-  const unsigned bytesF = WS_K * WS_F4_STEP * 16, bytesC = WS_K * WS_ROWS * 16;
+  const unsigned bytesF = KC * WS_F4_STEP * 16, bytesC = KC * WS_ROWS * 16;
   const bool feeds = redge != 0 && lane == out_lane;
 
   // Refill of a slot by the async proxy: the slot's previous contents were only read (no generic
@@ -220,8 +221,8 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, const float4*
   auto issue = [&](int ch) {  // lane 0 only
     const int slot = ch % WS_STAGES;
     mbar_expect_tx(&S.bar[slot], bytesF + bytesC);
-    bulk_copy(S.ringF + (size_t)slot * WS_K * WS_F4_STEP, Fs + (size_t)ch * WS_K * WS_F4_STEP, bytesF, &S.bar[slot]);
-    bulk_copy(S.ringC + (size_t)slot * WS_K * WS_ROWS, Cs + (size_t)ch * WS_K * WS_ROWS, bytesC, &S.bar[slot]);
+    bulk_copy(S.ringF + (size_t)slot * KC * WS_F4_STEP, Fs + (size_t)ch * KC * WS_F4_STEP, bytesF, &S.bar[slot]);
+    bulk_copy(S.ringC + (size_t)slot * KC * WS_ROWS, Cs + (size_t)ch * KC * WS_ROWS, bytesC, &S.bar[slot]);
   };
   int waited = 0;  // chunks whose copies have landed (and been accounted for)
   // bounded wait for the chunk in a slot; false on timeout
@@ -259,20 +260,20 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, const float4*
     __syncwarp();
     return false;
   };
-  // the neighbour's boundary vectors of steps s0 .. s0 + WS_K - 1 into S.stage: lane k polls
+  // the neighbour's boundary vectors of steps s0 .. s0 + KC - 1 into S.stage: lane k polls
   // edge entry s0 + 31 + k until the neighbour's store has landed (bounded; a neighbour that
   // gave up has set the error word)
   // The loop is warp-uniform (a vote decides whether any lane still waits), so that the warp
   // leaves it converged.
   auto poll_edge = [&](int s0) -> bool {
-    const float4* e = S.edge + s0 + (WS_ROWS - 1) + (lane & (WS_K - 1));
+    const float4* e = S.edge + s0 + (WS_ROWS - 1) + (lane & (KC - 1));
     uint4 v = ld_cluster4(e);
     long long spins = 0;
     while (__any_sync(0xffffffffu, unwritten(v))) {
       if (++spins > limit || ((spins & 255) == 0 && *((volatile int*)err) != 0)) return false;
       v = ld_cluster4(e);
     }
-    if (lane < WS_K)
+    if (lane < KC)
       S.stage[lane] = make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
                                   __uint_as_float(v.w));
     __syncwarp();
@@ -283,7 +284,7 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, const float4*
     for (int ch = 0; ch < WS_STAGES && ch < nch; ++ch) issue(ch);
   __syncwarp();
   issued = nch < WS_STAGES ? nch : WS_STAGES;
-  if (!has_in && lane < WS_K) S.stage[lane] = make_float4(0.f, 0.f, 0.f, 0.f);  // no neighbour: zero
+  if (!has_in && lane < KC) S.stage[lane] = make_float4(0.f, 0.f, 0.f, 0.f);  // no neighbour: zero
   __syncwarp();
 
   float4 v = make_float4(0.f, 0.f, 0.f, 0.f);  // this lane's vector at the previous step
@@ -295,8 +296,8 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, const float4*
     float4 A[4], B[4], c;
   };
   auto load = [&](Ops& o, int slot, int k) {
-    const float4* rF = S.ringF + (size_t)slot * WS_K * WS_F4_STEP;
-    const float4* rC = S.ringC + (size_t)slot * WS_K * WS_ROWS;
+    const float4* rF = S.ringF + (size_t)slot * KC * WS_F4_STEP;
+    const float4* rC = S.ringC + (size_t)slot * KC * WS_ROWS;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       o.A[q] = rF[k * WS_F4_STEP + q * WS_ROWS + lane];
@@ -327,7 +328,7 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, const float4*
     v = y;
   };
   // o[0] holds the next step's operands between chunks: the last step of a chunk loads the next
-  // chunk's first step into it.  A chunk runs as WS_K / WS_U blocks of WS_U unrolled steps, which
+  // chunk's first step into it.  A chunk runs as KC / WS_U blocks of WS_U unrolled steps, which
   // keeps the code of a pass small enough for the instruction cache.
   Ops o[2];
   float4 e[2];
@@ -335,11 +336,11 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, const float4*
   auto run_chunk = [&](int slot, int ch, int s0, auto cut_tag) {
     e[0] = S.stage[0];
 #pragma unroll 1
-    for (int kk = 0; kk < WS_K; kk += WS_U) {
+    for (int kk = 0; kk < KC; kk += WS_U) {
 #pragma unroll
       for (int u = 0; u < WS_U; ++u) {
         const int k = kk + u;
-        if (u + 1 < WS_U || kk + WS_U < WS_K) {
+        if (u + 1 < WS_U || kk + WS_U < KC) {
           load(o[(u + 1) & 1], slot, k + 1);
           e[(u + 1) & 1] = S.stage[k + 1];
         } else if (ch + 1 < nch) {
@@ -356,11 +357,11 @@ __device__ bool ws_pass(const LevelDev& L, const WsSmem& S, int b, const float4*
   if (!wait_slot(0)) return fail();
   load(o[0], 0, 0);
   for (int ch = 0; ch < nch; ++ch) {
-    const int s0 = ch * WS_K;
+    const int s0 = ch * KC;
     if (has_in && !poll_edge(s0)) return fail();
     const int slot = ch % WS_STAGES;
     // does lane 0 of strip 0 meet a wake-cut cell in this chunk?
-    const int ilo = FWD ? s0 : Mp - s0 - WS_K, ihi = FWD ? s0 + WS_K - 1 : Mp - 1 - s0;
+    const int ilo = FWD ? s0 : Mp - s0 - KC, ihi = FWD ? s0 + KC - 1 : Mp - 1 - s0;
     const bool cut = b == 0 && nw > 0 && (ilo < nw || ihi >= ni - nw);
     if (cut)
       run_chunk(slot, ch, s0, std::true_type{});
@@ -389,13 +390,14 @@ __device__ __forceinline__ void ws_clear_edge(const WsSmem& S, int Mp) {
 // whatever happened in its passes, so that a strip that gave up leaves no other one waiting on
 // a barrier; the last barrier also keeps every strip's shared memory alive until the
 // neighbours' remote stores into it have completed.
+template <int KC>
 __global__ void __launch_bounds__(32) k_sweep_ws(LevelDev L, const float4* Fb, const float4* Bb, const float4* C,
                                                  float4* Y, const float* cutG, float4* Z, int* err, long long limit) {
   pdl_entry();
   extern __shared__ __align__(128) unsigned char ws_raw[];
   const int nw = L.nw;
   const int Mp = ws_steps(L.ni, L.nj);
-  WsSmem S = ws_carve(ws_raw, Mp, nw);
+  WsSmem S = ws_carve<KC>(ws_raw, Mp, nw);
   const int b = blockIdx.x, nb = gridDim.x, lane = threadIdx.x;
   if (lane == 0) {
     for (int k = 0; k < WS_STAGES; ++k) mbar_init(&S.bar[k], 1);
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(32) k_sweep_ws(LevelDev L, const float4* Fb, c
   // forward: strip b feeds b + 1 (lane 31) and is fed by b - 1; backward the other way round
   const unsigned up = b < nb - 1 ? cluster_addr(S.edge, (unsigned)(b + 1)) : 0u;
   const unsigned down = b > 0 ? cluster_addr(S.edge, (unsigned)(b - 1)) : 0u;
-  bool ok = ws_pass<true>(L, S, b, Fb, C, Y, b > 0, up, err, limit, phase_bits);
+  bool ok = ws_pass<true, KC>(L, S, b, Fb, C, Y, b > 0, up, err, limit, phase_bits);
   // the backward pass reads, through the async proxy, the y this warp has just written
   asm volatile("fence.proxy.async.global;" ::: "memory");
   // every strip has read its edge buffer to the end before it is cleared for the backward pass,
@@ -418,7 +420,7 @@ __global__ void __launch_bounds__(32) k_sweep_ws(LevelDev L, const float4* Fb, c
   cluster_sync();
   ws_clear_edge(S, Mp);
   cluster_sync();
-  if (ok) ws_pass<false>(L, S, b, Bb, Y, Z, b < nb - 1, down, err, limit, phase_bits);
+  if (ok) ws_pass<false, KC>(L, S, b, Bb, Y, Z, b < nb - 1, down, err, limit, phase_bits);
   cluster_sync();
 }
 
@@ -642,20 +644,21 @@ constexpr size_t kWsSmemMax = 227 * 1024;
 }  // namespace
 
 bool ws_fits(int ni, int nj, int nw) {
-  return ws_strips(nj) <= 8 && ws_smem_bytes(ni, nj, nw) <= kWsSmemMax;  // one portable cluster per sweep
+  return ws_strips(nj) <= 8 && ws_smem_bytes(ni, nj, nw, WS_K) <= kWsSmemMax;  // one portable cluster per sweep
 }
 
 
 namespace {
+template <int KC>
 cudaError_t ws_sweep_launch(const LevelDev& L, float4* zout, int* err, long long limit, cudaStream_t st) {
   const int nb = ws_strips(L.nj);
-  const size_t sm = ws_smem_bytes(L.ni, L.nj, L.nw);
-  // the shared-memory limit is a per-device attribute: set once on each device (idempotent if
-  // two host threads race on the first launch)
+  const size_t sm = ws_smem_bytes(L.ni, L.nj, L.nw, KC);
+  // the shared-memory limit is a per-device attribute of each instance: set once on each device
+  // (idempotent if two host threads race on the first launch)
   static std::atomic<unsigned long long> attr_done{0};
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !(attr_done.load() & (1ull << dev))) {
-    if (cudaFuncSetAttribute(k_sweep_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemMax) ==
+    if (cudaFuncSetAttribute(k_sweep_ws<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemMax) ==
         cudaSuccess)
       attr_done.fetch_or(1ull << dev);
   }
@@ -676,7 +679,7 @@ cudaError_t ws_sweep_launch(const LevelDev& L, float4* zout, int* err, long long
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, k_sweep_ws, L, reinterpret_cast<const float4*>(L.wsF),
+  return cudaLaunchKernelEx(&cfg, k_sweep_ws<KC>, L, reinterpret_cast<const float4*>(L.wsF),
                             reinterpret_cast<const float4*>(L.wsB), reinterpret_cast<const float4*>(L.wsC),
                             reinterpret_cast<float4*>(L.wsY), static_cast<const float*>(L.wsCut), zout, err,
                             limit);
@@ -684,8 +687,11 @@ cudaError_t ws_sweep_launch(const LevelDev& L, float4* zout, int* err, long long
 }  // namespace
 
 int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int aw, double alpha, const double* rhs,
-                    long long* prog, int* err, long long limit, cudaStream_t st, int exact_iters) {
+                    long long* prog, int* err, long long limit, cudaStream_t st, int exact_iters, int chunk) {
   (void)prog;  // the warp strips exchange their boundary rows in shared memory, not through progress words
+  auto sweep = [&](float4* zout) {
+    return chunk == 8 ? ws_sweep_launch<8>(L, zout, err, limit, st) : ws_sweep_launch<WS_K>(L, zout, err, limit, st);
+  };
   const int g = (L.n + 127) / 128;
   float4* z0 = reinterpret_cast<float4*>(L.wsZ);
   float4* dz = z0 + ws_vec_floats(L.ni, L.nj) / 4;
@@ -705,7 +711,7 @@ int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int
   } else {
     launch_pdl(k_ws_rhs<double, false>, g, 128, 0, st, L, tb64, rhs, wC);
   }
-  ws_sweep_launch(L, z0, err, limit, st);
+  sweep(z0);
   launches += 2;
   const bool corr = refine && !mixed;
   if (corr) {
@@ -718,7 +724,7 @@ int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int
       launch_pdl(k_ws_defect_t<false>, g, 128, 0, st, L, tb64, z0c, L.wsT);
       launch_pdl(k_ws_defect_d<false>, g, 128, 0, st, L, tb64, rhs, wT, wC);
     }
-    ws_sweep_launch(L, dz, err, limit, st);
+    sweep(dz);
     launches += 3;
   }
   if (exact_iters > 0) {
@@ -732,7 +738,7 @@ int launch_ws_sweep(const LevelDev& L, int mixed, int refine, int do_update, int
       else
         launch_pdl(k_ws_exact_defect<double>, g, 128, 0, st, L, static_cast<const double*>(L.tb), rhs,
                    static_cast<const double*>(L.wsX), reinterpret_cast<float4*>(L.wsC));
-      ws_sweep_launch(L, z0, err, limit, st);
+      sweep(z0);
       launch_pdl(k_ws_accum, g, 128, 0, st, L, static_cast<const float4*>(z0), nullptr, L.wsX, 0);
       launches += 3;
     }

@@ -307,9 +307,11 @@ class Solver:
     def set_sweep(self, kind):
         """0 auto, 1 reference (one thread per cell), 2 one CTA, 3 strips of 8 rows, 4 strips of 16,
         5 hyperplane-staged (mixed precision), 6 / 7 staged with a ring of 4 / 8 steps, 8 strips of 4,
-        9 warp strips (FP32 recurrence; FP64 contexts add one FP64 defect correction)."""
+        9 warp strips (FP32 recurrence; FP64 contexts add one FP64 defect correction), 10 warp strips
+        staging chunks of 8 steps."""
         kinds = {"auto": 0, "reference": 1, "cta": 2, "strips": 3, "strips16": 4, "staged": 5, "staged4": 6,
-                 "staged8": 7, "strips4": 8, "warp": 9}
+                 "staged8": 7, "strips4": 8, "warp": 9,
+                 "warp8": 10}
         _check(self.lib.fasw_set_sweep(self.h, kinds.get(kind, kind)), "fasw_set_sweep")
 
     def set_exact_preconditioner(self, iters: int):

@@ -266,7 +266,7 @@ def test_graph_replayed_cycles_equal_eager_cycles():
     assert np.array_equal(a.get_state(), b.get_state())
 
 
-@pytest.mark.parametrize("kind", ["reference", "cta", "strips", "strips16", "strips4", "warp"])
+@pytest.mark.parametrize("kind", ["reference", "cta", "strips", "strips16", "strips4", "warp", "warp8"])
 @pytest.mark.parametrize("scheme", ["AW3", "ARK3J"])
 @pytest.mark.parametrize("ni,nj,nw", [(128, 32, 16), (72, 20, 8), (40, 12, 4), (256, 64, 32), (16, 6, 2),
                                       (64, 100, 8), (48, 33, 4)])
@@ -284,7 +284,7 @@ def test_sweep_kinds_match_the_oracle(kind, scheme, ni, nj, nw):
     assert rel_err(zg, zo) < 1e-11
 
 
-@pytest.mark.parametrize("kind", ["staged", "staged4", "staged8", "cta", "strips", "warp"])
+@pytest.mark.parametrize("kind", ["staged", "staged4", "staged8", "cta", "strips", "warp", "warp8"])
 @pytest.mark.parametrize("ni,nj,nw", [(128, 32, 16), (72, 20, 8), (16, 6, 2), (256, 64, 32), (128, 128, 16),
                                       (256, 256, 32), (192, 200, 24)])
 def test_mixed_sweep_is_the_fp32_preconditioner(kind, ni, nj, nw):
@@ -316,7 +316,7 @@ def test_staged_and_cta_fp32_sweeps_agree():
     assert rel_err(za, zb) < 1e-4
 
 
-@pytest.mark.parametrize("kind", ["cta", "strips", "strips16", "warp"])
+@pytest.mark.parametrize("kind", ["cta", "strips", "strips16", "warp", "warp8"])
 def test_cycle_history_with_fast_sweeps(kind):
     """Full FAS cycles with the transfer-block sweeps keep the 1e-8 history parity."""
     g = make_cgrid(128, 32)
