@@ -34,7 +34,8 @@ int sweep_strips(const LevelDev& L);
 // correction in FP64 contexts; the skewed blocks come from launch_sgs_prep).  Returns the
 // kernels launched.
 // Warp-strip layout: strips of WS_ROWS rows, a strip's operands stored step by step (lane jl at
-// step s holds cell i = s - jl), WS_K steps to a chunk, WS_F4_STEP float4 of blocks per step.
+// step s holds cell i = s - jl), the steps padded to whole chunks of WS_K (the default staging
+// chunk; kind 10 stages half-chunks of 8), WS_F4_STEP float4 of blocks per step.
 constexpr int WS_ROWS = 32;
 constexpr int WS_K = 16;
 constexpr int WS_F4_STEP = 8 * WS_ROWS;

@@ -35,7 +35,7 @@ namespace fasw {
 namespace {
 
 constexpr int WS_STAGES = 2;   // chunk buffers (one in use, one in flight)
-constexpr int WS_U = 8;        // steps unrolled together (a chunk is WS_K / WS_U such blocks)
+constexpr int WS_U = 8;        // steps unrolled together (a chunk of KC steps is KC / WS_U such blocks)
 constexpr unsigned WS_SENT = 0xFFFFFFFFu;  // "not yet written": a NaN payload no FP32 operation returns
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
