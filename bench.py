@@ -64,10 +64,10 @@ BYTES_PER_CELL = {"fp64": {"sgs": 1680.0, "residual": 232.0}, "mixed": {"sgs": 5
 # DRAM traffic per cell of one launch of the dominant kernel, from an ncu capture of a finest-level
 # launch (dram__bytes_read.sum + dram__bytes_write.sum over the cells of that launch); None where
 # no capture of the current kernel exists.
-# FP64: 395.1 MB read + 1.1 MB written by one finest-level application on the 262,144 cells of
+# FP64: 395.1 MB read + 1.2 MB written by one finest-level application on the 262,144 cells of
 # the 1024x256 grid (rhs, two sweep pairs, the defect kernels, the update), captured by ncu with
 # dram__bytes_read.sum and dram__bytes_write.sum.
-DRAM_BYTES_PER_CELL = {"fp64": {"sgs": 396.26e6 / 262144}, "mixed": {"sgs": None}}
+DRAM_BYTES_PER_CELL = {"fp64": {"sgs": 396.25e6 / 262144}, "mixed": {"sgs": None}}
 
 
 def level_visits(nlevels, gamma):
